@@ -1,0 +1,224 @@
+"""Pins for the oracle's sigma-counting BFS, RandomSP and exact percolation
+centrality against library routines, walk counts, brute-force enumeration,
+closed forms and the paper's invariants."""
+import os
+from fractions import Fraction
+
+import networkx as nx
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.sparse import csr_matrix
+from scipy.sparse.csgraph import shortest_path
+
+import oracle
+from paper_2509_11454_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_graph(n, m, directed, seed):
+    rng = np.random.default_rng(seed)
+    return synth.csr_from_edges(n, rng.integers(0, n, m), rng.integers(0, n, m), directed)
+
+
+def _dense(g):
+    a = np.zeros((g.n, g.n), dtype=np.int64)
+    for u in range(g.n):
+        a[u, g.col[g.row_ptr[u]:g.row_ptr[u + 1]]] = 1
+    return a
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_bfs_distances_match_scipy(directed):
+    g = _rand_graph(300, 700, directed, 1)
+    og = oracle.from_synth(g)
+    a = csr_matrix((np.ones(g.nnz), g.col, g.row_ptr), shape=(g.n, g.n))
+    ref = shortest_path(a, directed=True, unweighted=True)
+    for s in range(0, 300, 37):
+        _, dist, _, _, _, _ = oracle.bfs(og, s)
+        exp = np.where(np.isinf(ref[s]), -1, ref[s]).astype(np.int64)
+        assert np.array_equal(dist.astype(np.int64), exp)
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_sigma_equals_walk_counts(directed):
+    """sigma_st = number of length-d(s,t) walks from s to t: a walk whose
+    length equals the distance cannot revisit a vertex, so it is a shortest
+    path.  (A^d)_{st} by exact integer matrix powers."""
+    g = _rand_graph(60, 160, directed, 2)
+    og = oracle.from_synth(g)
+    A = _dense(g).astype(object)
+    powers = [np.eye(g.n, dtype=object)]
+    for _ in range(g.n):
+        powers.append(powers[-1].dot(A))
+        if len(powers) > 25:
+            break
+    for s in range(0, 60, 7):
+        _, dist, sigma, _, _, _ = oracle.bfs(og, s)
+        for t in range(g.n):
+            if dist[t] >= 0:
+                assert sigma[t] == float(powers[dist[t]][s, t])
+            else:
+                assert sigma[t] == 0.0
+
+
+def test_truncated_bfs_settles_target_level():
+    g = synth.grid_2d(12, 0.0, 0)
+    og = oracle.from_synth(g)
+    s, t = 0, 5 * 12 + 7
+    ret, dist, sigma, order, edges, _ = oracle.bfs(og, s, t)
+    full = oracle.bfs(og, s)
+    assert ret == full[1][t] == 12
+    # every vertex at distance <= d(t) is discovered with the full sigma;
+    # nothing beyond d(t)
+    m = full[1] <= ret
+    assert np.array_equal(dist[m], full[1][m]) and np.all(dist[~m] == -1)
+    assert np.array_equal(sigma[m], full[2][m])
+    deg = np.diff(g.row_ptr)
+    assert edges == int(deg[full[1] < ret].sum())
+
+
+def test_randomsp_uniform_over_shortest_paths():
+    """RandomSP returns each path of Gamma_st with probability 1/sigma_st."""
+    g = synth.grid_2d(5, 0.0, 0)
+    og = oracle.from_synth(g)
+    s, t = 0, 24  # opposite corners: C(8,4) = 70 shortest paths
+    _, dist, sigma, _, _, _ = oracle.bfs(og, s, t)
+    assert sigma[t] == 70.0
+    counts = {}
+    N = 70 * 300
+    for i in range(N):
+        k, path = oracle.backtrack(og, dist, sigma, s, t, 99, 3, i)
+        assert k == 7
+        counts[tuple(path)] = counts.get(tuple(path), 0) + 1
+    assert len(counts) == 70
+    obs = np.array(list(counts.values()))
+    assert stats.chisquare(obs).pvalue > 1e-4
+
+
+def test_backtrack_path_is_a_shortest_path():
+    g = synth.barabasi_albert(400, 2, 1)
+    og = oracle.from_synth(g)
+    adj = _dense(g)
+    rng = np.random.default_rng(0)
+    for i in range(50):
+        s, t = rng.integers(0, 400, 2)
+        if s == t:
+            continue
+        _, dist, sigma, _, _, _ = oracle.bfs(og, s, t)
+        k, path = oracle.backtrack(og, dist, sigma, s, t, 5, 2, i)
+        full = [t] + list(path) + [s]
+        assert k == dist[t] - 1
+        for a, b in zip(full[1:], full[:-1]):
+            assert adj[a, b] == 1
+        assert len(set(full)) == len(full)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_exact_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n = 8 + seed % 3
+    directed = seed % 2 == 1
+    g = _rand_graph(n, 2 * n + 2, directed, 100 + seed)
+    x = rng.random(n)
+    if seed >= 3:
+        x = (rng.random(n) > 0.5).astype(float)  # binary states, many ties
+        x[0], x[1] = 1.0, 0.0
+    og = oracle.from_synth(g)
+    pb, _ = oracle.brute_force_pc(n, g.row_ptr, g.col, x)
+    _, Cv = oracle.cv_literal(x)
+    pe = oracle.exact_pc(og, x, Cv)
+    assert np.allclose(pe, pb, rtol=1e-12, atol=1e-14)
+    assert np.all(pe >= 0) and np.all(pe <= 1 + 1e-12)
+
+
+def _prop7(n):
+    # a=0, b=1, c=2, H = 3..n-1
+    src = [0, 1] + list(range(3, n)) + [3]
+    dst = [1, 2] + [3 + (k + 1) % (n - 3) for k in range(n - 3)] + [0]
+    if n - 3 == 1:
+        src, dst = [0, 1, 3], [1, 2, 0]
+    g = synth.csr_from_edges(n, np.array(src), np.array(dst), directed=True)
+    x = np.zeros(n)
+    x[0], x[2] = 1.0, 0.5
+    return g, x
+
+
+def test_prop7_closed_form():
+    rows = []
+    with open(os.path.join(GOLDEN, "prop7_instance.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                n, frac = line.split()
+                rows.append((int(n), Fraction(frac)))
+    for n, pb in rows:
+        g, x = _prop7(n)
+        og = oracle.from_synth(g)
+        pe = oracle.exact_pc(og, x)
+        assert pe[1] == pytest.approx(float(pb), rel=1e-13)
+        others = np.delete(pe, 1)
+        assert np.all(others == 0.0)
+        if n <= 6:
+            pbf, _ = oracle.brute_force_pc(n, g.row_ptr, g.col, x)
+            assert pbf[1] == pytest.approx(float(pb), rel=1e-13)
+
+
+@pytest.mark.parametrize("directed", [True, False])
+def test_binary_states_reduce_to_subset_betweenness(directed):
+    """x in {0,1}: p(v) = B_{S1->S0}(v) / (|S1 minus v| |S0 minus v|) with B
+    the source-target subset betweenness (networkx, library routine)."""
+    g = _rand_graph(40, 120, directed, 7)
+    rng = np.random.default_rng(3)
+    x = (rng.random(40) < 0.3).astype(float)
+    og = oracle.from_synth(g)
+    pe = oracle.exact_pc(og, x)
+    G = nx.DiGraph() if directed else nx.Graph()
+    G.add_nodes_from(range(40))
+    for u in range(40):
+        for v in g.col[g.row_ptr[u]:g.row_ptr[u + 1]]:
+            G.add_edge(u, int(v))
+    S1 = [v for v in range(40) if x[v] == 1]
+    S0 = [v for v in range(40) if x[v] == 0]
+    B = nx.betweenness_centrality_subset(G, S1, S0, normalized=False)
+    for v in range(40):
+        Cv = (len(S1) - (x[v] == 1)) * (len(S0) - (x[v] == 0))
+        b = B[v] * (1.0 if directed else 2.0)  # networkx halves undirected sums
+        assert pe[v] == pytest.approx(b / Cv, rel=1e-12, abs=1e-15)
+
+
+def test_lemma3_and_normalisation():
+    """Lemma 3: rho <= sum_v p(v) <= d^ rho, rho = sum_{s,t} |I(tau_st)| kappa~(s,t)."""
+    for seed, directed in [(0, False), (1, True), (2, False)]:
+        g = _rand_graph(50, 150, directed, 40 + seed)
+        x = np.random.default_rng(seed).random(50)
+        og = oracle.from_synth(g)
+        prep = oracle.prepare(x)
+        pe = oracle.exact_pc(og, x, prep.Cv)
+        a = csr_matrix((np.ones(g.nnz), g.col, g.row_ptr), shape=(50, 50))
+        d = shortest_path(a, directed=True, unweighted=True)
+        R = np.maximum(0.0, x[:, None] - x[None, :])
+        I = np.where(np.isfinite(d) & (d >= 1), d - 1, 0.0)
+        rho = float((I * R).sum() / prep.c)
+        assert rho - 1e-12 <= pe.sum() <= prep.dhat * rho + 1e-12
+        # sum_{s != v != t} kappa(s,t,v) = 1 for every v (Section II-A)
+        for v in range(0, 50, 7):
+            m = np.ones(50, bool)
+            m[v] = False
+            assert R[np.ix_(m, m)].sum() / prep.Cv[v] == pytest.approx(1.0, rel=1e-12)
+
+
+def test_vertex_diameter_bound():
+    rng = np.random.default_rng(1)
+    for k in range(4):
+        g = _rand_graph(120, 150 + 40 * k, False, 70 + k)  # often disconnected
+        og = oracle.from_synth(g)
+        D = oracle.vertex_diam_ub(og)
+        a = csr_matrix((np.ones(g.nnz), g.col, g.row_ptr), shape=(120, 120))
+        d = shortest_path(a, directed=False, unweighted=True)
+        true = int(np.max(np.where(np.isfinite(d), d, 0))) - 1
+        assert D >= true
+    p = synth.path_graph(30)
+    assert oracle.vertex_diam_ub(oracle.from_synth(p)) == 2 * 28 - 1
+    gd = _rand_graph(30, 60, True, 3)
+    assert oracle.vertex_diam_ub(oracle.from_synth(gd)) == 28
