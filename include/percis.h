@@ -1,0 +1,198 @@
+/*
+ * percis.h -- C ABI of the GB300 (sm_103a) PercIS library.
+ *
+ * PercIS approximates the percolation centrality p(v) of every vertex
+ * (Definition 1: p(v) = sum over s != v != t of sigma_st(v)/sigma_st *
+ * kappa(s,t,v), kappa(s,t,v) = R(x_s - x_t) / sum_{u != v != w} R(x_u - x_w),
+ * R(x) = max(0, x)) by importance sampling (Section III): pairs (s,t) are
+ * drawn with probability kappa~(s,t) = R(x_s - x_t)/C, one shortest s-t path
+ * is drawn uniformly from Gamma_st, and p~(v) = (1/l) sum_i
+ * kappa(s_i,t_i,v)/kappa~(s_i,t_i) 1[v internal to path i].  Algorithm 1 sets
+ * l in two phases (Theorem 1, Propositions 2-3).
+ *
+ * Conventions for every call:
+ *  - All device work is ordered on the context's CUDA stream.
+ *  - Inputs are copied; the caller keeps ownership of every buffer it passes.
+ *  - Output buffers are caller-owned.  "device" pointers must be device (or
+ *    managed) memory of the context's device; "host" pointers plain host
+ *    memory.  Calls that take an `on_device` flag accept either.
+ *  - Node ids are 0-based int32; CSR row offsets are int64.
+ *  - No C++ exception crosses this boundary.  Every call returns a
+ *    percis_status; percis_last_error() gives a one-line reason.
+ *  - The library allocates its scratch memory with cudaMalloc (grow-only,
+ *    reused across calls) and frees it in percis_destroy().
+ *  - A context is not thread-safe; use one context per host thread/stream.
+ */
+#ifndef PERCIS_H
+#define PERCIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct percis_ctx percis_ctx;
+
+typedef enum {
+    PERCIS_OK = 0,
+    PERCIS_E_INVALID = 1,     /* bad argument, malformed CSR, x outside [0,1] or NaN */
+    PERCIS_E_DEGENERATE = 2,  /* some C_v <= 0: p(v) undefined (Section II-A) */
+    PERCIS_E_OOM = 3,         /* cudaMalloc failed */
+    PERCIS_E_CUDA = 4,        /* any other CUDA error (see percis_last_error) */
+    PERCIS_E_TIMEOUT = 5,     /* a device-side wait exceeded its budget; context still usable */
+    PERCIS_E_TOO_LARGE = 6,   /* request above a documented size cap */
+    PERCIS_E_NO_SAMPLE = 7,   /* backward/inspection before a sampling phase */
+    PERCIS_E_STATE = 8        /* call order: graph or states not loaded yet */
+} percis_status;
+
+/* How sampled paths are produced (same samples, same results):
+ *  BATCHED: samples are grouped by source; up to `lanes` distinct sources
+ *           share one persistent multi-source sigma-BFS launch (bitset
+ *           frontiers, one bit per source per vertex), followed in the same
+ *           launch by the per-sample backtrack.
+ *  PLAIN:   one single-source sigma-BFS launch plus one backtrack launch per
+ *           sampled pair (the baseline form). */
+enum { PERCIS_FORM_BATCHED = 0, PERCIS_FORM_PLAIN = 1 };
+
+typedef struct {
+    int32_t form;             /* PERCIS_FORM_*; default BATCHED */
+    int32_t lanes;            /* batched lane width: 0 = auto, else 64, 128, 256 or 512 */
+    int64_t ell1;             /* 0 = Algorithm 1 default max{1000, ceil(ln(1/delta)/eps)} */
+    int64_t ell;              /* 0 = Theorem 1 bound; > 0 forces the phase-2 sample size */
+    int64_t vertex_diam;      /* < 0 = VertexDiamUB of the loaded graph; >= 0 overrides D */
+    int32_t keep_paths;       /* 1 (default): keep phase-2 paths for percis_backward */
+    int32_t data_independent; /* 1: PercIS-DI (rho^ = D, v^ = d^2/4, no phase 1; Section IV-B) */
+    double timeout_s;         /* budget of every device-side wait (default 10 s) */
+} percis_options;
+
+typedef struct {
+    int64_t n, nnz;
+    int64_t ell1, ell;            /* phase sizes actually used */
+    int64_t vertex_diam;          /* D used in rho^ */
+    double C, dhat;               /* C = sum_{u,w} R(x_u - x_w); d^ = max_v C/C_v */
+    double rho_tilde, Lambda;     /* Proposition 2 statistics of phase 1 */
+    double rho_hat, v_hat, x_hat; /* Algorithm 1 */
+    double p1_max;                /* max_v phase-1 p~(v) */
+    int64_t zero_weight[2];       /* samples with R(x_s - x_t) = 0, per phase */
+    int64_t unreachable[2];       /* samples with Gamma_st empty, per phase */
+    int64_t sum_internal[2];      /* sum_i |I(tau_i)|, per phase */
+    int64_t sources[2];           /* distinct BFS sources (batched form), per phase */
+    int64_t batches[2];           /* persistent launches (batched form), per phase */
+    int32_t sigma_overflow;       /* 1 if some sigma reached 2^53 (paths no longer exact) */
+    int32_t lanes;                /* lane width used */
+    int64_t kernel_launches;      /* kernels this call launched */
+} percis_info;
+
+/* ------------------------------------------------------------ lifecycle */
+
+/* Create a context on `device`.  `stream` is a cudaStream_t (NULL = a new
+ * non-blocking stream owned by the context). */
+percis_status percis_create(percis_ctx **out, int device, void *stream);
+/* Free every buffer the context owns.  NULL is ignored. */
+void percis_destroy(percis_ctx *ctx);
+/* Switch the stream later calls are ordered on (not owned). */
+percis_status percis_set_stream(percis_ctx *ctx, void *stream);
+/* Last error message of this context ("" when none).  Owned by the context. */
+const char *percis_last_error(const percis_ctx *ctx);
+/* Fill `opt` with the defaults listed in percis_options. */
+void percis_default_options(percis_options *opt);
+percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt);
+
+/* ---------------------------------------------------------------- inputs */
+
+/* Load a graph G = (V, E) (Section II-A; directed or undirected,
+ * unweighted) in CSR form: row_ptr int64[n+1] (row_ptr[0] = 0,
+ * non-decreasing, row_ptr[n] = nnz), col int32[nnz] in [0, n).  For an
+ * undirected graph every edge must appear in both rows.  Self-loops are
+ * allowed and never lie on a shortest path.  Also computes VertexDiamUB
+ * (Algorithm 1): for undirected graphs one BFS from the largest-degree vertex
+ * of every component, D = 2*ecc - 1; for directed graphs D = n - 2.
+ * on_device: 1 if row_ptr/col are device pointers.  Errors: INVALID (bad
+ * sizes or indices), OOM, CUDA.  Synchronises the stream. */
+percis_status percis_load_csr(percis_ctx *ctx, int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                              int directed, int on_device);
+
+/* Set the percolation states x_v in [0,1] (Section II-A), double[n] in node
+ * order.  Sorts them non-increasingly (ties by node id), builds Algorithm 2's
+ * tables w_i, c_i, r_i, c (appendix, preprocessing loop), C_v = C - sum_u
+ * |x_v - x_u| and lambda_v = C/C_v = kappa/kappa~ (closed form of d_v in the
+ * proof of Proposition 5).  Errors: STATE (no graph), INVALID (NaN or outside
+ * [0,1]), DEGENERATE (some C_v <= 0, Section II-A).  Synchronises. */
+percis_status percis_set_states(percis_ctx *ctx, const double *x, int on_device);
+
+/* ------------------------------------------------------------ estimation */
+
+/* Algorithm 1 (PercIS): D, l1 phase-1 samples, rho^ (Proposition 2), v^
+ * (Proposition 3), x^, l = sup_{x in (0, x^]} d^2 ln(4 d^ rho^/(x delta)) /
+ * (g(x) h(eps d^/g(x))) (Theorem 1), l fresh phase-2 samples, and
+ * pc_out[v] = p~(v) = lambda_v cnt_v / l.  Samples are addressed by
+ * (seed, phase, index) through Philox4x32-10, so results do not depend on
+ * the form or the lane width.  eps, delta in (0,1).  pc_out: double[n],
+ * device memory if pc_on_device else host.  info: host, may be NULL.
+ * Errors: STATE, INVALID, TIMEOUT, CUDA, OOM.  Synchronises once after phase 1
+ * (the bound needs four scalars) and at the end. */
+percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_t seed, double *pc_out,
+                              int pc_on_device, percis_info *info);
+
+/* Exact percolation centrality (Definition 1) by all-sources sigma-BFS and a
+ * dependency accumulation with target weights R(x_s - x_w) (the extended
+ * Brandes method used for exact values, Section IV-A).  pc_out: double[n].
+ * Errors: TOO_LARGE when n * nnz > 2^40; STATE; CUDA.  Synchronises. */
+percis_status percis_exact_small(percis_ctx *ctx, double *pc_out, int pc_on_device);
+
+/* Vector-Jacobian product of the last estimate with respect to the states:
+ * grad_x[u] = sum_v grad_pc[v] dF_v/dx_u at the current x, where
+ * F_v(x) = (C/l) sum_i a_i(v) R(x_{s_i} - x_{t_i}) / (R_i C_v(x)) is the
+ * Section III-A estimator with the phase-2 sample (pairs, paths a_i, and the
+ * sampling weights R_i, C) held fixed, so F = p~ at the current x and E[dF]
+ * = dp (not in the paper: importance-sampling gradient).  The ramp's
+ * derivative at 0 is 0.  grad_pc, grad_x: double[n], device if on_device.
+ * Errors: NO_SAMPLE (no estimate with keep_paths), STATE, CUDA. */
+percis_status percis_backward(percis_ctx *ctx, const double *grad_pc, double *grad_x, int on_device);
+
+/* ------------------------------------------ stage entry points (parity) */
+
+/* Sorted states and Algorithm 2 tables.  Any output may be NULL.  Device
+ * outputs: perm int32[n] (sorted position i-1 -> node id), xs double[n],
+ * w/ci/r double[n+2] (1-based, index n+1 = 0), Cv/lambda double[n] (node
+ * order).  Host outputs: c, dhat (double), vertex_diam (int64). */
+percis_status percis_get_prep(percis_ctx *ctx, int32_t *perm, double *xs, double *w, double *ci, double *r, double *Cv,
+                              double *lambda, double *c, double *dhat, int64_t *vertex_diam);
+
+/* Algorithm 2 sampling of pairs i0 .. i0+count-1 with Philox tag `tag`
+ * (0 = phase 1, 1 = phase 2).  Device outputs s, t: int32[count] node ids. */
+percis_status percis_sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag, int64_t i0, int64_t count, int32_t *s,
+                                  int32_t *t);
+
+/* Single-source sigma-counting BFS with the plain kernel.  target < 0: full
+ * traversal; else truncated once target's level is discovered.  Device
+ * outputs dist int32[n] (-1 = not reached), sigma double[n] (0 = not
+ * reached); either may be NULL. */
+percis_status percis_bfs(percis_ctx *ctx, int32_t source, int32_t target, int32_t *dist, double *sigma);
+
+/* Multi-source sigma-counting BFS with the batched kernel, full traversal
+ * from nsrc distinct sources (nsrc <= 512).  Device outputs, source-major:
+ * dist int32[nsrc*n], sigma double[nsrc*n]. */
+percis_status percis_msbfs(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, int32_t *dist, double *sigma);
+
+/* One sampling phase (phase 0: pair tag 0, path tag 2; phase 1: pair tag 1,
+ * path tag 3) of `count` samples with the configured form.  Device outputs
+ * (any may be NULL): s, t int32[count]; kind int32[count] (0 = path sampled,
+ * 1 = R(x_s - x_t) = 0, 2 = t unreachable); ilen int32[count] = |I(tau)|;
+ * cnt int64[n] = number of sampled paths with v internal.  The paths stay
+ * in the context for percis_get_paths / percis_backward. */
+percis_status percis_run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count, int32_t *s, int32_t *t,
+                               int32_t *kind, int32_t *ilen, int64_t *cnt);
+
+/* Internal nodes of the paths of the last sampling phase, t-side first.
+ * Device outputs: path_ptr int64[count+1], path_nodes int32[path_ptr[count]]
+ * (pass path_nodes = NULL to size it first; *total receives the total). */
+percis_status percis_get_paths(percis_ctx *ctx, int64_t *path_ptr, int32_t *path_nodes, int64_t *total);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERCIS_H */

@@ -1,0 +1,162 @@
+// Internal declarations shared by the translation units of libpercis.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/percis.h"
+
+namespace percis {
+
+// Grow-only device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <class T>
+    T *as() const {
+        return static_cast<T *>(p);
+    }
+};
+
+// Control block of the persistent kernels (device memory, zeroed per launch).
+struct alignas(16) MsCtl {
+    uint32_t bar_count, bar_gen;  // GridBarrier
+    uint32_t status;
+    uint32_t ticket;
+    int32_t level;                // last level reached
+    int32_t done;
+    int32_t pad[2];
+    unsigned long long active[8];    // lanes still running (K <= 8 words)
+    unsigned long long nonempty[2][8];  // per-level OR of discovered bits (ping-pong)
+    long long edges_scanned;      // instrumentation
+};
+
+struct PlainCtl {
+    uint32_t bar_count, bar_gen;
+    uint32_t status;
+    int32_t qsize[2];
+    int32_t level;
+    int32_t found;
+    int32_t pad;
+};
+
+}  // namespace percis
+
+struct percis_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    percis_options opt{};
+    int num_sms = 0;
+    int64_t launches = 0;
+
+    // graph
+    bool have_graph = false;
+    int64_t n = 0, nnz = 0;
+    int directed = 0;
+    percis::DevBuf rp, col, irp, icol;  // irp/icol used only when directed
+    int64_t vertex_diam = -1;
+
+    // states and preprocessing
+    bool have_states = false;
+    percis::DevBuf x, xs, perm, w, ci, r, Cv, lam, grp_lo, grp_hi;
+    double c_host = 0.0, dhat_host = 0.0;
+    percis::DevBuf dscal;  // device scalars: [0] = c, [1] = dhat
+
+    // plain BFS state
+    percis::DevBuf ep, lvl, sigma1, qa, qb, plain_ctl;
+    int32_t epoch = 0;
+
+    // batched BFS state
+    percis::DevBuf vis, fhist, sigmaW, ms_ctl, remaining, found;
+    int32_t lanes_alloc = 0;
+    int32_t levels_alloc = 0;
+
+    // samples of the last phase
+    percis::DevBuf pair_s, pair_t, kind, ilen, path_off, arena, cnt, arena_top;
+    percis::DevBuf src_count, src_fill, src_off, lane_of_v, sorted_samples, samp_lane, samp_t, lane_src, lane_off;
+    int64_t phase_count = 0;
+    int64_t arena_cap = 0;
+    bool have_paths = false;
+    int last_phase = -1;
+    uint64_t last_seed = 0;
+    int64_t last_ell = 0;
+
+    // scratch for reductions/scans
+    percis::DevBuf scratch, red, status;
+    percis::DevBuf pc_tmp, grad_tmp, host_pinned;
+};
+
+namespace percis {
+
+// error helpers (api.cu)
+percis_status set_err(percis_ctx *ctx, percis_status st, const std::string &msg);
+percis_status cuda_err(percis_ctx *ctx, cudaError_t e, const char *where);
+percis_status ensure(percis_ctx *ctx, DevBuf &b, size_t bytes, const char *what);
+
+#define PERCIS_CHECK_LAUNCH(ctx, where)                         \
+    do {                                                        \
+        (ctx)->launches++;                                      \
+        cudaError_t e__ = cudaGetLastError();                   \
+        if (e__ != cudaSuccess) return cuda_err((ctx), e__, (where)); \
+    } while (0)
+
+#define PERCIS_CUDA(ctx, call)                                  \
+    do {                                                        \
+        cudaError_t e__ = (call);                               \
+        if (e__ != cudaSuccess) return cuda_err((ctx), e__, #call); \
+    } while (0)
+
+#define PERCIS_TRY(call)                       \
+    do {                                       \
+        percis_status s__ = (call);            \
+        if (s__ != PERCIS_OK) return s__;      \
+    } while (0)
+
+// util.cu: scans and simple fills
+percis_status scan_exclusive_i64(percis_ctx *ctx, const int64_t *in, int64_t *out, int64_t n);
+percis_status scan_exclusive_f64(percis_ctx *ctx, const double *in, double *out, int64_t n);
+int grid_for(percis_ctx *ctx, int64_t work, int block);
+
+// prep.cu
+percis_status prep_graph(percis_ctx *ctx);  // transpose (directed), validation, VertexDiamUB
+percis_status prep_states(percis_ctx *ctx);  // sort, tables, C_v, lambda, d^
+
+// sampler.cu
+percis_status sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag, int64_t i0, int64_t count, int32_t *s,
+                           int32_t *t, int32_t *kind);
+percis_status group_by_source(percis_ctx *ctx, int64_t count, int64_t *n_sources, int64_t *n_valid);
+
+// bfs_plain.cu
+percis_status plain_bfs(percis_ctx *ctx, const int32_t *s_dev, const int32_t *t_dev, int64_t idx, int32_t s_host,
+                        int32_t t_host);
+percis_status plain_backtrack(percis_ctx *ctx, uint64_t seed, uint32_t tag, int64_t idx);
+percis_status plain_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count);
+percis_status plain_dist_sigma(percis_ctx *ctx, int32_t *dist, double *sigma);
+percis_status vertex_diam_ub(percis_ctx *ctx, int64_t *D);
+
+// msbfs.cu
+percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count, int64_t n_sources,
+                            int64_t *batches);
+percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, int32_t *dist, double *sigma);
+int choose_lanes(percis_ctx *ctx, int64_t n_sources);
+
+// backward.cu
+percis_status backward_fixed(percis_ctx *ctx, const double *g, double *grad);
+
+// exact.cu
+percis_status exact_pc(percis_ctx *ctx, double *pc);
+
+// bounds.cpp
+struct Bounds {
+    double rho_tilde, Lambda, rho_hat, v_hat, x_hat;
+    int64_t ell;
+};
+Bounds compute_bounds(double eps, double delta, double dhat, int64_t D, int64_t ell1, int64_t sum_ilen,
+                      int64_t sum_ilen2, double p1_max, int data_independent);
+int64_t ell1_default(double eps, double delta);
+
+}  // namespace percis

@@ -1,0 +1,516 @@
+// Batched form of RandomSP: up to W = 64*K distinct sources ("lanes") share
+// one persistent cooperative launch.  Per vertex the launch keeps K 64-bit
+// words of visited bits and, for every level L, K words of frontier bits
+// F_L(v) (bit j set iff v is at distance L from lane j's source).  A level is
+// one pull pass over all vertices:
+//     c = active & ~visited(v),  F_{L+1}(v) = OR_{u in in(v)} F_L(u) & c,
+//     sigma_j(v) = sum over u in in(v) with bit j of F_L(u) & c of sigma_j(u)
+// (the sigma recurrence of the oracle, summed in any order: the values are
+// integers below 2^53, so every order gives the same exact result).  A lane
+// retires once every target of its samples is discovered (its level is then
+// complete) or its frontier is empty.  After the last level the same launch
+// backtracks every sample of the batch (one warp per sample) exactly as the
+// plain form does, reading the frontier history for the predecessor test.
+//
+// Layout in HBM (vertex-major so one warp reads a vertex's lanes coalesced):
+//   visited  uint64 [n][K]
+//   history  uint64 [Lcap+1][n][K]
+//   sigma    double [n][W]
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace percis {
+
+namespace {
+
+constexpr int kMsBlock = 256;
+
+struct MsArgs {
+    int64_t n;
+    const int64_t *irp;
+    const int32_t *icol;
+    uint64_t *vis;
+    uint64_t *fh;
+    double *sigma;
+    MsCtl *ctl;
+    int32_t Lcap;
+    int32_t lane_base;
+    int32_t nlanes;
+    const int32_t *lane_src;
+    const long long *lane_off;
+    const int32_t *samp_t;
+    const int32_t *samp_lane;
+    const int32_t *sorted_samples;
+    int32_t *found;
+    int32_t *remaining;
+    uint64_t seed;
+    uint32_t tag;
+    int32_t *kind;
+    int32_t *ilen;
+    long long *path_off;
+    int32_t *arena;
+    unsigned long long *arena_top;
+    int64_t arena_cap;
+    unsigned long long *cnt;
+    int32_t full;
+    uint64_t budget_ns;
+};
+
+template <int K>
+__device__ __forceinline__ void load_words(const uint64_t *p, uint64_t (&out)[K]) {
+    if constexpr (K == 1) {
+        out[0] = __ldcg(p);
+    } else {
+#pragma unroll
+        for (int w = 0; w < K; w += 2) {
+            const ulonglong2 q = __ldcg(reinterpret_cast<const ulonglong2 *>(p + w));
+            out[w] = q.x;
+            out[w + 1] = q.y;
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
+    constexpr int W = 64 * K;
+    MsCtl *ctl = a.ctl;
+    GridBarrier *bar = reinterpret_cast<GridBarrier *>(ctl);
+    uint32_t *status = &ctl->status;
+    const int lane = threadIdx.x & 31;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gwarp = tid >> 5;
+    const int64_t nwarps = nthreads >> 5;
+    const int64_t n = a.n;
+    const int64_t nk = n * K;
+    const long long p0 = a.full ? 0 : a.lane_off[a.lane_base];
+    const long long p1 = a.full ? 0 : a.lane_off[a.lane_base + a.nlanes];
+
+    // ---- prologue: clear visited and level-0 frontier, reset lane state
+    for (int64_t i = tid; i < nk; i += nthreads) {
+        a.vis[i] = 0ull;
+        a.fh[i] = 0ull;
+    }
+    for (long long p = p0 + tid; p < p1; p += nthreads) a.found[p] = -1;
+    if (blockIdx.x == 0) {
+        for (int j = threadIdx.x; j < W; j += blockDim.x) a.remaining[j] = 0;
+        if (threadIdx.x < K) {
+            const int lo = threadIdx.x * 64;
+            const int cntl = max(0, min(64, a.nlanes - lo));
+            ctl->active[threadIdx.x] = cntl == 64 ? ~0ull : ((1ull << cntl) - 1ull);
+            ctl->nonempty[0][threadIdx.x] = 0ull;
+            ctl->nonempty[1][threadIdx.x] = 0ull;
+        }
+        if (threadIdx.x == 0) {
+            ctl->ticket = 0;
+            ctl->level = 0;
+        }
+    }
+    if (!grid_sync(bar, status, a.budget_ns)) return;
+    for (int64_t j = tid; j < a.nlanes; j += nthreads) {
+        const int32_t v = a.lane_src[a.lane_base + j];
+        const uint64_t bit = 1ull << (j & 63);
+        atomicOr((unsigned long long *)&a.vis[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
+        atomicOr((unsigned long long *)&a.fh[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
+        a.sigma[(int64_t)v * W + j] = 1.0;
+        if (!a.full) {
+            const long long q0 = a.lane_off[a.lane_base + j], q1 = a.lane_off[a.lane_base + j + 1];
+            a.remaining[j] = (int32_t)(q1 - q0);
+        }
+    }
+    if (!grid_sync(bar, status, a.budget_ns)) return;
+
+    __shared__ unsigned long long s_nonempty[K];
+    int L = 0;
+    for (;;) {
+        uint64_t act[K];
+        bool any_act = false;
+#pragma unroll
+        for (int w = 0; w < K; ++w) {
+            act[w] = ld_relaxed_u64((const uint64_t *)&ctl->active[w]);
+            any_act |= act[w] != 0;
+        }
+        if (!any_act) break;
+        if (threadIdx.x < K) s_nonempty[threadIdx.x] = 0ull;
+        __syncthreads();
+        const uint64_t *fcur = a.fh + (int64_t)L * nk;
+        uint64_t *fnext = a.fh + (int64_t)(L + 1) * nk;
+
+        // ---- phase A: pull pass over all vertices (warp per vertex)
+        for (int64_t v = gwarp; v < n; v += nwarps) {
+            uint64_t c[K];
+            uint64_t vw[K];
+            load_words<K>(a.vis + v * K, vw);
+            bool any = false;
+#pragma unroll
+            for (int w = 0; w < K; ++w) {
+                c[w] = act[w] & ~vw[w];
+                any |= c[w] != 0;
+            }
+            if (!any) {
+                if (lane < K) fnext[v * K + lane] = 0ull;
+                continue;
+            }
+            uint64_t nbp[K];
+            double acc0[K], acc1[K];
+#pragma unroll
+            for (int w = 0; w < K; ++w) {
+                nbp[w] = 0ull;
+                acc0[w] = 0.0;
+                acc1[w] = 0.0;
+            }
+            const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+            for (int64_t base = e0; base < e1; base += 32) {
+                const int64_t e = base + lane;
+                int32_t u = 0;
+                uint64_t f[K];
+                if (e < e1) {
+                    u = a.icol[e];
+                    load_words<K>(fcur + (int64_t)u * K, f);
+                } else {
+#pragma unroll
+                    for (int w = 0; w < K; ++w) f[w] = 0ull;
+                }
+#pragma unroll
+                for (int w = 0; w < K; ++w) {
+                    const uint64_t fw = f[w] & c[w];
+                    nbp[w] |= fw;
+                    unsigned nz = __ballot_sync(0xffffffffu, fw != 0ull);
+                    while (nz) {
+                        const int j = __ffs(nz) - 1;
+                        nz &= nz - 1;
+                        const uint64_t fj = shfl64(fw, j);
+                        const int32_t uj = __shfl_sync(0xffffffffu, u, j);
+                        const double *srow = a.sigma + (int64_t)uj * W + 64 * w;
+                        if ((fj >> lane) & 1ull) acc0[w] += __ldcg(srow + lane);
+                        if ((fj >> (lane + 32)) & 1ull) acc1[w] += __ldcg(srow + lane + 32);
+                    }
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < K; ++w) {
+                const uint64_t nb = warp_or64(nbp[w]);
+                if (lane == 0) {
+                    fnext[v * K + w] = nb;
+                    if (nb) {
+                        a.vis[v * K + w] = vw[w] | nb;
+                        atomicOr(&s_nonempty[w], (unsigned long long)nb);
+                    }
+                }
+                if (nb) {
+                    double *drow = a.sigma + v * W + 64 * w;
+                    if ((nb >> lane) & 1ull) {
+                        drow[lane] = acc0[w];
+                        if (acc0[w] >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
+                    }
+                    if ((nb >> (lane + 32)) & 1ull) {
+                        drow[lane + 32] = acc1[w];
+                        if (acc1[w] >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < K && s_nonempty[threadIdx.x])
+            atomicOr(&ctl->nonempty[L & 1][threadIdx.x], s_nonempty[threadIdx.x]);
+        if (!grid_sync(bar, status, a.budget_ns)) return;
+
+        // ---- phase B: mark settled targets, then the last block retires lanes
+        if (!a.full) {
+            for (long long p = p0 + tid; p < p1; p += nthreads) {
+                if (a.found[p] >= 0) continue;
+                const int32_t j = a.samp_lane[p] - a.lane_base;
+                const int32_t t = a.samp_t[p];
+                if ((__ldcg(&a.vis[(int64_t)t * K + (j >> 6)]) >> (j & 63)) & 1ull) {
+                    a.found[p] = L + 1;
+                    atomicSub(&a.remaining[j], 1);
+                }
+            }
+        }
+        __syncthreads();
+        __shared__ int s_last;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (threadIdx.x < K) {
+                const int w = threadIdx.x;
+                uint64_t nact = act[w] & ld_relaxed_u64((const uint64_t *)&ctl->nonempty[L & 1][w]);
+                if (!a.full) {
+                    uint64_t m = nact;
+                    while (m) {
+                        const int b = __ffsll((long long)m) - 1;
+                        m &= m - 1;
+                        if (atomicAdd(&a.remaining[w * 64 + b], 0) <= 0) nact &= ~(1ull << b);
+                    }
+                }
+                ctl->active[w] = nact;
+                ctl->nonempty[L & 1][w] = 0ull;
+            }
+            if (threadIdx.x == 0) {
+                ctl->ticket = 0;
+                ctl->level = L + 1;
+            }
+        }
+        if (!grid_sync(bar, status, a.budget_ns)) return;
+        ++L;
+        bool more = false;
+#pragma unroll
+        for (int w = 0; w < K; ++w) more |= ld_relaxed_u64((const uint64_t *)&ctl->active[w]) != 0ull;
+        if (!more) break;
+        if (L + 1 > a.Lcap) {
+            if (tid == 0) atomicOr(status, DEV_NEED_LEVELS);
+            return;
+        }
+    }
+    if (a.full) return;
+
+    // ---- backtrack every sample of the batch (warp per sample)
+    for (long long p = p0 + gwarp; p < p1; p += nwarps) {
+        const int32_t i = a.sorted_samples[p];
+        const int32_t j = a.samp_lane[p] - a.lane_base;
+        const int32_t t = a.samp_t[p];
+        const int32_t s = a.lane_src[a.lane_base + j];
+        const int32_t d = __ldcg(&a.found[p]);
+        if (d < 0) {
+            if (lane == 0) {
+                a.kind[i] = 2;
+                a.ilen[i] = 0;
+                a.path_off[i] = 0;
+            }
+            continue;
+        }
+        const int32_t len = d - 1;
+        unsigned long long off = 0;
+        if (lane == 0) {
+            off = atomicAdd(a.arena_top, (unsigned long long)len);
+            a.ilen[i] = len;
+            a.path_off[i] = (long long)off;
+            if ((int64_t)(off + len) > a.arena_cap) atomicOr(status, DEV_ARENA_OVERFLOW);
+        }
+        off = __shfl_sync(0xffffffffu, off, 0);
+        const bool store = (int64_t)(off + len) <= a.arena_cap;
+        const int wj = j >> 6;
+        const uint64_t bj = 1ull << (j & 63);
+        int32_t w = t;
+        int32_t lw = d;
+        uint32_t step = 0;
+        int32_t k = 0;
+        while (w != s) {
+            const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step), __ldcg(&a.sigma[(int64_t)w * W + j]));
+            const uint64_t *fprev = a.fh + (int64_t)(lw - 1) * nk;
+            const int64_t e0 = a.irp[w], e1 = a.irp[w + 1];
+            double carry = 0.0;
+            int32_t pick = -1;
+            for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
+                const int64_t e = base + lane;
+                int32_t pv = -1;
+                double val = 0.0;
+                if (e < e1) {
+                    pv = a.icol[e];
+                    if (__ldcg(&fprev[(int64_t)pv * K + wj]) & bj) val = __ldcg(&a.sigma[(int64_t)pv * W + j]);
+                }
+                const double cum = __dadd_rn(carry, warp_inclusive_scan(val));
+                const unsigned hit = __ballot_sync(0xffffffffu, val > 0.0 && cum >= target);
+                if (hit) pick = __shfl_sync(0xffffffffu, pv, __ffs(hit) - 1);
+                carry = __shfl_sync(0xffffffffu, cum, 31);
+            }
+            if (pick < 0) {
+                if (lane == 0) atomicOr(status, DEV_BAD_PATH);
+                break;
+            }
+            if (pick != s) {
+                if (lane == 0) {
+                    if (store) a.arena[off + k] = pick;
+                    atomicAdd(&a.cnt[pick], 1ULL);
+                }
+                ++k;
+            }
+            w = pick;
+            --lw;
+            ++step;
+        }
+    }
+}
+
+// dist/sigma of every lane after a full traversal, source-major output.
+template <int K>
+__global__ void k_ms_extract(const uint64_t *fh, const double *sigma, int64_t n, int32_t levels, int32_t nsrc,
+                             int32_t *dist, double *sig) {
+    constexpr int W = 64 * K;
+    const int64_t total = n * (int64_t)nsrc;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+        const int64_t j = q / n, v = q % n;
+        int32_t d = -1;
+        for (int32_t L = 0; L <= levels; ++L) {
+            if ((fh[(int64_t)L * n * K + v * K + (j >> 6)] >> (j & 63)) & 1ull) {
+                d = L;
+                break;
+            }
+        }
+        if (dist) dist[q] = d;
+        if (sig) sig[q] = d >= 0 ? sigma[v * W + j] : 0.0;
+    }
+}
+
+struct GridCache {
+    int grid[4] = {0, 0, 0, 0};
+};
+GridCache g_ms_grid;
+
+template <int K>
+int ms_grid(percis_ctx *ctx) {
+    const int idx = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : 3;
+    if (g_ms_grid.grid[idx] == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs<K>, kMsBlock, 0);
+        g_ms_grid.grid[idx] = std::max(1, per_sm) * ctx->num_sms;
+    }
+    return g_ms_grid.grid[idx];
+}
+
+template <int K>
+percis_status launch_ms(percis_ctx *ctx, MsArgs &a) {
+    void *args[] = {&a};
+    const int grid = ms_grid<K>(ctx);
+    PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_msbfs<K>, dim3(grid), dim3(kMsBlock), args, 0,
+                                                 ctx->stream));
+    ctx->launches++;
+    return PERCIS_OK;
+}
+
+percis_status launch_ms_k(percis_ctx *ctx, int K, MsArgs &a) {
+    switch (K) {
+        case 1: return launch_ms<1>(ctx, a);
+        case 2: return launch_ms<2>(ctx, a);
+        case 4: return launch_ms<4>(ctx, a);
+        default: return launch_ms<8>(ctx, a);
+    }
+}
+
+percis_status ensure_ms(percis_ctx *ctx, int W, int Lcap) {
+    const int64_t n = ctx->n;
+    const int K = W / 64;
+    PERCIS_TRY(ensure(ctx, ctx->vis, sizeof(uint64_t) * n * K, "visited bits"));
+    PERCIS_TRY(ensure(ctx, ctx->fhist, sizeof(uint64_t) * n * K * (int64_t)(Lcap + 1), "frontier history"));
+    PERCIS_TRY(ensure(ctx, ctx->sigmaW, sizeof(double) * n * W, "lane sigma"));
+    PERCIS_TRY(ensure(ctx, ctx->remaining, sizeof(int32_t) * 512, "lane remaining"));
+    PERCIS_TRY(ensure(ctx, ctx->ms_ctl, sizeof(MsCtl), "ms ctl"));
+    return PERCIS_OK;
+}
+
+void fill_common(percis_ctx *ctx, MsArgs &a, int Lcap) {
+    a.n = ctx->n;
+    a.irp = ctx->directed ? ctx->irp.as<int64_t>() : ctx->rp.as<int64_t>();
+    a.icol = ctx->directed ? ctx->icol.as<int32_t>() : ctx->col.as<int32_t>();
+    a.vis = ctx->vis.as<uint64_t>();
+    a.fh = ctx->fhist.as<uint64_t>();
+    a.sigma = ctx->sigmaW.as<double>();
+    a.ctl = ctx->ms_ctl.as<MsCtl>();
+    a.Lcap = Lcap;
+    a.budget_ns = (uint64_t)(ctx->opt.timeout_s * 1e9);
+}
+
+}  // namespace
+
+int choose_lanes(percis_ctx *ctx, int64_t n_sources) {
+    int W = ctx->opt.lanes;
+    if (W != 64 && W != 128 && W != 256 && W != 512) {
+        W = 512;
+        while (W > 64 && (int64_t)W / 2 >= n_sources) W /= 2;
+        // keep the lane sigma array within a modest share of device memory
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            while (W > 64 && (double)ctx->n * W * 8.0 > 0.25 * (double)total_b) W /= 2;
+        }
+    }
+    return W;
+}
+
+percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count, int64_t n_sources,
+                            int64_t *batches) {
+    const int W = choose_lanes(ctx, n_sources);
+    const int K = W / 64;
+    int Lcap = std::max(ctx->levels_alloc, 32);
+    PERCIS_TRY(ensure_ms(ctx, W, Lcap));
+    ctx->levels_alloc = Lcap;
+    ctx->lanes_alloc = W;
+    PERCIS_TRY(ensure(ctx, ctx->found, sizeof(int32_t) * (count + 1), "found"));
+    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ms_ctl.p, 0, sizeof(MsCtl), ctx->stream));
+    const int64_t B = (n_sources + W - 1) / W;
+    *batches = B;
+    MsArgs a{};
+    fill_common(ctx, a, Lcap);
+    a.lane_src = ctx->lane_src.as<int32_t>();
+    a.lane_off = ctx->lane_off.as<long long>();
+    a.samp_t = ctx->samp_t.as<int32_t>();
+    a.samp_lane = ctx->samp_lane.as<int32_t>();
+    a.sorted_samples = ctx->sorted_samples.as<int32_t>();
+    a.found = ctx->found.as<int32_t>();
+    a.remaining = ctx->remaining.as<int32_t>();
+    a.seed = seed;
+    a.tag = tag_path;
+    a.kind = ctx->kind.as<int32_t>();
+    a.ilen = ctx->ilen.as<int32_t>();
+    a.path_off = ctx->path_off.as<long long>();
+    a.arena = ctx->arena.as<int32_t>();
+    a.arena_top = ctx->arena_top.as<unsigned long long>();
+    a.arena_cap = ctx->arena_cap;
+    a.cnt = ctx->cnt.as<unsigned long long>();
+    a.full = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        a.lane_base = (int32_t)(b * W);
+        a.nlanes = (int32_t)std::min<int64_t>(W, n_sources - b * W);
+        PERCIS_TRY(launch_ms_k(ctx, K, a));
+    }
+    return PERCIS_OK;
+}
+
+// Full traversal from nsrc <= 512 sources (inspection and exact centrality).
+percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, int32_t *dist, double *sigma) {
+    int W = 64;
+    while (W < nsrc) W *= 2;
+    const int K = W / 64;
+    int Lcap = std::max(ctx->levels_alloc, 32);
+    for (int attempt = 0; attempt < 12; ++attempt) {
+        PERCIS_TRY(ensure_ms(ctx, W, Lcap));
+        ctx->levels_alloc = Lcap;
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ms_ctl.p, 0, sizeof(MsCtl), ctx->stream));
+        MsArgs a{};
+        fill_common(ctx, a, Lcap);
+        a.lane_src = sources;
+        a.lane_base = 0;
+        a.nlanes = nsrc;
+        a.remaining = ctx->remaining.as<int32_t>();
+        a.full = 1;
+        PERCIS_TRY(launch_ms_k(ctx, K, a));
+        MsCtl hc;
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(&hc, ctx->ms_ctl.p, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
+        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (hc.status & DEV_TIMEOUT) return set_err(ctx, PERCIS_E_TIMEOUT, "batched BFS timed out");
+        if (hc.status & DEV_NEED_LEVELS) {
+            Lcap *= 2;
+            continue;
+        }
+        const int levels = hc.level;
+        if (!dist && !sigma) return PERCIS_OK;
+        const int grid = grid_for(ctx, ctx->n * nsrc, 256);
+        switch (K) {
+            case 1: k_ms_extract<1><<<grid, 256, 0, ctx->stream>>>(ctx->fhist.as<uint64_t>(), ctx->sigmaW.as<double>(), ctx->n, levels, nsrc, dist, sigma); break;
+            case 2: k_ms_extract<2><<<grid, 256, 0, ctx->stream>>>(ctx->fhist.as<uint64_t>(), ctx->sigmaW.as<double>(), ctx->n, levels, nsrc, dist, sigma); break;
+            case 4: k_ms_extract<4><<<grid, 256, 0, ctx->stream>>>(ctx->fhist.as<uint64_t>(), ctx->sigmaW.as<double>(), ctx->n, levels, nsrc, dist, sigma); break;
+            default: k_ms_extract<8><<<grid, 256, 0, ctx->stream>>>(ctx->fhist.as<uint64_t>(), ctx->sigmaW.as<double>(), ctx->n, levels, nsrc, dist, sigma); break;
+        }
+        PERCIS_CHECK_LAUNCH(ctx, "ms extract");
+        return PERCIS_OK;
+    }
+    return set_err(ctx, PERCIS_E_TOO_LARGE, "frontier history exceeded the level cap");
+}
+
+}  // namespace percis

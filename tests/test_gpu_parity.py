@@ -1,0 +1,334 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer and index results (sorted order, tables, pairs, distances, sigma,
+paths, counts) must be bit-exact; sigma is exact below 2^53 so its FP64
+values must match exactly too.  Estimates: 1e-9 absolute.  Gradients: 1e-10
+norm-wise relative to the oracle's VJP and 1e-6 to finite differences.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_11454_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def binding():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_11454_gb300 import binding as b
+
+    b.load_library()
+    return b
+
+
+def _engine(binding, g, x=None, **opts):
+    eng = binding.PercIS(0)
+    if opts:
+        eng.set_options(**opts)
+    eng.load_csr(g.row_ptr, g.col, directed=g.directed)
+    if x is not None:
+        eng.set_states(x)
+    return eng
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+GRAPHS = {
+    "er1000": lambda: synth.erdos_renyi(1000, 8.0, 0),
+    "ba3000": lambda: synth.barabasi_albert(3000, 3, 1),
+    "rmat12": lambda: synth.rmat(12, 8, 0.57, 0.19, 0.19, 2),
+    "grid30": lambda: synth.grid_2d(30, 0.05, 3),
+}
+
+
+@pytest.fixture(scope="module", params=list(GRAPHS))
+def gcase(request):
+    g = GRAPHS[request.param]()
+    return request.param, g, oracle.from_synth(g)
+
+
+def _states(name, n):
+    if name == "ba3000":
+        return synth.states_outbreak(n, 0.1, 0.5, 1.0, 0)  # 90% ties at 0
+    if name == "rmat12":
+        return synth.states_beta(n, 0.5, 2.0, 0)
+    return synth.states_uniform(n, 0)
+
+
+def test_prep_bitexact(binding, gcase):
+    name, g, og = gcase
+    x = _states(name, g.n)
+    eng = _engine(binding, g, x)
+    got = eng.prep()
+    prep = oracle.prepare(x, cv_method="sorted")
+    assert np.array_equal(_np(got["perm"]), prep.perm)
+    assert np.array_equal(_np(got["xs"]), prep.xs)
+    for k in ("w", "ci", "r"):
+        assert np.array_equal(_np(got[k]), getattr(prep, k)), k
+    assert got["c"] == prep.c
+    assert np.array_equal(_np(got["Cv"]), prep.Cv)
+    assert np.array_equal(_np(got["lam"]), prep.lam)
+    assert got["dhat"] == prep.dhat
+    assert got["vertex_diam"] == oracle.vertex_diam_ub(og)
+    eng.close()
+
+
+def test_pairs_bitexact(binding, gcase):
+    name, g, og = gcase
+    x = _states(name, g.n)
+    eng = _engine(binding, g, x)
+    prep = oracle.prepare(x)
+    for tag, i0, cnt in [(0, 0, 20000), (1, 123457, 5001)]:
+        s, t = eng.sample_pairs(seed=77, tag=tag, i0=i0, count=cnt)
+        rs, rt, _, _ = oracle.sample_pairs(prep, 77, tag, i0, cnt)
+        assert np.array_equal(_np(s), rs)
+        assert np.array_equal(_np(t), rt)
+    eng.close()
+
+
+def test_plain_bfs_bitexact(binding, gcase):
+    name, g, og = gcase
+    eng = _engine(binding, g)
+    rng = np.random.default_rng(0)
+    for src in rng.integers(0, g.n, 4):
+        for tgt in (-1, int(rng.integers(0, g.n))):
+            dist, sig = eng.bfs(int(src), tgt)
+            ret, rd, rsig, _, _, _ = oracle.bfs(og, int(src), tgt)
+            if tgt < 0:
+                assert np.array_equal(_np(dist), rd)
+                assert np.array_equal(_np(sig), rsig)
+            else:
+                # truncated: every vertex the oracle settled matches exactly
+                m = rd >= 0
+                assert np.array_equal(_np(dist)[m], rd[m])
+                assert np.array_equal(_np(sig)[m], rsig[m])
+    eng.close()
+
+
+@pytest.mark.parametrize("nsrc", [1, 5, 64, 100, 200, 512])
+def test_msbfs_bitexact(binding, gcase, nsrc):
+    name, g, og = gcase
+    eng = _engine(binding, g)
+    rng = np.random.default_rng(nsrc)
+    srcs = rng.choice(g.n, size=nsrc, replace=False)
+    dist, sig = eng.msbfs(srcs)
+    dist, sig = _np(dist), _np(sig)
+    check = list(range(nsrc)) if nsrc <= 8 else list(rng.choice(nsrc, 8, replace=False)) + [nsrc - 1]
+    for j in check:
+        _, rd, rsig, _, _, _ = oracle.bfs(og, int(srcs[j]))
+        assert np.array_equal(dist[j], rd), j
+        assert np.array_equal(sig[j], rsig), j
+    eng.close()
+
+
+@pytest.mark.parametrize("form", ["batched", "plain"])
+def test_phase_bitexact(binding, gcase, form):
+    name, g, og = gcase
+    x = _states(name, g.n)
+    count = 600 if form == "plain" else 3000
+    eng = _engine(binding, g, x, form=form)
+    prep = oracle.prepare(x)
+    got = eng.run_phase(seed=11, phase=1, count=count)
+    ph = oracle.run_samples(og, prep, 11, 1, 3, 0, count, keep_paths=True)
+    assert np.array_equal(_np(got["s"]), ph.s)
+    assert np.array_equal(_np(got["t"]), ph.t)
+    assert np.array_equal(_np(got["kind"]), ph.kind)
+    assert np.array_equal(_np(got["ilen"]), ph.ilen)
+    assert np.array_equal(_np(got["cnt"]), ph.cnt)
+    ptr, nodes = eng.get_paths(count)
+    assert np.array_equal(_np(ptr), ph.path_ptr)
+    assert np.array_equal(_np(nodes), ph.path_nodes)
+    eng.close()
+
+
+def test_estimate_matches_oracle(binding):
+    g, x, eps, delta = synth.workload("er1000")
+    og = oracle.from_synth(g)
+    eng = _engine(binding, g, x)
+    pc, info = eng.estimate(eps, delta, seed=5)
+    res = oracle.percis(og, x, eps, delta, 5, keep_paths=False)
+    assert info["ell1"] == res.ell1
+    assert info["vertex_diam"] == res.D
+    assert info["rho_tilde"] == res.rho_tilde and info["Lambda"] == res.Lam
+    assert abs(info["ell"] - res.ell) <= 1
+    if info["ell"] != res.ell:
+        res = oracle.percis(og, x, eps, delta, 5, ell=info["ell"], keep_paths=False)
+    assert np.max(np.abs(_np(pc) - res.pc)) <= 1e-9
+    assert info["rho_hat"] == pytest.approx(res.rho_hat, rel=1e-12)
+    assert info["v_hat"] == pytest.approx(res.v_hat, rel=1e-12)
+    # same seed, other form, other lane width: identical estimate
+    eng2 = _engine(binding, g, x, form="plain")
+    pc2, info2 = eng2.estimate(eps, delta, seed=5)
+    assert np.array_equal(_np(pc2), _np(pc))
+    eng3 = _engine(binding, g, x, lanes=64)
+    pc3, _ = eng3.estimate(eps, delta, seed=5)
+    assert np.array_equal(_np(pc3), _np(pc))
+    for e in (eng, eng2, eng3):
+        e.close()
+
+
+def test_backward_matches_oracle_and_fd(binding):
+    g = synth.barabasi_albert(2000, 4, 0)
+    og = oracle.from_synth(g)
+    x = synth.states_uniform(g.n, 0)
+    ell = 4000
+    eng = _engine(binding, g, x, ell1=1000, ell=ell)
+    pc, info = eng.estimate(0.01, 0.1, seed=9)
+    prep = oracle.prepare(x, cv_method="sorted")
+    ph = oracle.run_samples(og, prep, 9, 1, 3, 0, ell, keep_paths=True)
+    F = prep.lam * ph.cnt / ell
+    assert np.max(np.abs(_np(pc) - F)) <= 1e-12
+    gvec = np.random.default_rng(2).standard_normal(g.n)
+    gx = _np(eng.backward(torch.as_tensor(gvec, device="cuda")))
+    ref = oracle.vjp_fixed(prep, ell, ph, F, gvec)
+    assert np.linalg.norm(gx - ref) / np.linalg.norm(ref) <= 1e-10
+    h = 1e-6
+    checked = 0
+    for u in np.random.default_rng(3).permutation(g.n)[:200]:
+        if np.any(np.abs(np.delete(x, u) - x[u]) < 4 * h):
+            continue
+        touch = (ph.kind == 0) & ((ph.s == u) | (ph.t == u))
+        if np.any(np.abs(x[ph.s[touch]] - x[ph.t[touch]]) <= 1e-3):
+            continue
+        fd = oracle.fd_fixed(prep, ell, ph, gvec, int(u), h)
+        assert gx[u] == pytest.approx(fd, rel=1e-6, abs=1e-12 * np.abs(gx).max())
+        checked += 1
+        if checked >= 25:
+            break
+    assert checked >= 10
+    eng.close()
+
+
+def test_autograd_function(binding):
+    g = synth.barabasi_albert(500, 3, 4)
+    x = torch.as_tensor(synth.states_uniform(g.n, 4), device="cuda").requires_grad_(True)
+    eng = _engine(binding, g, None, ell1=500, ell=1500)
+    pc = binding.percolation_centrality(x, eng, 0.05, 0.1, seed=1)
+    w = torch.randn(g.n, device="cuda", dtype=torch.float64)
+    (pc * w).sum().backward()
+    og = oracle.from_synth(g)
+    prep = oracle.prepare(x.detach().cpu().numpy(), cv_method="sorted")
+    ph = oracle.run_samples(og, prep, 1, 1, 3, 0, 1500, keep_paths=True)
+    ref = oracle.vjp_fixed(prep, 1500, ph, prep.lam * ph.cnt / 1500, w.cpu().numpy())
+    assert np.linalg.norm(_np(x.grad) - ref) / np.linalg.norm(ref) <= 1e-10
+    eng.close()
+
+
+@pytest.mark.parametrize("name", ["er1000", "rmat12", "grid30"])
+def test_exact_small_matches_oracle(binding, name):
+    g = GRAPHS[name]() if name != "er1000" else synth.erdos_renyi(1000, 8.0, 0)
+    og = oracle.from_synth(g)
+    x = _states(name, g.n)
+    eng = _engine(binding, g, x)
+    pc = _np(eng.exact())
+    ref = oracle.exact_pc(og, x, oracle.prepare(x).Cv)
+    assert np.max(np.abs(pc - ref)) <= 1e-9
+    eng.close()
+
+
+def test_epsilon_guarantee_gpu(binding):
+    g, x, eps, delta = synth.workload("er1000")
+    og = oracle.from_synth(g)
+    exact = oracle.exact_pc(og, x, oracle.prepare(x).Cv)
+    eng = _engine(binding, g, x)
+    ok = 0
+    for seed in range(20):
+        pc, _ = eng.estimate(eps, delta, seed=seed)
+        ok += int(np.max(np.abs(_np(pc) - exact)) <= eps)
+    assert ok >= 18
+    eng.close()
+
+
+def test_full_size_outbreak_sampled(binding):
+    """Barabasi-Albert n=100,000 (m=5), 10% outbreak states, eps=0.005: the
+    launch configuration the benchmark times.  Pairs, |I| and paths are
+    checked on sampled indices against the oracle; counts and estimates via
+    properties that hold at any size."""
+    g, x, eps, delta = synth.workload("ba100k_outbreak")
+    og = oracle.from_synth(g)
+    eng = _engine(binding, g, x)
+    pc, info = eng.estimate(eps, delta, seed=0)
+    ell = info["ell"]
+    assert info["ell1"] == 1000 and ell > 10000
+    prep = oracle.prepare(x)
+    s, t = eng.sample_pairs(0, 1, 0, ell)
+    rs, rt, _, _ = oracle.sample_pairs(prep, 0, 1, 0, ell)
+    assert np.array_equal(_np(s), rs) and np.array_equal(_np(t), rt)
+    ptr, nodes = eng.get_paths(ell)
+    ptr, nodes = _np(ptr), _np(nodes)
+    cnt = np.bincount(nodes, minlength=g.n)
+    assert np.max(np.abs(_np(pc) - prep.lam * cnt / ell)) <= 1e-12
+    for i in np.random.default_rng(0).choice(ell, 25, replace=False):
+        ph = oracle.run_samples(og, prep, 0, 1, 3, int(i), 1, keep_paths=True)
+        assert np.array_equal(nodes[ptr[i]:ptr[i + 1]], ph.path_nodes), i
+    eng.close()
+
+
+def test_edge_cases(binding):
+    # directed graph with unreachable targets, n = 2, binary states with ties
+    gd = synth.csr_from_edges(6, np.array([0, 1, 2, 4]), np.array([1, 2, 3, 5]), directed=True)
+    x = np.array([1.0, 0.9, 0.8, 0.0, 0.7, 0.1])
+    ogd = oracle.from_synth(gd)
+    eng = _engine(binding, gd, x, ell1=50, ell=400)
+    got = eng.run_phase(seed=3, phase=1, count=400)
+    ph = oracle.run_samples(ogd, oracle.prepare(x), 3, 1, 3, 0, 400, keep_paths=True)
+    assert np.array_equal(_np(got["kind"]), ph.kind) and (ph.kind == 2).any()
+    assert np.array_equal(_np(got["cnt"]), ph.cnt)
+    eng.close()
+    g2 = synth.path_graph(2)
+    eng = _engine(binding, g2, np.array([1.0, 0.0]), ell1=10, ell=10)
+    pc, info = eng.estimate(0.1, 0.1, seed=0)
+    assert np.all(_np(pc) == 0.0) and info["sum_internal"][1] == 0
+    eng.close()
+
+
+def test_errors_are_reported(binding):
+    g = synth.path_graph(5)
+    eng = _engine(binding, g)
+    with pytest.raises(binding.PercisError) as e:
+        eng.set_states(np.array([0.5, 0.5, 0.5, 0.5, 0.5]))
+    assert e.value.status == 2  # DEGENERATE
+    with pytest.raises(binding.PercisError) as e:
+        eng.set_states(np.array([0.5, 1.5, 0.5, 0.5, 0.5]))
+    assert e.value.status == 1
+    with pytest.raises(binding.PercisError) as e:
+        eng.set_states(np.array([0.5, np.nan, 0.5, 0.5, 0.5]))
+    assert e.value.status == 1
+    eng.set_states(np.array([0.9, 0.5, 0.1, 0.3, 0.7]))
+    with pytest.raises(binding.PercisError) as e:
+        eng.backward(torch.zeros(5, dtype=torch.float64, device="cuda"))
+    assert e.value.status == 7
+    bad = binding.PercIS(0)
+    with pytest.raises(binding.PercisError) as e:
+        bad.load_csr(np.array([0, 2, 1, 3], dtype=np.int64), np.array([1, 2, 0], dtype=np.int32))
+    assert e.value.status == 1
+    with pytest.raises(binding.PercisError) as e:
+        bad.load_csr(np.array([0, 1, 2], dtype=np.int64), np.array([1, 7], dtype=np.int32))
+    assert e.value.status == 1
+    bad.close()
+    eng.close()
+
+
+def test_device_wait_budget_reports_timeout(binding):
+    """A budget too small for any grid barrier makes every bounded wait give
+    up; the call returns TIMEOUT and the context stays usable."""
+    g = synth.barabasi_albert(2000, 3, 5)
+    x = synth.states_uniform(g.n, 5)
+    eng = _engine(binding, g, x, ell1=100, ell=200)
+    eng.set_options(timeout_s=1e-9)
+    with pytest.raises(binding.PercisError) as e:
+        eng.estimate(0.05, 0.1, seed=0)
+    assert e.value.status == 5
+    eng.set_options(timeout_s=10.0)
+    pc, info = eng.estimate(0.05, 0.1, seed=0)
+    og = oracle.from_synth(g)
+    ph = oracle.run_samples(og, oracle.prepare(x), 0, 1, 3, 0, 200, keep_paths=False)
+    assert np.array_equal(np.round(_np(pc) * 200 / oracle.prepare(x).lam).astype(np.int64), ph.cnt)
+    eng.close()
