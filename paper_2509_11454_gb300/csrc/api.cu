@@ -522,6 +522,15 @@ percis_status percis_msbfs(percis_ctx *ctx, int32_t nsrc, const int32_t *sources
     PERCIS_TRY(need_graph(ctx));
     if (nsrc < 1 || nsrc > 512 || !sources) return set_err(ctx, PERCIS_E_INVALID, "need 1..512 sources");
     DeviceGuard g(ctx->device);
+    {
+        int32_t hsrc[512];
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(hsrc, sources, sizeof(int32_t) * nsrc, cudaMemcpyDeviceToHost, ctx->stream));
+        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        std::sort(hsrc, hsrc + nsrc);
+        for (int i = 0; i < nsrc; ++i)
+            if (hsrc[i] < 0 || hsrc[i] >= ctx->n || (i > 0 && hsrc[i] == hsrc[i - 1]))
+                return set_err(ctx, PERCIS_E_INVALID, "sources must be distinct vertex ids");
+    }
     clear_status(ctx);
     PERCIS_TRY(msbfs_full(ctx, nsrc, sources, dist, sigma));
     PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

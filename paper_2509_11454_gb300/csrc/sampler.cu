@@ -39,7 +39,9 @@ __global__ void k_sample_pairs(int64_t n, const double *__restrict__ xs, const i
             else a = d + 1;
             d = (a + b) >> 1;
         }
-        const int64_t t = b + 1;
+        // t <= n whenever c_s > 0, which holds for every s the first search can
+        // return; the clamp only keeps the index in bounds.
+        const int64_t t = b + 1 <= n ? b + 1 : n;
         const int32_t sn = perm[s - 1], tn = perm[t - 1];
         if (s_out) s_out[k] = sn;
         if (t_out) t_out[k] = tn;
