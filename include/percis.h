@@ -157,7 +157,8 @@ percis_status percis_backward(percis_ctx *ctx, const double *grad_pc, double *gr
 /* Sorted states and Algorithm 2 tables.  Any output may be NULL.  Device
  * outputs: perm int32[n] (sorted position i-1 -> node id), xs double[n],
  * w/ci/r double[n+2] (1-based, index n+1 = 0), Cv/lambda double[n] (node
- * order).  Host outputs: c, dhat (double), vertex_diam (int64). */
+ * order).  Host outputs: c, dhat (double; 0 before states are set),
+ * vertex_diam (int64).  Device outputs need states (else STATE). */
 percis_status percis_get_prep(percis_ctx *ctx, int32_t *perm, double *xs, double *w, double *ci, double *r, double *Cv,
                               double *lambda, double *c, double *dhat, int64_t *vertex_diam);
 

@@ -472,8 +472,9 @@ percis_status percis_get_prep(percis_ctx *ctx, int32_t *perm, double *xs, double
     DeviceGuard g(ctx->device);
     if (vertex_diam) *vertex_diam = ctx->vertex_diam;
     if (!ctx->have_states) {
-        if (perm || xs || w || ci || r || Cv || lambda || c || dhat)
-            return set_err(ctx, PERCIS_E_STATE, "no states set");
+        if (perm || xs || w || ci || r || Cv || lambda) return set_err(ctx, PERCIS_E_STATE, "no states set");
+        if (c) *c = 0.0;
+        if (dhat) *dhat = 0.0;
         return PERCIS_OK;
     }
     const int64_t n = ctx->n;

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_bfs(PlainArgs a) {
         ctl->qsize[0] = 1;
         ctl->qsize[1] = 0;
         ctl->level = 0;
+        ctl->found = 0;
     }
     if (!grid_sync(bar, status, a.budget_ns)) return;
     const int lane = threadIdx.x & 31;
@@ -103,13 +104,18 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_bfs(PlainArgs a) {
             if (lane == 0) {
                 a.sigma[wv] = acc;
                 if (acc >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
+                if (wv == t) atomicExch(&ctl->found, 1);
             }
         }
         if (!grid_sync(bar, status, a.budget_ns)) return;
         ++L;
         if (nn > 0) ecc = L;
         if (nn == 0) break;
-        if (t >= 0 && __ldcg(&a.ep[t]) == a.epoch) break;
+        // Exit tests read only values that stay fixed until every block has
+        // passed the next barrier: qsize of this level and the sticky found
+        // flag (ep[t] itself may be claimed by a faster block in the next
+        // level's expansion, which would split the grid).
+        if (t >= 0 && ld_relaxed_u32((const uint32_t *)&ctl->found)) break;
         int32_t *tmp = cur;
         cur = nxt;
         nxt = tmp;
