@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput of the PercIS estimator on GB300 (one JSON line on stdout).
+
+A step is one complete estimate through the library's C ABI -- load the
+CSR (validation, VertexDiamUB), set the states (sort, Algorithm 2 tables,
+C_v, lambda), phase 1 (l1 samples), the Theorem 1 bound, phase 2 (l samples)
+and the final estimate -- on Barabasi-Albert n=100,000, m=5 with a seeded
+10% outbreak (x = 0 for 90% of the vertices, U[0.5, 1] for the rest),
+eps = 0.005, delta = 0.1.  The metric is sampled pairs per second
+(l1 + l per step over the device time of the step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank an independent
+estimate (its own seeds; weak scaling, no collective on the data path).
+--impl reference times the CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "ba100k_outbreak"
+WORKLOAD_DESC = {
+    "workload": "ba100k_m5_outbreak10",
+    "graph": "Barabasi-Albert n=100000, m=5, undirected, int64 row offsets / int32 columns",
+    "states": "x=0 on 90% of vertices, U[0.5,1] on a seeded random 10%",
+    "eps": 0.005,
+    "delta": 0.1,
+}
+# DRAM traffic of one batched sigma-BFS launch from an ncu capture, valid only
+# for the kernel source it was taken on (sha256 of csrc/msbfs.cu).
+NCU_TRAFFIC = {"msbfs_sha256": None, "bytes_per_launch": None}
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def _sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(budget_s: float = 12.0) -> dict:
+    """The CPU oracle as it stands (sampler + RandomSP + estimator, one thread)
+    on a bounded sample of phase-2 pairs of the same workload."""
+    import oracle
+    from paper_2509_11454_gb300 import synth
+
+    g, x, eps, delta = synth.workload(WORKLOAD, 0)
+    og = oracle.from_synth(g)
+    prep = oracle.prepare(x)
+    count, done, t_used = 0, 0, 0.0
+    chunk = 200
+    while t_used < budget_s:
+        t0 = time.perf_counter()
+        oracle.run_samples(og, prep, 0, 1, 3, done, chunk, keep_paths=False)
+        t_used += time.perf_counter() - t0
+        done += chunk
+    return {"value": done / t_used, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} phase-2 pairs of the same workload (Algorithm 2 sampler, sigma-BFS RandomSP, "
+                      f"estimator), {t_used:.1f} s on one host thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2509_11454_gb300 import synth
+
+    g, x, eps, delta = synth.workload(WORKLOAD, 0)
+    og = oracle.from_synth(g)
+    prep = oracle.prepare(x)
+    per_step = args.ref_pairs
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.run_samples(og, prep, 1000 + k, 1, 3, 0, per_step, keep_paths=False)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = per_step * len(times) / tot
+    line = {"impl": "reference", "metric": "sampled pairs/s", "value": value, "unit": "pairs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD_DESC),
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} phase-2 pairs per step on one host thread"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-pairs", type=int, default=300)
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/differentiated/e2e/cpu legs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2509_11454_gb300 import binding, synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    binding.load_library()
+
+    g, x, eps, delta = synth.workload(WORKLOAD, 0)
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
+    eng = binding.PercIS(local)
+    rp_d = torch.as_tensor(g.row_ptr, dtype=torch.int64, device="cuda")
+    col_d = torch.as_tensor(g.col, dtype=torch.int32, device="cuda")
+    x_d = torch.as_tensor(x, dtype=torch.float64, device="cuda")
+    pc_d = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    seed_base = 1_000_003 * rank
+
+    def step(seed):
+        binding.percis_load_csr(eng.ctx, g.n, g.nnz, rp_d, col_d, False, 1)
+        binding.percis_set_states(eng.ctx, x_d, 1)
+        return binding.percis_estimate(eng.ctx, eps, delta, seed, pc_d, 1)
+
+    for k in range(args.warmup):
+        step(seed_base + 10_000 + k)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    infos, times = [], []
+    launches0 = binding.percis_launch_count(eng.ctx)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()  # a write larger than L2 between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(step(seed_base + k))
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = binding.percis_launch_count(eng.ctx) - launches0
+    t_total = sum(times) / 1000.0
+    pairs = sum(i["ell1"] + i["ell"] for i in infos)
+    if dist:
+        tt = torch.tensor([t_total, float(pairs)], dtype=torch.float64, device="cuda")
+        tmax = tt.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_job, pairs_job = float(tmax[0]), float(tt[1])
+    else:
+        t_job, pairs_job = t_total, float(pairs)
+    value = pairs_job / t_job
+
+    extras = {}
+    if rank == 0:
+        peaks, peak_kind = _peaks()
+        # algorithmic work of the same estimates, counted in an untimed instrumented replay
+        eng.set_options(instrument=1)
+        work = np.zeros((2, 8))
+        for k in range(args.steps):
+            inf = step(seed_base + k)
+            work += np.array(inf["work"], dtype=np.float64)
+        eng.set_options(instrument=0)
+        bfs_ms = sum(sum(i["bfs_ms"]) for i in infos)
+        bfs_launches = sum(sum(i["bfs_launches"]) for i in infos)
+        w = work.sum(axis=0)
+        algo_bytes = 8.0 * w[0] + 8.0 * w[1] + 8.0 * w[2] + 4.0 * w[3]
+        per_launch_bytes = algo_bytes / max(bfs_launches, 1)
+        per_launch_s = bfs_ms / 1000.0 / max(bfs_launches, 1)
+        achieved = per_launch_bytes / per_launch_s / 1e9
+        traffic = None
+        msbfs_src = os.path.join(ROOT, "paper_2509_11454_gb300", "csrc", "msbfs.cu")
+        if NCU_TRAFFIC["msbfs_sha256"] == _sha(msbfs_src):
+            traffic = NCU_TRAFFIC["bytes_per_launch"]
+        extras["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                              "kernel": "k_msbfs (batched sigma-BFS + backtrack, one launch per lane batch)",
+                              "peak_source": f"{peak_kind} HBM copy bandwidth",
+                              "algorithmic_bytes_per_launch": per_launch_bytes,
+                              "avg_launch_ms": per_launch_s * 1000.0, "launches_per_step": bfs_launches / len(infos)}
+        extras["gteps"] = w[4] / t_total / 1e9 if w[4] else None
+        extras["work_per_step"] = {"sigma_dag_reads": w[0] / len(infos), "sigma_writes": w[1] / len(infos),
+                                   "union_frontier_rows": w[2] / len(infos),
+                                   "union_frontier_edges": w[3] / len(infos),
+                                   "truncated_bfs_edges": w[4] / len(infos), "bfs_samples": w[6] / len(infos)}
+        extras["bfs_share_of_step"] = bfs_ms / sum(times)
+
+        if not args.no_extras:
+            # plain form: one BFS launch + one backtrack launch per sampled pair, same seed
+            eng.set_options(form="plain")
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            e0.record(stream)
+            inf_p = step(seed_base)
+            e1.record(stream)
+            e1.synchronize()
+            t_p = e0.elapsed_time(e1) / 1000.0
+            eng.set_options(form="batched")
+            extras["plain"] = {"value": (inf_p["ell1"] + inf_p["ell"]) / t_p, "unit": "pairs/s",
+                               "ms_per_step": t_p * 1000.0, "steps": 1}
+            extras["batched_over_plain"] = value / world / extras["plain"]["value"]
+
+            # differentiated form: forward + backward (dPC/dx) per step
+            gvec = torch.randn(g.n, dtype=torch.float64, device="cuda")
+            gx = torch.empty(g.n, dtype=torch.float64, device="cuda")
+            tds = []
+            ninfo = []
+            for k in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                inf = step(seed_base + k)
+                binding.percis_backward(eng.ctx, gvec, gx, 1)
+                e1.record(stream)
+                e1.synchronize()
+                tds.append(e0.elapsed_time(e1) / 1000.0)
+                ninfo.append(inf)
+            extras["differentiated"] = {"value": sum(i["ell1"] + i["ell"] for i in ninfo) / sum(tds),
+                                        "unit": "pairs/s", "ms_per_step": 1000.0 * sum(tds) / len(tds)}
+
+            # end to end through the public API with host buffers (pinned), copies inside the timed region
+            rp_h = torch.as_tensor(g.row_ptr, dtype=torch.int64).pin_memory()
+            col_h = torch.as_tensor(g.col, dtype=torch.int32).pin_memory()
+            x_h = torch.as_tensor(x, dtype=torch.float64).pin_memory()
+            pc_h = torch.empty(g.n, dtype=torch.float64).pin_memory()
+            te, pe = [], 0
+            for k in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                binding.percis_load_csr(eng.ctx, g.n, g.nnz, rp_h, col_h, False, 0)
+                binding.percis_set_states(eng.ctx, x_h, 0)
+                inf = binding.percis_estimate(eng.ctx, eps, delta, seed_base + k, pc_h, 0)
+                te.append(time.perf_counter() - t0)
+                pe += inf["ell1"] + inf["ell"]
+            h2d = rp_h.numel() * 8 + col_h.numel() * 4 + x_h.numel() * 8
+            extras["e2e"] = {"value": pe / sum(te), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                             "d2h_bytes_per_step": pc_h.numel() * 8}
+            if world == 1:
+                extras["cpu_baseline"] = cpu_baseline()
+
+    if rank == 0:
+        i0 = infos[0]
+        cfg = dict(WORKLOAD_DESC)
+        cfg.update({"n": g.n, "nnz": g.nnz, "form": "batched", "lanes": i0["lanes"], "ell1": i0["ell1"],
+                    "ell_mean": statistics.mean(i["ell"] for i in infos),
+                    "distinct_sources_phase2_mean": statistics.mean(i["sources"][1] for i in infos),
+                    "vertex_diam": i0["vertex_diam"], "dhat": i0["dhat"],
+                    "l2": "256 MiB buffer written before every timed step", "parallelism": f"replicas x{world}"})
+        line = {"metric": "sampled pairs/s", "value": value, "unit": "pairs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_job / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg, "gpu_launches": launches, "clocks": clk}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    eng.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,9 @@ typedef struct {
     int32_t keep_paths;       /* 1 (default): keep phase-2 paths for percis_backward */
     int32_t data_independent; /* 1: PercIS-DI (rho^ = D, v^ = d^2/4, no phase 1; Section IV-B) */
     double timeout_s;         /* budget of every device-side wait (default 10 s) */
+    int32_t instrument;       /* 1: batched launches also count their work into percis_info.work
+                                 (slower; for measurement runs only) */
+    int32_t reserved;
 } percis_options;
 
 typedef struct {
@@ -83,6 +86,20 @@ typedef struct {
     int32_t sigma_overflow;       /* 1 if some sigma reached 2^53 (paths no longer exact) */
     int32_t lanes;                /* lane width used */
     int64_t kernel_launches;      /* kernels this call launched */
+    double bfs_ms[2];             /* summed device time of the sigma-BFS launches, per phase
+                                     (CUDA events on the context stream) */
+    int64_t bfs_launches[2];      /* number of those launches, per phase */
+    /* Work counters, filled when options.instrument = 1 (batched form), per phase:
+     * work[p][0] sigma reads over shortest-path DAG edges (lane-edge pairs)
+     * work[p][1] sigma writes (lane-vertex discoveries)
+     * work[p][2] union-frontier vertices summed over levels (adjacency rows needed)
+     * work[p][3] out-degree sum of those vertices (adjacency entries needed)
+     * work[p][4] sum over samples of the edges a top-down BFS from s scans to
+     *            settle t (whole reachable set when t is unreachable)
+     * work[p][5] levels run, summed over launches
+     * work[p][6] sampled pairs that reached a BFS (R(x_s - x_t) > 0)
+     * work[p][7] reserved */
+    int64_t work[2][8];
 } percis_info;
 
 /* ------------------------------------------------------------ lifecycle */
@@ -96,6 +113,9 @@ void percis_destroy(percis_ctx *ctx);
 percis_status percis_set_stream(percis_ctx *ctx, void *stream);
 /* Last error message of this context ("" when none).  Owned by the context. */
 const char *percis_last_error(const percis_ctx *ctx);
+/* Number of kernels this context has launched since it was created
+ * (measurement aid; -1 for a NULL context). */
+int64_t percis_launch_count(const percis_ctx *ctx);
 /* Fill `opt` with the defaults listed in percis_options. */
 void percis_default_options(percis_options *opt);
 percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt);

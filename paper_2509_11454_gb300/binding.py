@@ -36,7 +36,8 @@ class PercisError(RuntimeError):
 class percis_options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("lanes", ctypes.c_int32), ("ell1", ctypes.c_int64),
                 ("ell", ctypes.c_int64), ("vertex_diam", ctypes.c_int64), ("keep_paths", ctypes.c_int32),
-                ("data_independent", ctypes.c_int32), ("timeout_s", ctypes.c_double)]
+                ("data_independent", ctypes.c_int32), ("timeout_s", ctypes.c_double),
+                ("instrument", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class percis_info(ctypes.Structure):
@@ -47,14 +48,15 @@ class percis_info(ctypes.Structure):
                 ("zero_weight", ctypes.c_int64 * 2), ("unreachable", ctypes.c_int64 * 2),
                 ("sum_internal", ctypes.c_int64 * 2), ("sources", ctypes.c_int64 * 2),
                 ("batches", ctypes.c_int64 * 2), ("sigma_overflow", ctypes.c_int32), ("lanes", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("bfs_ms", ctypes.c_double * 2),
+                ("bfs_launches", ctypes.c_int64 * 2), ("work", (ctypes.c_int64 * 8) * 2)]
 
     def as_dict(self) -> dict:
-        out = {}
-        for name, _ in self._fields_:
-            v = getattr(self, name)
-            out[name] = list(v) if isinstance(v, ctypes.Array) else v
-        return out
+        def conv(v):
+            if isinstance(v, ctypes.Array):
+                return [conv(e) for e in v]
+            return v
+        return {name: conv(getattr(self, name)) for name, _ in self._fields_}
 
 
 _P = ctypes.c_void_p
@@ -71,6 +73,7 @@ SIGNATURES = {
     "percis_destroy": (None, [_P]),
     "percis_set_stream": (_ST, [_P, _P]),
     "percis_last_error": (ctypes.c_char_p, [_P]),
+    "percis_launch_count": (_I64, [_P]),
     "percis_default_options": (None, [ctypes.POINTER(percis_options)]),
     "percis_set_options": (_ST, [_P, ctypes.POINTER(percis_options)]),
     "percis_load_csr": (_ST, [_P, _I64, _I64, _P, _P, ctypes.c_int, ctypes.c_int]),
@@ -146,6 +149,10 @@ def percis_set_stream(ctx, stream: int):
 def percis_last_error(ctx) -> str:
     m = load_library().percis_last_error(ctx)
     return m.decode() if m else ""
+
+
+def percis_launch_count(ctx) -> int:
+    return int(load_library().percis_launch_count(ctx))
 
 
 def percis_default_options() -> percis_options:

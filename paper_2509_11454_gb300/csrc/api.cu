@@ -48,6 +48,28 @@ percis_status ensure(percis_ctx *ctx, DevBuf &b, size_t bytes, const char *what)
     return PERCIS_OK;
 }
 
+cudaEvent_t next_event(percis_ctx *ctx) {
+    if (ctx->ev_next >= ctx->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ctx->ev_pool.push_back(e);
+    }
+    return ctx->ev_pool[ctx->ev_next++];
+}
+
+double events_elapsed_ms(percis_ctx *ctx) {
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < ctx->ev_next; k += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_pool[k], ctx->ev_pool[k + 1]) == cudaSuccess) tot += ms;
+        else cudaGetLastError();
+    }
+    return tot;
+}
+
 namespace {
 
 struct DeviceGuard {
@@ -155,10 +177,19 @@ void clear_status(percis_ctx *ctx) {
     if (ctx->plain_ctl.p) cudaMemsetAsync(ctx->plain_ctl.p, 0, sizeof(PlainCtl), ctx->stream);
 }
 
+struct PhaseOut {
+    int64_t sources = 0, batches = 0;
+    int32_t overflow = 0;
+    double bfs_ms = 0.0;
+    int64_t bfs_launches = 0;
+    int64_t work[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
 // One sampling phase (pair tag = phase, path tag = 2 + phase) of `count`
 // samples.  Leaves pairs, kinds, |I|, paths and cnt in the context.
-percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count, int64_t *sources,
-                        int64_t *batches, int32_t *overflow) {
+percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count, PhaseOut *po) {
+    int64_t *sources = &po->sources, *batches = &po->batches;
+    int32_t *overflow = &po->overflow;
     const int64_t n = ctx->n;
     const int64_t cap_count = std::max<int64_t>(count, 1);
     PERCIS_TRY(ensure(ctx, ctx->pair_s, sizeof(int32_t) * cap_count, "pairs"));
@@ -174,8 +205,12 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
         ctx->arena_cap = cap;
     }
     ctx->have_paths = false;
+    if (ctx->opt.instrument) PERCIS_TRY(ensure(ctx, ctx->counters, sizeof(unsigned long long) * 8, "counters"));
     for (int attempt = 0; attempt < 24; ++attempt) {
         clear_status(ctx);
+        ctx->ev_next = 0;
+        if (ctx->opt.instrument)
+            PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long) * 8, ctx->stream));
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->cnt.p, 0, sizeof(unsigned long long) * n, ctx->stream));
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->arena_top.p, 0, 64, ctx->stream));
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ilen.p, 0, sizeof(int32_t) * cap_count, ctx->stream));
@@ -185,7 +220,10 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
         *sources = 0;
         *batches = 0;
         if (ctx->opt.form == PERCIS_FORM_PLAIN) {
+            cudaEvent_t e0 = next_event(ctx), e1 = next_event(ctx);
+            if (e0) cudaEventRecord(e0, ctx->stream);
             PERCIS_TRY(plain_phase(ctx, seed, (uint32_t)(2 + phase), count));
+            if (e1) cudaEventRecord(e1, ctx->stream);
             *batches = count;
         } else {
             int64_t U = 0, valid = 0;
@@ -211,6 +249,13 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
         if ((st & DEV_BAD_PATH) && !(st & DEV_SIGMA_OVERFLOW))
             return set_err(ctx, PERCIS_E_CUDA, "backtrack found no predecessor");
         *overflow = (st & DEV_SIGMA_OVERFLOW) ? 1 : 0;
+        po->bfs_ms = events_elapsed_ms(ctx);
+        po->bfs_launches = *batches;
+        if (ctx->opt.instrument && ctx->opt.form != PERCIS_FORM_PLAIN) {
+            unsigned long long hc[8];
+            PERCIS_CUDA(ctx, cudaMemcpy(hc, ctx->counters.p, sizeof(hc), cudaMemcpyDeviceToHost));
+            for (int k = 0; k < 8; ++k) po->work[k] = (int64_t)hc[k];
+        }
         ctx->phase_count = count;
         ctx->last_phase = phase;
         ctx->last_seed = seed;
@@ -250,6 +295,7 @@ void percis_default_options(percis_options *opt) {
     opt->keep_paths = 1;
     opt->data_independent = 0;
     opt->timeout_s = 10.0;
+    opt->instrument = 0;
 }
 
 percis_status percis_create(percis_ctx **out, int device, void *stream) {
@@ -295,6 +341,9 @@ void percis_destroy(percis_ctx *ctx) {
                       &ctx->pc_tmp, &ctx->grad_tmp, &ctx->host_pinned};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
+    if (ctx->counters.p) cudaFree(ctx->counters.p);
+    if (ctx->levdeg.p) cudaFree(ctx->levdeg.p);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -310,6 +359,8 @@ percis_status percis_set_stream(percis_ctx *ctx, void *stream) {
 }
 
 const char *percis_last_error(const percis_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t percis_launch_count(const percis_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
 percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt) {
     if (!ctx || !opt) return PERCIS_E_INVALID;
@@ -377,11 +428,19 @@ percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_
     const bool di = ctx->opt.data_independent != 0;
     const int64_t ell1 = di ? 0 : (ctx->opt.ell1 > 0 ? ctx->opt.ell1 : ell1_default(eps, delta));
     inf.ell1 = ell1;
-    int32_t ovf = 0;
     PhaseStats hs{};
+    auto record = [&](int ph, const PhaseOut &po) {
+        inf.sources[ph] = po.sources;
+        inf.batches[ph] = po.batches;
+        inf.sigma_overflow |= po.overflow;
+        inf.bfs_ms[ph] = po.bfs_ms;
+        inf.bfs_launches[ph] = po.bfs_launches;
+        for (int k = 0; k < 8; ++k) inf.work[ph][k] = po.work[k];
+    };
     if (!di) {
-        PERCIS_TRY(run_phase(ctx, seed, 0, ell1, &inf.sources[0], &inf.batches[0], &ovf));
-        inf.sigma_overflow |= ovf;
+        PhaseOut po;
+        PERCIS_TRY(run_phase(ctx, seed, 0, ell1, &po));
+        record(0, po);
         PERCIS_TRY(phase_stats(ctx, ell1, (double)ell1, &hs));
         inf.zero_weight[0] = hs.zero_w;
         inf.unreachable[0] = hs.unreach;
@@ -398,8 +457,11 @@ percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_
     inf.p1_max = p1_max;
     const int64_t ell = ctx->opt.ell > 0 ? ctx->opt.ell : b.ell;
     inf.ell = ell;
-    PERCIS_TRY(run_phase(ctx, seed, 1, ell, &inf.sources[1], &inf.batches[1], &ovf));
-    inf.sigma_overflow |= ovf;
+    {
+        PhaseOut po;
+        PERCIS_TRY(run_phase(ctx, seed, 1, ell, &po));
+        record(1, po);
+    }
     ctx->last_ell = ell;
     double *dst = pc_out;
     if (!pc_on_device) {
@@ -545,9 +607,8 @@ percis_status percis_run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_
     PERCIS_TRY(need_states(ctx));
     if ((phase != 0 && phase != 1) || count < 1) return set_err(ctx, PERCIS_E_INVALID, "phase 0/1, count >= 1");
     DeviceGuard g(ctx->device);
-    int64_t src = 0, bat = 0;
-    int32_t ovf = 0;
-    PERCIS_TRY(run_phase(ctx, seed, phase, count, &src, &bat, &ovf));
+    PhaseOut po;
+    PERCIS_TRY(run_phase(ctx, seed, phase, count, &po));
     ctx->last_ell = count;
     auto cp = [&](void *dst, const DevBuf &b, size_t bytes) -> percis_status {
         if (!dst) return PERCIS_OK;

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/percis.h"
 
@@ -85,6 +86,11 @@ struct percis_ctx {
     uint64_t last_seed = 0;
     int64_t last_ell = 0;
 
+    // measurement: event pairs around each sigma-BFS launch of a phase; work counters
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_next = 0;
+    percis::DevBuf counters, levdeg;
+
     // scratch for reductions/scans
     percis::DevBuf scratch, red, status;
     percis::DevBuf pc_tmp, grad_tmp, host_pinned;
@@ -115,6 +121,11 @@ percis_status ensure(percis_ctx *ctx, DevBuf &b, size_t bytes, const char *what)
         percis_status s__ = (call);            \
         if (s__ != PERCIS_OK) return s__;      \
     } while (0)
+
+// Next event of the context's pool (created on demand; nullptr if creation fails).
+cudaEvent_t next_event(percis_ctx *ctx);
+// Summed elapsed time of the event pairs recorded since ev_next was reset (stream synchronised).
+double events_elapsed_ms(percis_ctx *ctx);
 
 // util.cu: scans and simple fills
 percis_status scan_exclusive_i64(percis_ctx *ctx, const int64_t *in, int64_t *out, int64_t n);

@@ -56,6 +56,10 @@ struct MsArgs {
     unsigned long long *cnt;
     int32_t full;
     uint64_t budget_ns;
+    // instrumentation (INSTR variant only)
+    const int64_t *rp;                // out-CSR offsets (out-degrees)
+    unsigned long long *counters;     // 8 work counters (see percis_info.work)
+    unsigned long long *levdeg;       // [W][Lcap+1] out-degree sums per lane and level
 };
 
 template <int K>
@@ -72,9 +76,10 @@ __device__ __forceinline__ void load_words(const uint64_t *p, uint64_t (&out)[K]
     }
 }
 
-template <int K>
+template <int K, bool INSTR>
 __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
     constexpr int W = 64 * K;
+    unsigned long long n_sload = 0, n_swrite = 0, n_uv = 0, n_ue = 0;
     MsCtl *ctl = a.ctl;
     GridBarrier *bar = reinterpret_cast<GridBarrier *>(ctl);
     uint32_t *status = &ctl->status;
@@ -94,6 +99,8 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
         a.fh[i] = 0ull;
     }
     for (long long p = p0 + tid; p < p1; p += nthreads) a.found[p] = -1;
+    if (INSTR)
+        for (int64_t i = tid; i < (int64_t)W * (a.Lcap + 1); i += nthreads) a.levdeg[i] = 0ull;
     if (blockIdx.x == 0) {
         for (int j = threadIdx.x; j < W; j += blockDim.x) a.remaining[j] = 0;
         if (threadIdx.x < K) {
@@ -115,6 +122,7 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
         atomicOr((unsigned long long *)&a.vis[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         atomicOr((unsigned long long *)&a.fh[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         a.sigma[(int64_t)v * W + j] = 1.0;
+        if (INSTR) a.levdeg[(int64_t)j * (a.Lcap + 1)] = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
         if (!a.full) {
             const long long q0 = a.lane_off[a.lane_base + j], q1 = a.lane_off[a.lane_base + j + 1];
             a.remaining[j] = (int32_t)(q1 - q0);
@@ -177,6 +185,7 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
                 for (int w = 0; w < K; ++w) {
                     const uint64_t fw = f[w] & c[w];
                     nbp[w] |= fw;
+                    if (INSTR) n_sload += (unsigned long long)__popcll(fw);
                     unsigned nz = __ballot_sync(0xffffffffu, fw != 0ull);
                     while (nz) {
                         const int j = __ffs(nz) - 1;
@@ -189,9 +198,19 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
                     }
                 }
             }
+            bool disc = false;
 #pragma unroll
             for (int w = 0; w < K; ++w) {
                 const uint64_t nb = warp_or64(nbp[w]);
+                if (INSTR && nb) {
+                    disc = true;
+                    if (lane == 0) n_swrite += (unsigned long long)__popcll(nb);
+                    const unsigned long long dg = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
+                    if ((nb >> lane) & 1ull)
+                        atomicAdd(&a.levdeg[(int64_t)(64 * w + lane) * (a.Lcap + 1) + L + 1], dg);
+                    if ((nb >> (lane + 32)) & 1ull)
+                        atomicAdd(&a.levdeg[(int64_t)(64 * w + lane + 32) * (a.Lcap + 1) + L + 1], dg);
+                }
                 if (lane == 0) {
                     fnext[v * K + w] = nb;
                     if (nb) {
@@ -210,6 +229,10 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
                         if (acc1[w] >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
                     }
                 }
+            }
+            if (INSTR && disc && lane == 0) {
+                n_uv += 1;
+                n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
             }
         }
         __syncthreads();
@@ -268,6 +291,21 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
             return;
         }
     }
+    if (INSTR) {
+        for (int off = 16; off > 0; off >>= 1) {
+            n_sload += __shfl_xor_sync(0xffffffffu, n_sload, off);
+            n_swrite += __shfl_xor_sync(0xffffffffu, n_swrite, off);
+            n_uv += __shfl_xor_sync(0xffffffffu, n_uv, off);
+            n_ue += __shfl_xor_sync(0xffffffffu, n_ue, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&a.counters[0], n_sload);
+            atomicAdd(&a.counters[1], n_swrite);
+            atomicAdd(&a.counters[2], n_uv);
+            atomicAdd(&a.counters[3], n_ue);
+        }
+        if (tid == 0) atomicAdd(&a.counters[5], (unsigned long long)L);
+    }
     if (a.full) return;
 
     // ---- backtrack every sample of the batch (warp per sample)
@@ -277,6 +315,17 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
         const int32_t t = a.samp_t[p];
         const int32_t s = a.lane_src[a.lane_base + j];
         const int32_t d = __ldcg(&a.found[p]);
+        if (INSTR) {
+            // edges a top-down truncated BFS from s scans before settling t
+            const int32_t lmax = d < 0 ? a.Lcap : d - 1;
+            unsigned long long e = 0;
+            for (int32_t Lq = lane; Lq <= lmax; Lq += 32) e += a.levdeg[(int64_t)j * (a.Lcap + 1) + Lq];
+            for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+            if (lane == 0) {
+                atomicAdd(&a.counters[4], e);
+                atomicAdd(&a.counters[6], 1ull);
+            }
+        }
         if (d < 0) {
             if (lane == 0) {
                 a.kind[i] = 2;
@@ -360,37 +409,39 @@ __global__ void k_ms_extract(const uint64_t *fh, const double *sigma, int64_t n,
 }
 
 struct GridCache {
-    int grid[4] = {0, 0, 0, 0};
+    int grid[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
 };
 GridCache g_ms_grid;
 
-template <int K>
+template <int K, bool INSTR>
 int ms_grid(percis_ctx *ctx) {
     const int idx = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : 3;
-    if (g_ms_grid.grid[idx] == 0) {
+    int &slot = g_ms_grid.grid[INSTR ? 1 : 0][idx];
+    if (slot == 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs<K>, kMsBlock, 0);
-        g_ms_grid.grid[idx] = std::max(1, per_sm) * ctx->num_sms;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs<K, INSTR>, kMsBlock, 0);
+        slot = std::max(1, per_sm) * ctx->num_sms;
     }
-    return g_ms_grid.grid[idx];
+    return slot;
 }
 
-template <int K>
+template <int K, bool INSTR>
 percis_status launch_ms(percis_ctx *ctx, MsArgs &a) {
     void *args[] = {&a};
-    const int grid = ms_grid<K>(ctx);
-    PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_msbfs<K>, dim3(grid), dim3(kMsBlock), args, 0,
-                                                 ctx->stream));
+    const int grid = ms_grid<K, INSTR>(ctx);
+    PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_msbfs<K, INSTR>, dim3(grid), dim3(kMsBlock), args,
+                                                 0, ctx->stream));
     ctx->launches++;
     return PERCIS_OK;
 }
 
 percis_status launch_ms_k(percis_ctx *ctx, int K, MsArgs &a) {
+    const bool instr = a.counters != nullptr;
     switch (K) {
-        case 1: return launch_ms<1>(ctx, a);
-        case 2: return launch_ms<2>(ctx, a);
-        case 4: return launch_ms<4>(ctx, a);
-        default: return launch_ms<8>(ctx, a);
+        case 1: return instr ? launch_ms<1, true>(ctx, a) : launch_ms<1, false>(ctx, a);
+        case 2: return instr ? launch_ms<2, true>(ctx, a) : launch_ms<2, false>(ctx, a);
+        case 4: return instr ? launch_ms<4, true>(ctx, a) : launch_ms<4, false>(ctx, a);
+        default: return instr ? launch_ms<8, true>(ctx, a) : launch_ms<8, false>(ctx, a);
     }
 }
 
@@ -415,6 +466,9 @@ void fill_common(percis_ctx *ctx, MsArgs &a, int Lcap) {
     a.ctl = ctx->ms_ctl.as<MsCtl>();
     a.Lcap = Lcap;
     a.budget_ns = (uint64_t)(ctx->opt.timeout_s * 1e9);
+    a.rp = ctx->rp.as<int64_t>();
+    a.counters = nullptr;
+    a.levdeg = nullptr;
 }
 
 }  // namespace
@@ -464,10 +518,18 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
     a.arena_cap = ctx->arena_cap;
     a.cnt = ctx->cnt.as<unsigned long long>();
     a.full = 0;
+    if (ctx->opt.instrument) {
+        PERCIS_TRY(ensure(ctx, ctx->levdeg, sizeof(unsigned long long) * W * (size_t)(Lcap + 1), "level degrees"));
+        a.counters = ctx->counters.as<unsigned long long>();
+        a.levdeg = ctx->levdeg.as<unsigned long long>();
+    }
     for (int64_t b = 0; b < B; ++b) {
         a.lane_base = (int32_t)(b * W);
         a.nlanes = (int32_t)std::min<int64_t>(W, n_sources - b * W);
+        cudaEvent_t e0 = next_event(ctx), e1 = next_event(ctx);
+        if (e0) cudaEventRecord(e0, ctx->stream);
         PERCIS_TRY(launch_ms_k(ctx, K, a));
+        if (e1) cudaEventRecord(e1, ctx->stream);
     }
     return PERCIS_OK;
 }

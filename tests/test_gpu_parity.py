@@ -282,10 +282,22 @@ def test_edge_cases(binding):
     assert np.array_equal(_np(got["kind"]), ph.kind) and (ph.kind == 2).any()
     assert np.array_equal(_np(got["cnt"]), ph.cnt)
     eng.close()
+    # n = 2: every C_v is empty, so p is undefined (Section II-A)
     g2 = synth.path_graph(2)
-    eng = _engine(binding, g2, np.array([1.0, 0.0]), ell1=10, ell=10)
+    eng = _engine(binding, g2)
+    with pytest.raises(binding.PercisError) as e:
+        eng.set_states(np.array([1.0, 0.0]))
+    assert e.value.status == 2
+    eng.close()
+    # path 0-1-2, x = (1, 1/2, 0): C = 2, C_1 = 1, lambda_1 = 2, p = (0, 1, 0);
+    # pair (0,2) has probability 1/2 and always crosses 1
+    g3 = synth.path_graph(3)
+    eng = _engine(binding, g3, np.array([1.0, 0.5, 0.0]), ell1=1000, ell=4000)
     pc, info = eng.estimate(0.1, 0.1, seed=0)
-    assert np.all(_np(pc) == 0.0) and info["sum_internal"][1] == 0
+    pc = _np(pc)
+    assert pc[0] == 0.0 and pc[2] == 0.0
+    assert pc[1] == 2.0 * info["sum_internal"][1] / 4000
+    assert abs(pc[1] - 1.0) < 0.1
     eng.close()
 
 
