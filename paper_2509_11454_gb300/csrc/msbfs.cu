@@ -131,79 +131,98 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
     if (!grid_sync(bar, status, a.budget_ns)) return;
 
     __shared__ unsigned long long s_nonempty[K];
+    __shared__ unsigned long long s_act[K];
     int L = 0;
     for (;;) {
-        uint64_t act[K];
         bool any_act = false;
 #pragma unroll
-        for (int w = 0; w < K; ++w) {
-            act[w] = ld_relaxed_u64((const uint64_t *)&ctl->active[w]);
-            any_act |= act[w] != 0;
-        }
+        for (int w = 0; w < K; ++w) any_act |= ld_relaxed_u64((const uint64_t *)&ctl->active[w]) != 0ull;
         if (!any_act) break;
-        if (threadIdx.x < K) s_nonempty[threadIdx.x] = 0ull;
+        if (threadIdx.x < K) {
+            s_nonempty[threadIdx.x] = 0ull;
+            s_act[threadIdx.x] = ld_relaxed_u64((const uint64_t *)&ctl->active[threadIdx.x]);
+        }
         __syncthreads();
         const uint64_t *fcur = a.fh + (int64_t)L * nk;
         uint64_t *fnext = a.fh + (int64_t)(L + 1) * nk;
 
-        // ---- phase A: pull pass over all vertices (warp per vertex)
-        for (int64_t v = gwarp; v < n; v += nwarps) {
-            uint64_t c[K];
-            uint64_t vw[K];
-            load_words<K>(a.vis + v * K, vw);
-            bool any = false;
-#pragma unroll
-            for (int w = 0; w < K; ++w) {
-                c[w] = act[w] & ~vw[w];
-                any |= c[w] != 0;
-            }
-            if (!any) {
-                if (lane < K) fnext[v * K + lane] = 0ull;
+        // ---- phase A: pull pass, one warp per (vertex, lane word) item
+        for (int64_t it = gwarp; it < nk; it += nwarps) {
+            const int64_t v = it / K;
+            const int w = (int)(it - v * K);
+            const uint64_t vw = __ldcg(&a.vis[it]);
+            const uint64_t cw = s_act[w] & ~vw;
+            if (cw == 0ull) {
+                if (lane == 0) fnext[it] = 0ull;
                 continue;
             }
-            uint64_t nbp[K];
-            double acc0[K], acc1[K];
-#pragma unroll
-            for (int w = 0; w < K; ++w) {
-                nbp[w] = 0ull;
-                acc0[w] = 0.0;
-                acc1[w] = 0.0;
-            }
+            uint64_t nbp = 0ull;
+            double acc0 = 0.0, acc1 = 0.0;
             const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
             for (int64_t base = e0; base < e1; base += 32) {
                 const int64_t e = base + lane;
                 int32_t u = 0;
-                uint64_t f[K];
+                uint64_t fw = 0ull;
                 if (e < e1) {
                     u = a.icol[e];
-                    load_words<K>(fcur + (int64_t)u * K, f);
-                } else {
-#pragma unroll
-                    for (int w = 0; w < K; ++w) f[w] = 0ull;
+                    fw = __ldcg(&fcur[(int64_t)u * K + w]) & cw;
                 }
-#pragma unroll
-                for (int w = 0; w < K; ++w) {
-                    const uint64_t fw = f[w] & c[w];
-                    nbp[w] |= fw;
-                    if (INSTR) n_sload += (unsigned long long)__popcll(fw);
-                    unsigned nz = __ballot_sync(0xffffffffu, fw != 0ull);
-                    while (nz) {
-                        const int j = __ffs(nz) - 1;
-                        nz &= nz - 1;
-                        const uint64_t fj = shfl64(fw, j);
-                        const int32_t uj = __shfl_sync(0xffffffffu, u, j);
-                        const double *srow = a.sigma + (int64_t)uj * W + 64 * w;
-                        if ((fj >> lane) & 1ull) acc0[w] += __ldcg(srow + lane);
-                        if ((fj >> (lane + 32)) & 1ull) acc1[w] += __ldcg(srow + lane + 32);
-                    }
+                nbp |= fw;
+                if (INSTR) n_sload += (unsigned long long)__popcll(fw);
+                unsigned nz = __ballot_sync(0xffffffffu, fw != 0ull);
+                while (nz) {
+                    // up to four parents per round so their sigma loads overlap
+                    const int j0 = __ffs(nz) - 1;
+                    nz &= nz - 1;
+                    const bool h1 = nz != 0u;
+                    const int j1 = h1 ? __ffs(nz) - 1 : j0;
+                    if (h1) nz &= nz - 1;
+                    const bool h2 = nz != 0u;
+                    const int j2 = h2 ? __ffs(nz) - 1 : j0;
+                    if (h2) nz &= nz - 1;
+                    const bool h3 = nz != 0u;
+                    const int j3 = h3 ? __ffs(nz) - 1 : j0;
+                    if (h3) nz &= nz - 1;
+                    const uint64_t f0 = shfl64(fw, j0);
+                    const uint64_t f1 = h1 ? shfl64(fw, j1) : 0ull;
+                    const uint64_t f2 = h2 ? shfl64(fw, j2) : 0ull;
+                    const uint64_t f3 = h3 ? shfl64(fw, j3) : 0ull;
+                    const double *r0 = a.sigma + (int64_t)__shfl_sync(0xffffffffu, u, j0) * W + 64 * w;
+                    const double *r1 = a.sigma + (int64_t)__shfl_sync(0xffffffffu, u, j1) * W + 64 * w;
+                    const double *r2 = a.sigma + (int64_t)__shfl_sync(0xffffffffu, u, j2) * W + 64 * w;
+                    const double *r3 = a.sigma + (int64_t)__shfl_sync(0xffffffffu, u, j3) * W + 64 * w;
+                    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+                    if ((f0 >> lane) & 1ull) a0 = __ldcg(r0 + lane);
+                    if ((f1 >> lane) & 1ull) a1 = __ldcg(r1 + lane);
+                    if ((f2 >> lane) & 1ull) a2 = __ldcg(r2 + lane);
+                    if ((f3 >> lane) & 1ull) a3 = __ldcg(r3 + lane);
+                    if ((f0 >> (lane + 32)) & 1ull) b0 = __ldcg(r0 + lane + 32);
+                    if ((f1 >> (lane + 32)) & 1ull) b1 = __ldcg(r1 + lane + 32);
+                    if ((f2 >> (lane + 32)) & 1ull) b2 = __ldcg(r2 + lane + 32);
+                    if ((f3 >> (lane + 32)) & 1ull) b3 = __ldcg(r3 + lane + 32);
+                    acc0 += (a0 + a1) + (a2 + a3);
+                    acc1 += (b0 + b1) + (b2 + b3);
                 }
             }
-            bool disc = false;
-#pragma unroll
-            for (int w = 0; w < K; ++w) {
-                const uint64_t nb = warp_or64(nbp[w]);
-                if (INSTR && nb) {
-                    disc = true;
+            const uint64_t nb = warp_or64(nbp);
+            if (lane == 0) {
+                fnext[it] = nb;
+                if (nb) {
+                    a.vis[it] = vw | nb;
+                    atomicOr(&s_nonempty[w], (unsigned long long)nb);
+                }
+            }
+            if (nb) {
+                double *drow = a.sigma + v * W + 64 * w;
+                if ((nb >> lane) & 1ull) {
+                    drow[lane] = acc0;
+                    if (acc0 >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
+                }
+                if ((nb >> (lane + 32)) & 1ull) {
+                    drow[lane + 32] = acc1;
+                    if (acc1 >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
+                }
+                if (INSTR) {
                     if (lane == 0) n_swrite += (unsigned long long)__popcll(nb);
                     const unsigned long long dg = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
                     if ((nb >> lane) & 1ull)
@@ -211,34 +230,25 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
                     if ((nb >> (lane + 32)) & 1ull)
                         atomicAdd(&a.levdeg[(int64_t)(64 * w + lane + 32) * (a.Lcap + 1) + L + 1], dg);
                 }
-                if (lane == 0) {
-                    fnext[v * K + w] = nb;
-                    if (nb) {
-                        a.vis[v * K + w] = vw[w] | nb;
-                        atomicOr(&s_nonempty[w], (unsigned long long)nb);
-                    }
-                }
-                if (nb) {
-                    double *drow = a.sigma + v * W + 64 * w;
-                    if ((nb >> lane) & 1ull) {
-                        drow[lane] = acc0[w];
-                        if (acc0[w] >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
-                    }
-                    if ((nb >> (lane + 32)) & 1ull) {
-                        drow[lane + 32] = acc1[w];
-                        if (acc1[w] >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
-                    }
-                }
-            }
-            if (INSTR && disc && lane == 0) {
-                n_uv += 1;
-                n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
             }
         }
         __syncthreads();
         if (threadIdx.x < K && s_nonempty[threadIdx.x])
             atomicOr(&ctl->nonempty[L & 1][threadIdx.x], s_nonempty[threadIdx.x]);
         if (!grid_sync(bar, status, a.budget_ns)) return;
+
+        if (INSTR) {
+            // union frontier of the new level: adjacency rows and entries a
+            // top-down expansion of it needs
+            for (int64_t v = tid; v < n; v += nthreads) {
+                bool any = false;
+                for (int w = 0; w < K; ++w) any |= __ldcg(&fnext[v * K + w]) != 0ull;
+                if (any) {
+                    n_uv += 1;
+                    n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
+                }
+            }
+        }
 
         // ---- phase B: mark settled targets, then the last block retires lanes
         if (!a.full) {
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
             __threadfence();
             if (threadIdx.x < K) {
                 const int w = threadIdx.x;
-                uint64_t nact = act[w] & ld_relaxed_u64((const uint64_t *)&ctl->nonempty[L & 1][w]);
+                uint64_t nact = s_act[w] & ld_relaxed_u64((const uint64_t *)&ctl->nonempty[L & 1][w]);
                 if (!a.full) {
                     uint64_t m = nact;
                     while (m) {
