@@ -206,6 +206,7 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
     }
     ctx->have_paths = false;
     if (ctx->opt.instrument) PERCIS_TRY(ensure(ctx, ctx->counters, sizeof(unsigned long long) * 8, "counters"));
+    ctx->sigma_fp64 = false;
     for (int attempt = 0; attempt < 24; ++attempt) {
         clear_status(ctx);
         ctx->ev_next = 0;
@@ -244,6 +245,10 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
             const int64_t cap = (int64_t)top + (int64_t)top / 4 + 1024;
             PERCIS_TRY(ensure(ctx, ctx->arena, sizeof(int32_t) * cap, "path arena"));
             ctx->arena_cap = cap;
+            continue;
+        }
+        if ((st & DEV_SIGMA_OVERFLOW) && ctx->opt.form != PERCIS_FORM_PLAIN && !ctx->sigma_fp64) {
+            ctx->sigma_fp64 = true;  // exact integer counts reached 2^53: redo with FP64 sigma
             continue;
         }
         if ((st & DEV_BAD_PATH) && !(st & DEV_SIGMA_OVERFLOW))

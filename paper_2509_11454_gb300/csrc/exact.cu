@@ -7,6 +7,7 @@
 // are pulled over out-neighbours (one warp per vertex, lanes spread over the
 // warp), and p(v) = sum_{s != v} delta_s(v) / C_v.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -15,11 +16,13 @@ namespace percis {
 
 namespace {
 
-template <int K>
+template <int K, bool FPSIG>
 __global__ void k_dependency(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *fh, int32_t L,
-                             const double *sigma, double *delta, const double *x, const int32_t *lane_src,
+                             const void *sigma_v, double *delta, const double *x, const int32_t *lane_src,
                              int32_t nlanes, double *num) {
     constexpr int W = 64 * K;
+    using S = typename std::conditional<FPSIG, double, unsigned long long>::type;
+    const S *sigma = static_cast<const S *>(sigma_v);
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -35,8 +38,8 @@ __global__ void k_dependency(int64_t n, const int64_t *rp, const int32_t *col, c
             const bool b0 = (bits >> lane) & 1ull, b1 = (bits >> (lane + 32)) & 1ull;
             const double xs0 = (b0 && j0 < nlanes) ? x[lane_src[j0]] : 0.0;
             const double xs1 = (b1 && j1 < nlanes) ? x[lane_src[j1]] : 0.0;
-            const double sv0 = b0 ? sigma[v * W + j0] : 0.0;
-            const double sv1 = b1 ? sigma[v * W + j1] : 0.0;
+            const double sv0 = b0 ? (double)sigma[v * W + j0] : 0.0;
+            const double sv1 = b1 ? (double)sigma[v * W + j1] : 0.0;
             double a0 = 0.0, a1 = 0.0;
             for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
                 const int32_t c = col[e];
@@ -44,11 +47,11 @@ __global__ void k_dependency(int64_t n, const int64_t *rp, const int32_t *col, c
                 if (!m) continue;
                 if ((m >> lane) & 1ull) {
                     const double cf = fmax(0.0, xs0 - x[c]) + delta[(int64_t)c * W + j0];
-                    a0 += sv0 / sigma[(int64_t)c * W + j0] * cf;
+                    a0 += sv0 / (double)sigma[(int64_t)c * W + j0] * cf;
                 }
                 if ((m >> (lane + 32)) & 1ull) {
                     const double cf = fmax(0.0, xs1 - x[c]) + delta[(int64_t)c * W + j1];
-                    a1 += sv1 / sigma[(int64_t)c * W + j1] * cf;
+                    a1 += sv1 / (double)sigma[(int64_t)c * W + j1] * cf;
                 }
             }
             if (b0) delta[v * W + j0] = a0;
@@ -74,11 +77,16 @@ __global__ void k_divide(const double *num, const double *Cv, int64_t n, double 
 }
 
 template <int K>
-percis_status dependency_levels(percis_ctx *ctx, int levels, const double *sig, double *delta, const int32_t *src,
+percis_status dependency_levels(percis_ctx *ctx, int levels, const void *sig, double *delta, const int32_t *src,
                                 int32_t nlanes, double *num) {
     const int grid = grid_for(ctx, ctx->n * 32, 256);
     for (int L = levels; L >= 0; --L) {
-        k_dependency<K><<<grid, 256, 0, ctx->stream>>>(ctx->n, ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
+        if (ctx->sigma_fp64)
+            k_dependency<K, true><<<grid, 256, 0, ctx->stream>>>(ctx->n, ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                               ctx->fhist.as<uint64_t>(), L, sig, delta,
+                                                               ctx->x.as<double>(), src, nlanes, num);
+        else
+        k_dependency<K, false><<<grid, 256, 0, ctx->stream>>>(ctx->n, ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
                                                       ctx->fhist.as<uint64_t>(), L, sig, delta, ctx->x.as<double>(),
                                                       src, nlanes, num);
         PERCIS_CHECK_LAUNCH(ctx, "dependency");
@@ -110,10 +118,10 @@ percis_status exact_pc(percis_ctx *ctx, double *pc) {
         const int levels = hc.level;
         percis_status st;
         switch (Wl / 64) {
-            case 1: st = dependency_levels<1>(ctx, levels, ctx->sigmaW.as<double>(), delta, src, cnt, num); break;
-            case 2: st = dependency_levels<2>(ctx, levels, ctx->sigmaW.as<double>(), delta, src, cnt, num); break;
-            case 4: st = dependency_levels<4>(ctx, levels, ctx->sigmaW.as<double>(), delta, src, cnt, num); break;
-            default: st = dependency_levels<8>(ctx, levels, ctx->sigmaW.as<double>(), delta, src, cnt, num); break;
+            case 1: st = dependency_levels<1>(ctx, levels, ctx->sigmaW.p, delta, src, cnt, num); break;
+            case 2: st = dependency_levels<2>(ctx, levels, ctx->sigmaW.p, delta, src, cnt, num); break;
+            case 4: st = dependency_levels<4>(ctx, levels, ctx->sigmaW.p, delta, src, cnt, num); break;
+            default: st = dependency_levels<8>(ctx, levels, ctx->sigmaW.p, delta, src, cnt, num); break;
         }
         if (st != PERCIS_OK) return st;
     }

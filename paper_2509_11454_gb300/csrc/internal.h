@@ -75,6 +75,7 @@ struct percis_ctx {
     percis::DevBuf vis, fhist, sigmaW, ms_ctl, remaining, found;
     int32_t lanes_alloc = 0;
     int32_t levels_alloc = 0;
+    bool sigma_fp64 = false;  // batched sigma kept in FP64 (after a count reached 2^53)
 
     // samples of the last phase
     percis::DevBuf pair_s, pair_t, kind, ilen, path_off, arena, cnt, arena_top;

@@ -12,11 +12,19 @@
 // backtracks every sample of the batch (one warp per sample) exactly as the
 // plain form does, reading the frontier history for the predecessor test.
 //
+// sigma is kept as exact unsigned 64-bit integers: a dependent FP64 add costs
+// ~64 cycles on GB300 while integer adds are cheap, and below 2^53 every
+// conversion to FP64 is exact, so the backtrack compares exactly the FP64
+// values a plain FP64 implementation would.  If any sigma reaches 2^53 the
+// launch flags DEV_SIGMA_OVERFLOW and the host reruns the phase with the FP64
+// variant (FPSIG = true), where counts beyond 2^53 are rounded like FP64 sums.
+//
 // Layout in HBM (vertex-major so one warp reads a vertex's lanes coalesced):
 //   visited  uint64 [n][K]
 //   history  uint64 [Lcap+1][n][K]
-//   sigma    double [n][W]
+//   sigma    uint64 or double [n][W]
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -33,7 +41,7 @@ struct MsArgs {
     const int32_t *icol;
     uint64_t *vis;
     uint64_t *fh;
-    double *sigma;
+    void *sigma;
     MsCtl *ctl;
     int32_t Lcap;
     int32_t lane_base;
@@ -76,9 +84,23 @@ __device__ __forceinline__ void load_words(const uint64_t *p, uint64_t (&out)[K]
     }
 }
 
-template <int K, bool INSTR>
-__global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
+template <class S>
+__device__ __forceinline__ S warp_incl_scan(S v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const S o = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += o;
+    }
+    return v;
+}
+
+template <int K, bool INSTR, bool FPSIG>
+__global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     constexpr int W = 64 * K;
+    using S = typename std::conditional<FPSIG, double, unsigned long long>::type;
+    S *sig = static_cast<S *>(a.sigma);
+    bool ovf = false;
     unsigned long long n_sload = 0, n_swrite = 0, n_uv = 0, n_ue = 0;
     MsCtl *ctl = a.ctl;
     GridBarrier *bar = reinterpret_cast<GridBarrier *>(ctl);
@@ -121,7 +143,7 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
         const uint64_t bit = 1ull << (j & 63);
         atomicOr((unsigned long long *)&a.vis[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         atomicOr((unsigned long long *)&a.fh[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
-        a.sigma[(int64_t)v * W + j] = 1.0;
+        sig[(int64_t)v * W + j] = S(1);
         if (INSTR) a.levdeg[(int64_t)j * (a.Lcap + 1)] = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
         if (!a.full) {
             const long long q0 = a.lane_off[a.lane_base + j], q1 = a.lane_off[a.lane_base + j + 1];
@@ -157,7 +179,7 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
                 continue;
             }
             uint64_t nbp = 0ull;
-            double acc0 = 0.0, acc1 = 0.0;
+            S acc0 = S(0), acc1 = S(0);
             const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
             for (int64_t base = e0; base < e1; base += 32) {
                 const int64_t e = base + lane;
@@ -187,11 +209,11 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
                     const uint64_t f1 = h1 ? shfl64(fw, j1) : 0ull;
                     const uint64_t f2 = h2 ? shfl64(fw, j2) : 0ull;
                     const uint64_t f3 = h3 ? shfl64(fw, j3) : 0ull;
-                    const double *r0 = a.sigma + (int64_t)__shfl_sync(0xffffffffu, u, j0) * W + 64 * w;
-                    const double *r1 = a.sigma + (int64_t)__shfl_sync(0xffffffffu, u, j1) * W + 64 * w;
-                    const double *r2 = a.sigma + (int64_t)__shfl_sync(0xffffffffu, u, j2) * W + 64 * w;
-                    const double *r3 = a.sigma + (int64_t)__shfl_sync(0xffffffffu, u, j3) * W + 64 * w;
-                    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+                    const S *r0 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j0) * W + 64 * w;
+                    const S *r1 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j1) * W + 64 * w;
+                    const S *r2 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j2) * W + 64 * w;
+                    const S *r3 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j3) * W + 64 * w;
+                    S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0), b0 = S(0), b1 = S(0), b2 = S(0), b3 = S(0);
                     if ((f0 >> lane) & 1ull) a0 = __ldcg(r0 + lane);
                     if ((f1 >> lane) & 1ull) a1 = __ldcg(r1 + lane);
                     if ((f2 >> lane) & 1ull) a2 = __ldcg(r2 + lane);
@@ -200,8 +222,16 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
                     if ((f1 >> (lane + 32)) & 1ull) b1 = __ldcg(r1 + lane + 32);
                     if ((f2 >> (lane + 32)) & 1ull) b2 = __ldcg(r2 + lane + 32);
                     if ((f3 >> (lane + 32)) & 1ull) b3 = __ldcg(r3 + lane + 32);
-                    acc0 += (a0 + a1) + (a2 + a3);
-                    acc1 += (b0 + b1) + (b2 + b3);
+                    if (FPSIG) {
+                        // keep the in-adjacency order of the additions
+                        acc0 += a0; acc0 += a1; acc0 += a2; acc0 += a3;
+                        acc1 += b0; acc1 += b1; acc1 += b2; acc1 += b3;
+                    } else {
+                        acc0 += (a0 + a1) + (a2 + a3);
+                        acc1 += (b0 + b1) + (b2 + b3);
+                    }
+                    // integer mode: flag before four more addends could wrap 2^64
+                    if (!FPSIG) ovf |= (acc0 >= S(kTwo53)) | (acc1 >= S(kTwo53));
                 }
             }
             const uint64_t nb = warp_or64(nbp);
@@ -213,14 +243,14 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
                 }
             }
             if (nb) {
-                double *drow = a.sigma + v * W + 64 * w;
+                S *drow = sig + v * W + 64 * w;
                 if ((nb >> lane) & 1ull) {
                     drow[lane] = acc0;
-                    if (acc0 >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
+                    if (FPSIG && acc0 >= S(kTwo53)) ovf = true;
                 }
                 if ((nb >> (lane + 32)) & 1ull) {
                     drow[lane + 32] = acc1;
-                    if (acc1 >= kTwo53) atomicOr(status, DEV_SIGMA_OVERFLOW);
+                    if (FPSIG && acc1 >= S(kTwo53)) ovf = true;
                 }
                 if (INSTR) {
                     if (lane == 0) n_swrite += (unsigned long long)__popcll(nb);
@@ -232,6 +262,8 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
                 }
             }
         }
+        if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, DEV_SIGMA_OVERFLOW);
+        ovf = false;
         __syncthreads();
         if (threadIdx.x < K && s_nonempty[threadIdx.x])
             atomicOr(&ctl->nonempty[L & 1][threadIdx.x], s_nonempty[threadIdx.x]);
@@ -361,21 +393,23 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
         uint32_t step = 0;
         int32_t k = 0;
         while (w != s) {
-            const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step), __ldcg(&a.sigma[(int64_t)w * W + j]));
+            const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step),
+                                            (double)__ldcg(&sig[(int64_t)w * W + j]));
             const uint64_t *fprev = a.fh + (int64_t)(lw - 1) * nk;
             const int64_t e0 = a.irp[w], e1 = a.irp[w + 1];
-            double carry = 0.0;
+            S carry = S(0);
             int32_t pick = -1;
             for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
                 const int64_t e = base + lane;
                 int32_t pv = -1;
-                double val = 0.0;
+                S val = S(0);
                 if (e < e1) {
                     pv = a.icol[e];
-                    if (__ldcg(&fprev[(int64_t)pv * K + wj]) & bj) val = __ldcg(&a.sigma[(int64_t)pv * W + j]);
+                    if (__ldcg(&fprev[(int64_t)pv * K + wj]) & bj) val = __ldcg(&sig[(int64_t)pv * W + j]);
                 }
-                const double cum = __dadd_rn(carry, warp_inclusive_scan(val));
-                const unsigned hit = __ballot_sync(0xffffffffu, val > 0.0 && cum >= target);
+                // running sums are exact (integers; FP64 sums of integers below 2^53)
+                const S cum = carry + warp_incl_scan<S>(val);
+                const unsigned hit = __ballot_sync(0xffffffffu, val > S(0) && (double)cum >= target);
                 if (hit) pick = __shfl_sync(0xffffffffu, pv, __ffs(hit) - 1);
                 carry = __shfl_sync(0xffffffffu, cum, 31);
             }
@@ -398,10 +432,12 @@ __global__ void __launch_bounds__(kMsBlock) k_msbfs(MsArgs a) {
 }
 
 // dist/sigma of every lane after a full traversal, source-major output.
-template <int K>
-__global__ void k_ms_extract(const uint64_t *fh, const double *sigma, int64_t n, int32_t levels, int32_t nsrc,
+template <int K, bool FPSIG>
+__global__ void k_ms_extract(const uint64_t *fh, const void *sigma_v, int64_t n, int32_t levels, int32_t nsrc,
                              int32_t *dist, double *sig) {
     constexpr int W = 64 * K;
+    using S = typename std::conditional<FPSIG, double, unsigned long long>::type;
+    const S *sigma = static_cast<const S *>(sigma_v);
     const int64_t total = n * (int64_t)nsrc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
@@ -414,45 +450,50 @@ __global__ void k_ms_extract(const uint64_t *fh, const double *sigma, int64_t n,
             }
         }
         if (dist) dist[q] = d;
-        if (sig) sig[q] = d >= 0 ? sigma[v * W + j] : 0.0;
+        if (sig) sig[q] = d >= 0 ? (double)sigma[v * W + j] : 0.0;
     }
 }
 
 struct GridCache {
-    int grid[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    int grid[2][2][4] = {};
 };
 GridCache g_ms_grid;
 
-template <int K, bool INSTR>
+template <int K, bool INSTR, bool FPSIG>
 int ms_grid(percis_ctx *ctx) {
     const int idx = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : 3;
-    int &slot = g_ms_grid.grid[INSTR ? 1 : 0][idx];
+    int &slot = g_ms_grid.grid[INSTR ? 1 : 0][FPSIG ? 1 : 0][idx];
     if (slot == 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs<K, INSTR>, kMsBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs<K, INSTR, FPSIG>, kMsBlock, 0);
         slot = std::max(1, per_sm) * ctx->num_sms;
     }
     return slot;
 }
 
-template <int K, bool INSTR>
+template <int K, bool INSTR, bool FPSIG>
 percis_status launch_ms(percis_ctx *ctx, MsArgs &a) {
     void *args[] = {&a};
-    const int grid = ms_grid<K, INSTR>(ctx);
-    PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_msbfs<K, INSTR>, dim3(grid), dim3(kMsBlock), args,
-                                                 0, ctx->stream));
+    const int grid = ms_grid<K, INSTR, FPSIG>(ctx);
+    PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_msbfs<K, INSTR, FPSIG>, dim3(grid), dim3(kMsBlock),
+                                                 args, 0, ctx->stream));
     ctx->launches++;
     return PERCIS_OK;
 }
 
-percis_status launch_ms_k(percis_ctx *ctx, int K, MsArgs &a) {
+template <bool FPSIG>
+percis_status launch_ms_k2(percis_ctx *ctx, int K, MsArgs &a) {
     const bool instr = a.counters != nullptr;
     switch (K) {
-        case 1: return instr ? launch_ms<1, true>(ctx, a) : launch_ms<1, false>(ctx, a);
-        case 2: return instr ? launch_ms<2, true>(ctx, a) : launch_ms<2, false>(ctx, a);
-        case 4: return instr ? launch_ms<4, true>(ctx, a) : launch_ms<4, false>(ctx, a);
-        default: return instr ? launch_ms<8, true>(ctx, a) : launch_ms<8, false>(ctx, a);
+        case 1: return instr ? launch_ms<1, true, FPSIG>(ctx, a) : launch_ms<1, false, FPSIG>(ctx, a);
+        case 2: return instr ? launch_ms<2, true, FPSIG>(ctx, a) : launch_ms<2, false, FPSIG>(ctx, a);
+        case 4: return instr ? launch_ms<4, true, FPSIG>(ctx, a) : launch_ms<4, false, FPSIG>(ctx, a);
+        default: return instr ? launch_ms<8, true, FPSIG>(ctx, a) : launch_ms<8, false, FPSIG>(ctx, a);
     }
+}
+
+percis_status launch_ms_k(percis_ctx *ctx, int K, MsArgs &a) {
+    return ctx->sigma_fp64 ? launch_ms_k2<true>(ctx, K, a) : launch_ms_k2<false>(ctx, K, a);
 }
 
 percis_status ensure_ms(percis_ctx *ctx, int W, int Lcap) {
@@ -472,7 +513,7 @@ void fill_common(percis_ctx *ctx, MsArgs &a, int Lcap) {
     a.icol = ctx->directed ? ctx->icol.as<int32_t>() : ctx->col.as<int32_t>();
     a.vis = ctx->vis.as<uint64_t>();
     a.fh = ctx->fhist.as<uint64_t>();
-    a.sigma = ctx->sigmaW.as<double>();
+    a.sigma = ctx->sigmaW.p;
     a.ctl = ctx->ms_ctl.as<MsCtl>();
     a.Lcap = Lcap;
     a.budget_ns = (uint64_t)(ctx->opt.timeout_s * 1e9);
@@ -546,6 +587,7 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
 
 // Full traversal from nsrc <= 512 sources (inspection and exact centrality).
 percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, int32_t *dist, double *sigma) {
+    ctx->sigma_fp64 = false;
     int W = 64;
     while (W < nsrc) W *= 2;
     const int K = W / 64;
@@ -570,14 +612,30 @@ percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, 
             Lcap *= 2;
             continue;
         }
+        if ((hc.status & DEV_SIGMA_OVERFLOW) && !ctx->sigma_fp64) {
+            ctx->sigma_fp64 = true;  // counts reached 2^53: redo with FP64 sigma
+            continue;
+        }
         const int levels = hc.level;
         if (!dist && !sigma) return PERCIS_OK;
         const int grid = grid_for(ctx, ctx->n * nsrc, 256);
-        switch (K) {
-            case 1: k_ms_extract<1><<<grid, 256, 0, ctx->stream>>>(ctx->fhist.as<uint64_t>(), ctx->sigmaW.as<double>(), ctx->n, levels, nsrc, dist, sigma); break;
-            case 2: k_ms_extract<2><<<grid, 256, 0, ctx->stream>>>(ctx->fhist.as<uint64_t>(), ctx->sigmaW.as<double>(), ctx->n, levels, nsrc, dist, sigma); break;
-            case 4: k_ms_extract<4><<<grid, 256, 0, ctx->stream>>>(ctx->fhist.as<uint64_t>(), ctx->sigmaW.as<double>(), ctx->n, levels, nsrc, dist, sigma); break;
-            default: k_ms_extract<8><<<grid, 256, 0, ctx->stream>>>(ctx->fhist.as<uint64_t>(), ctx->sigmaW.as<double>(), ctx->n, levels, nsrc, dist, sigma); break;
+        const void *sg = ctx->sigmaW.p;
+        const uint64_t *fhp = ctx->fhist.as<uint64_t>();
+        const int64_t nn = ctx->n;
+        if (ctx->sigma_fp64) {
+            switch (K) {
+                case 1: k_ms_extract<1, true><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
+                case 2: k_ms_extract<2, true><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
+                case 4: k_ms_extract<4, true><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
+                default: k_ms_extract<8, true><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
+            }
+        } else {
+            switch (K) {
+                case 1: k_ms_extract<1, false><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
+                case 2: k_ms_extract<2, false><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
+                case 4: k_ms_extract<4, false><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
+                default: k_ms_extract<8, false><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
+            }
         }
         PERCIS_CHECK_LAUNCH(ctx, "ms extract");
         return PERCIS_OK;

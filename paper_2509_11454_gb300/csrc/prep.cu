@@ -98,43 +98,86 @@ __global__ void k_gather_sorted(const double *x, const int32_t *perm, int64_t n,
 
 // ------------------------------------------------------- Algorithm 2 scan
 // The preprocessing recurrence of Algorithm 2 is evaluated sequentially in
-// exactly its order (i = n down to 1) by one thread, so that w, c_i, r and c
-// are bit-identical to any other sequential evaluation: the sampled pairs
-// depend on them through exact comparisons.  The block stages x into shared
-// memory so that thread 0 only waits on shared-memory latency.
-constexpr int kScanStage = 4096;
+// exactly its order (i = n down to 1) so that w, c_i, r and c are
+// bit-identical to any other sequential evaluation: the sampled pairs depend
+// on them through exact comparisons.  A dependent FP64 add costs ~64 cycles
+// on this GPU, so the block stages x_i and the products (n-i+1) x_i (each an
+// independent rounding) into shared memory, and thread 0 runs the three
+// recurrences software-pipelined: step k adds w_k while c_{k-1} and the sums
+// r, c of element k-2 use results of earlier steps, so one step costs about
+// one FP64 latency instead of four.
+constexpr int kScanStage = 2048;
 
 __global__ void k_tables(const double *xs, int64_t n, double *w, double *ci, double *r, double *dscal) {
-    __shared__ double tile[kScanStage];
-    double wn = 0.0, rn = 0.0, c = 0.0;
+    __shared__ double tx[kScanStage];
+    __shared__ double tt[kScanStage];
     if (threadIdx.x == 0) {
         w[n + 1] = 0.0;
         r[n + 1] = 0.0;
         ci[n + 1] = 0.0;
         w[0] = r[0] = ci[0] = 0.0;
     }
+    // pipeline registers (thread 0): w of the last two elements, c_i pending
+    double wn = 0.0, rn = 0.0, c = 0.0;
+    double w_prev = 0.0, t_prev = 0.0;  // element k-1: its w and product
+    double cv_prev = 0.0;               // element k-2's clamped c_i, waiting for r and c
+    int64_t i_prev = -1, i_prev2 = -1;
     for (int64_t hi = n; hi >= 1; hi -= kScanStage) {
         const int64_t lo = max((int64_t)1, hi - kScanStage + 1);
         const int cnt = (int)(hi - lo + 1);
         __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) tile[k] = xs[lo - 1 + k];
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const int64_t i = lo + k;
+            const double xi = xs[i - 1];
+            tx[k] = xi;
+            tt[k] = __dmul_rn((double)(n - i + 1), xi);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int k = cnt - 1; k >= 0; --k) {
                 const int64_t i = lo + k;
-                const double xi = tile[k];
-                wn = __dadd_rn(wn, xi);
-                double cv = __dsub_rn(__dmul_rn((double)(n - i + 1), xi), wn);
-                if (cv < 0.0) cv = 0.0;
-                rn = __dadd_rn(rn, cv);
-                c = __dadd_rn(c, cv);
-                w[i] = wn;
-                ci[i] = cv;
-                r[i] = rn;
+                // element i: w_i = w_{i+1} + x_i
+                const double w_new = __dadd_rn(wn, tx[k]);
+                // element i_prev: c = (n-i+1) x - w, clamped at 0
+                double cvp = __dsub_rn(t_prev, w_prev);
+                if (__double_as_longlong(cvp) < 0) cvp = 0.0;
+                // element i_prev2: r and c sums
+                if (i_prev2 >= 1) {
+                    rn = __dadd_rn(rn, cv_prev);
+                    c = __dadd_rn(c, cv_prev);
+                    r[i_prev2] = rn;
+                }
+                if (i_prev >= 1) {
+                    ci[i_prev] = cvp;
+                    w[i_prev] = w_prev;
+                }
+                cv_prev = cvp;
+                i_prev2 = i_prev;
+                i_prev = i;
+                w_prev = w_new;
+                t_prev = tt[k];
+                wn = w_new;
             }
         }
     }
-    if (threadIdx.x == 0) dscal[0] = c;
+    if (threadIdx.x == 0) {
+        // drain: element i_prev (w known), then the last two r/c sums
+        double cvp = __dsub_rn(t_prev, w_prev);
+        if (__double_as_longlong(cvp) < 0) cvp = 0.0;
+        if (i_prev2 >= 1) {
+            rn = __dadd_rn(rn, cv_prev);
+            c = __dadd_rn(c, cv_prev);
+            r[i_prev2] = rn;
+        }
+        if (i_prev >= 1) {
+            ci[i_prev] = cvp;
+            w[i_prev] = w_prev;
+            rn = __dadd_rn(rn, cvp);
+            c = __dadd_rn(c, cvp);
+            r[i_prev] = rn;
+        }
+        dscal[0] = c;
+    }
 }
 
 // C_v = c - A_v with A_i = (w_1 - w_i) - (i-1) x_i + (n-i) x_i - w_{i+1} for

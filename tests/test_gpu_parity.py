@@ -40,6 +40,12 @@ def _np(t):
     return t.cpu().numpy()
 
 
+def _sigma_equal(got, ref):
+    """sigma is exact below 2^53; above it both sides carry FP64 roundings."""
+    exact = ref < 2.0 ** 53
+    return np.array_equal(got[exact], ref[exact]) and np.allclose(got[~exact], ref[~exact], rtol=1e-13, atol=0)
+
+
 GRAPHS = {
     "er1000": lambda: synth.erdos_renyi(1000, 8.0, 0),
     "ba3000": lambda: synth.barabasi_albert(3000, 3, 1),
@@ -103,12 +109,12 @@ def test_plain_bfs_bitexact(binding, gcase):
             ret, rd, rsig, _, _, _ = oracle.bfs(og, int(src), tgt)
             if tgt < 0:
                 assert np.array_equal(_np(dist), rd)
-                assert np.array_equal(_np(sig), rsig)
+                assert _sigma_equal(_np(sig), rsig)
             else:
                 # truncated: every vertex the oracle settled matches exactly
                 m = rd >= 0
                 assert np.array_equal(_np(dist)[m], rd[m])
-                assert np.array_equal(_np(sig)[m], rsig[m])
+                assert _sigma_equal(_np(sig)[m], rsig[m])
     eng.close()
 
 
@@ -124,7 +130,7 @@ def test_msbfs_bitexact(binding, gcase, nsrc):
     for j in check:
         _, rd, rsig, _, _, _ = oracle.bfs(og, int(srcs[j]))
         assert np.array_equal(dist[j], rd), j
-        assert np.array_equal(sig[j], rsig), j
+        assert _sigma_equal(sig[j], rsig), j
     eng.close()
 
 
