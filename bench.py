@@ -169,6 +169,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-pairs", type=int, default=300)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/differentiated/e2e/cpu legs")
+    ap.add_argument("--lanes", type=int, default=0, help="batched lane width (0 = library default)")
+    ap.add_argument("--lane-order", type=int, default=-1, help="0 = by vertex id, 1 = by hub neighbour")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -193,6 +195,10 @@ def main():
     stream = torch.cuda.Stream(device=local)
     torch.cuda.set_stream(stream)
     eng = binding.PercIS(local)
+    if args.lanes:
+        eng.set_options(lanes=args.lanes)
+    if args.lane_order >= 0:
+        eng.set_options(lane_order=args.lane_order)
     rp_d = torch.as_tensor(g.row_ptr, dtype=torch.int64, device="cuda")
     col_d = torch.as_tensor(g.col, dtype=torch.int32, device="cuda")
     x_d = torch.as_tensor(x, dtype=torch.float64, device="cuda")
@@ -333,7 +339,8 @@ def main():
     if rank == 0:
         i0 = infos[0]
         cfg = dict(WORKLOAD_DESC)
-        cfg.update({"n": g.n, "nnz": g.nnz, "form": "batched", "lanes": i0["lanes"], "ell1": i0["ell1"],
+        cfg.update({"n": g.n, "nnz": g.nnz, "form": "batched", "lanes": i0["lanes"],
+                    "lane_order": ["vertex id", "hub neighbour"][eng.options.lane_order], "ell1": i0["ell1"],
                     "ell_mean": statistics.mean(i["ell"] for i in infos),
                     "distinct_sources_phase2_mean": statistics.mean(i["sources"][1] for i in infos),
                     "vertex_diam": i0["vertex_diam"], "dhat": i0["dhat"],

@@ -67,7 +67,9 @@ typedef struct {
     double timeout_s;         /* budget of every device-side wait (default 10 s) */
     int32_t instrument;       /* 1: batched launches also count their work into percis_info.work
                                  (slower; for measurement runs only) */
-    int32_t reserved;
+    int32_t lane_order;       /* batched lane assignment: 0 = sources by vertex id, 1 (default) =
+                                 sources grouped by their highest-degree neighbour, so that lanes
+                                 with similar BFS levels share 64-bit words and sigma sectors */
 } percis_options;
 
 typedef struct {

@@ -60,6 +60,7 @@ struct percis_ctx {
     int directed = 0;
     percis::DevBuf rp, col, irp, icol;  // irp/icol used only when directed
     int64_t vertex_diam = -1;
+    percis::DevBuf vorder;  // vertices sorted by (highest-degree neighbour, id): lane order of sources
 
     // states and preprocessing
     bool have_states = false;

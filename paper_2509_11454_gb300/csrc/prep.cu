@@ -253,6 +253,26 @@ __global__ void k_edge_keys(const int64_t *rp, const int32_t *col, int64_t n, ui
     }
 }
 
+// key(v) = (highest-degree out-neighbour of v, ties to the smallest id) << 32 | v;
+// vertices without neighbours use themselves.
+__global__ void k_hub_keys(const int64_t *rp, const int32_t *col, int64_t n, uint64_t *keys, int32_t *vals) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        int32_t best = (int32_t)v;
+        int64_t bdeg = -1;
+        for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+            const int32_t u = col[e];
+            const int64_t d = rp[u + 1] - rp[u];
+            if (d > bdeg || (d == bdeg && u < best)) {
+                bdeg = d;
+                best = u;
+            }
+        }
+        keys[v] = ((uint64_t)(uint32_t)best << 32) | (uint32_t)v;
+        vals[v] = (int32_t)v;
+    }
+}
+
 __global__ void k_indeg(const int32_t *col, int64_t nnz, long long *cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
@@ -332,6 +352,29 @@ percis_status prep_graph(percis_ctx *ctx) {
         cudaFree(v2.p);
         if (rs != PERCIS_OK) return rs;
         PERCIS_CUDA(ctx, cudaGetLastError());
+    }
+    {
+        // lane order of batched sources: grouped by highest-degree neighbour
+        PERCIS_TRY(ensure(ctx, ctx->vorder, sizeof(int32_t) * n, "vertex order"));
+        DevBuf k1, k2, v2;
+        cudaError_t e = cudaMalloc(&k1.p, sizeof(uint64_t) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&k2.p, sizeof(uint64_t) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&v2.p, sizeof(int32_t) * n);
+        percis_status rs = PERCIS_OK;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rs = set_err(ctx, PERCIS_E_OOM, "vertex order scratch");
+        } else {
+            k_hub_keys<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                                     n, k1.as<uint64_t>(), ctx->vorder.as<int32_t>());
+            ctx->launches++;
+            rs = merge_sort(ctx, k1.as<uint64_t>(), ctx->vorder.as<int32_t>(), k2.as<uint64_t>(), v2.as<int32_t>(), n);
+        }
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(k1.p);
+        cudaFree(k2.p);
+        cudaFree(v2.p);
+        if (rs != PERCIS_OK) return rs;
     }
     int64_t D = 0;
     PERCIS_TRY(vertex_diam_ub(ctx, &D));

@@ -61,6 +61,18 @@ __global__ void k_head_flags(const long long *src_count, int64_t n, long long *h
         head[v] = src_count[v] > 0 ? 1 : 0;
 }
 
+// Per-vertex quantities permuted into lane order (perm = vorder) and back.
+__global__ void k_gather_ll(const long long *in, const int32_t *perm, int64_t n, long long *out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) out[k] = in[perm[k]];
+}
+
+__global__ void k_scatter_ll(const long long *in, const int32_t *perm, int64_t n, long long *out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) out[perm[k]] = in[k];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = in[n];
+}
+
 __global__ void k_scatter_samples(const int32_t *s, const int32_t *t, const int32_t *kind, int64_t count,
                                   const long long *src_off, const long long *lane_of_v, int32_t *src_fill,
                                   int32_t *sorted_samples, int32_t *samp_t, int32_t *samp_lane) {
@@ -102,8 +114,10 @@ percis_status sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag, int64_t
 }
 
 // Group the valid samples of the last phase (pair_s, pair_t, kind) by source.
-// Lane j (0 <= j < U) is the j-th distinct source in id order; its samples
-// sit at positions lane_off[j] .. lane_off[j+1]-1 of sorted_samples.
+// Lane j (0 <= j < U) is the j-th distinct source in lane order (vertex id
+// order, or the load-time vertex order that groups vertices by their
+// highest-degree neighbour); its samples sit at positions lane_off[j] ..
+// lane_off[j+1]-1 of sorted_samples.
 percis_status group_by_source(percis_ctx *ctx, int64_t count, int64_t *n_sources, int64_t *n_valid) {
     const int64_t n = ctx->n;
     PERCIS_TRY(ensure(ctx, ctx->src_count, sizeof(long long) * (n + 1), "src count"));
@@ -124,14 +138,28 @@ percis_status group_by_source(percis_ctx *ctx, int64_t count, int64_t *n_sources
     k_count_sources<<<grid_for(ctx, count, block), block, 0, ctx->stream>>>(ctx->pair_s.as<int32_t>(),
                                                                           ctx->kind.as<int32_t>(), count, cnt);
     PERCIS_CHECK_LAUNCH(ctx, "count sources");
-    PERCIS_TRY(scan_exclusive_i64(ctx, (const int64_t *)cnt, (int64_t *)off, n));
-    // head flags reuse lane_of_v's storage shifted: compute into src_fill-sized temp via lov then scan in place
-    k_head_flags<<<grid_for(ctx, n, block), block, 0, ctx->stream>>>(cnt, n, lov);
-    PERCIS_CHECK_LAUNCH(ctx, "head flags");
-    PERCIS_TRY(ensure(ctx, ctx->red, sizeof(long long) * (n + 1), "head scan"));
-    PERCIS_TRY(scan_exclusive_i64(ctx, (const int64_t *)lov, ctx->red.as<int64_t>(), n));
-    PERCIS_CUDA(ctx, cudaMemcpyAsync(lov, ctx->red.p, sizeof(long long) * (n + 1), cudaMemcpyDeviceToDevice,
-                                     ctx->stream));
+    PERCIS_TRY(ensure(ctx, ctx->red, sizeof(long long) * (2 * n + 2), "head scan"));
+    long long *tmp = ctx->red.as<long long>();  // n+1 scratch
+    long long *tmp2 = tmp + n + 1;              // n+1 scratch
+    if (ctx->opt.lane_order == 1) {
+        // sources in lane order: offsets and lane ids are scans over vorder
+        const int32_t *perm = ctx->vorder.as<int32_t>();
+        k_gather_ll<<<grid_for(ctx, n, block), block, 0, ctx->stream>>>(cnt, perm, n, tmp2);
+        PERCIS_CHECK_LAUNCH(ctx, "gather counts");
+        PERCIS_TRY(scan_exclusive_i64(ctx, (const int64_t *)tmp2, (int64_t *)tmp, n));
+        k_scatter_ll<<<grid_for(ctx, n, block), block, 0, ctx->stream>>>(tmp, perm, n, off);
+        PERCIS_CHECK_LAUNCH(ctx, "scatter offsets");
+        k_head_flags<<<grid_for(ctx, n, block), block, 0, ctx->stream>>>(tmp2, n, tmp2);
+        PERCIS_CHECK_LAUNCH(ctx, "head flags");
+        PERCIS_TRY(scan_exclusive_i64(ctx, (const int64_t *)tmp2, (int64_t *)tmp, n));
+        k_scatter_ll<<<grid_for(ctx, n, block), block, 0, ctx->stream>>>(tmp, perm, n, lov);
+        PERCIS_CHECK_LAUNCH(ctx, "scatter lanes");
+    } else {
+        PERCIS_TRY(scan_exclusive_i64(ctx, (const int64_t *)cnt, (int64_t *)off, n));
+        k_head_flags<<<grid_for(ctx, n, block), block, 0, ctx->stream>>>(cnt, n, tmp2);
+        PERCIS_CHECK_LAUNCH(ctx, "head flags");
+        PERCIS_TRY(scan_exclusive_i64(ctx, (const int64_t *)tmp2, (int64_t *)lov, n));
+    }
     k_scatter_samples<<<grid_for(ctx, count, block), block, 0, ctx->stream>>>(
         ctx->pair_s.as<int32_t>(), ctx->pair_t.as<int32_t>(), ctx->kind.as<int32_t>(), count, off, lov,
         ctx->src_fill.as<int32_t>(), ctx->sorted_samples.as<int32_t>(), ctx->samp_t.as<int32_t>(),
