@@ -70,6 +70,11 @@ typedef struct {
     int32_t lane_order;       /* batched lane assignment: 0 = sources by vertex id, 1 (default) =
                                  sources grouped by their highest-degree neighbour, so that lanes
                                  with similar BFS levels share 64-bit words and sigma sectors */
+    int32_t direction;        /* batched levels: 0 = pull (each unvisited vertex sums over its
+                                 in-neighbours), 1 = push (each frontier vertex adds its counts to
+                                 its out-neighbours), 2 (default) = push while the frontier's
+                                 out-edges stay below nnz/4, else pull */
+    int32_t reserved;
 } percis_options;
 
 typedef struct {

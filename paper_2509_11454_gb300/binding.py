@@ -37,7 +37,8 @@ class percis_options(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("lanes", ctypes.c_int32), ("ell1", ctypes.c_int64),
                 ("ell", ctypes.c_int64), ("vertex_diam", ctypes.c_int64), ("keep_paths", ctypes.c_int32),
                 ("data_independent", ctypes.c_int32), ("timeout_s", ctypes.c_double),
-                ("instrument", ctypes.c_int32), ("lane_order", ctypes.c_int32)]
+                ("instrument", ctypes.c_int32), ("lane_order", ctypes.c_int32),
+                ("direction", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class percis_info(ctypes.Structure):

@@ -302,6 +302,7 @@ void percis_default_options(percis_options *opt) {
     opt->timeout_s = 10.0;
     opt->instrument = 0;
     opt->lane_order = 1;
+    opt->direction = 2;
 }
 
 percis_status percis_create(percis_ctx **out, int device, void *stream) {
@@ -344,7 +345,8 @@ void percis_destroy(percis_ctx *ctx) {
                       &ctx->ilen, &ctx->path_off, &ctx->arena, &ctx->cnt, &ctx->arena_top, &ctx->src_count,
                       &ctx->src_fill, &ctx->src_off, &ctx->lane_of_v, &ctx->sorted_samples, &ctx->samp_lane,
                       &ctx->samp_t, &ctx->lane_src, &ctx->lane_off, &ctx->scratch, &ctx->red, &ctx->status,
-                      &ctx->pc_tmp, &ctx->grad_tmp, &ctx->host_pinned, &ctx->vorder};
+                      &ctx->pc_tmp, &ctx->grad_tmp, &ctx->host_pinned, &ctx->vorder,
+                      &ctx->fq0, &ctx->fq1, &ctx->qstamp};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->counters.p) cudaFree(ctx->counters.p);
@@ -375,6 +377,7 @@ percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt) {
     if (opt->lanes != 0 && opt->lanes != 64 && opt->lanes != 128 && opt->lanes != 256 && opt->lanes != 512)
         return set_err(ctx, PERCIS_E_INVALID, "lanes must be 0, 64, 128, 256 or 512");
     if (opt->lane_order != 0 && opt->lane_order != 1) return set_err(ctx, PERCIS_E_INVALID, "lane_order must be 0 or 1");
+    if (opt->direction < 0 || opt->direction > 2) return set_err(ctx, PERCIS_E_INVALID, "direction must be 0, 1 or 2");
     if (opt->ell1 < 0 || opt->ell1 == 1 || opt->ell < 0 || !(opt->timeout_s > 0.0))
         return set_err(ctx, PERCIS_E_INVALID, "bad sample sizes or timeout");
     ctx->opt = *opt;

@@ -27,11 +27,11 @@ struct alignas(16) MsCtl {
     uint32_t status;
     uint32_t ticket;
     int32_t level;                // last level reached
-    int32_t done;
-    int32_t pad[2];
+    int32_t push_next;            // direction of the next level (1 = push)
+    int32_t qn[2];                // frontier queue sizes (ping-pong by level parity)
     unsigned long long active[8];    // lanes still running (K <= 8 words)
     unsigned long long nonempty[2][8];  // per-level OR of discovered bits (ping-pong)
-    long long edges_scanned;      // instrumentation
+    unsigned long long fedges[2];    // out-degree sum of the frontier queue (ping-pong)
 };
 
 struct PlainCtl {
@@ -77,6 +77,9 @@ struct percis_ctx {
     int32_t lanes_alloc = 0;
     int32_t levels_alloc = 0;
     bool sigma_fp64 = false;  // batched sigma kept in FP64 (after a count reached 2^53)
+    percis::DevBuf fq0, fq1, qstamp;  // frontier queues and per-vertex level stamps
+    int32_t stamp_base = 1;
+    int64_t max_indeg = 0;
 
     // samples of the last phase
     percis::DevBuf pair_s, pair_t, kind, ilen, path_off, arena, cnt, arena_top;

@@ -64,6 +64,15 @@ struct MsArgs {
     unsigned long long *cnt;
     int32_t full;
     uint64_t budget_ns;
+    // push levels: out-adjacency, frontier queues, level stamps
+    const int32_t *col;
+    int32_t *fq0;
+    int32_t *fq1;
+    int32_t *qstamp;
+    int32_t stamp_base;
+    int32_t policy;                   // 0 = pull every level, 1 = push every level, 2 = by frontier size
+    unsigned long long push_edges;    // policy 2: push while the frontier's out-edges stay below this
+    unsigned long long wrap_guard;    // a pushed count >= this could wrap 2^64 at a high in-degree vertex
     // instrumentation (INSTR variant only)
     const int64_t *rp;                // out-CSR offsets (out-degrees)
     unsigned long long *counters;     // 8 work counters (see percis_info.work)
@@ -115,10 +124,17 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     const long long p0 = a.full ? 0 : a.lane_off[a.lane_base];
     const long long p1 = a.full ? 0 : a.lane_off[a.lane_base + a.nlanes];
 
-    // ---- prologue: clear visited and level-0 frontier, reset lane state
+    // ---- prologue: clear visited, frontiers 0 and 1, (push) sigma; reset lane state
     for (int64_t i = tid; i < nk; i += nthreads) {
         a.vis[i] = 0ull;
         a.fh[i] = 0ull;
+        a.fh[nk + i] = 0ull;
+    }
+    if (a.policy != 0) {
+        // pushes accumulate into sigma, so every count starts at zero
+        ulonglong2 *s2 = reinterpret_cast<ulonglong2 *>(a.sigma);
+        const int64_t n2 = n * (int64_t)W / 2;
+        for (int64_t i = tid; i < n2; i += nthreads) s2[i] = make_ulonglong2(0ull, 0ull);
     }
     for (long long p = p0 + tid; p < p1; p += nthreads) a.found[p] = -1;
     if (INSTR)
@@ -135,6 +151,9 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         if (threadIdx.x == 0) {
             ctl->ticket = 0;
             ctl->level = 0;
+            ctl->qn[0] = a.nlanes;
+            ctl->qn[1] = 0;
+            ctl->push_next = a.policy != 0;
         }
     }
     if (!grid_sync(bar, status, a.budget_ns)) return;
@@ -144,6 +163,8 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         atomicOr((unsigned long long *)&a.vis[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         atomicOr((unsigned long long *)&a.fh[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         sig[(int64_t)v * W + j] = S(1);
+        a.fq0[j] = v;
+        a.qstamp[v] = a.stamp_base;
         if (INSTR) a.levdeg[(int64_t)j * (a.Lcap + 1)] = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
         if (!a.full) {
             const long long q0 = a.lane_off[a.lane_base + j], q1 = a.lane_off[a.lane_base + j + 1];
@@ -167,99 +188,194 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         __syncthreads();
         const uint64_t *fcur = a.fh + (int64_t)L * nk;
         uint64_t *fnext = a.fh + (int64_t)(L + 1) * nk;
+        const int32_t *qcur = (L & 1) ? a.fq1 : a.fq0;
+        int32_t *qnext = (L & 1) ? a.fq0 : a.fq1;
+        int32_t *qn_next = &ctl->qn[(L + 1) & 1];
+        const int32_t stamp_next = a.stamp_base + L + 1;
+        const bool push = ld_relaxed_u32((const uint32_t *)&ctl->push_next) != 0u;
 
-        // ---- phase A: pull pass, one warp per (vertex, lane word) item
-        for (int64_t it = gwarp; it < nk; it += nwarps) {
-            const int64_t v = it / K;
-            const int w = (int)(it - v * K);
-            const uint64_t vw = __ldcg(&a.vis[it]);
-            const uint64_t cw = s_act[w] & ~vw;
-            if (cw == 0ull) {
-                if (lane == 0) fnext[it] = 0ull;
-                continue;
-            }
-            uint64_t nbp = 0ull;
-            S acc0 = S(0), acc1 = S(0);
-            const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
-            for (int64_t base = e0; base < e1; base += 32) {
-                const int64_t e = base + lane;
-                int32_t u = 0;
-                uint64_t fw = 0ull;
-                if (e < e1) {
-                    u = a.icol[e];
-                    fw = __ldcg(&fcur[(int64_t)u * K + w]) & cw;
-                }
-                nbp |= fw;
-                if (INSTR) n_sload += (unsigned long long)__popcll(fw);
-                unsigned nz = __ballot_sync(0xffffffffu, fw != 0ull);
-                while (nz) {
-                    // up to four parents per round so their sigma loads overlap
-                    const int j0 = __ffs(nz) - 1;
-                    nz &= nz - 1;
-                    const bool h1 = nz != 0u;
-                    const int j1 = h1 ? __ffs(nz) - 1 : j0;
-                    if (h1) nz &= nz - 1;
-                    const bool h2 = nz != 0u;
-                    const int j2 = h2 ? __ffs(nz) - 1 : j0;
-                    if (h2) nz &= nz - 1;
-                    const bool h3 = nz != 0u;
-                    const int j3 = h3 ? __ffs(nz) - 1 : j0;
-                    if (h3) nz &= nz - 1;
-                    const uint64_t f0 = shfl64(fw, j0);
-                    const uint64_t f1 = h1 ? shfl64(fw, j1) : 0ull;
-                    const uint64_t f2 = h2 ? shfl64(fw, j2) : 0ull;
-                    const uint64_t f3 = h3 ? shfl64(fw, j3) : 0ull;
-                    const S *r0 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j0) * W + 64 * w;
-                    const S *r1 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j1) * W + 64 * w;
-                    const S *r2 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j2) * W + 64 * w;
-                    const S *r3 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j3) * W + 64 * w;
-                    S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0), b0 = S(0), b1 = S(0), b2 = S(0), b3 = S(0);
-                    if ((f0 >> lane) & 1ull) a0 = __ldcg(r0 + lane);
-                    if ((f1 >> lane) & 1ull) a1 = __ldcg(r1 + lane);
-                    if ((f2 >> lane) & 1ull) a2 = __ldcg(r2 + lane);
-                    if ((f3 >> lane) & 1ull) a3 = __ldcg(r3 + lane);
-                    if ((f0 >> (lane + 32)) & 1ull) b0 = __ldcg(r0 + lane + 32);
-                    if ((f1 >> (lane + 32)) & 1ull) b1 = __ldcg(r1 + lane + 32);
-                    if ((f2 >> (lane + 32)) & 1ull) b2 = __ldcg(r2 + lane + 32);
-                    if ((f3 >> (lane + 32)) & 1ull) b3 = __ldcg(r3 + lane + 32);
-                    if (FPSIG) {
-                        // keep the in-adjacency order of the additions
-                        acc0 += a0; acc0 += a1; acc0 += a2; acc0 += a3;
-                        acc1 += b0; acc1 += b1; acc1 += b2; acc1 += b3;
-                    } else {
-                        acc0 += (a0 + a1) + (a2 + a3);
-                        acc1 += (b0 + b1) + (b2 + b3);
+        if (push) {
+            // ---- phase A (push): one warp per (frontier vertex, lane word); the
+            // parent's counts are loaded once and added to every unvisited
+            // out-neighbour with fire-and-forget reductions.
+            const int64_t qn = (int64_t)ld_relaxed_u32((const uint32_t *)&ctl->qn[L & 1]);
+            for (int64_t it = gwarp; it < qn * K; it += nwarps) {
+                const int64_t k = it / K;
+                const int w = (int)(it - k * K);
+                const int32_t u = __ldcg(&qcur[k]);
+                const uint64_t fu = __ldcg(&fcur[(int64_t)u * K + w]) & s_act[w];
+                if (fu == 0ull) continue;
+                const S *urow = sig + (int64_t)u * W + 64 * w;
+                const S su0 = ((fu >> lane) & 1ull) ? __ldcg(urow + lane) : S(0);
+                const S su1 = ((fu >> (lane + 32)) & 1ull) ? __ldcg(urow + lane + 32) : S(0);
+                if (!FPSIG) ovf |= (su0 >= (S)a.wrap_guard) | (su1 >= (S)a.wrap_guard);
+                const int64_t e0 = a.rp[u], e1 = a.rp[u + 1];
+                for (int64_t base = e0; base < e1; base += 32) {
+                    const int64_t e = base + lane;
+                    int32_t v = 0;
+                    uint64_t m = 0ull;
+                    if (e < e1) {
+                        v = a.col[e];
+                        m = fu & ~__ldcg(&a.vis[(int64_t)v * K + w]);
                     }
-                    // integer mode: flag before four more addends could wrap 2^64
-                    if (!FPSIG) ovf |= (acc0 >= S(kTwo53)) | (acc1 >= S(kTwo53));
+                    bool app = false;
+                    if (m) {
+                        const unsigned long long old =
+                            atomicOr((unsigned long long *)&fnext[(int64_t)v * K + w], (unsigned long long)m);
+                        if (old == 0ull) app = atomicMax(&a.qstamp[v], stamp_next) < stamp_next;
+                    }
+                    const unsigned am = __ballot_sync(0xffffffffu, app);
+                    if (am) {
+                        const int leader = __ffs(am) - 1;
+                        int pos = 0;
+                        if (lane == leader) pos = atomicAdd(qn_next, __popc(am));
+                        pos = __shfl_sync(0xffffffffu, pos, leader);
+                        if (app) qnext[pos + __popc(am & ((1u << lane) - 1u))] = v;
+                    }
+                    if (INSTR) n_sload += (unsigned long long)__popcll(m);
+                    unsigned nz = __ballot_sync(0xffffffffu, m != 0ull);
+                    while (nz) {
+                        const int j = __ffs(nz) - 1;
+                        nz &= nz - 1;
+                        const uint64_t mj = shfl64(m, j);
+                        S *vrow = sig + (int64_t)__shfl_sync(0xffffffffu, v, j) * W + 64 * w;
+                        if ((mj >> lane) & 1ull) atomicAdd(vrow + lane, su0);
+                        if ((mj >> (lane + 32)) & 1ull) atomicAdd(vrow + lane + 32, su1);
+                    }
                 }
             }
-            const uint64_t nb = warp_or64(nbp);
-            if (lane == 0) {
-                fnext[it] = nb;
+        } else {
+            // ---- phase A (pull): one warp per (vertex, lane word) item
+            for (int64_t it = gwarp; it < nk; it += nwarps) {
+                const int64_t v = it / K;
+                const int w = (int)(it - v * K);
+                const uint64_t vw = __ldcg(&a.vis[it]);
+                const uint64_t cw = s_act[w] & ~vw;
+                if (cw == 0ull) {
+                    if (lane == 0) fnext[it] = 0ull;
+                    continue;
+                }
+                uint64_t nbp = 0ull;
+                S acc0 = S(0), acc1 = S(0);
+                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+                for (int64_t base = e0; base < e1; base += 32) {
+                    const int64_t e = base + lane;
+                    int32_t u = 0;
+                    uint64_t fw = 0ull;
+                    if (e < e1) {
+                        u = a.icol[e];
+                        fw = __ldcg(&fcur[(int64_t)u * K + w]) & cw;
+                    }
+                    nbp |= fw;
+                    if (INSTR) n_sload += (unsigned long long)__popcll(fw);
+                    unsigned nz = __ballot_sync(0xffffffffu, fw != 0ull);
+                    while (nz) {
+                        // up to four parents per round so their count loads overlap
+                        const int j0 = __ffs(nz) - 1;
+                        nz &= nz - 1;
+                        const bool h1 = nz != 0u;
+                        const int j1 = h1 ? __ffs(nz) - 1 : j0;
+                        if (h1) nz &= nz - 1;
+                        const bool h2 = nz != 0u;
+                        const int j2 = h2 ? __ffs(nz) - 1 : j0;
+                        if (h2) nz &= nz - 1;
+                        const bool h3 = nz != 0u;
+                        const int j3 = h3 ? __ffs(nz) - 1 : j0;
+                        if (h3) nz &= nz - 1;
+                        const uint64_t f0 = shfl64(fw, j0);
+                        const uint64_t f1 = h1 ? shfl64(fw, j1) : 0ull;
+                        const uint64_t f2 = h2 ? shfl64(fw, j2) : 0ull;
+                        const uint64_t f3 = h3 ? shfl64(fw, j3) : 0ull;
+                        const S *r0 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j0) * W + 64 * w;
+                        const S *r1 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j1) * W + 64 * w;
+                        const S *r2 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j2) * W + 64 * w;
+                        const S *r3 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j3) * W + 64 * w;
+                        S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0), b0 = S(0), b1 = S(0), b2 = S(0), b3 = S(0);
+                        if ((f0 >> lane) & 1ull) a0 = __ldcg(r0 + lane);
+                        if ((f1 >> lane) & 1ull) a1 = __ldcg(r1 + lane);
+                        if ((f2 >> lane) & 1ull) a2 = __ldcg(r2 + lane);
+                        if ((f3 >> lane) & 1ull) a3 = __ldcg(r3 + lane);
+                        if ((f0 >> (lane + 32)) & 1ull) b0 = __ldcg(r0 + lane + 32);
+                        if ((f1 >> (lane + 32)) & 1ull) b1 = __ldcg(r1 + lane + 32);
+                        if ((f2 >> (lane + 32)) & 1ull) b2 = __ldcg(r2 + lane + 32);
+                        if ((f3 >> (lane + 32)) & 1ull) b3 = __ldcg(r3 + lane + 32);
+                        if (FPSIG) {
+                            // keep the in-adjacency order of the additions
+                            acc0 += a0; acc0 += a1; acc0 += a2; acc0 += a3;
+                            acc1 += b0; acc1 += b1; acc1 += b2; acc1 += b3;
+                        } else {
+                            acc0 += (a0 + a1) + (a2 + a3);
+                            acc1 += (b0 + b1) + (b2 + b3);
+                            // flag before four more addends could wrap 2^64
+                            ovf |= (acc0 >= S(kTwo53)) | (acc1 >= S(kTwo53));
+                        }
+                    }
+                }
+                const uint64_t nb = warp_or64(nbp);
+                bool app = false;
+                if (lane == 0) {
+                    fnext[it] = nb;
+                    if (nb) app = atomicMax(&a.qstamp[v], stamp_next) < stamp_next;
+                }
+                if (app) qnext[atomicAdd(qn_next, 1)] = (int32_t)v;
                 if (nb) {
-                    a.vis[it] = vw | nb;
-                    atomicOr(&s_nonempty[w], (unsigned long long)nb);
+                    S *drow = sig + v * W + 64 * w;
+                    if ((nb >> lane) & 1ull) drow[lane] = acc0;
+                    if ((nb >> (lane + 32)) & 1ull) drow[lane + 32] = acc1;
                 }
             }
-            if (nb) {
-                S *drow = sig + v * W + 64 * w;
-                if ((nb >> lane) & 1ull) {
-                    drow[lane] = acc0;
-                    if (FPSIG && acc0 >= S(kTwo53)) ovf = true;
+        }
+        if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, DEV_SIGMA_OVERFLOW);
+        ovf = false;
+        if (!grid_sync(bar, status, a.budget_ns)) return;
+
+        // ---- phase B (1): settle the new frontier: visited bits, nonempty lanes,
+        // final counts checked against 2^53, next frontier's out-edges
+        {
+            const int64_t qn1 = (int64_t)ld_relaxed_u32((const uint32_t *)qn_next);
+            unsigned long long fe = 0ull;
+            for (int64_t it = tid; it < qn1 * K; it += nthreads) {
+                const int64_t k = it / K;
+                const int w = (int)(it - k * K);
+                const int32_t v = __ldcg(&qnext[k]);
+                const uint64_t nb = __ldcg(&fnext[(int64_t)v * K + w]);
+                if (!nb) continue;
+                a.vis[(int64_t)v * K + w] = __ldcg(&a.vis[(int64_t)v * K + w]) | nb;
+                atomicOr(&s_nonempty[w], (unsigned long long)nb);
+                if (w == 0) {
+                    fe += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
+                    if (INSTR) {
+                        n_uv += 1;
+                        n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
+                    }
                 }
-                if ((nb >> (lane + 32)) & 1ull) {
-                    drow[lane + 32] = acc1;
-                    if (FPSIG && acc1 >= S(kTwo53)) ovf = true;
+                if (push) {
+                    // pushed counts are complete only now: check them against 2^53
+                    uint64_t mm = nb;
+                    const S *vrow = sig + (int64_t)v * W + 64 * w;
+                    while (mm) {
+                        const int b = __ffsll((long long)mm) - 1;
+                        mm &= mm - 1;
+                        if (__ldcg(vrow + b) >= S(kTwo53)) ovf = true;
+                    }
                 }
                 if (INSTR) {
-                    if (lane == 0) n_swrite += (unsigned long long)__popcll(nb);
+                    n_swrite += (unsigned long long)__popcll(nb);
                     const unsigned long long dg = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
-                    if ((nb >> lane) & 1ull)
-                        atomicAdd(&a.levdeg[(int64_t)(64 * w + lane) * (a.Lcap + 1) + L + 1], dg);
-                    if ((nb >> (lane + 32)) & 1ull)
-                        atomicAdd(&a.levdeg[(int64_t)(64 * w + lane + 32) * (a.Lcap + 1) + L + 1], dg);
+                    uint64_t m2 = nb;
+                    while (m2) {
+                        const int b = __ffsll((long long)m2) - 1;
+                        m2 &= m2 - 1;
+                        atomicAdd(&a.levdeg[(int64_t)(64 * w + b) * (a.Lcap + 1) + L + 1], dg);
+                    }
                 }
+            }
+            // frontier out-edges for the direction choice
+            for (int off = 16; off > 0; off >>= 1) fe += __shfl_xor_sync(0xffffffffu, fe, off);
+            if (lane == 0 && fe) atomicAdd(&ctl->fedges[(L + 1) & 1], fe);
+            if (L + 2 <= a.Lcap) {
+                uint64_t *f2 = a.fh + (int64_t)(L + 2) * nk;
+                for (int64_t i = tid; i < nk; i += nthreads) f2[i] = 0ull;
             }
         }
         if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, DEV_SIGMA_OVERFLOW);
@@ -267,20 +383,6 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         __syncthreads();
         if (threadIdx.x < K && s_nonempty[threadIdx.x])
             atomicOr(&ctl->nonempty[L & 1][threadIdx.x], s_nonempty[threadIdx.x]);
-        if (!grid_sync(bar, status, a.budget_ns)) return;
-
-        if (INSTR) {
-            // union frontier of the new level: adjacency rows and entries a
-            // top-down expansion of it needs
-            for (int64_t v = tid; v < n; v += nthreads) {
-                bool any = false;
-                for (int w = 0; w < K; ++w) any |= __ldcg(&fnext[v * K + w]) != 0ull;
-                if (any) {
-                    n_uv += 1;
-                    n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
-                }
-            }
-        }
 
         // ---- phase B: mark settled targets, then the last block retires lanes
         if (!a.full) {
@@ -288,7 +390,8 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 if (a.found[p] >= 0) continue;
                 const int32_t j = a.samp_lane[p] - a.lane_base;
                 const int32_t t = a.samp_t[p];
-                if ((__ldcg(&a.vis[(int64_t)t * K + (j >> 6)]) >> (j & 63)) & 1ull) {
+                const int64_t q = (int64_t)t * K + (j >> 6);
+                if (((__ldcg(&a.vis[q]) | __ldcg(&fnext[q])) >> (j & 63)) & 1ull) {
                     a.found[p] = L + 1;
                     atomicSub(&a.remaining[j], 1);
                 }
@@ -320,6 +423,10 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             if (threadIdx.x == 0) {
                 ctl->ticket = 0;
                 ctl->level = L + 1;
+                ctl->qn[L & 1] = 0;  // the queue just consumed is refilled at level L+2
+                const unsigned long long fe = ctl->fedges[(L + 1) & 1];
+                ctl->fedges[L & 1] = 0ull;
+                ctl->push_next = a.policy == 1 || (a.policy == 2 && fe < a.push_edges);
             }
         }
         if (!grid_sync(bar, status, a.budget_ns)) return;
@@ -499,6 +606,14 @@ percis_status launch_ms_k(percis_ctx *ctx, int K, MsArgs &a) {
 percis_status ensure_ms(percis_ctx *ctx, int W, int Lcap) {
     const int64_t n = ctx->n;
     const int K = W / 64;
+    const bool fresh_stamps = ctx->qstamp.bytes < sizeof(int32_t) * (size_t)n;
+    PERCIS_TRY(ensure(ctx, ctx->fq0, sizeof(int32_t) * n, "frontier queue"));
+    PERCIS_TRY(ensure(ctx, ctx->fq1, sizeof(int32_t) * n, "frontier queue"));
+    PERCIS_TRY(ensure(ctx, ctx->qstamp, sizeof(int32_t) * n, "level stamps"));
+    if (fresh_stamps || ctx->stamp_base > (1 << 30)) {
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->qstamp.p, 0, sizeof(int32_t) * n, ctx->stream));
+        ctx->stamp_base = 1;
+    }
     PERCIS_TRY(ensure(ctx, ctx->vis, sizeof(uint64_t) * n * K, "visited bits"));
     PERCIS_TRY(ensure(ctx, ctx->fhist, sizeof(uint64_t) * n * K * (int64_t)(Lcap + 1), "frontier history"));
     PERCIS_TRY(ensure(ctx, ctx->sigmaW, sizeof(double) * n * W, "lane sigma"));
@@ -518,8 +633,22 @@ void fill_common(percis_ctx *ctx, MsArgs &a, int Lcap) {
     a.Lcap = Lcap;
     a.budget_ns = (uint64_t)(ctx->opt.timeout_s * 1e9);
     a.rp = ctx->rp.as<int64_t>();
+    a.col = ctx->col.as<int32_t>();
     a.counters = nullptr;
     a.levdeg = nullptr;
+    a.fq0 = ctx->fq0.as<int32_t>();
+    a.fq1 = ctx->fq1.as<int32_t>();
+    a.qstamp = ctx->qstamp.as<int32_t>();
+    a.policy = ctx->opt.direction;
+    a.push_edges = (unsigned long long)std::max<int64_t>(ctx->nnz / 4, 1);
+    // no vertex has more than max_indeg parents: counts below 2^63 / max_indeg cannot wrap 2^64
+    a.wrap_guard = (unsigned long long)(9223372036854775807LL / std::max<int64_t>(ctx->max_indeg, 1));
+}
+
+// Each launch stamps its levels with fresh values, so the stamps never need clearing.
+void next_stamps(percis_ctx *ctx, MsArgs &a) {
+    a.stamp_base = ctx->stamp_base;
+    ctx->stamp_base += a.Lcap + 2;
 }
 
 }  // namespace
@@ -579,6 +708,7 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
         a.nlanes = (int32_t)std::min<int64_t>(W, n_sources - b * W);
         cudaEvent_t e0 = next_event(ctx), e1 = next_event(ctx);
         if (e0) cudaEventRecord(e0, ctx->stream);
+        next_stamps(ctx, a);
         PERCIS_TRY(launch_ms_k(ctx, K, a));
         if (e1) cudaEventRecord(e1, ctx->stream);
     }
@@ -603,6 +733,7 @@ percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, 
         a.nlanes = nsrc;
         a.remaining = ctx->remaining.as<int32_t>();
         a.full = 1;
+        next_stamps(ctx, a);
         PERCIS_TRY(launch_ms_k(ctx, K, a));
         MsCtl hc;
         PERCIS_CUDA(ctx, cudaMemcpyAsync(&hc, ctx->ms_ctl.p, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));

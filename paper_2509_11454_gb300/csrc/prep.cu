@@ -273,6 +273,20 @@ __global__ void k_hub_keys(const int64_t *rp, const int32_t *col, int64_t n, uin
     }
 }
 
+__global__ void k_max_rowlen(const int64_t *rp, int64_t n, unsigned long long *out) {
+    unsigned long long m = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long d = (unsigned long long)(rp[v + 1] - rp[v]);
+        m = m > d ? m : d;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+        m = m > o ? m : o;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 __global__ void k_indeg(const int32_t *col, int64_t nnz, long long *cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
@@ -375,6 +389,16 @@ percis_status prep_graph(percis_ctx *ctx) {
         cudaFree(k2.p);
         cudaFree(v2.p);
         if (rs != PERCIS_OK) return rs;
+    }
+    {
+        const int64_t *irp = ctx->directed ? ctx->irp.as<int64_t>() : ctx->rp.as<int64_t>();
+        PERCIS_CUDA(ctx, cudaMemsetAsync(st, 0, 64, ctx->stream));
+        k_max_rowlen<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(irp, n, (unsigned long long *)st);
+        PERCIS_CHECK_LAUNCH(ctx, "max in-degree");
+        unsigned long long md = 0;
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(&md, st, sizeof(md), cudaMemcpyDeviceToHost, ctx->stream));
+        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx->max_indeg = (int64_t)md;
     }
     int64_t D = 0;
     PERCIS_TRY(vertex_diam_ub(ctx, &D));

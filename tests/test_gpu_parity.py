@@ -118,10 +118,11 @@ def test_plain_bfs_bitexact(binding, gcase):
     eng.close()
 
 
+@pytest.mark.parametrize("direction", [0, 1, 2])
 @pytest.mark.parametrize("nsrc", [1, 5, 64, 100, 200, 512])
-def test_msbfs_bitexact(binding, gcase, nsrc):
+def test_msbfs_bitexact(binding, gcase, nsrc, direction):
     name, g, og = gcase
-    eng = _engine(binding, g)
+    eng = _engine(binding, g, direction=direction)
     rng = np.random.default_rng(nsrc)
     srcs = rng.choice(g.n, size=nsrc, replace=False)
     dist, sig = eng.msbfs(srcs)
@@ -134,12 +135,12 @@ def test_msbfs_bitexact(binding, gcase, nsrc):
     eng.close()
 
 
-@pytest.mark.parametrize("form", ["batched", "plain"])
-def test_phase_bitexact(binding, gcase, form):
+@pytest.mark.parametrize("form,direction", [("batched", 0), ("batched", 1), ("batched", 2), ("plain", 2)])
+def test_phase_bitexact(binding, gcase, form, direction):
     name, g, og = gcase
     x = _states(name, g.n)
     count = 600 if form == "plain" else 3000
-    eng = _engine(binding, g, x, form=form)
+    eng = _engine(binding, g, x, form=form, direction=direction)
     prep = oracle.prepare(x)
     got = eng.run_phase(seed=11, phase=1, count=count)
     ph = oracle.run_samples(og, prep, 11, 1, 3, 0, count, keep_paths=True)
