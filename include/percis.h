@@ -214,6 +214,12 @@ percis_status percis_msbfs(percis_ctx *ctx, int32_t nsrc, const int32_t *sources
 percis_status percis_run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count, int32_t *s, int32_t *t,
                                int32_t *kind, int32_t *ilen, int64_t *cnt);
 
+/* Per-level profile of the last batched launch (measurement aid).  For each
+ * level L < min(cap, 32) writes four int64 to out[4L..4L+3]: device time from
+ * the launch's first level to the end of level L (ns), direction (1 = push),
+ * frontier queue size, frontier out-edges.  Returns the number of levels. */
+int64_t percis_last_levels(percis_ctx *ctx, int64_t *out, int64_t cap);
+
 /* Internal nodes of the paths of the last sampling phase, t-side first.
  * Device outputs: path_ptr int64[count+1], path_nodes int32[path_ptr[count]]
  * (pass path_nodes = NULL to size it first; *total receives the total). */

@@ -88,6 +88,7 @@ SIGNATURES = {
     "percis_msbfs": (_ST, [_P, _I32, _P, _P, _P]),
     "percis_run_phase": (_ST, [_P, _U64, ctypes.c_int, _I64, _P, _P, _P, _P, _P]),
     "percis_get_paths": (_ST, [_P, _P, _P, _P]),
+    "percis_last_levels": (_I64, [_P, _P, _I64]),
 }
 
 _lib = None
@@ -223,6 +224,12 @@ def percis_get_paths(ctx, path_ptr=None, path_nodes=None) -> int:
     tot = ctypes.c_int64()
     _check(ctx, load_library().percis_get_paths(ctx, _ptr(path_ptr), _ptr(path_nodes), ctypes.byref(tot)))
     return tot.value
+
+
+def percis_last_levels(ctx, cap: int = 32) -> list[tuple[int, int, int, int]]:
+    out = np.zeros(4 * cap, dtype=np.int64)
+    k = int(load_library().percis_last_levels(ctx, out.ctypes.data, cap))
+    return [tuple(int(v) for v in out[4 * i:4 * i + 4]) for i in range(k)]
 
 
 # ------------------------------------------------------ torch-facing engine

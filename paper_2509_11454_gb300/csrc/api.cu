@@ -638,6 +638,21 @@ percis_status percis_run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_
     return PERCIS_OK;
 }
 
+int64_t percis_last_levels(percis_ctx *ctx, int64_t *out, int64_t cap) {
+    if (!ctx || !ctx->ms_ctl.p || !out) return 0;
+    DeviceGuard g(ctx->device);
+    MsCtl hc;
+    if (cudaMemcpyAsync(&hc, ctx->ms_ctl.p, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int64_t lv = std::min<int64_t>(std::min<int64_t>(hc.level, 32), cap);
+    for (int64_t L = 0; L < lv; ++L)
+        for (int k = 0; k < 4; ++k) out[4 * L + k] = (int64_t)hc.lvl_rec[L][k];
+    return lv;
+}
+
 percis_status percis_get_paths(percis_ctx *ctx, int64_t *path_ptr, int32_t *path_nodes, int64_t *total) {
     PERCIS_TRY(need_states(ctx));
     if (!ctx->have_paths) return set_err(ctx, PERCIS_E_NO_SAMPLE, "no sampling phase yet");

@@ -32,6 +32,8 @@ struct alignas(16) MsCtl {
     unsigned long long active[8];    // lanes still running (K <= 8 words)
     unsigned long long nonempty[2][8];  // per-level OR of discovered bits (ping-pong)
     unsigned long long fedges[2];    // out-degree sum of the frontier queue (ping-pong)
+    unsigned long long t_start;      // globaltimer at the first level
+    unsigned long long lvl_rec[32][4];  // per level: end time, direction, queue size, out-edges
 };
 
 struct PlainCtl {

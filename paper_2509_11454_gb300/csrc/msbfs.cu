@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             ctl->qn[0] = a.nlanes;
             ctl->qn[1] = 0;
             ctl->push_next = a.policy != 0;
+            ctl->t_start = globaltimer_ns();
         }
     }
     if (!grid_sync(bar, status, a.budget_ns)) return;
@@ -218,20 +219,8 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                         v = a.col[e];
                         m = fu & ~__ldcg(&a.vis[(int64_t)v * K + w]);
                     }
-                    bool app = false;
-                    if (m) {
-                        const unsigned long long old =
-                            atomicOr((unsigned long long *)&fnext[(int64_t)v * K + w], (unsigned long long)m);
-                        if (old == 0ull) app = atomicMax(&a.qstamp[v], stamp_next) < stamp_next;
-                    }
-                    const unsigned am = __ballot_sync(0xffffffffu, app);
-                    if (am) {
-                        const int leader = __ffs(am) - 1;
-                        int pos = 0;
-                        if (lane == leader) pos = atomicAdd(qn_next, __popc(am));
-                        pos = __shfl_sync(0xffffffffu, pos, leader);
-                        if (app) qnext[pos + __popc(am & ((1u << lane) - 1u))] = v;
-                    }
+                    // fire-and-forget: the new frontier is collected in phase B
+                    if (m) atomicOr((unsigned long long *)&fnext[(int64_t)v * K + w], (unsigned long long)m);
                     if (INSTR) n_sload += (unsigned long long)__popcll(m);
                     unsigned nz = __ballot_sync(0xffffffffu, m != 0ull);
                     while (nz) {
@@ -329,6 +318,34 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         ovf = false;
         if (!grid_sync(bar, status, a.budget_ns)) return;
 
+        if (push) {
+            // collect the vertices that gained frontier bits into the next queue
+            // (warp-aggregated appends; each vertex is looked at by one thread)
+            for (int64_t vb = gwarp * 32; vb < n; vb += nwarps * 32) {
+                const int64_t v = vb + lane;
+                bool any = false;
+                if (v < n) {
+                    if (K == 1) {
+                        any = __ldcg(&fnext[v]) != 0ull;
+                    } else {
+                        uint64_t f[K];
+                        load_words<K>(fnext + v * K, f);
+#pragma unroll
+                        for (int w = 0; w < K; ++w) any |= f[w] != 0ull;
+                    }
+                }
+                const unsigned am = __ballot_sync(0xffffffffu, any);
+                if (am) {
+                    const int leader = __ffs(am) - 1;
+                    int pos = 0;
+                    if (lane == leader) pos = atomicAdd(qn_next, __popc(am));
+                    pos = __shfl_sync(0xffffffffu, pos, leader);
+                    if (any) qnext[pos + __popc(am & ((1u << lane) - 1u))] = (int32_t)v;
+                }
+            }
+            if (!grid_sync(bar, status, a.budget_ns)) return;
+        }
+
         // ---- phase B (1): settle the new frontier: visited bits, nonempty lanes,
         // final counts checked against 2^53, next frontier's out-edges
         {
@@ -423,6 +440,12 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             if (threadIdx.x == 0) {
                 ctl->ticket = 0;
                 ctl->level = L + 1;
+                if (L < 32) {
+                    ctl->lvl_rec[L][0] = globaltimer_ns() - ctl->t_start;
+                    ctl->lvl_rec[L][1] = push ? 1ull : 0ull;
+                    ctl->lvl_rec[L][2] = (unsigned long long)ctl->qn[L & 1];
+                    ctl->lvl_rec[L][3] = ctl->fedges[L & 1];
+                }
                 ctl->qn[L & 1] = 0;  // the queue just consumed is refilled at level L+2
                 const unsigned long long fe = ctl->fedges[(L + 1) & 1];
                 ctl->fedges[L & 1] = 0ull;
