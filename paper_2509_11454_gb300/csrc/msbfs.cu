@@ -93,28 +93,6 @@ __device__ __forceinline__ void load_words(const uint64_t *p, uint64_t (&out)[K]
     }
 }
 
-// Position of the nth (0-based) set bit of m; m must have more than nth bits set.
-__device__ __forceinline__ int select_bit64(uint64_t m, int nth) {
-    int pos = 0;
-    uint32_t x = (uint32_t)m;
-    int c = __popc(x);
-    if (nth >= c) {
-        nth -= c;
-        pos = 32;
-        x = (uint32_t)(m >> 32);
-    }
-    c = __popc(x & 0xffffu);
-    if (nth >= c) { nth -= c; pos += 16; x >>= 16; }
-    c = __popc(x & 0xffu);
-    if (nth >= c) { nth -= c; pos += 8; x >>= 8; }
-    c = __popc(x & 0xfu);
-    if (nth >= c) { nth -= c; pos += 4; x >>= 4; }
-    c = __popc(x & 0x3u);
-    if (nth >= c) { nth -= c; pos += 2; x >>= 2; }
-    if (nth >= (int)(x & 1u)) pos += 1;
-    return pos;
-}
-
 template <class S>
 __device__ __forceinline__ S warp_incl_scan(S v) {
     const int lane = threadIdx.x & 31;
@@ -198,11 +176,6 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
 
     __shared__ unsigned long long s_nonempty[K];
     __shared__ unsigned long long s_act[K];
-    // per-warp lane accumulators of the flattened integer gather
-    __shared__ unsigned long long s_acc[kMsBlock / 32][64];
-    unsigned long long *wacc = s_acc[threadIdx.x >> 5];
-    wacc[lane] = 0ull;
-    wacc[lane + 32] = 0ull;
     int L = 0;
     for (;;) {
         bool any_act = false;
@@ -284,37 +257,6 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                     }
                     nbp |= fw;
                     if (INSTR) n_sload += (unsigned long long)__popcll(fw);
-                    if (!FPSIG) {
-                        // flattened gather: every (parent, lane) pair of this chunk gets
-                        // one thread, so each round issues up to 32 independent loads;
-                        // per-lane sums go to the warp's shared accumulators (exact
-                        // integer adds, any order)
-                        const int cnt = __popcll(fw);
-                        const int incl = warp_incl_scan<int>(cnt);
-                        const int excl = incl - cnt;
-                        const int total = __shfl_sync(0xffffffffu, incl, 31);
-                        for (int r0 = 0; r0 < total; r0 += 32) {
-                            const int rr = r0 + lane;
-                            // owner: the last lane whose exclusive prefix is <= rr
-                            int k = 0;
-#pragma unroll
-                            for (int step = 16; step > 0; step >>= 1) {
-                                const int e2 = __shfl_sync(0xffffffffu, excl, k + step);
-                                if (e2 <= rr) k += step;
-                            }
-                            const uint64_t fk = shfl64(fw, k);
-                            const int32_t uk = __shfl_sync(0xffffffffu, u, k);
-                            const int ek = __shfl_sync(0xffffffffu, excl, k);
-                            if (rr < total) {
-                                const int j = select_bit64(fk, rr - ek);
-                                const unsigned long long val =
-                                    __ldcg((const unsigned long long *)(sig + (int64_t)uk * W + 64 * w + j));
-                                atomicAdd(&wacc[j], val);
-                                ovf |= val >= a.wrap_guard;  // a sum of such counts could wrap 2^64
-                            }
-                        }
-                        continue;
-                    }
                     unsigned nz = __ballot_sync(0xffffffffu, fw != 0ull);
                     while (nz) {
                         // up to four parents per round so their count loads overlap
@@ -357,15 +299,6 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                             ovf |= (acc0 >= S(kTwo53)) | (acc1 >= S(kTwo53));
                         }
                     }
-                }
-                if (!FPSIG) {
-                    __syncwarp();
-                    acc0 = (S)wacc[lane];
-                    acc1 = (S)wacc[lane + 32];
-                    wacc[lane] = 0ull;
-                    wacc[lane + 32] = 0ull;
-                    __syncwarp();
-                    ovf |= (acc0 >= S(kTwo53)) | (acc1 >= S(kTwo53));
                 }
                 const uint64_t nb = warp_or64(nbp);
                 bool app = false;
