@@ -206,7 +206,7 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
     }
     ctx->have_paths = false;
     if (ctx->opt.instrument) PERCIS_TRY(ensure(ctx, ctx->counters, sizeof(unsigned long long) * 8, "counters"));
-    ctx->sigma_fp64 = false;
+    ctx->sigma_mode = 0;
     for (int attempt = 0; attempt < 24; ++attempt) {
         clear_status(ctx);
         ctx->ev_next = 0;
@@ -247,9 +247,15 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
             ctx->arena_cap = cap;
             continue;
         }
-        if ((st & DEV_SIGMA_OVERFLOW) && ctx->opt.form != PERCIS_FORM_PLAIN && !ctx->sigma_fp64) {
-            ctx->sigma_fp64 = true;  // exact integer counts reached 2^53: redo with FP64 sigma
-            continue;
+        if (ctx->opt.form != PERCIS_FORM_PLAIN) {
+            if ((st & DEV_SIGMA_WIDE) && ctx->sigma_mode == 0) {
+                ctx->sigma_mode = 1;  // a count reached 2^32: redo with 64-bit storage
+                continue;
+            }
+            if ((st & DEV_SIGMA_OVERFLOW) && ctx->sigma_mode == 1) {
+                ctx->sigma_mode = 2;  // a count reached 2^53: redo with FP64 counts
+                continue;
+            }
         }
         if ((st & DEV_BAD_PATH) && !(st & DEV_SIGMA_OVERFLOW))
             return set_err(ctx, PERCIS_E_CUDA, "backtrack found no predecessor");

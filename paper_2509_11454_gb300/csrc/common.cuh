@@ -17,9 +17,37 @@ enum : uint32_t {
     DEV_BAD_PATH = 1u << 4,        // backtrack found no predecessor (sigma inexact)
     DEV_BAD_STATE = 1u << 5,       // x NaN or outside [0,1]
     DEV_DEGENERATE = 1u << 6,      // some C_v <= 0
+    DEV_SIGMA_WIDE = 1u << 7,      // some sigma >= 2^32: 32-bit storage too narrow
 };
 
 constexpr double kTwo53 = 9007199254740992.0;
+
+// Storage of the batched sigma counts.  Mode 0: 32-bit integers (exact below
+// 2^32), mode 1: 64-bit integers (exact below 2^53, the FP64 range), mode 2:
+// FP64.  Sums are always formed in 64-bit integers (modes 0, 1) or FP64.
+template <int SM>
+struct SigmaMode;
+template <>
+struct SigmaMode<0> {
+    using ST = unsigned int;
+    using S = unsigned long long;
+    static constexpr unsigned long long limit = 1ull << 32;
+    static constexpr uint32_t flag = DEV_SIGMA_WIDE;
+};
+template <>
+struct SigmaMode<1> {
+    using ST = unsigned long long;
+    using S = unsigned long long;
+    static constexpr unsigned long long limit = 1ull << 53;
+    static constexpr uint32_t flag = DEV_SIGMA_OVERFLOW;
+};
+template <>
+struct SigmaMode<2> {
+    using ST = double;
+    using S = double;
+    static constexpr unsigned long long limit = 1ull << 53;
+    static constexpr uint32_t flag = DEV_SIGMA_OVERFLOW;
+};
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, multipliers 0xD2511F53 /

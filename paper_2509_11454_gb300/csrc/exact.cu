@@ -16,13 +16,13 @@ namespace percis {
 
 namespace {
 
-template <int K, bool FPSIG>
+template <int K, int SM>
 __global__ void k_dependency(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *fh, int32_t L,
                              const void *sigma_v, double *delta, const double *x, const int32_t *lane_src,
                              int32_t nlanes, double *num) {
     constexpr int W = 64 * K;
-    using S = typename std::conditional<FPSIG, double, unsigned long long>::type;
-    const S *sigma = static_cast<const S *>(sigma_v);
+    using ST = typename SigmaMode<SM>::ST;
+    const ST *sigma = static_cast<const ST *>(sigma_v);
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -81,14 +81,18 @@ percis_status dependency_levels(percis_ctx *ctx, int levels, const void *sig, do
                                 int32_t nlanes, double *num) {
     const int grid = grid_for(ctx, ctx->n * 32, 256);
     for (int L = levels; L >= 0; --L) {
-        if (ctx->sigma_fp64)
-            k_dependency<K, true><<<grid, 256, 0, ctx->stream>>>(ctx->n, ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
-                                                               ctx->fhist.as<uint64_t>(), L, sig, delta,
-                                                               ctx->x.as<double>(), src, nlanes, num);
+        if (ctx->sigma_mode == 2)
+            k_dependency<K, 2><<<grid, 256, 0, ctx->stream>>>(ctx->n, ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                            ctx->fhist.as<uint64_t>(), L, sig, delta,
+                                                            ctx->x.as<double>(), src, nlanes, num);
+        else if (ctx->sigma_mode == 1)
+            k_dependency<K, 1><<<grid, 256, 0, ctx->stream>>>(ctx->n, ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                            ctx->fhist.as<uint64_t>(), L, sig, delta,
+                                                            ctx->x.as<double>(), src, nlanes, num);
         else
-        k_dependency<K, false><<<grid, 256, 0, ctx->stream>>>(ctx->n, ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
-                                                      ctx->fhist.as<uint64_t>(), L, sig, delta, ctx->x.as<double>(),
-                                                      src, nlanes, num);
+            k_dependency<K, 0><<<grid, 256, 0, ctx->stream>>>(ctx->n, ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                            ctx->fhist.as<uint64_t>(), L, sig, delta,
+                                                            ctx->x.as<double>(), src, nlanes, num);
         PERCIS_CHECK_LAUNCH(ctx, "dependency");
     }
     return PERCIS_OK;

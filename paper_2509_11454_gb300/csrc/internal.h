@@ -78,7 +78,7 @@ struct percis_ctx {
     percis::DevBuf vis, fhist, sigmaW, ms_ctl, remaining, found;
     int32_t lanes_alloc = 0;
     int32_t levels_alloc = 0;
-    bool sigma_fp64 = false;  // batched sigma kept in FP64 (after a count reached 2^53)
+    int sigma_mode = 0;  // batched sigma storage: 0 = 32-bit, 1 = 64-bit integers, 2 = FP64
     percis::DevBuf fq0, fq1, qstamp;  // frontier queues and per-vertex level stamps
     int32_t stamp_base = 1;
     int64_t max_indeg = 0;

@@ -12,12 +12,13 @@
 // backtracks every sample of the batch (one warp per sample) exactly as the
 // plain form does, reading the frontier history for the predecessor test.
 //
-// sigma is kept as exact unsigned 64-bit integers: a dependent FP64 add costs
-// ~64 cycles on GB300 while integer adds are cheap, and below 2^53 every
-// conversion to FP64 is exact, so the backtrack compares exactly the FP64
-// values a plain FP64 implementation would.  If any sigma reaches 2^53 the
-// launch flags DEV_SIGMA_OVERFLOW and the host reruns the phase with the FP64
-// variant (FPSIG = true), where counts beyond 2^53 are rounded like FP64 sums.
+// sigma is kept as exact integers: a dependent FP64 add costs ~64 cycles on
+// GB300 while integer adds are cheap, and below 2^53 every conversion to FP64
+// is exact, so the backtrack compares exactly the FP64 values a plain FP64
+// implementation would.  Counts are stored in 32 bits (half the bytes per
+// sector) until one reaches 2^32 (DEV_SIGMA_WIDE: the host reruns the phase
+// with 64-bit storage), and in FP64 once one reaches 2^53
+// (DEV_SIGMA_OVERFLOW), where counts beyond 2^53 round like FP64 sums.
 //
 // Layout in HBM (vertex-major so one warp reads a vertex's lanes coalesced):
 //   visited  uint64 [n][K]
@@ -73,6 +74,7 @@ struct MsArgs {
     int32_t policy;                   // 0 = pull every level, 1 = push every level, 2 = by frontier size
     unsigned long long push_edges;    // policy 2: push while the frontier's out-edges stay below this
     unsigned long long wrap_guard;    // a pushed count >= this could wrap 2^64 at a high in-degree vertex
+    unsigned long long wrap_guard32;  // the same for 32-bit storage
     // instrumentation (INSTR variant only)
     const int64_t *rp;                // out-CSR offsets (out-degrees)
     unsigned long long *counters;     // 8 work counters (see percis_info.work)
@@ -104,11 +106,15 @@ __device__ __forceinline__ S warp_incl_scan(S v) {
     return v;
 }
 
-template <int K, bool INSTR, bool FPSIG>
+template <int K, bool INSTR, int SM>
 __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     constexpr int W = 64 * K;
-    using S = typename std::conditional<FPSIG, double, unsigned long long>::type;
-    S *sig = static_cast<S *>(a.sigma);
+    constexpr bool FPSIG = SM == 2;
+    using S = typename SigmaMode<SM>::S;
+    using ST = typename SigmaMode<SM>::ST;
+    constexpr unsigned long long kLimit = SigmaMode<SM>::limit;
+    const unsigned long long wrap_guard = SM == 0 ? a.wrap_guard32 : a.wrap_guard;
+    ST *sig = static_cast<ST *>(a.sigma);
     bool ovf = false;
     unsigned long long n_sload = 0, n_swrite = 0, n_uv = 0, n_ue = 0;
     MsCtl *ctl = a.ctl;
@@ -133,7 +139,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     if (a.policy != 0) {
         // pushes accumulate into sigma, so every count starts at zero
         ulonglong2 *s2 = reinterpret_cast<ulonglong2 *>(a.sigma);
-        const int64_t n2 = n * (int64_t)W / 2;
+        const int64_t n2 = n * (int64_t)W * (int64_t)sizeof(ST) / 16;
         for (int64_t i = tid; i < n2; i += nthreads) s2[i] = make_ulonglong2(0ull, 0ull);
     }
     for (long long p = p0 + tid; p < p1; p += nthreads) a.found[p] = -1;
@@ -163,7 +169,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         const uint64_t bit = 1ull << (j & 63);
         atomicOr((unsigned long long *)&a.vis[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         atomicOr((unsigned long long *)&a.fh[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
-        sig[(int64_t)v * W + j] = S(1);
+        sig[(int64_t)v * W + j] = ST(1);
         a.fq0[j] = v;
         a.qstamp[v] = a.stamp_base;
         if (INSTR) a.levdeg[(int64_t)j * (a.Lcap + 1)] = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
@@ -206,10 +212,11 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 const int32_t u = __ldcg(&qcur[k]);
                 const uint64_t fu = __ldcg(&fcur[(int64_t)u * K + w]) & s_act[w];
                 if (fu == 0ull) continue;
-                const S *urow = sig + (int64_t)u * W + 64 * w;
-                const S su0 = ((fu >> lane) & 1ull) ? __ldcg(urow + lane) : S(0);
-                const S su1 = ((fu >> (lane + 32)) & 1ull) ? __ldcg(urow + lane + 32) : S(0);
-                if (!FPSIG) ovf |= (su0 >= (S)a.wrap_guard) | (su1 >= (S)a.wrap_guard);
+                const ST *urow = sig + (int64_t)u * W + 64 * w;
+                const ST su0 = ((fu >> lane) & 1ull) ? __ldcg(urow + lane) : ST(0);
+                const ST su1 = ((fu >> (lane + 32)) & 1ull) ? __ldcg(urow + lane + 32) : ST(0);
+                // no vertex has more parents than max_indeg: counts below the guard cannot wrap the storage
+                if (!FPSIG) ovf |= ((S)su0 >= (S)wrap_guard) | ((S)su1 >= (S)wrap_guard);
                 const int64_t e0 = a.rp[u], e1 = a.rp[u + 1];
                 for (int64_t base = e0; base < e1; base += 32) {
                     const int64_t e = base + lane;
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                         const int j = __ffs(nz) - 1;
                         nz &= nz - 1;
                         const uint64_t mj = shfl64(m, j);
-                        S *vrow = sig + (int64_t)__shfl_sync(0xffffffffu, v, j) * W + 64 * w;
+                        ST *vrow = sig + (int64_t)__shfl_sync(0xffffffffu, v, j) * W + 64 * w;
                         if ((mj >> lane) & 1ull) atomicAdd(vrow + lane, su0);
                         if ((mj >> (lane + 32)) & 1ull) atomicAdd(vrow + lane + 32, su1);
                     }
@@ -275,10 +282,10 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                         const uint64_t f1 = h1 ? shfl64(fw, j1) : 0ull;
                         const uint64_t f2 = h2 ? shfl64(fw, j2) : 0ull;
                         const uint64_t f3 = h3 ? shfl64(fw, j3) : 0ull;
-                        const S *r0 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j0) * W + 64 * w;
-                        const S *r1 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j1) * W + 64 * w;
-                        const S *r2 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j2) * W + 64 * w;
-                        const S *r3 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j3) * W + 64 * w;
+                        const ST *r0 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j0) * W + 64 * w;
+                        const ST *r1 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j1) * W + 64 * w;
+                        const ST *r2 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j2) * W + 64 * w;
+                        const ST *r3 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j3) * W + 64 * w;
                         S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0), b0 = S(0), b1 = S(0), b2 = S(0), b3 = S(0);
                         if ((f0 >> lane) & 1ull) a0 = __ldcg(r0 + lane);
                         if ((f1 >> lane) & 1ull) a1 = __ldcg(r1 + lane);
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                             acc0 += (a0 + a1) + (a2 + a3);
                             acc1 += (b0 + b1) + (b2 + b3);
                             // flag before four more addends could wrap 2^64
-                            ovf |= (acc0 >= S(kTwo53)) | (acc1 >= S(kTwo53));
+                            ovf |= (acc0 >= kLimit) | (acc1 >= kLimit);
                         }
                     }
                 }
@@ -308,13 +315,13 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 }
                 if (app) qnext[atomicAdd(qn_next, 1)] = (int32_t)v;
                 if (nb) {
-                    S *drow = sig + v * W + 64 * w;
-                    if ((nb >> lane) & 1ull) drow[lane] = acc0;
-                    if ((nb >> (lane + 32)) & 1ull) drow[lane + 32] = acc1;
+                    ST *drow = sig + v * W + 64 * w;
+                    if ((nb >> lane) & 1ull) drow[lane] = (ST)acc0;
+                    if ((nb >> (lane + 32)) & 1ull) drow[lane + 32] = (ST)acc1;
                 }
             }
         }
-        if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, DEV_SIGMA_OVERFLOW);
+        if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, SigmaMode<SM>::flag);
         ovf = false;
         if (!grid_sync(bar, status, a.budget_ns)) return;
 
@@ -366,14 +373,15 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                         n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
                     }
                 }
-                if (push) {
-                    // pushed counts are complete only now: check them against 2^53
+                if (push && SM != 0) {
+                    // pushed counts are complete only now: check them against the
+                    // exact range (32-bit storage is covered by the wrap guard)
                     uint64_t mm = nb;
-                    const S *vrow = sig + (int64_t)v * W + 64 * w;
+                    const ST *vrow = sig + (int64_t)v * W + 64 * w;
                     while (mm) {
                         const int b = __ffsll((long long)mm) - 1;
                         mm &= mm - 1;
-                        if (__ldcg(vrow + b) >= S(kTwo53)) ovf = true;
+                        if ((S)__ldcg(vrow + b) >= (S)kLimit) ovf = true;
                     }
                 }
                 if (INSTR) {
@@ -395,7 +403,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 for (int64_t i = tid; i < nk; i += nthreads) f2[i] = 0ull;
             }
         }
-        if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, DEV_SIGMA_OVERFLOW);
+        if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, SigmaMode<SM>::flag);
         ovf = false;
         __syncthreads();
         if (threadIdx.x < K && s_nonempty[threadIdx.x])
@@ -524,7 +532,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         int32_t k = 0;
         while (w != s) {
             const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step),
-                                            (double)__ldcg(&sig[(int64_t)w * W + j]));
+                                            (double)(S)__ldcg(&sig[(int64_t)w * W + j]));
             const uint64_t *fprev = a.fh + (int64_t)(lw - 1) * nk;
             const int64_t e0 = a.irp[w], e1 = a.irp[w + 1];
             S carry = S(0);
@@ -535,7 +543,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 S val = S(0);
                 if (e < e1) {
                     pv = a.icol[e];
-                    if (__ldcg(&fprev[(int64_t)pv * K + wj]) & bj) val = __ldcg(&sig[(int64_t)pv * W + j]);
+                    if (__ldcg(&fprev[(int64_t)pv * K + wj]) & bj) val = (S)__ldcg(&sig[(int64_t)pv * W + j]);
                 }
                 // running sums are exact (integers; FP64 sums of integers below 2^53)
                 const S cum = carry + warp_incl_scan<S>(val);
@@ -562,12 +570,12 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
 }
 
 // dist/sigma of every lane after a full traversal, source-major output.
-template <int K, bool FPSIG>
+template <int K, int SM>
 __global__ void k_ms_extract(const uint64_t *fh, const void *sigma_v, int64_t n, int32_t levels, int32_t nsrc,
                              int32_t *dist, double *sig) {
     constexpr int W = 64 * K;
-    using S = typename std::conditional<FPSIG, double, unsigned long long>::type;
-    const S *sigma = static_cast<const S *>(sigma_v);
+    using ST = typename SigmaMode<SM>::ST;
+    const ST *sigma = static_cast<const ST *>(sigma_v);
     const int64_t total = n * (int64_t)nsrc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
@@ -585,45 +593,49 @@ __global__ void k_ms_extract(const uint64_t *fh, const void *sigma_v, int64_t n,
 }
 
 struct GridCache {
-    int grid[2][2][4] = {};
+    int grid[2][3][4] = {};
 };
 GridCache g_ms_grid;
 
-template <int K, bool INSTR, bool FPSIG>
+template <int K, bool INSTR, int SM>
 int ms_grid(percis_ctx *ctx) {
     const int idx = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : 3;
-    int &slot = g_ms_grid.grid[INSTR ? 1 : 0][FPSIG ? 1 : 0][idx];
+    int &slot = g_ms_grid.grid[INSTR ? 1 : 0][SM][idx];
     if (slot == 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs<K, INSTR, FPSIG>, kMsBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs<K, INSTR, SM>, kMsBlock, 0);
         slot = std::max(1, per_sm) * ctx->num_sms;
     }
     return slot;
 }
 
-template <int K, bool INSTR, bool FPSIG>
+template <int K, bool INSTR, int SM>
 percis_status launch_ms(percis_ctx *ctx, MsArgs &a) {
     void *args[] = {&a};
-    const int grid = ms_grid<K, INSTR, FPSIG>(ctx);
-    PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_msbfs<K, INSTR, FPSIG>, dim3(grid), dim3(kMsBlock),
+    const int grid = ms_grid<K, INSTR, SM>(ctx);
+    PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_msbfs<K, INSTR, SM>, dim3(grid), dim3(kMsBlock),
                                                  args, 0, ctx->stream));
     ctx->launches++;
     return PERCIS_OK;
 }
 
-template <bool FPSIG>
+template <int SM>
 percis_status launch_ms_k2(percis_ctx *ctx, int K, MsArgs &a) {
     const bool instr = a.counters != nullptr;
     switch (K) {
-        case 1: return instr ? launch_ms<1, true, FPSIG>(ctx, a) : launch_ms<1, false, FPSIG>(ctx, a);
-        case 2: return instr ? launch_ms<2, true, FPSIG>(ctx, a) : launch_ms<2, false, FPSIG>(ctx, a);
-        case 4: return instr ? launch_ms<4, true, FPSIG>(ctx, a) : launch_ms<4, false, FPSIG>(ctx, a);
-        default: return instr ? launch_ms<8, true, FPSIG>(ctx, a) : launch_ms<8, false, FPSIG>(ctx, a);
+        case 1: return instr ? launch_ms<1, true, SM>(ctx, a) : launch_ms<1, false, SM>(ctx, a);
+        case 2: return instr ? launch_ms<2, true, SM>(ctx, a) : launch_ms<2, false, SM>(ctx, a);
+        case 4: return instr ? launch_ms<4, true, SM>(ctx, a) : launch_ms<4, false, SM>(ctx, a);
+        default: return instr ? launch_ms<8, true, SM>(ctx, a) : launch_ms<8, false, SM>(ctx, a);
     }
 }
 
 percis_status launch_ms_k(percis_ctx *ctx, int K, MsArgs &a) {
-    return ctx->sigma_fp64 ? launch_ms_k2<true>(ctx, K, a) : launch_ms_k2<false>(ctx, K, a);
+    switch (ctx->sigma_mode) {
+        case 0: return launch_ms_k2<0>(ctx, K, a);
+        case 1: return launch_ms_k2<1>(ctx, K, a);
+        default: return launch_ms_k2<2>(ctx, K, a);
+    }
 }
 
 percis_status ensure_ms(percis_ctx *ctx, int W, int Lcap) {
@@ -666,6 +678,7 @@ void fill_common(percis_ctx *ctx, MsArgs &a, int Lcap) {
     a.push_edges = (unsigned long long)std::max<int64_t>(ctx->nnz / 4, 1);
     // no vertex has more than max_indeg parents: counts below 2^63 / max_indeg cannot wrap 2^64
     a.wrap_guard = (unsigned long long)(9223372036854775807LL / std::max<int64_t>(ctx->max_indeg, 1));
+    a.wrap_guard32 = (unsigned long long)(4294967295LL / std::max<int64_t>(ctx->max_indeg, 1));
 }
 
 // Each launch stamps its levels with fresh values, so the stamps never need clearing.
@@ -740,7 +753,7 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
 
 // Full traversal from nsrc <= 512 sources (inspection and exact centrality).
 percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, int32_t *dist, double *sigma) {
-    ctx->sigma_fp64 = false;
+    ctx->sigma_mode = 0;
     int W = 64;
     while (W < nsrc) W *= 2;
     const int K = W / 64;
@@ -766,8 +779,12 @@ percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, 
             Lcap *= 2;
             continue;
         }
-        if ((hc.status & DEV_SIGMA_OVERFLOW) && !ctx->sigma_fp64) {
-            ctx->sigma_fp64 = true;  // counts reached 2^53: redo with FP64 sigma
+        if ((hc.status & DEV_SIGMA_WIDE) && ctx->sigma_mode == 0) {
+            ctx->sigma_mode = 1;  // counts reached 2^32: redo with 64-bit storage
+            continue;
+        }
+        if ((hc.status & DEV_SIGMA_OVERFLOW) && ctx->sigma_mode == 1) {
+            ctx->sigma_mode = 2;  // counts reached 2^53: redo with FP64 sigma
             continue;
         }
         const int levels = hc.level;
@@ -776,21 +793,24 @@ percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, 
         const void *sg = ctx->sigmaW.p;
         const uint64_t *fhp = ctx->fhist.as<uint64_t>();
         const int64_t nn = ctx->n;
-        if (ctx->sigma_fp64) {
-            switch (K) {
-                case 1: k_ms_extract<1, true><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
-                case 2: k_ms_extract<2, true><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
-                case 4: k_ms_extract<4, true><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
-                default: k_ms_extract<8, true><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
-            }
+#define PERCIS_EXTRACT(KK, SMM) \
+    k_ms_extract<KK, SMM><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma)
+#define PERCIS_EXTRACT_K(SMM)            \
+    switch (K) {                         \
+        case 1: PERCIS_EXTRACT(1, SMM); break; \
+        case 2: PERCIS_EXTRACT(2, SMM); break; \
+        case 4: PERCIS_EXTRACT(4, SMM); break; \
+        default: PERCIS_EXTRACT(8, SMM); break; \
+    }
+        if (ctx->sigma_mode == 0) {
+            PERCIS_EXTRACT_K(0);
+        } else if (ctx->sigma_mode == 1) {
+            PERCIS_EXTRACT_K(1);
         } else {
-            switch (K) {
-                case 1: k_ms_extract<1, false><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
-                case 2: k_ms_extract<2, false><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
-                case 4: k_ms_extract<4, false><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
-                default: k_ms_extract<8, false><<<grid, 256, 0, ctx->stream>>>(fhp, sg, nn, levels, nsrc, dist, sigma); break;
-            }
+            PERCIS_EXTRACT_K(2);
         }
+#undef PERCIS_EXTRACT_K
+#undef PERCIS_EXTRACT
         PERCIS_CHECK_LAUNCH(ctx, "ms extract");
         return PERCIS_OK;
     }
