@@ -171,7 +171,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip plain/differentiated/e2e/cpu legs")
     ap.add_argument("--lanes", type=int, default=0, help="batched lane width (0 = library default)")
     ap.add_argument("--lane-order", type=int, default=-1, help="0 = by vertex id, 1 = by hub neighbour")
-    ap.add_argument("--direction", type=int, default=-1, help="0 = pull, 1 = push, 2 = by frontier size")
+    ap.add_argument("--direction", type=int, default=-1, help="0 = pull, 1 = push, 2 = by work estimate")
+    ap.add_argument("--push-alpha", type=float, default=0.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -202,6 +203,8 @@ def main():
         eng.set_options(lane_order=args.lane_order)
     if args.direction >= 0:
         eng.set_options(direction=args.direction)
+    if args.push_alpha > 0:
+        eng.set_options(push_alpha=args.push_alpha)
     rp_d = torch.as_tensor(g.row_ptr, dtype=torch.int64, device="cuda")
     col_d = torch.as_tensor(g.col, dtype=torch.int32, device="cuda")
     x_d = torch.as_tensor(x, dtype=torch.float64, device="cuda")
@@ -344,7 +347,8 @@ def main():
         cfg = dict(WORKLOAD_DESC)
         cfg.update({"n": g.n, "nnz": g.nnz, "form": "batched", "lanes": i0["lanes"],
                     "lane_order": ["vertex id", "hub neighbour"][eng.options.lane_order],
-                    "direction": ["pull", "push", "push while frontier out-edges < nnz/4"][eng.options.direction],
+                    "direction": ["pull", "push", "per level by work estimate"][eng.options.direction],
+                    "push_alpha": eng.options.push_alpha or 1.0,
                     "ell1": i0["ell1"],
                     "ell_mean": statistics.mean(i["ell"] for i in infos),
                     "distinct_sources_phase2_mean": statistics.mean(i["sources"][1] for i in infos),

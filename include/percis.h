@@ -72,9 +72,11 @@ typedef struct {
                                  with similar BFS levels share 64-bit words and sigma sectors */
     int32_t direction;        /* batched levels: 0 = pull (each unvisited vertex sums over its
                                  in-neighbours), 1 = push (each frontier vertex adds its counts to
-                                 its out-neighbours), 2 (default) = push while the frontier's
-                                 out-edges stay below nnz/4, else pull */
+                                 its out-neighbours), 2 (default) = per level, push while
+                                 push_alpha * (frontier out-edges x words) < (in-edges x words
+                                 of vertices with an unvisited active lane) */
     int32_t reserved;
+    double push_alpha;        /* direction 2 threshold; 0 = default (1.0) */
 } percis_options;
 
 typedef struct {

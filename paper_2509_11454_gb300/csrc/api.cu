@@ -309,6 +309,7 @@ void percis_default_options(percis_options *opt) {
     opt->instrument = 0;
     opt->lane_order = 1;
     opt->direction = 2;
+    opt->push_alpha = 0.0;
 }
 
 percis_status percis_create(percis_ctx **out, int device, void *stream) {
@@ -384,6 +385,7 @@ percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt) {
         return set_err(ctx, PERCIS_E_INVALID, "lanes must be 0, 64, 128, 256 or 512");
     if (opt->lane_order != 0 && opt->lane_order != 1) return set_err(ctx, PERCIS_E_INVALID, "lane_order must be 0 or 1");
     if (opt->direction < 0 || opt->direction > 2) return set_err(ctx, PERCIS_E_INVALID, "direction must be 0, 1 or 2");
+    if (!(opt->push_alpha >= 0.0)) return set_err(ctx, PERCIS_E_INVALID, "push_alpha must be >= 0");
     if (opt->ell1 < 0 || opt->ell1 == 1 || opt->ell < 0 || !(opt->timeout_s > 0.0))
         return set_err(ctx, PERCIS_E_INVALID, "bad sample sizes or timeout");
     ctx->opt = *opt;

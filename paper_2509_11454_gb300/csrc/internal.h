@@ -31,7 +31,8 @@ struct alignas(16) MsCtl {
     int32_t qn[2];                // frontier queue sizes (ping-pong by level parity)
     unsigned long long active[8];    // lanes still running (K <= 8 words)
     unsigned long long nonempty[2][8];  // per-level OR of discovered bits (ping-pong)
-    unsigned long long fedges[2];    // out-degree sum of the frontier queue (ping-pong)
+    unsigned long long fedges[2];    // push work of the next level: frontier out-edges x words (ping-pong)
+    unsigned long long uedges[2];    // pull work of the next level: unvisited in-edges x words (ping-pong)
     unsigned long long t_start;      // globaltimer at the first level
     unsigned long long lvl_rec[32][4];  // per level: end time, direction, queue size, out-edges
 };

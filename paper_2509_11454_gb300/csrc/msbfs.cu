@@ -71,8 +71,8 @@ struct MsArgs {
     int32_t *fq1;
     int32_t *qstamp;
     int32_t stamp_base;
-    int32_t policy;                   // 0 = pull every level, 1 = push every level, 2 = by frontier size
-    unsigned long long push_edges;    // policy 2: push while the frontier's out-edges stay below this
+    int32_t policy;                   // 0 = pull every level, 1 = push every level, 2 = by work estimate
+    double push_alpha;                // policy 2: push while alpha * push work < pull work
     unsigned long long wrap_guard;    // a pushed count >= this could wrap 2^64 at a high in-degree vertex
     unsigned long long wrap_guard32;  // the same for 32-bit storage
     // instrumentation (INSTR variant only)
@@ -366,12 +366,10 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 if (!nb) continue;
                 a.vis[(int64_t)v * K + w] = __ldcg(&a.vis[(int64_t)v * K + w]) | nb;
                 atomicOr(&s_nonempty[w], (unsigned long long)nb);
-                if (w == 0) {
-                    fe += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
-                    if (INSTR) {
-                        n_uv += 1;
-                        n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
-                    }
+                fe += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
+                if (INSTR && w == 0) {
+                    n_uv += 1;
+                    n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
                 }
                 if (push && SM != 0) {
                     // pushed counts are complete only now: check them against the
@@ -401,6 +399,20 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             if (L + 2 <= a.Lcap) {
                 uint64_t *f2 = a.fh + (int64_t)(L + 2) * nk;
                 for (int64_t i = tid; i < nk; i += nthreads) f2[i] = 0ull;
+            }
+            if (a.policy == 2) {
+                // pull work of the next level: in-edges of every (vertex, word) that
+                // still has an unvisited active lane (visited bits now include level L+1
+                // except for the vertices this pass is still updating, a small excess)
+                unsigned long long ue = 0ull;
+                for (int64_t it = tid; it < nk; it += nthreads) {
+                    const int64_t v = it / K;
+                    const int w = (int)(it - v * K);
+                    const uint64_t vw = __ldcg(&a.vis[it]) | __ldcg(&fnext[it]);
+                    if (s_act[w] & ~vw) ue += (unsigned long long)(a.irp[v + 1] - a.irp[v]);
+                }
+                for (int off = 16; off > 0; off >>= 1) ue += __shfl_xor_sync(0xffffffffu, ue, off);
+                if (lane == 0 && ue) atomicAdd(&ctl->uedges[(L + 1) & 1], ue);
             }
         }
         if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, SigmaMode<SM>::flag);
@@ -450,14 +462,16 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 ctl->level = L + 1;
                 if (L < 32) {
                     ctl->lvl_rec[L][0] = globaltimer_ns() - ctl->t_start;
-                    ctl->lvl_rec[L][1] = push ? 1ull : 0ull;
+                    ctl->lvl_rec[L][1] = (push ? 1ull : 0ull) | (ctl->uedges[L & 1] << 1);
                     ctl->lvl_rec[L][2] = (unsigned long long)ctl->qn[L & 1];
                     ctl->lvl_rec[L][3] = ctl->fedges[L & 1];
                 }
                 ctl->qn[L & 1] = 0;  // the queue just consumed is refilled at level L+2
                 const unsigned long long fe = ctl->fedges[(L + 1) & 1];
+                const unsigned long long ue = ctl->uedges[(L + 1) & 1];
                 ctl->fedges[L & 1] = 0ull;
-                ctl->push_next = a.policy == 1 || (a.policy == 2 && fe < a.push_edges);
+                ctl->uedges[L & 1] = 0ull;
+                ctl->push_next = a.policy == 1 || (a.policy == 2 && a.push_alpha * (double)fe < (double)ue);
             }
         }
         if (!grid_sync(bar, status, a.budget_ns)) return;
@@ -675,7 +689,7 @@ void fill_common(percis_ctx *ctx, MsArgs &a, int Lcap) {
     a.fq1 = ctx->fq1.as<int32_t>();
     a.qstamp = ctx->qstamp.as<int32_t>();
     a.policy = ctx->opt.direction;
-    a.push_edges = (unsigned long long)std::max<int64_t>(ctx->nnz / 4, 1);
+    a.push_alpha = ctx->opt.push_alpha > 0.0 ? ctx->opt.push_alpha : 1.0;
     // no vertex has more than max_indeg parents: counts below 2^63 / max_indeg cannot wrap 2^64
     a.wrap_guard = (unsigned long long)(9223372036854775807LL / std::max<int64_t>(ctx->max_indeg, 1));
     a.wrap_guard32 = (unsigned long long)(4294967295LL / std::max<int64_t>(ctx->max_indeg, 1));
