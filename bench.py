@@ -348,7 +348,7 @@ def main():
         cfg.update({"n": g.n, "nnz": g.nnz, "form": "batched", "lanes": i0["lanes"],
                     "lane_order": ["vertex id", "hub neighbour"][eng.options.lane_order],
                     "direction": ["pull", "push", "per level by work estimate"][eng.options.direction],
-                    "push_alpha": eng.options.push_alpha or 1.0,
+                    "push_alpha": eng.options.push_alpha or 0.5,
                     "ell1": i0["ell1"],
                     "ell_mean": statistics.mean(i["ell"] for i in infos),
                     "distinct_sources_phase2_mean": statistics.mean(i["sources"][1] for i in infos),

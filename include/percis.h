@@ -76,7 +76,7 @@ typedef struct {
                                  push_alpha * (frontier out-edges x words) < (in-edges x words
                                  of vertices with an unvisited active lane) */
     int32_t reserved;
-    double push_alpha;        /* direction 2 threshold; 0 = default (1.0) */
+    double push_alpha;        /* direction 2 threshold; 0 = default (0.5) */
 } percis_options;
 
 typedef struct {

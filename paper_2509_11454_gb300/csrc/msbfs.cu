@@ -689,7 +689,7 @@ void fill_common(percis_ctx *ctx, MsArgs &a, int Lcap) {
     a.fq1 = ctx->fq1.as<int32_t>();
     a.qstamp = ctx->qstamp.as<int32_t>();
     a.policy = ctx->opt.direction;
-    a.push_alpha = ctx->opt.push_alpha > 0.0 ? ctx->opt.push_alpha : 1.0;
+    a.push_alpha = ctx->opt.push_alpha > 0.0 ? ctx->opt.push_alpha : 0.5;
     // no vertex has more than max_indeg parents: counts below 2^63 / max_indeg cannot wrap 2^64
     a.wrap_guard = (unsigned long long)(9223372036854775807LL / std::max<int64_t>(ctx->max_indeg, 1));
     a.wrap_guard32 = (unsigned long long)(4294967295LL / std::max<int64_t>(ctx->max_indeg, 1));

@@ -102,26 +102,26 @@ __global__ void k_gather_sorted(const double *x, const int32_t *perm, int64_t n,
 // bit-identical to any other sequential evaluation: the sampled pairs depend
 // on them through exact comparisons.  A dependent FP64 add costs ~64 cycles
 // on this GPU, so the block stages x_i and the products (n-i+1) x_i (each an
-// independent rounding) into shared memory, and thread 0 runs the three
-// recurrences software-pipelined: step k adds w_k while c_{k-1} and the sums
-// r, c of element k-2 use results of earlier steps, so one step costs about
-// one FP64 latency instead of four.
-constexpr int kScanStage = 2048;
+// independent rounding) into shared memory and thread 0 runs the chains in
+// blocks of eight elements: the eight dependent adds of w for one block are
+// interleaved with the c_i = max(0, (n-i+1)x_i - w_i) and the running sums r
+// and c of the previous block, so each element costs about one FP64 latency.
+// Results are staged in shared memory and written out by the whole block.
+constexpr int kScanStage = 1024;
+constexpr int kScanBlk = 8;
+
+__device__ __forceinline__ double clamp0(double v) { return __double_as_longlong(v) < 0 ? 0.0 : v; }
 
 __global__ void k_tables(const double *xs, int64_t n, double *w, double *ci, double *r, double *dscal) {
-    __shared__ double tx[kScanStage];
-    __shared__ double tt[kScanStage];
+    __shared__ double tx[kScanStage], tt[kScanStage];
+    __shared__ double ow[kScanStage], oc[kScanStage], orr[kScanStage];
     if (threadIdx.x == 0) {
         w[n + 1] = 0.0;
         r[n + 1] = 0.0;
         ci[n + 1] = 0.0;
         w[0] = r[0] = ci[0] = 0.0;
     }
-    // pipeline registers (thread 0): w of the last two elements, c_i pending
-    double wn = 0.0, rn = 0.0, c = 0.0;
-    double w_prev = 0.0, t_prev = 0.0;  // element k-1: its w and product
-    double cv_prev = 0.0;               // element k-2's clamped c_i, waiting for r and c
-    int64_t i_prev = -1, i_prev2 = -1;
+    double wn = 0.0, rn = 0.0, c = 0.0;  // thread 0's running values across tiles
     for (int64_t hi = n; hi >= 1; hi -= kScanStage) {
         const int64_t lo = max((int64_t)1, hi - kScanStage + 1);
         const int cnt = (int)(hi - lo + 1);
@@ -134,50 +134,65 @@ __global__ void k_tables(const double *xs, int64_t n, double *w, double *ci, dou
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int k = cnt - 1; k >= 0; --k) {
-                const int64_t i = lo + k;
-                // element i: w_i = w_{i+1} + x_i
-                const double w_new = __dadd_rn(wn, tx[k]);
-                // element i_prev: c = (n-i+1) x - w, clamped at 0
-                double cvp = __dsub_rn(t_prev, w_prev);
-                if (__double_as_longlong(cvp) < 0) cvp = 0.0;
-                // element i_prev2: r and c sums
-                if (i_prev2 >= 1) {
-                    rn = __dadd_rn(rn, cv_prev);
-                    c = __dadd_rn(c, cv_prev);
-                    r[i_prev2] = rn;
+            // elements in processing order are k = cnt-1, cnt-2, ..., 0
+            const int nblk = cnt / kScanBlk;
+            double pw[kScanBlk], pt[kScanBlk];
+            int pk = 0;  // highest k of the previous block
+            for (int b = 0; b <= nblk; ++b) {
+                const bool cur = b < nblk, prev = b > 0;
+                const int kb = cnt - 1 - b * kScanBlk;
+                double x[kScanBlk], t[kScanBlk], wv[kScanBlk];
+                if (cur) {
+#pragma unroll
+                    for (int j = 0; j < kScanBlk; ++j) {
+                        x[j] = tx[kb - j];
+                        t[j] = tt[kb - j];
+                    }
                 }
-                if (i_prev >= 1) {
-                    ci[i_prev] = cvp;
-                    w[i_prev] = w_prev;
+#pragma unroll
+                for (int j = 0; j < kScanBlk; ++j) {
+                    if (cur) {
+                        wn = __dadd_rn(wn, x[j]);
+                        wv[j] = wn;
+                    }
+                    if (prev) {
+                        const double cv = clamp0(__dsub_rn(pt[j], pw[j]));
+                        rn = __dadd_rn(rn, cv);
+                        c = __dadd_rn(c, cv);
+                        oc[pk - j] = cv;
+                        orr[pk - j] = rn;
+                    }
                 }
-                cv_prev = cvp;
-                i_prev2 = i_prev;
-                i_prev = i;
-                w_prev = w_new;
-                t_prev = tt[k];
-                wn = w_new;
+                if (cur) {
+#pragma unroll
+                    for (int j = 0; j < kScanBlk; ++j) {
+                        ow[kb - j] = wv[j];
+                        pw[j] = wv[j];
+                        pt[j] = t[j];
+                    }
+                    pk = kb;
+                }
+            }
+            // the lowest cnt % 8 elements, one at a time
+            for (int k = cnt - 1 - nblk * kScanBlk; k >= 0; --k) {
+                wn = __dadd_rn(wn, tx[k]);
+                const double cv = clamp0(__dsub_rn(tt[k], wn));
+                rn = __dadd_rn(rn, cv);
+                c = __dadd_rn(c, cv);
+                ow[k] = wn;
+                oc[k] = cv;
+                orr[k] = rn;
             }
         }
-    }
-    if (threadIdx.x == 0) {
-        // drain: element i_prev (w known), then the last two r/c sums
-        double cvp = __dsub_rn(t_prev, w_prev);
-        if (__double_as_longlong(cvp) < 0) cvp = 0.0;
-        if (i_prev2 >= 1) {
-            rn = __dadd_rn(rn, cv_prev);
-            c = __dadd_rn(c, cv_prev);
-            r[i_prev2] = rn;
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const int64_t i = lo + k;
+            w[i] = ow[k];
+            ci[i] = oc[k];
+            r[i] = orr[k];
         }
-        if (i_prev >= 1) {
-            ci[i_prev] = cvp;
-            w[i_prev] = w_prev;
-            rn = __dadd_rn(rn, cvp);
-            c = __dadd_rn(c, cvp);
-            r[i_prev] = rn;
-        }
-        dscal[0] = c;
     }
+    if (threadIdx.x == 0) dscal[0] = c;
 }
 
 // C_v = c - A_v with A_i = (w_1 - w_i) - (i-1) x_i + (n-i) x_i - w_{i+1} for
