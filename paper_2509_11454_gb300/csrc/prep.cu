@@ -100,99 +100,101 @@ __global__ void k_gather_sorted(const double *x, const int32_t *perm, int64_t n,
 // The preprocessing recurrence of Algorithm 2 is evaluated sequentially in
 // exactly its order (i = n down to 1) so that w, c_i, r and c are
 // bit-identical to any other sequential evaluation: the sampled pairs depend
-// on them through exact comparisons.  A dependent FP64 add costs ~64 cycles
-// on this GPU, so the block stages x_i and the products (n-i+1) x_i (each an
-// independent rounding) into shared memory and thread 0 runs the chains in
-// blocks of eight elements: the eight dependent adds of w for one block are
-// interleaved with the c_i = max(0, (n-i+1)x_i - w_i) and the running sums r
-// and c of the previous block, so each element costs about one FP64 latency.
-// Results are staged in shared memory and written out by the whole block.
-constexpr int kScanStage = 1024;
-constexpr int kScanBlk = 8;
+// on them through exact comparisons.
+//
+// On this GPU a warp-wide FP64 add occupies its sub-partition's FP64 pipe for
+// ~64 cycles, so one thread can retire about one FP64 operation per 64 cycles
+// whatever the dependences.  The three sequential parts therefore run on
+// different warps (different sub-partitions) and everything parallel runs on
+// the rest of the block:
+//   warp 0 (one lane):  w_i = w_{i+1} + x_i                 (one add per element)
+//   warps 2..7:         c_i = max(0, (n-i+1) x_i - w_i)     (parallel)
+//   warp 1 (one lane):  r_i = r_{i+1} + c_i                 (one add per element)
+// and c = r_1 (Algorithm 2 accumulates c over the same c_i in the same order
+// as r).  Tiles of 512 elements flow through a four-slot ring, one stage per
+// tile: stage s loads tile s, adds w over tile s-1, computes c_i of tile s-2,
+// adds r over tile s-3 and writes tile s-4 out.
+constexpr int kTile = 512;
+constexpr int kRing = 4;
 
-__device__ __forceinline__ double clamp0(double v) { return __double_as_longlong(v) < 0 ? 0.0 : v; }
+struct TableSlots {
+    double x[kRing][kTile], t[kRing][kTile], w[kRing][kTile], c[kRing][kTile], r[kRing][kTile];
+};
 
-__global__ void k_tables(const double *xs, int64_t n, double *w, double *ci, double *r, double *dscal) {
-    __shared__ double tx[kScanStage], tt[kScanStage];
-    __shared__ double ow[kScanStage], oc[kScanStage], orr[kScanStage];
+__global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, double *w, double *ci, double *r,
+                                                double *dscal) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    TableSlots &S = *reinterpret_cast<TableSlots *>(smem);
+    const int64_t T = (n + kTile - 1) / kTile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wtid = threadIdx.x - 64, wcount = blockDim.x - 64;  // warps 2.. form the worker group
     if (threadIdx.x == 0) {
         w[n + 1] = 0.0;
         r[n + 1] = 0.0;
         ci[n + 1] = 0.0;
         w[0] = r[0] = ci[0] = 0.0;
     }
-    double wn = 0.0, rn = 0.0, c = 0.0;  // thread 0's running values across tiles
-    for (int64_t hi = n; hi >= 1; hi -= kScanStage) {
-        const int64_t lo = max((int64_t)1, hi - kScanStage + 1);
-        const int cnt = (int)(hi - lo + 1);
-        __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-            const int64_t i = lo + k;
-            const double xi = xs[i - 1];
-            tx[k] = xi;
-            tt[k] = __dmul_rn((double)(n - i + 1), xi);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            // elements in processing order are k = cnt-1, cnt-2, ..., 0
-            const int nblk = cnt / kScanBlk;
-            double pw[kScanBlk], pt[kScanBlk];
-            int pk = 0;  // highest k of the previous block
-            for (int b = 0; b <= nblk; ++b) {
-                const bool cur = b < nblk, prev = b > 0;
-                const int kb = cnt - 1 - b * kScanBlk;
-                double x[kScanBlk], t[kScanBlk], wv[kScanBlk];
-                if (cur) {
-#pragma unroll
-                    for (int j = 0; j < kScanBlk; ++j) {
-                        x[j] = tx[kb - j];
-                        t[j] = tt[kb - j];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kScanBlk; ++j) {
-                    if (cur) {
-                        wn = __dadd_rn(wn, x[j]);
-                        wv[j] = wn;
-                    }
-                    if (prev) {
-                        const double cv = clamp0(__dsub_rn(pt[j], pw[j]));
-                        rn = __dadd_rn(rn, cv);
-                        c = __dadd_rn(c, cv);
-                        oc[pk - j] = cv;
-                        orr[pk - j] = rn;
-                    }
-                }
-                if (cur) {
-#pragma unroll
-                    for (int j = 0; j < kScanBlk; ++j) {
-                        ow[kb - j] = wv[j];
-                        pw[j] = wv[j];
-                        pt[j] = t[j];
-                    }
-                    pk = kb;
+    double wn = 0.0, rn = 0.0;
+    // tile s covers positions i in [hi - cnt + 1, hi], hi = n - s * kTile; local k = i - lo
+    for (int64_t st = 0; st < T + 4; ++st) {
+        if (warp >= 2) {
+            const int64_t so = st - 4;  // write out
+            if (so >= 0 && so < T) {
+                const int slot = (int)(so % kRing);
+                const int64_t hi = n - so * kTile;
+                const int cnt = (int)min((int64_t)kTile, hi);
+                const int64_t lo = hi - cnt + 1;
+                for (int k = wtid; k < cnt; k += wcount) {
+                    w[lo + k] = S.w[slot][k];
+                    ci[lo + k] = S.c[slot][k];
+                    r[lo + k] = S.r[slot][k];
                 }
             }
-            // the lowest cnt % 8 elements, one at a time
-            for (int k = cnt - 1 - nblk * kScanBlk; k >= 0; --k) {
-                wn = __dadd_rn(wn, tx[k]);
-                const double cv = clamp0(__dsub_rn(tt[k], wn));
-                rn = __dadd_rn(rn, cv);
-                c = __dadd_rn(c, cv);
-                ow[k] = wn;
-                oc[k] = cv;
-                orr[k] = rn;
+            if (st < T) {  // load tile st
+                const int slot = (int)(st % kRing);
+                const int64_t hi = n - st * kTile;
+                const int cnt = (int)min((int64_t)kTile, hi);
+                const int64_t lo = hi - cnt + 1;
+                for (int k = wtid; k < cnt; k += wcount) {
+                    const int64_t i = lo + k;
+                    const double xi = xs[i - 1];
+                    S.x[slot][k] = xi;
+                    S.t[slot][k] = __dmul_rn((double)(n - i + 1), xi);
+                }
+            }
+            const int64_t sc = st - 2;  // c_i of tile st-2
+            if (sc >= 0 && sc < T) {
+                const int slot = (int)(sc % kRing);
+                const int cnt = (int)min((int64_t)kTile, n - sc * kTile);
+                for (int k = wtid; k < cnt; k += wcount) {
+                    const double cv = __dsub_rn(S.t[slot][k], S.w[slot][k]);
+                    S.c[slot][k] = __double_as_longlong(cv) < 0 ? 0.0 : cv;
+                }
+            }
+        } else if (warp == 0 && lane == 0) {
+            const int64_t sw = st - 1;  // w over tile st-1
+            if (sw >= 0 && sw < T) {
+                const int slot = (int)(sw % kRing);
+                const int cnt = (int)min((int64_t)kTile, n - sw * kTile);
+                for (int k = cnt - 1; k >= 0; --k) {
+                    wn = __dadd_rn(wn, S.x[slot][k]);
+                    S.w[slot][k] = wn;
+                }
+            }
+        } else if (warp == 1 && lane == 0) {
+            const int64_t sr = st - 3;  // r over tile st-3
+            if (sr >= 0 && sr < T) {
+                const int slot = (int)(sr % kRing);
+                const int cnt = (int)min((int64_t)kTile, n - sr * kTile);
+                for (int k = cnt - 1; k >= 0; --k) {
+                    rn = __dadd_rn(rn, S.c[slot][k]);
+                    S.r[slot][k] = rn;
+                }
             }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-            const int64_t i = lo + k;
-            w[i] = ow[k];
-            ci[i] = oc[k];
-            r[i] = orr[k];
-        }
     }
-    if (threadIdx.x == 0) dscal[0] = c;
+    if (warp == 1 && lane == 0) dscal[0] = rn;  // c = r_1
 }
 
 // C_v = c - A_v with A_i = (w_1 - w_i) - (i-1) x_i + (n-i) x_i - w_{i+1} for
@@ -450,8 +452,15 @@ percis_status prep_states(percis_ctx *ctx) {
     PERCIS_TRY(merge_sort(ctx, k1, perm, k2, v2, n));
     k_gather_sorted<<<g, 256, 0, ctx->stream>>>(ctx->x.as<double>(), perm, n, ctx->xs.as<double>());
     PERCIS_CHECK_LAUNCH(ctx, "gather sorted");
-    k_tables<<<1, 256, 0, ctx->stream>>>(ctx->xs.as<double>(), n, ctx->w.as<double>(), ctx->ci.as<double>(),
-                                         ctx->r.as<double>(), ctx->dscal.as<double>());
+    static bool smem_set = false;
+    if (!smem_set) {
+        PERCIS_CUDA(ctx, cudaFuncSetAttribute(k_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)sizeof(TableSlots)));
+        smem_set = true;
+    }
+    k_tables<<<1, 256, sizeof(TableSlots), ctx->stream>>>(ctx->xs.as<double>(), n, ctx->w.as<double>(),
+                                                         ctx->ci.as<double>(), ctx->r.as<double>(),
+                                                         ctx->dscal.as<double>());
     PERCIS_CHECK_LAUNCH(ctx, "tables");
     PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->dscal.as<double>() + 1, 0, sizeof(double), ctx->stream));
     k_cv_lambda<<<g, 256, 0, ctx->stream>>>(ctx->xs.as<double>(), perm, ctx->w.as<double>(), ctx->dscal.as<double>(),
