@@ -176,7 +176,18 @@ __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, dou
             if (sw >= 0 && sw < T) {
                 const int slot = (int)(sw % kRing);
                 const int cnt = (int)min((int64_t)kTile, n - sw * kTile);
-                for (int k = cnt - 1; k >= 0; --k) {
+                int k = cnt - 1;
+                for (; k >= 7; k -= 8) {  // operands loaded ahead of the dependent adds
+                    double v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = S.x[slot][k - j];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        wn = __dadd_rn(wn, v[j]);
+                        S.w[slot][k - j] = wn;
+                    }
+                }
+                for (; k >= 0; --k) {
                     wn = __dadd_rn(wn, S.x[slot][k]);
                     S.w[slot][k] = wn;
                 }
@@ -186,7 +197,18 @@ __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, dou
             if (sr >= 0 && sr < T) {
                 const int slot = (int)(sr % kRing);
                 const int cnt = (int)min((int64_t)kTile, n - sr * kTile);
-                for (int k = cnt - 1; k >= 0; --k) {
+                int k = cnt - 1;
+                for (; k >= 7; k -= 8) {
+                    double v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = S.c[slot][k - j];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        rn = __dadd_rn(rn, v[j]);
+                        S.r[slot][k - j] = rn;
+                    }
+                }
+                for (; k >= 0; --k) {
                     rn = __dadd_rn(rn, S.c[slot][k]);
                     S.r[slot][k] = rn;
                 }
