@@ -227,6 +227,42 @@ int64_t percis_last_levels(percis_ctx *ctx, int64_t *out, int64_t cap);
  * (pass path_nodes = NULL to size it first; *total receives the total). */
 percis_status percis_get_paths(percis_ctx *ctx, int64_t *path_ptr, int32_t *path_nodes, int64_t *total);
 
+/* ------------------------------------------------ allocation-free call */
+
+/* Largest graph (vertices) percis_bfs_noalloc accepts; its scratch is two
+ * int32 frontier queues of this length plus a 256-byte control block, 8 MiB
+ * in a static device array that every GPU using the library keeps until the
+ * process exits. */
+#define PERCIS_NOALLOC_MAX_N 1048576
+
+/* The single-source sigma-counting BFS of percis_bfs for callers that cannot
+ * allocate device memory: for instance a process that hands all of the GPU's
+ * memory to its own pool at start-up, or a latency-critical path that cannot
+ * take cudaMalloc's implicit device synchronisation.  It needs no context and
+ * calls no cudaMalloc, cudaFree or allocating library routine.  (The paper has
+ * no counterpart; this is a calling convention of this library.)
+ *
+ * Runs on the calling thread's current CUDA device and on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream), and synchronises that
+ * stream before returning.  All pointers are device pointers of that device:
+ * row_ptr int64[n+1] / col int32[nnz] the CSR (valid as percis_load_csr
+ * requires; column indices outside [0, n) make the call return INVALID);
+ * in_row_ptr / in_col the in-adjacency of a directed graph, or both NULL for
+ * an undirected graph (in-lists = CSR rows).  target < 0: full traversal;
+ * else the traversal stops once target's level is discovered.  Outputs
+ * dist int32[n] (-1 = not reached) and sigma double[n] (0 = not reached),
+ * written in full.  Results equal percis_bfs's.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and the launch size; make that first call before any
+ * stream capture.  Every call uses the same scratch array and clears what
+ * must start at zero; calls that overlap on the GPU race on it, so serialise
+ * them.  Errors: INVALID (n outside [1, PERCIS_NOALLOC_MAX_N], NULL pointer,
+ * vertex out of range), TIMEOUT, CUDA. */
+percis_status percis_bfs_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col, const int64_t *in_row_ptr,
+                                 const int32_t *in_col, int32_t source, int32_t target, int32_t *dist, double *sigma,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

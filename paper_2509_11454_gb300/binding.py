@@ -89,6 +89,7 @@ SIGNATURES = {
     "percis_run_phase": (_ST, [_P, _U64, ctypes.c_int, _I64, _P, _P, _P, _P, _P]),
     "percis_get_paths": (_ST, [_P, _P, _P, _P]),
     "percis_last_levels": (_I64, [_P, _P, _I64]),
+    "percis_bfs_noalloc": (_ST, [_I64, _P, _P, _P, _P, _I32, _I32, _P, _P, _P]),
 }
 
 _lib = None
@@ -224,6 +225,13 @@ def percis_get_paths(ctx, path_ptr=None, path_nodes=None) -> int:
     tot = ctypes.c_int64()
     _check(ctx, load_library().percis_get_paths(ctx, _ptr(path_ptr), _ptr(path_nodes), ctypes.byref(tot)))
     return tot.value
+
+
+def percis_bfs_noalloc(n: int, row_ptr, col, in_row_ptr, in_col, source: int, target: int, dist, sigma,
+                       stream: int | None = None) -> int:
+    """Allocation-free single-source sigma BFS (device tensors); returns the status code."""
+    return int(load_library().percis_bfs_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(in_row_ptr), _ptr(in_col),
+                                                 source, target, _ptr(dist), _ptr(sigma), stream))
 
 
 def percis_last_levels(ctx, cap: int = 32) -> list[tuple[int, int, int, int]]:

@@ -18,6 +18,7 @@ enum : uint32_t {
     DEV_BAD_STATE = 1u << 5,       // x NaN or outside [0,1]
     DEV_DEGENERATE = 1u << 6,      // some C_v <= 0
     DEV_SIGMA_WIDE = 1u << 7,      // some sigma >= 2^32: 32-bit storage too narrow
+    DEV_BAD_INPUT = 1u << 8,       // a column index outside [0, n) (unvalidated input)
 };
 
 constexpr double kTwo53 = 9007199254740992.0;
