@@ -43,7 +43,8 @@ WORKLOAD_DESC = {
 }
 # DRAM traffic of one batched sigma-BFS launch from an ncu capture, valid only
 # for the kernel source it was taken on (sha256 of csrc/msbfs.cu).
-NCU_TRAFFIC = {"msbfs_sha256": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"msbfs_sha256": "fda36146203be3fa0e82ab030f18e6640c606aad1f28fbb043888e7069da9660",
+               "bytes_per_launch": 818932736 + 962884096}  # profiles/k_msbfs_ba100k_outbreak.md
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
 
