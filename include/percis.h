@@ -217,9 +217,12 @@ percis_status percis_run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_
                                int32_t *kind, int32_t *ilen, int64_t *cnt);
 
 /* Per-level profile of the last batched launch (measurement aid).  For each
- * level L < min(cap, 32) writes four int64 to out[4L..4L+3]: device time from
- * the launch's first level to the end of level L (ns), direction (1 = push),
- * frontier queue size, frontier out-edges.  Returns the number of levels. */
+ * level L < min(cap, 32) writes six int64 to out[6L..6L+5]: device time from
+ * the launch's start to the end of level L (ns); direction in bit 0 (1 = push)
+ * and the pull-work estimate that chose it in the bits above; frontier queue
+ * size; push-work estimate (frontier out-edges x words); time at the end of
+ * the level's first pass; time after the new frontier was collected.
+ * Returns the number of levels. */
 int64_t percis_last_levels(percis_ctx *ctx, int64_t *out, int64_t cap);
 
 /* Internal nodes of the paths of the last sampling phase, t-side first.

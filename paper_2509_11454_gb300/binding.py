@@ -234,10 +234,10 @@ def percis_bfs_noalloc(n: int, row_ptr, col, in_row_ptr, in_col, source: int, ta
                                                  source, target, _ptr(dist), _ptr(sigma), stream))
 
 
-def percis_last_levels(ctx, cap: int = 32) -> list[tuple[int, int, int, int]]:
-    out = np.zeros(4 * cap, dtype=np.int64)
+def percis_last_levels(ctx, cap: int = 32) -> list[tuple[int, ...]]:
+    out = np.zeros(6 * cap, dtype=np.int64)
     k = int(load_library().percis_last_levels(ctx, out.ctypes.data, cap))
-    return [tuple(int(v) for v in out[4 * i:4 * i + 4]) for i in range(k)]
+    return [tuple(int(v) for v in out[6 * i:6 * i + 6]) for i in range(k)]
 
 
 # ------------------------------------------------------ torch-facing engine

@@ -657,7 +657,7 @@ int64_t percis_last_levels(percis_ctx *ctx, int64_t *out, int64_t cap) {
     }
     const int64_t lv = std::min<int64_t>(std::min<int64_t>(hc.level, 32), cap);
     for (int64_t L = 0; L < lv; ++L)
-        for (int k = 0; k < 4; ++k) out[4 * L + k] = (int64_t)hc.lvl_rec[L][k];
+        for (int k = 0; k < 6; ++k) out[6 * L + k] = (int64_t)hc.lvl_rec[L][k];
     return lv;
 }
 

@@ -34,7 +34,8 @@ struct alignas(16) MsCtl {
     unsigned long long fedges[2];    // push work of the next level: frontier out-edges x words (ping-pong)
     unsigned long long uedges[2];    // pull work of the next level: unvisited in-edges x words (ping-pong)
     unsigned long long t_start;      // globaltimer at the first level
-    unsigned long long lvl_rec[32][4];  // per level: end time, direction, queue size, out-edges
+    unsigned long long lvl_rec[32][6];  // per level: end time, direction, queue size, out-edges,
+                                        // time after phase A, time after the queue build
 };
 
 struct PlainCtl {

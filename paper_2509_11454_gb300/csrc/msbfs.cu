@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, SigmaMode<SM>::flag);
         ovf = false;
         if (!grid_sync(bar, status, a.budget_ns)) return;
+        if (tid == 0 && L < 32) ctl->lvl_rec[L][4] = globaltimer_ns() - ctl->t_start;
 
         if (push) {
             // collect the vertices that gained frontier bits into the next queue
@@ -352,6 +353,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             }
             if (!grid_sync(bar, status, a.budget_ns)) return;
         }
+        if (tid == 0 && L < 32) ctl->lvl_rec[L][5] = globaltimer_ns() - ctl->t_start;
 
         // ---- phase B (1): settle the new frontier: visited bits, nonempty lanes,
         // final counts checked against 2^53, next frontier's out-edges
