@@ -84,7 +84,9 @@ def _declare(L):
     L.orc_backtrack.argtypes = [P, P, P, P, I32, I32, U64, U32, U64, P]
     L.orc_backtrack.restype = I32
     L.orc_run_samples.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, F64, P, U64, U32, U32, I64, I64,
-                                  P, P, P, P, P, P, P, P, I64, P, P]
+                                  P, P, P, P, P, P, P, P, I64, P, P, P]
+    L.orc_allpaths.argtypes = [I64, P, P, P, P, I32, I32, P, P]
+    L.orc_allpaths.restype = I32
     L.orc_run_samples.restype = ctypes.c_int
     L.orc_cv_literal.argtypes = [I64, P, P]
     L.orc_cv_literal.restype = F64
@@ -264,10 +266,11 @@ class Phase:
     path_nodes: np.ndarray
     edges: np.ndarray
     overflow: bool
+    acc_all: np.ndarray | None = None
 
 
 def run_samples(g: OGraph, prep: Prep, seed: int, tag_pair: int, tag_path: int, i0: int, count: int,
-                keep_paths: bool = True, path_cap: int | None = None) -> Phase:
+                keep_paths: bool = True, path_cap: int | None = None, allpaths: bool = False) -> Phase:
     """One sampling phase: Algorithm 2 pairs, RandomSP paths, estimator sums."""
     n = g.n
     s = np.zeros(count, dtype=np.int32)
@@ -276,6 +279,7 @@ def run_samples(g: OGraph, prep: Prep, seed: int, tag_pair: int, tag_path: int, 
     ilen = np.zeros(count, dtype=np.int32)
     cnt = np.zeros(n, dtype=np.int64)
     acc = np.zeros(n)
+    acc_all = np.zeros(n) if allpaths else None
     edges = np.zeros(count, dtype=np.int64)
     ovf = np.zeros(1, dtype=np.int32)
     if keep_paths:
@@ -285,10 +289,12 @@ def run_samples(g: OGraph, prep: Prep, seed: int, tag_pair: int, tag_path: int, 
             pn = np.zeros(cap, dtype=np.int32)
             cnt[:] = 0
             acc[:] = 0
+            if acc_all is not None:
+                acc_all[:] = 0
             rc = lib().orc_run_samples(n, _p(g.rp), _p(g.col), _p(g.irp), _p(g.icol), _p(prep.x), _p(prep.xs),
                                        _p(prep.perm), _p(prep.w), _p(prep.ci), _p(prep.r), prep.c, _p(prep.Cv),
                                        seed, tag_pair, tag_path, i0, count, _p(s), _p(t), _p(kind), _p(ilen),
-                                       _p(cnt), _p(acc), _p(pp), _p(pn), cap, _p(edges), _p(ovf))
+                                       _p(cnt), _p(acc), _p(pp), _p(pn), cap, _p(edges), _p(ovf), _p(acc_all))
             if rc == -1:
                 cap = int(pp[-1]) + 1
                 continue
@@ -300,10 +306,19 @@ def run_samples(g: OGraph, prep: Prep, seed: int, tag_pair: int, tag_path: int, 
         rc = lib().orc_run_samples(n, _p(g.rp), _p(g.col), _p(g.irp), _p(g.icol), _p(prep.x), _p(prep.xs),
                                    _p(prep.perm), _p(prep.w), _p(prep.ci), _p(prep.r), prep.c, _p(prep.Cv),
                                    seed, tag_pair, tag_path, i0, count, _p(s), _p(t), _p(kind), _p(ilen),
-                                   _p(cnt), _p(acc), None, None, 0, _p(edges), _p(ovf))
+                                   _p(cnt), _p(acc), None, None, 0, _p(edges), _p(ovf), _p(acc_all))
     if rc == -2:
         raise RuntimeError("oracle backtrack failed (sigma not exact?)")
-    return Phase(s, t, kind, ilen, cnt, acc, pp, pn, edges, bool(ovf[0]))
+    return Phase(s, t, kind, ilen, cnt, acc, pp, pn, edges, bool(ovf[0]), acc_all)
+
+
+def allpaths(g: OGraph, dist, sigma, s: int, t: int):
+    """Internal nodes of all shortest s-t paths and f(v) = sigma_sv tau_v / sigma_st."""
+    nodes = np.zeros(g.n, dtype=np.int32)
+    frac = np.zeros(g.n)
+    k = lib().orc_allpaths(g.n, _p(g.irp), _p(g.icol), _p(_c(dist, np.int32)), _p(_c(sigma, np.float64)), int(s),
+                           int(t), _p(nodes), _p(frac))
+    return nodes[:max(k, 0)], frac[:max(k, 0)]
 
 
 def exact_pc(g: OGraph, x, Cv=None):
@@ -504,7 +519,7 @@ class Result:
 
 
 def percis(g: OGraph, x, eps: float, delta: float, seed: int, ell1: int | None = None, ell: int | None = None,
-           D: int | None = None, prep: Prep | None = None, keep_paths: bool = True) -> Result:
+           D: int | None = None, prep: Prep | None = None, keep_paths: bool = True, allpaths: bool = False) -> Result:
     """Algorithm 1 (PercIS): D, phase 1 (l1 samples, pair tag 0, path tag 2),
     rho^, v^, x^, l, then phase 2 (l fresh samples, pair tag 1, path tag 3).
     The phase-1 estimate uses 1/l1 (the 1/l printed in that line of
@@ -516,16 +531,16 @@ def percis(g: OGraph, x, eps: float, delta: float, seed: int, ell1: int | None =
     if D is None:
         D = vertex_diam_ub(g)
     l1 = ell1 if ell1 is not None else ell1_default(eps, delta)
-    ph1 = run_samples(g, prep, seed, 0, 2, 0, l1, keep_paths=False)
-    p1 = ph1.acc / l1
+    ph1 = run_samples(g, prep, seed, 0, 2, 0, l1, keep_paths=False, allpaths=allpaths)
+    p1 = (ph1.acc_all if allpaths else ph1.acc) / l1
     p1_max = float(p1.max())
     rh, rt, Lam = rho_hat(ph1.ilen, D, delta)
     vh = v_hat(p1_max, prep.dhat, l1, delta)
     xh = x_hat(vh, prep.dhat)
     if ell is None:
         ell, _ = ell_sup(eps, delta, prep.dhat, rh, xh)
-    ph2 = run_samples(g, prep, seed, 1, 3, 0, ell, keep_paths=keep_paths)
-    pc = ph2.acc / ell
+    ph2 = run_samples(g, prep, seed, 1, 3, 0, ell, keep_paths=keep_paths, allpaths=allpaths)
+    pc = (ph2.acc_all if allpaths else ph2.acc) / ell
     pc_counts = prep.lam * ph2.cnt / ell
     return Result(pc, pc_counts, ph2.cnt, l1, ell, D, prep.dhat, rt, Lam, rh, vh, xh, p1_max, ph1, ph2, prep)
 

@@ -256,6 +256,58 @@ int32_t orc_backtrack(const int64_t *irp, const int32_t *icol, const int32_t *di
     return k;
 }
 
+/* All shortest paths at once (the Rao-Blackwellised form of the Section III-A
+ * estimator: E over the uniform path of 1[v in I] is sigma_st(v)/sigma_st).
+ * After the truncated BFS from s to t, tau_w = number of shortest w-t paths by
+ * a reverse sweep from t over the shortest-path DAG (tau_t = 1,
+ * tau_u = sum of tau_w over w with u in pred(w)), and every internal v gets
+ * f(v) = sigma_sv * tau_v / sigma_st.  Writes the internal nodes and their f
+ * (t-side levels first, each level in discovery order) and returns their
+ * number, or -1 when t was not reached. */
+int32_t orc_allpaths(int64_t n, const int64_t *irp, const int32_t *icol, const int32_t *dist, const double *sigma,
+                     int32_t s, int32_t t, int32_t *nodes, double *frac) {
+    if (dist[t] < 0) return -1;
+    const int32_t d = dist[t];
+    double *tau = (double *)calloc((size_t)n, sizeof(double));
+    char *in = (char *)calloc((size_t)n, 1);
+    int32_t *cur = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *nxt = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t nc = 1, k = 0;
+    cur[0] = t;
+    tau[t] = 1.0;
+    for (int32_t L = d - 1; L >= 1; L--) {
+        int64_t nn = 0;
+        for (int64_t q = 0; q < nc; q++) {
+            const int32_t w = cur[q];
+            for (int64_t e = irp[w]; e < irp[w + 1]; e++) {
+                const int32_t p = icol[e];
+                if (dist[p] != L) continue;
+                if (!in[p]) {
+                    in[p] = 1;
+                    nxt[nn++] = p;
+                }
+                tau[p] += tau[w];
+            }
+        }
+        for (int64_t q = 0; q < nn; q++) {
+            const int32_t v = nxt[q];
+            nodes[k] = v;
+            frac[k] = sigma[v] * tau[v] / sigma[t];
+            k++;
+        }
+        int32_t *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        nc = nn;
+    }
+    (void)s;
+    free(tau);
+    free(in);
+    free(cur);
+    free(nxt);
+    return (int32_t)k;
+}
+
 /* One sampling phase of Algorithm 1 (Algorithm 2 + RandomSP + estimator).
  * Samples i0 .. i0+count-1: pair tag `tag_pair`, path tag `tag_path`.
  * kind[k]: 0 = path sampled, 1 = zero weight (R(x_s-x_t) = 0), 2 = t not
@@ -273,11 +325,13 @@ int orc_run_samples(int64_t n, const int64_t *rp, const int32_t *col, const int6
                     const double *r, double c, const double *Cv, uint64_t seed, uint32_t tag_pair, uint32_t tag_path,
                     int64_t i0, int64_t count, int32_t *s_out, int32_t *t_out, int32_t *kind, int32_t *ilen,
                     int64_t *cnt, double *acc, int64_t *path_ptr, int32_t *path_nodes, int64_t path_cap,
-                    int64_t *edges, int32_t *overflow) {
+                    int64_t *edges, int32_t *overflow, double *acc_all) {
     int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     double *sigma = (double *)malloc(sizeof(double) * (size_t)n);
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     int32_t *path = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t *apn = acc_all ? (int32_t *)malloc(sizeof(int32_t) * (size_t)n) : NULL;
+    double *apf = acc_all ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
     int rc = 0;
     int64_t pp = 0;
     if (path_ptr) path_ptr[0] = 0;
@@ -305,6 +359,11 @@ int orc_run_samples(int64_t n, const int64_t *rp, const int32_t *col, const int6
                 }
                 kind[k] = 0;
                 len = got;
+                if (acc_all) {
+                    /* all-paths form: kappa/kappa~ weighted fractions */
+                    const int32_t na = orc_allpaths(n, irp, icol, dist, sigma, s, t, apn, apf);
+                    for (int32_t q = 0; q < na; q++) acc_all[apn[q]] += (R / Cv[apn[q]]) / (R / c) * apf[q];
+                }
                 for (int32_t q = 0; q < got; q++) {
                     int32_t v = path[q];
                     cnt[v] += 1;
@@ -326,6 +385,8 @@ int orc_run_samples(int64_t n, const int64_t *rp, const int32_t *col, const int6
     free(sigma);
     free(order);
     free(path);
+    free(apn);
+    free(apf);
     return rc;
 }
 

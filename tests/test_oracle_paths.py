@@ -222,3 +222,37 @@ def test_vertex_diameter_bound():
     assert oracle.vertex_diam_ub(oracle.from_synth(p)) == 2 * 28 - 1
     gd = _rand_graph(30, 60, True, 3)
     assert oracle.vertex_diam_ub(oracle.from_synth(gd)) == 28
+
+
+def test_allpaths_fractions_match_path_enumeration():
+    """f(v) = sigma_sv tau_v / sigma_st equals sigma_st(v)/sigma_st counted by
+    enumerating Gamma_st (brute force), and sums to d(s,t) - 1."""
+    for seed, directed in [(0, False), (1, True), (2, False)]:
+        g = _rand_graph(9, 22, directed, 200 + seed)
+        og = oracle.from_synth(g)
+        _, paths = oracle.brute_force_pc(g.n, g.row_ptr, g.col, np.random.default_rng(seed).random(g.n))
+        for (s, t), G in paths.items():
+            _, dist, sigma, _, _, _ = oracle.bfs(og, s, t)
+            nodes, frac = oracle.allpaths(og, dist, sigma, s, t)
+            ref = {}
+            for p in G:
+                for v in p[1:-1]:
+                    ref[v] = ref.get(v, 0) + 1.0 / len(G)
+            assert dict(zip(nodes.tolist(), frac.tolist())) == pytest.approx(ref, rel=1e-12)
+            assert frac.sum() == pytest.approx(len(G[0]) - 2, rel=1e-12, abs=1e-12)
+
+
+def test_allpaths_estimator_unbiased():
+    """The all-paths estimator has the same expectation as the path estimator (Lemma 1)."""
+    g = synth.barabasi_albert(14, 2, 11)
+    og = oracle.from_synth(g)
+    x = np.random.default_rng(11).random(14)
+    prep = oracle.prepare(x)
+    pe = oracle.exact_pc(og, x, prep.Cv)
+    ell, reps = 200, 150
+    est = np.zeros(14)
+    for k in range(reps):
+        ph = oracle.run_samples(og, prep, 50 + k, 1, 3, 0, ell, keep_paths=False, allpaths=True)
+        est += ph.acc_all / ell
+    sd = np.sqrt(np.maximum(pe * (prep.dhat - pe), 1e-30) / (ell * reps))
+    assert np.all(np.abs(est / reps - pe) <= 5 * sd + 1e-12)
