@@ -75,7 +75,10 @@ typedef struct {
                                  its out-neighbours), 2 (default) = per level, push while
                                  push_alpha * (frontier out-edges x words) < (in-edges x words
                                  of vertices with an unvisited active lane) */
-    int32_t reserved;
+    int32_t estimator;        /* 0 (default) = one uniform path per sample (Section III-A);
+                                 1 = all paths: every internal v of every shortest s-t path
+                                 gets sigma_sv sigma_vt / sigma_st (same expectation; the
+                                 Rao-Blackwellised form; batched form only; no backward) */
     double push_alpha;        /* direction 2 threshold; 0 = default (0.5) */
 } percis_options;
 

@@ -38,7 +38,7 @@ class percis_options(ctypes.Structure):
                 ("ell", ctypes.c_int64), ("vertex_diam", ctypes.c_int64), ("keep_paths", ctypes.c_int32),
                 ("data_independent", ctypes.c_int32), ("timeout_s", ctypes.c_double),
                 ("instrument", ctypes.c_int32), ("lane_order", ctypes.c_int32),
-                ("direction", ctypes.c_int32), ("reserved", ctypes.c_int32), ("push_alpha", ctypes.c_double)]
+                ("direction", ctypes.c_int32), ("estimator", ctypes.c_int32), ("push_alpha", ctypes.c_double)]
 
 
 class percis_info(ctypes.Structure):
@@ -272,6 +272,8 @@ class PercIS:
         for k, v in kw.items():
             if k == "form" and isinstance(v, str):
                 v = {"batched": FORM_BATCHED, "plain": FORM_PLAIN}[v]
+            if k == "estimator" and isinstance(v, str):
+                v = {"path": 0, "allpaths": 1}[v]
             setattr(self.options, k, v)
         percis_set_options(self.ctx, self.options)
 

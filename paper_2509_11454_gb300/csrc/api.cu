@@ -93,7 +93,7 @@ struct alignas(16) PhaseStats {
 };
 
 __global__ void k_phase_stats(int64_t count, const int32_t *kind, const int32_t *ilen, int64_t n, const double *lam,
-                              const unsigned long long *cnt, double ell, PhaseStats *out) {
+                              const unsigned long long *cnt, const double *acc, double ell, PhaseStats *out) {
     long long s1 = 0, s2 = 0, zw = 0, un = 0;
     double pm = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -105,7 +105,7 @@ __global__ void k_phase_stats(int64_t count, const int32_t *kind, const int32_t 
         un += kind[i] == 2;
     }
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        pm = fmax(pm, lam[v] * (double)cnt[v] / ell);
+        pm = fmax(pm, lam[v] * (acc ? acc[v] : (double)cnt[v]) / ell);
     for (int off = 16; off > 0; off >>= 1) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, off);
         s2 += __shfl_xor_sync(0xffffffffu, s2, off);
@@ -122,11 +122,12 @@ __global__ void k_phase_stats(int64_t count, const int32_t *kind, const int32_t 
     }
 }
 
-// p~(v) = lambda_v cnt_v / l
-__global__ void k_finalize(const double *lam, const unsigned long long *cnt, int64_t n, double ell, double *pc) {
+// p~(v) = lambda_v cnt_v / l  (all-paths: lambda_v acc_v / l)
+__global__ void k_finalize(const double *lam, const unsigned long long *cnt, const double *acc, int64_t n, double ell,
+                           double *pc) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        pc[v] = lam[v] * (double)cnt[v] / ell;
+        pc[v] = lam[v] * (acc ? acc[v] : (double)cnt[v]) / ell;
 }
 
 __global__ void k_ilen_i64(const int32_t *ilen, int64_t count, long long *out) {
@@ -213,6 +214,10 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
         if (ctx->opt.instrument)
             PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long) * 8, ctx->stream));
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->cnt.p, 0, sizeof(unsigned long long) * n, ctx->stream));
+        if (ctx->opt.estimator == 1) {
+            PERCIS_TRY(ensure(ctx, ctx->acc_ap, sizeof(double) * n, "all-paths sums"));
+            PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->acc_ap.p, 0, sizeof(double) * n, ctx->stream));
+        }
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->arena_top.p, 0, 64, ctx->stream));
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ilen.p, 0, sizeof(int32_t) * cap_count, ctx->stream));
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->path_off.p, 0, sizeof(long long) * cap_count, ctx->stream));
@@ -270,7 +275,7 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
         ctx->phase_count = count;
         ctx->last_phase = phase;
         ctx->last_seed = seed;
-        ctx->have_paths = true;
+        ctx->have_paths = ctx->opt.estimator == 0;  // the all-paths form stores no paths
         return PERCIS_OK;
     }
     return set_err(ctx, PERCIS_E_TOO_LARGE, "phase could not be sized (levels/arena)");
@@ -281,7 +286,8 @@ percis_status phase_stats(percis_ctx *ctx, int64_t count, double ell, PhaseStats
     PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(PhaseStats), ctx->stream));
     k_phase_stats<<<grid_for(ctx, std::max(count, ctx->n), 256), 256, 0, ctx->stream>>>(
         count, ctx->kind.as<int32_t>(), ctx->ilen.as<int32_t>(), ctx->n, ctx->lam.as<double>(),
-        ctx->cnt.as<unsigned long long>(), ell, ctx->red.as<PhaseStats>());
+        ctx->cnt.as<unsigned long long>(), ctx->opt.estimator == 1 ? ctx->acc_ap.as<double>() : nullptr, ell,
+        ctx->red.as<PhaseStats>());
     PERCIS_CHECK_LAUNCH(ctx, "phase stats");
     PERCIS_CUDA(ctx, cudaMemcpyAsync(hs, ctx->red.p, sizeof(PhaseStats), cudaMemcpyDeviceToHost, ctx->stream));
     PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -310,6 +316,7 @@ void percis_default_options(percis_options *opt) {
     opt->lane_order = 1;
     opt->direction = 2;
     opt->push_alpha = 0.0;
+    opt->estimator = 0;
 }
 
 percis_status percis_create(percis_ctx **out, int device, void *stream) {
@@ -353,7 +360,8 @@ void percis_destroy(percis_ctx *ctx) {
                       &ctx->src_fill, &ctx->src_off, &ctx->lane_of_v, &ctx->sorted_samples, &ctx->samp_lane,
                       &ctx->samp_t, &ctx->lane_src, &ctx->lane_off, &ctx->scratch, &ctx->red, &ctx->status,
                       &ctx->pc_tmp, &ctx->grad_tmp, &ctx->host_pinned, &ctx->vorder,
-                      &ctx->fq0, &ctx->fq1, &ctx->qstamp};
+                      &ctx->fq0, &ctx->fq1, &ctx->qstamp, &ctx->acc_ap,
+                      &ctx->ap_tau, &ctx->ap_stamp, &ctx->ap_list};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->counters.p) cudaFree(ctx->counters.p);
@@ -386,6 +394,9 @@ percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt) {
     if (opt->lane_order != 0 && opt->lane_order != 1) return set_err(ctx, PERCIS_E_INVALID, "lane_order must be 0 or 1");
     if (opt->direction < 0 || opt->direction > 2) return set_err(ctx, PERCIS_E_INVALID, "direction must be 0, 1 or 2");
     if (!(opt->push_alpha >= 0.0)) return set_err(ctx, PERCIS_E_INVALID, "push_alpha must be >= 0");
+    if (opt->estimator != 0 && opt->estimator != 1) return set_err(ctx, PERCIS_E_INVALID, "estimator must be 0 or 1");
+    if (opt->estimator == 1 && opt->form == PERCIS_FORM_PLAIN)
+        return set_err(ctx, PERCIS_E_INVALID, "the all-paths estimator runs in the batched form");
     if (opt->ell1 < 0 || opt->ell1 == 1 || opt->ell < 0 || !(opt->timeout_s > 0.0))
         return set_err(ctx, PERCIS_E_INVALID, "bad sample sizes or timeout");
     ctx->opt = *opt;
@@ -487,7 +498,8 @@ percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_
         dst = ctx->pc_tmp.as<double>();
     }
     k_finalize<<<grid_for(ctx, ctx->n, 256), 256, 0, ctx->stream>>>(
-        ctx->lam.as<double>(), ctx->cnt.as<unsigned long long>(), ctx->n, (double)ell, dst);
+        ctx->lam.as<double>(), ctx->cnt.as<unsigned long long>(),
+        ctx->opt.estimator == 1 ? ctx->acc_ap.as<double>() : nullptr, ctx->n, (double)ell, dst);
     PERCIS_CHECK_LAUNCH(ctx, "finalize");
     if (info) {
         PhaseStats h2{};
@@ -527,7 +539,7 @@ percis_status percis_backward(percis_ctx *ctx, const double *grad_pc, double *gr
     PERCIS_TRY(need_states(ctx));
     if (!grad_pc || !grad_x) return set_err(ctx, PERCIS_E_INVALID, "NULL gradient buffer");
     if (!ctx->have_paths || ctx->last_phase != 1 || ctx->last_ell <= 0)
-        return set_err(ctx, PERCIS_E_NO_SAMPLE, "backward needs a completed estimate");
+        return set_err(ctx, PERCIS_E_NO_SAMPLE, "backward needs a completed estimate of the one-path form");
     DeviceGuard g(ctx->device);
     const int64_t n = ctx->n;
     const double *gin = grad_pc;

@@ -79,6 +79,14 @@ struct MsArgs {
     const int64_t *rp;                // out-CSR offsets (out-degrees)
     unsigned long long *counters;     // 8 work counters (see percis_info.work)
     unsigned long long *levdeg;       // [W][Lcap+1] out-degree sums per lane and level
+    // all-paths estimator: per-warp scratch (tau counts, claim stamps, two level lists)
+    int32_t allpaths;
+    int32_t ap_warps;
+    int32_t ap_epoch;
+    double *acc_ap;                   // per-vertex sum of sigma_sv tau_v / sigma_st
+    unsigned long long *ap_tau;       // [ap_warps][n]
+    int32_t *ap_stamp;                // [ap_warps][n]
+    int32_t *ap_list;                 // [ap_warps][2n]
 };
 
 template <int K>
@@ -504,6 +512,90 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     }
     if (a.full) return;
 
+    if (a.allpaths) {
+        // ---- all-paths form (warp per sample): reverse sweep from t over the
+        // shortest-path DAG of lane j; tau_v = number of shortest v-t paths
+        // (exact integers), and every internal v receives
+        // f(v) = sigma_sv tau_v / sigma_st.  Scratch is per warp; entries are
+        // valid only where the claim stamp equals this sample's epoch.
+        if (gwarp >= a.ap_warps) return;
+        S *tau = reinterpret_cast<S *>(a.ap_tau) + gwarp * n;  // integers, or FP64 beyond 2^53
+        int32_t *stamp = a.ap_stamp + gwarp * n;
+        int32_t *la = a.ap_list + gwarp * 2 * n;
+        int32_t *lb = la + n;
+        const unsigned lt = (1u << lane) - 1u;
+        for (long long p = p0 + gwarp; p < p1; p += a.ap_warps) {
+            const int32_t i = a.sorted_samples[p];
+            const int32_t j = a.samp_lane[p] - a.lane_base;
+            const int32_t t = a.samp_t[p];
+            const int32_t d = __ldcg(&a.found[p]);
+            if (lane == 0) {
+                if (d < 0) a.kind[i] = 2;
+                a.ilen[i] = d < 0 ? 0 : d - 1;
+                a.path_off[i] = 0;
+            }
+            if (d < 2) continue;
+            const int32_t ep = a.ap_epoch + (int32_t)(p - p0) + 1;
+            const int wj = j >> 6;
+            const uint64_t bj = 1ull << (j & 63);
+            const double sst = (double)(S)__ldcg(&sig[(int64_t)t * W + j]);
+            if (lane == 0) {
+                la[0] = t;
+                tau[t] = S(1);
+                stamp[t] = ep;
+            }
+            int na = 1;
+            __syncwarp();
+            for (int L = d - 1; L >= 1; --L) {
+                const uint64_t *fL = a.fh + (int64_t)L * nk;
+                int nb = 0;
+                // claim the predecessors at level L (first claimer zeroes tau)
+                for (int q = 0; q < na; ++q) {
+                    const int32_t w = __ldcg(&la[q]);
+                    const int64_t e0 = a.irp[w], e1 = a.irp[w + 1];
+                    for (int64_t base = e0; base < e1; base += 32) {
+                        const int64_t ee = base + lane;
+                        bool mine = false;
+                        int32_t pv = 0;
+                        if (ee < e1) {
+                            pv = a.icol[ee];
+                            if (__ldcg(&fL[(int64_t)pv * K + wj]) & bj) {
+                                mine = atomicExch(&stamp[pv], ep) != ep;
+                                if (mine) tau[pv] = S(0);
+                            }
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, mine);
+                        if (mine) lb[nb + __popc(m & lt)] = pv;
+                        nb += __popc(m);
+                    }
+                }
+                __syncwarp();
+                // tau_p += tau_w over the DAG edges into level L+1
+                for (int q = 0; q < na; ++q) {
+                    const int32_t w = __ldcg(&la[q]);
+                    const S tw = __ldcg(&tau[w]);
+                    const int64_t e0 = a.irp[w], e1 = a.irp[w + 1];
+                    for (int64_t ee = e0 + lane; ee < e1; ee += 32) {
+                        const int32_t pv = a.icol[ee];
+                        if (__ldcg(&fL[(int64_t)pv * K + wj]) & bj) atomicAdd(&tau[pv], tw);
+                    }
+                }
+                __syncwarp();
+                for (int q = lane; q < nb; q += 32) {
+                    const int32_t v = __ldcg(&lb[q]);
+                    const double f = (double)(S)__ldcg(&sig[(int64_t)v * W + j]) * (double)__ldcg(&tau[v]) / sst;
+                    atomicAdd(&a.acc_ap[v], f);
+                }
+                __syncwarp();
+                int32_t *tmp = la;
+                la = lb;
+                lb = tmp;
+                na = nb;
+            }
+        }
+        return;
+    }
+
     // ---- backtrack every sample of the batch (warp per sample)
     for (long long p = p0 + gwarp; p < p1; p += nwarps) {
         const int32_t i = a.sorted_samples[p];
@@ -646,6 +738,15 @@ percis_status launch_ms_k2(percis_ctx *ctx, int K, MsArgs &a) {
     }
 }
 
+int ms_grid_for(percis_ctx *ctx, int K) {
+    switch (K) {
+        case 1: return ms_grid<1, false, 0>(ctx);
+        case 2: return ms_grid<2, false, 0>(ctx);
+        case 4: return ms_grid<4, false, 0>(ctx);
+        default: return ms_grid<8, false, 0>(ctx);
+    }
+}
+
 percis_status launch_ms_k(percis_ctx *ctx, int K, MsArgs &a) {
     switch (ctx->sigma_mode) {
         case 0: return launch_ms_k2<0>(ctx, K, a);
@@ -755,12 +856,42 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
         a.counters = ctx->counters.as<unsigned long long>();
         a.levdeg = ctx->levdeg.as<unsigned long long>();
     }
+    a.allpaths = ctx->opt.estimator == 1;
+    if (a.allpaths) {
+        // per-warp scratch of 20 n bytes, within a 8 GiB budget
+        const int64_t n = ctx->n;
+        const int64_t per_warp = 20 * n;
+        const int64_t warps = (int64_t)ms_grid_for(ctx, K) * (kMsBlock / 32);
+        const int64_t ap_warps = std::max<int64_t>(1, std::min<int64_t>(warps, (8ll << 30) / per_warp));
+        if (ctx->ap_warps != ap_warps || ctx->ap_n != n) {
+            PERCIS_TRY(ensure(ctx, ctx->ap_tau, sizeof(unsigned long long) * n * ap_warps, "all-paths tau"));
+            PERCIS_TRY(ensure(ctx, ctx->ap_stamp, sizeof(int32_t) * n * ap_warps, "all-paths stamps"));
+            PERCIS_TRY(ensure(ctx, ctx->ap_list, sizeof(int32_t) * 2 * n * ap_warps, "all-paths lists"));
+            PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ap_stamp.p, 0, sizeof(int32_t) * n * ap_warps, ctx->stream));
+            ctx->ap_warps = ap_warps;
+            ctx->ap_n = n;
+            ctx->ap_epoch = 0;
+        }
+        if (ctx->ap_epoch > (1 << 30)) {
+            PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ap_stamp.p, 0, sizeof(int32_t) * n * ap_warps, ctx->stream));
+            ctx->ap_epoch = 0;
+        }
+        a.ap_warps = (int32_t)ap_warps;
+        a.acc_ap = ctx->acc_ap.as<double>();
+        a.ap_tau = ctx->ap_tau.as<unsigned long long>();
+        a.ap_stamp = ctx->ap_stamp.as<int32_t>();
+        a.ap_list = ctx->ap_list.as<int32_t>();
+    }
     for (int64_t b = 0; b < B; ++b) {
         a.lane_base = (int32_t)(b * W);
         a.nlanes = (int32_t)std::min<int64_t>(W, n_sources - b * W);
         cudaEvent_t e0 = next_event(ctx), e1 = next_event(ctx);
         if (e0) cudaEventRecord(e0, ctx->stream);
         next_stamps(ctx, a);
+        if (a.allpaths) {
+            a.ap_epoch = ctx->ap_epoch;
+            ctx->ap_epoch += (int32_t)std::min<int64_t>(count, 1 << 30) + 1;
+        }
         PERCIS_TRY(launch_ms_k(ctx, K, a));
         if (e1) cudaEventRecord(e1, ctx->stream);
     }

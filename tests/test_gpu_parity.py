@@ -181,6 +181,52 @@ def test_estimate_matches_oracle(binding):
         e.close()
 
 
+@pytest.mark.parametrize("name", ["er1000", "ba3000", "rmat12", "grid30"])
+def test_allpaths_estimate_matches_oracle(binding, name):
+    """All-paths form: p(v) = lambda_v sum_i sigma_sv tau_v / sigma_st / l over
+    the same sampled pairs; per-sample fractions are exact ratios, the sums
+    differ from the oracle's only in rounding order."""
+    g = GRAPHS[name]()
+    og = oracle.from_synth(g)
+    x = _states(name, g.n)
+    eng = _engine(binding, g, x, estimator="allpaths", ell1=1500, ell=4000)
+    pc, info = eng.estimate(0.05, 0.1, seed=9)
+    res = oracle.percis(og, x, 0.05, 0.1, 9, ell1=1500, ell=4000, keep_paths=False, allpaths=True)
+    ref = res.pc
+    assert info["ell"] == 4000 and info["ell1"] == 1500
+    assert info["rho_tilde"] == res.rho_tilde
+    assert info["p1_max"] == pytest.approx(res.p1_max, rel=1e-12)
+    assert np.allclose(_np(pc), ref, rtol=1e-12, atol=1e-15)
+    # same pairs as the one-path form: identical rho~ and sum over v of the
+    # unnormalised sums equals sum_i |I(tau_i)| (each sample spreads d-1)
+    lam = res.prep.lam
+    tot = float(np.sum(_np(pc) / lam)) * 4000
+    assert tot == pytest.approx(float(res.phase2.ilen.sum()), rel=1e-10)
+    with pytest.raises(binding.PercisError):
+        eng.backward(torch.ones(g.n, dtype=torch.float64, device="cuda"))
+    eng.close()
+
+
+def test_allpaths_lower_variance(binding):
+    """Rao-Blackwellisation: on the same pairs the all-paths estimate is
+    closer to the exact value than the one-path estimate (summed squared
+    error over vertices, a grid with many shortest paths per pair)."""
+    g = synth.grid_2d(24, 0.0, 0)
+    x = synth.states_uniform(g.n, 4)
+    eng = _engine(binding, g, x)
+    exact = eng.exact()
+    e1 = e2 = 0.0
+    for seed in range(4):
+        eng.set_options(estimator="path", ell1=1000, ell=3000)
+        p1, _ = eng.estimate(0.05, 0.1, seed=seed)
+        eng.set_options(estimator="allpaths")
+        p2, _ = eng.estimate(0.05, 0.1, seed=seed)
+        e1 += float(torch.sum((p1 - exact) ** 2))
+        e2 += float(torch.sum((p2 - exact) ** 2))
+    assert e2 < 0.7 * e1
+    eng.close()
+
+
 def test_backward_matches_oracle_and_fd(binding):
     g = synth.barabasi_albert(2000, 4, 0)
     og = oracle.from_synth(g)

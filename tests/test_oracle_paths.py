@@ -256,3 +256,23 @@ def test_allpaths_estimator_unbiased():
         est += ph.acc_all / ell
     sd = np.sqrt(np.maximum(pe * (prep.dhat - pe), 1e-30) / (ell * reps))
     assert np.all(np.abs(est / reps - pe) <= 5 * sd + 1e-12)
+
+
+def test_allpaths_estimator_lower_error():
+    """Averaging over all shortest s-t paths (a conditional expectation of the
+    one-path estimator given the pair) cannot raise the variance; on a grid,
+    where pairs have many shortest paths, the squared error drops well below
+    the one-path estimator's on the same pairs."""
+    g = synth.grid_2d(24, 0.0, 0)
+    x = synth.states_uniform(g.n, 4)
+    og = oracle.from_synth(g)
+    prep = oracle.prepare(x)
+    ex = oracle.exact_pc(og, x, prep.Cv)
+    e1 = e2 = 0.0
+    for seed in range(4):
+        r1 = oracle.percis(og, x, 0.05, 0.1, seed, ell1=1000, ell=3000, keep_paths=False, prep=prep)
+        r2 = oracle.percis(og, x, 0.05, 0.1, seed, ell1=1000, ell=3000, keep_paths=False, prep=prep, allpaths=True)
+        assert np.array_equal(r1.phase2.s, r2.phase2.s) and np.array_equal(r1.phase2.ilen, r2.phase2.ilen)
+        e1 += float(((r1.pc - ex) ** 2).sum())
+        e2 += float(((r2.pc - ex) ** 2).sum())
+    assert e2 < 0.6 * e1
