@@ -52,7 +52,9 @@ def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, directed: bool, nam
         src, dst = np.concatenate([src, dst]), np.concatenate([dst, src])
     keep = src != dst
     src, dst = src[keep], dst[keep]
-    key = np.unique(src * n + dst)
+    key = np.sort(src * n + dst)
+    if key.size:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     rows = key // n
     cols = (key % n).astype(np.int32)
     counts = np.bincount(rows, minlength=n)
@@ -139,16 +141,17 @@ def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int,
     n_edges = edge_factor * n
     rng = np.random.default_rng(seed)
     srcs, dsts = [], []
-    ab, abc = a + b, a + b + c
+    # quadrant thresholds on 32-bit uniform integers (probabilities exact to 2^-32)
+    ta, tab, tabc = (np.uint32(min(round(p * 2.0 ** 32), 2 ** 32 - 1)) for p in (a, a + b, a + b + c))
     done = 0
     while done < n_edges:
         cnt = min(chunk, n_edges - done)
         u = np.zeros(cnt, dtype=np.int64)
         v = np.zeros(cnt, dtype=np.int64)
         for bit in range(scale):
-            r = rng.random(cnt)
-            ubit = r >= ab  # quadrants c, d
-            vbit = ((r >= a) & (r < ab)) | (r >= abc)  # quadrants b, d
+            r = rng.integers(0, 2 ** 32, size=cnt, dtype=np.uint32)
+            ubit = r >= tab  # quadrants c, d
+            vbit = ((r >= ta) & (r < tab)) | (r >= tabc)  # quadrants b, d
             u |= ubit.astype(np.int64) << bit
             v |= vbit.astype(np.int64) << bit
         srcs.append(u)
