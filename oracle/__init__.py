@@ -519,23 +519,31 @@ class Result:
 
 
 def percis(g: OGraph, x, eps: float, delta: float, seed: int, ell1: int | None = None, ell: int | None = None,
-           D: int | None = None, prep: Prep | None = None, keep_paths: bool = True, allpaths: bool = False) -> Result:
+           D: int | None = None, prep: Prep | None = None, keep_paths: bool = True, allpaths: bool = False,
+           data_independent: bool = False) -> Result:
     """Algorithm 1 (PercIS): D, phase 1 (l1 samples, pair tag 0, path tag 2),
     rho^, v^, x^, l, then phase 2 (l fresh samples, pair tag 1, path tag 3).
     The phase-1 estimate uses 1/l1 (the 1/l printed in that line of
-    Algorithm 1 is read as the phase-1 sample size)."""
+    Algorithm 1 is read as the phase-1 sample size).
+
+    data_independent: PercIS-DI (Section V, sample-size experiment): no first
+    phase; rho^ = D and v^ = d^2/4 (its largest possible value)."""
     if prep is None:
         prep = prepare(x)
     if not np.all(prep.Cv > 0):
         raise ValueError("degenerate states: some C_v = 0 (p(v) undefined)")
     if D is None:
         D = vertex_diam_ub(g)
-    l1 = ell1 if ell1 is not None else ell1_default(eps, delta)
-    ph1 = run_samples(g, prep, seed, 0, 2, 0, l1, keep_paths=False, allpaths=allpaths)
-    p1 = (ph1.acc_all if allpaths else ph1.acc) / l1
-    p1_max = float(p1.max())
-    rh, rt, Lam = rho_hat(ph1.ilen, D, delta)
-    vh = v_hat(p1_max, prep.dhat, l1, delta)
+    if data_independent:
+        l1, ph1, p1_max, rt, Lam = 0, None, 0.0, 0.0, 0.0
+        rh, vh = float(D), prep.dhat * prep.dhat / 4.0
+    else:
+        l1 = ell1 if ell1 is not None else ell1_default(eps, delta)
+        ph1 = run_samples(g, prep, seed, 0, 2, 0, l1, keep_paths=False, allpaths=allpaths)
+        p1 = (ph1.acc_all if allpaths else ph1.acc) / l1
+        p1_max = float(p1.max())
+        rh, rt, Lam = rho_hat(ph1.ilen, D, delta)
+        vh = v_hat(p1_max, prep.dhat, l1, delta)
     xh = x_hat(vh, prep.dhat)
     if ell is None:
         ell, _ = ell_sup(eps, delta, prep.dhat, rh, xh)

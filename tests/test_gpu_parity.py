@@ -227,6 +227,23 @@ def test_allpaths_lower_variance(binding):
     eng.close()
 
 
+def test_percis_di_matches_oracle(binding):
+    """PercIS-DI: no first phase, rho^ = D, v^ = d^2/4; l and the estimate
+    as the oracle computes them."""
+    g, x, eps, delta = synth.workload("er1000")
+    og = oracle.from_synth(g)
+    eng = _engine(binding, g, x, data_independent=1)
+    pc, info = eng.estimate(eps, delta, seed=3)
+    res = oracle.percis(og, x, eps, delta, 3, keep_paths=False, data_independent=True)
+    assert info["ell1"] == 0 and info["batches"][0] == 0
+    assert info["rho_hat"] == res.rho_hat and info["v_hat"] == pytest.approx(res.v_hat, rel=1e-15)
+    assert abs(info["ell"] - res.ell) <= 1
+    if info["ell"] != res.ell:
+        res = oracle.percis(og, x, eps, delta, 3, ell=info["ell"], keep_paths=False, data_independent=True)
+    assert np.max(np.abs(_np(pc) - res.pc)) <= 1e-9
+    eng.close()
+
+
 def test_backward_matches_oracle_and_fd(binding):
     g = synth.barabasi_albert(2000, 4, 0)
     og = oracle.from_synth(g)
@@ -321,6 +338,87 @@ def test_full_size_outbreak_sampled(binding):
     for i in np.random.default_rng(0).choice(ell, 25, replace=False):
         ph = oracle.run_samples(og, prep, 0, 1, 3, int(i), 1, keep_paths=True)
         assert np.array_equal(nodes[ptr[i]:ptr[i + 1]], ph.path_nodes), i
+    eng.close()
+
+
+@pytest.mark.slow
+def test_full_size_rmat22_sampled(binding):
+    """Directed R-MAT scale 22 (edge factor 16), Beta(0.5, 2) states,
+    eps=0.01: every phase-2 pair bit-exact, sampled paths (reachable and
+    unreachable targets) against the oracle one by one, and the estimate
+    equal to lambda_v cnt_v / l over the returned paths."""
+    g, x, eps, delta = synth.workload("rmat22_beta")
+    og = oracle.from_synth(g)
+    eng = _engine(binding, g, x)
+    pc, info = eng.estimate(eps, delta, seed=0)
+    ell = info["ell"]
+    assert info["ell1"] == 1000 and info["vertex_diam"] == g.n - 2
+    prep = oracle.prepare(x)
+    s, t = eng.sample_pairs(0, 1, 0, ell)
+    rs, rt, _, _ = oracle.sample_pairs(prep, 0, 1, 0, ell)
+    assert np.array_equal(_np(s), rs) and np.array_equal(_np(t), rt)
+    ptr, nodes = eng.get_paths(ell)
+    ptr, nodes = _np(ptr), _np(nodes)
+    cnt = np.bincount(nodes, minlength=g.n)
+    assert np.max(np.abs(_np(pc) - prep.lam * cnt / ell)) <= 1e-12
+    assert info["sum_internal"][1] == int(ptr[-1])
+    rng = np.random.default_rng(0)
+    long_ = np.flatnonzero(np.diff(ptr) >= 2)
+    picks = np.concatenate([rng.choice(ell, 6, replace=False), rng.choice(long_, 4, replace=False)])
+    kinds = set()
+    for i in picks:
+        ph = oracle.run_samples(og, prep, 0, 1, 3, int(i), 1, keep_paths=True)
+        kinds.add(int(ph.kind[0]))
+        assert np.array_equal(nodes[ptr[i]:ptr[i + 1]], ph.path_nodes), i
+    assert 0 in kinds
+    eng.close()
+
+
+@pytest.mark.slow
+def test_full_size_differentiation_ba200k(binding):
+    """Barabasi-Albert n=200,000 (m=4), uniform states: the full-size
+    forward + backward (l from the bound at eps=0.01) satisfies the two
+    invariances of the fixed-sample estimator (F is unchanged by x -> x + c
+    and by x -> a x, so sum_u grad_u = 0 and sum_u x_u grad_u = 0); on the
+    same graph with l fixed to 2,000 the gradient equals the oracle's VJP
+    and central finite differences on sampled coordinates."""
+    g, x, eps, delta = synth.workload("ba200k_uniform")
+    og = oracle.from_synth(g)
+    gvec = np.random.default_rng(2).standard_normal(g.n)
+    eng = _engine(binding, g, x)
+    pc, info = eng.estimate(eps, delta, seed=0)
+    assert info["ell"] > 10000
+    gx = _np(eng.backward(torch.as_tensor(gvec, device="cuda")))
+    scale = np.sum(np.abs(gx))
+    assert abs(np.sum(gx)) <= 1e-10 * scale
+    assert abs(np.sum(x * gx)) <= 1e-10 * np.sum(np.abs(x * gx))
+    ell = 2000
+    eng.set_options(ell1=1000, ell=ell)
+    pc, info = eng.estimate(eps, delta, seed=4)
+    prep = oracle.prepare(x, cv_method="sorted")
+    ph = oracle.run_samples(og, prep, 4, 1, 3, 0, ell, keep_paths=True)
+    F = prep.lam * ph.cnt / ell
+    assert np.max(np.abs(_np(pc) - F)) <= 1e-12
+    gx = _np(eng.backward(torch.as_tensor(gvec, device="cuda")))
+    ref = oracle.vjp_fixed(prep, ell, ph, F, gvec)
+    assert np.linalg.norm(gx - ref) / np.linalg.norm(ref) <= 1e-10
+    h = 1e-6
+    checked = 0
+    xs = np.sort(x)
+    for u in np.random.default_rng(3).permutation(g.n)[:400]:
+        k = np.searchsorted(xs, x[u])
+        near = xs[max(0, k - 2):k + 3]
+        if np.sum(np.abs(near - x[u]) < 4 * h) > 1:
+            continue
+        touch = (ph.kind == 0) & ((ph.s == u) | (ph.t == u))
+        if np.any(np.abs(x[ph.s[touch]] - x[ph.t[touch]]) <= 1e-3):
+            continue
+        fd = oracle.fd_fixed(prep, ell, ph, gvec, int(u), h)
+        assert gx[u] == pytest.approx(fd, rel=1e-6, abs=1e-12 * np.abs(gx).max())
+        checked += 1
+        if checked >= 12:
+            break
+    assert checked >= 8
     eng.close()
 
 

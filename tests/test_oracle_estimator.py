@@ -170,3 +170,41 @@ def test_is_gradient_is_unbiased_for_exact_gradient():
     mean = acc / reps
     sd = np.sqrt(np.maximum(sq / reps - mean ** 2, 0) / reps)
     assert np.all(np.abs(mean - exact) <= 5 * sd + 1e-3 * np.abs(exact).max())
+
+
+def test_fixed_sample_vjp_invariances():
+    """R(x_s - x_t) and C_v(x) are unchanged by x -> x + c and scale by a
+    under x -> a x, so the fixed-sample estimator F is invariant under both
+    and its VJP satisfies sum_u grad_u = 0 and sum_u x_u grad_u = 0 (Euler's
+    identity for degree-0 homogeneous functions)."""
+    g = synth.barabasi_albert(300, 3, 6)
+    og = oracle.from_synth(g)
+    x = np.random.default_rng(6).random(300)
+    prep = oracle.prepare(x, cv_method="sorted")
+    ell = 1500
+    ph = oracle.run_samples(og, prep, 21, 1, 3, 0, ell, keep_paths=True)
+    F = ph.acc / ell
+    gvec = np.random.default_rng(7).standard_normal(300)
+    grad = oracle.vjp_fixed(prep, ell, ph, F, gvec)
+    assert abs(grad.sum()) <= 1e-11 * np.abs(grad).sum()
+    assert abs((x * grad).sum()) <= 1e-11 * np.abs(x * grad).sum()
+
+
+def test_percis_di_guarantee_and_larger_sample():
+    """PercIS-DI (rho^ = D, v^ = d^2/4, no first phase) keeps the eps
+    guarantee (>= 18 of 20 seeds on G(1000, M=4000)) and never needs fewer
+    samples than the data-dependent bound (Section V: DI is always larger)."""
+    g, x, eps, delta = synth.workload("er1000")
+    og = oracle.from_synth(g)
+    prep = oracle.prepare(x)
+    pe = oracle.exact_pc(og, x, prep.Cv)
+    D = oracle.vertex_diam_ub(og)
+    ok = 0
+    for seed in range(20):
+        res = oracle.percis(og, x, eps, delta, seed, prep=prep, D=D, keep_paths=False, data_independent=True)
+        assert res.ell1 == 0 and res.rho_hat == D and res.x_hat == pytest.approx(prep.dhat / 2, rel=1e-12)
+        ok += int(np.max(np.abs(res.pc - pe)) <= eps)
+        if seed < 3:
+            dd = oracle.percis(og, x, eps, delta, seed, prep=prep, D=D, keep_paths=False)
+            assert res.ell >= dd.ell
+    assert ok >= 18
