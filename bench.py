@@ -132,6 +132,25 @@ def cpu_baseline(budget_s: float = 12.0) -> dict:
                       f"estimator), {t_used:.1f} s on one host thread"}
 
 
+def replica_seed_base(rank: int) -> int:
+    """Each replica draws its own Philox streams (seeds far apart per rank)."""
+    return 1_000_003 * rank
+
+
+def job_totals(t_local: float, pairs_local: int, dist, device: str):
+    """Whole-job time (max over ranks) and pairs (sum over ranks); replicas
+    exchange nothing else."""
+    if dist is None:
+        return t_local, float(pairs_local)
+    import torch
+
+    tt = torch.tensor([t_local, float(pairs_local)], dtype=torch.float64, device=device)
+    tmax = tt.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tt[1])
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -211,7 +230,7 @@ def main():
     x_d = torch.as_tensor(x, dtype=torch.float64, device="cuda")
     pc_d = torch.empty(g.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    seed_base = 1_000_003 * rank
+    seed_base = replica_seed_base(rank)
 
     def step(seed):
         binding.percis_load_csr(eng.ctx, g.n, g.nnz, rp_d, col_d, False, 1)
@@ -243,14 +262,7 @@ def main():
     launches = binding.percis_launch_count(eng.ctx) - launches0
     t_total = sum(times) / 1000.0
     pairs = sum(i["ell1"] + i["ell"] for i in infos)
-    if dist:
-        tt = torch.tensor([t_total, float(pairs)], dtype=torch.float64, device="cuda")
-        tmax = tt.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_job, pairs_job = float(tmax[0]), float(tt[1])
-    else:
-        t_job, pairs_job = t_total, float(pairs)
+    t_job, pairs_job = job_totals(t_total, pairs, dist, "cuda")
     value = pairs_job / t_job
 
     extras = {}

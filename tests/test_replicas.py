@@ -1,0 +1,68 @@
+"""Replicas on several GPUs: the host logic of the multi-rank bench (job
+totals over ranks, per-rank seeds, the reference arm on rank 0 only), run as
+world-size-2 gloo process groups on the CPU."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t_local = [2.0, 3.5][rank]
+    pairs_local = [1000, 1500][rank]
+    t, p = bench.job_totals(t_local, pairs_local, dist, "cpu")
+    q.put((rank, t, p, bench.replica_seed_base(rank)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_job_totals_two_ranks():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, pairs, seed in got:
+        assert t == 3.5 and pairs == 2500.0  # slowest rank's time, all ranks' pairs
+    assert got[0][3] != got[1][3]
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """--impl reference at N=2: rank 0 alone runs the oracle and prints one
+    JSON line; the other rank exits 0 without work."""
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-pairs", "20"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
+    assert rec["e2e"]["h2d_bytes_per_step"] == 0
