@@ -28,7 +28,8 @@ struct alignas(16) MsCtl {
     uint32_t ticket;
     int32_t level;                // last level reached
     int32_t push_next;            // direction of the next level (1 = push)
-    int32_t qn[2];                // frontier queue sizes (ping-pong by level parity)
+    int32_t qn[2];                // frontier queue sizes (ping-pong by level parity): light vertices from the front
+    int32_t qh[2];                // and vertices of in-degree > 32 from the back of the same array
     unsigned long long active[8];    // lanes still running (K <= 8 words)
     unsigned long long nonempty[2][8];  // per-level OR of discovered bits (ping-pong)
     unsigned long long fedges[2];    // push work of the next level: frontier out-edges x words (ping-pong)

@@ -73,8 +73,6 @@ struct MsArgs {
     int32_t stamp_base;
     int32_t policy;                   // 0 = pull every level, 1 = push every level, 2 = by work estimate
     double push_alpha;                // policy 2: push while alpha * push work < pull work
-    unsigned long long wrap_guard;    // a pushed count >= this could wrap 2^64 at a high in-degree vertex
-    unsigned long long wrap_guard32;  // the same for 32-bit storage
     // instrumentation (INSTR variant only)
     const int64_t *rp;                // out-CSR offsets (out-degrees)
     unsigned long long *counters;     // 8 work counters (see percis_info.work)
@@ -114,6 +112,59 @@ __device__ __forceinline__ S warp_incl_scan(S v) {
     return v;
 }
 
+// Sum the counts of one 32-edge chunk's parents into the 64 lanes of word w:
+// lane l's edge has parent u and frontier bits fw (already restricted to the
+// lanes being counted).  Parents are taken in edge order, four per round so
+// their loads overlap; acc0 / acc1 collect lanes l and l+32 of the word.
+template <int SM, class ST, class S>
+__device__ __forceinline__ void gather_chunk(const ST *sig, int W, int w, uint64_t fw, int32_t u, S &acc0, S &acc1,
+                                             bool &ovf) {
+    constexpr bool FPSIG = SM == 2;
+    constexpr unsigned long long kLimit = SigmaMode<SM>::limit;
+    const int lane = threadIdx.x & 31;
+    unsigned nz = __ballot_sync(0xffffffffu, fw != 0ull);
+    while (nz) {
+        const int j0 = __ffs(nz) - 1;
+        nz &= nz - 1;
+        const bool h1 = nz != 0u;
+        const int j1 = h1 ? __ffs(nz) - 1 : j0;
+        if (h1) nz &= nz - 1;
+        const bool h2 = nz != 0u;
+        const int j2 = h2 ? __ffs(nz) - 1 : j0;
+        if (h2) nz &= nz - 1;
+        const bool h3 = nz != 0u;
+        const int j3 = h3 ? __ffs(nz) - 1 : j0;
+        if (h3) nz &= nz - 1;
+        const uint64_t f0 = shfl64(fw, j0);
+        const uint64_t f1 = h1 ? shfl64(fw, j1) : 0ull;
+        const uint64_t f2 = h2 ? shfl64(fw, j2) : 0ull;
+        const uint64_t f3 = h3 ? shfl64(fw, j3) : 0ull;
+        const ST *r0 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j0) * W + 64 * w;
+        const ST *r1 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j1) * W + 64 * w;
+        const ST *r2 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j2) * W + 64 * w;
+        const ST *r3 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j3) * W + 64 * w;
+        S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0), b0 = S(0), b1 = S(0), b2 = S(0), b3 = S(0);
+        if ((f0 >> lane) & 1ull) a0 = __ldcg(r0 + lane);
+        if ((f1 >> lane) & 1ull) a1 = __ldcg(r1 + lane);
+        if ((f2 >> lane) & 1ull) a2 = __ldcg(r2 + lane);
+        if ((f3 >> lane) & 1ull) a3 = __ldcg(r3 + lane);
+        if ((f0 >> (lane + 32)) & 1ull) b0 = __ldcg(r0 + lane + 32);
+        if ((f1 >> (lane + 32)) & 1ull) b1 = __ldcg(r1 + lane + 32);
+        if ((f2 >> (lane + 32)) & 1ull) b2 = __ldcg(r2 + lane + 32);
+        if ((f3 >> (lane + 32)) & 1ull) b3 = __ldcg(r3 + lane + 32);
+        if (FPSIG) {
+            // keep the in-adjacency order of the additions
+            acc0 += a0; acc0 += a1; acc0 += a2; acc0 += a3;
+            acc1 += b0; acc1 += b1; acc1 += b2; acc1 += b3;
+        } else {
+            acc0 += (a0 + a1) + (a2 + a3);
+            acc1 += (b0 + b1) + (b2 + b3);
+            // flag before four more addends could wrap 2^64
+            ovf |= (acc0 >= kLimit) | (acc1 >= kLimit);
+        }
+    }
+}
+
 template <int K, bool INSTR, int SM>
 __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     constexpr int W = 64 * K;
@@ -121,7 +172,6 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     using S = typename SigmaMode<SM>::S;
     using ST = typename SigmaMode<SM>::ST;
     constexpr unsigned long long kLimit = SigmaMode<SM>::limit;
-    const unsigned long long wrap_guard = SM == 0 ? a.wrap_guard32 : a.wrap_guard;
     ST *sig = static_cast<ST *>(a.sigma);
     bool ovf = false;
     unsigned long long n_sload = 0, n_swrite = 0, n_uv = 0, n_ue = 0;
@@ -144,12 +194,6 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         a.fh[i] = 0ull;
         a.fh[nk + i] = 0ull;
     }
-    if (a.policy != 0) {
-        // pushes accumulate into sigma, so every count starts at zero
-        ulonglong2 *s2 = reinterpret_cast<ulonglong2 *>(a.sigma);
-        const int64_t n2 = n * (int64_t)W * (int64_t)sizeof(ST) / 16;
-        for (int64_t i = tid; i < n2; i += nthreads) s2[i] = make_ulonglong2(0ull, 0ull);
-    }
     for (long long p = p0 + tid; p < p1; p += nthreads) a.found[p] = -1;
     if (INSTR)
         for (int64_t i = tid; i < (int64_t)W * (a.Lcap + 1); i += nthreads) a.levdeg[i] = 0ull;
@@ -167,6 +211,8 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             ctl->level = 0;
             ctl->qn[0] = a.nlanes;
             ctl->qn[1] = 0;
+            ctl->qh[0] = 0;
+            ctl->qh[1] = 0;
             ctl->push_next = a.policy != 0;
             ctl->t_start = globaltimer_ns();
         }
@@ -179,7 +225,6 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         atomicOr((unsigned long long *)&a.fh[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         sig[(int64_t)v * W + j] = ST(1);
         a.fq0[j] = v;
-        a.qstamp[v] = a.stamp_base;
         if (INSTR) a.levdeg[(int64_t)j * (a.Lcap + 1)] = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
         if (!a.full) {
             const long long q0 = a.lane_off[a.lane_base + j], q1 = a.lane_off[a.lane_base + j + 1];
@@ -190,6 +235,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
 
     __shared__ unsigned long long s_nonempty[K];
     __shared__ unsigned long long s_act[K];
+    __shared__ unsigned long long s_cont[K];
     int L = 0;
     for (;;) {
         bool any_act = false;
@@ -206,131 +252,69 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         const int32_t *qcur = (L & 1) ? a.fq1 : a.fq0;
         int32_t *qnext = (L & 1) ? a.fq0 : a.fq1;
         int32_t *qn_next = &ctl->qn[(L + 1) & 1];
-        const int32_t stamp_next = a.stamp_base + L + 1;
+        int32_t *qh_next = &ctl->qh[(L + 1) & 1];
         const bool push = ld_relaxed_u32((const uint32_t *)&ctl->push_next) != 0u;
 
+        // ---- phase A1: discover level L+1 (frontier bits only; counts follow in A2).
+        // One warp per vertex with all K lane words at once: lane w < K holds
+        // word w, edges are spread over the lanes and their K words are loaded
+        // together.
         if (push) {
-            // ---- phase A (push): one warp per (frontier vertex, lane word); the
-            // parent's counts are loaded once and added to every unvisited
-            // out-neighbour with fire-and-forget reductions.
             const int64_t qn = (int64_t)ld_relaxed_u32((const uint32_t *)&ctl->qn[L & 1]);
-            for (int64_t it = gwarp; it < qn * K; it += nwarps) {
-                const int64_t k = it / K;
-                const int w = (int)(it - k * K);
-                const int32_t u = __ldcg(&qcur[k]);
-                const uint64_t fu = __ldcg(&fcur[(int64_t)u * K + w]) & s_act[w];
-                if (fu == 0ull) continue;
-                const ST *urow = sig + (int64_t)u * W + 64 * w;
-                const ST su0 = ((fu >> lane) & 1ull) ? __ldcg(urow + lane) : ST(0);
-                const ST su1 = ((fu >> (lane + 32)) & 1ull) ? __ldcg(urow + lane + 32) : ST(0);
-                // no vertex has more parents than max_indeg: counts below the guard cannot wrap the storage
-                if (!FPSIG) ovf |= ((S)su0 >= (S)wrap_guard) | ((S)su1 >= (S)wrap_guard);
+            const int64_t qh = (int64_t)ld_relaxed_u32((const uint32_t *)&ctl->qh[L & 1]);
+            for (int64_t k = gwarp; k < qn + qh; k += nwarps) {
+                const int32_t u = __ldcg(&qcur[k < qn ? k : n - 1 - (k - qn)]);
+                uint64_t fl = 0ull;
+                if (lane < K) fl = __ldcg(&fcur[(int64_t)u * K + lane]) & s_act[lane];
+                if (!__ballot_sync(0xffffffffu, fl != 0ull)) continue;
+                uint64_t fu[K];
+#pragma unroll
+                for (int w = 0; w < K; ++w) fu[w] = shfl64(fl, w);
                 const int64_t e0 = a.rp[u], e1 = a.rp[u + 1];
-                for (int64_t base = e0; base < e1; base += 32) {
-                    const int64_t e = base + lane;
-                    int32_t v = 0;
-                    uint64_t m = 0ull;
-                    if (e < e1) {
-                        v = a.col[e];
-                        m = fu & ~__ldcg(&a.vis[(int64_t)v * K + w]);
-                    }
-                    // fire-and-forget: the new frontier is collected in phase B
-                    if (m) atomicOr((unsigned long long *)&fnext[(int64_t)v * K + w], (unsigned long long)m);
-                    if (INSTR) n_sload += (unsigned long long)__popcll(m);
-                    unsigned nz = __ballot_sync(0xffffffffu, m != 0ull);
-                    while (nz) {
-                        const int j = __ffs(nz) - 1;
-                        nz &= nz - 1;
-                        const uint64_t mj = shfl64(m, j);
-                        ST *vrow = sig + (int64_t)__shfl_sync(0xffffffffu, v, j) * W + 64 * w;
-                        if ((mj >> lane) & 1ull) atomicAdd(vrow + lane, su0);
-                        if ((mj >> (lane + 32)) & 1ull) atomicAdd(vrow + lane + 32, su1);
+                for (int64_t e = e0 + lane; e < e1; e += 32) {
+                    const int32_t v = a.col[e];
+                    uint64_t vv[K];
+                    load_words<K>(a.vis + (int64_t)v * K, vv);
+#pragma unroll
+                    for (int w = 0; w < K; ++w) {
+                        const uint64_t m = fu[w] & ~vv[w];
+                        // fire-and-forget: the new frontier is collected after the barrier
+                        if (m) atomicOr((unsigned long long *)&fnext[(int64_t)v * K + w], (unsigned long long)m);
                     }
                 }
             }
         } else {
-            // ---- phase A (pull): one warp per (vertex, lane word) item
-            for (int64_t it = gwarp; it < nk; it += nwarps) {
-                const int64_t v = it / K;
-                const int w = (int)(it - v * K);
-                const uint64_t vw = __ldcg(&a.vis[it]);
-                const uint64_t cw = s_act[w] & ~vw;
-                if (cw == 0ull) {
-                    if (lane == 0) fnext[it] = 0ull;
-                    continue;
-                }
-                uint64_t nbp = 0ull;
-                S acc0 = S(0), acc1 = S(0);
+            // every vertex with unvisited active lanes; the scan stops once each
+            // such lane has found a parent
+            for (int64_t v = gwarp; v < n; v += nwarps) {
+                uint64_t cl = 0ull;
+                if (lane < K) cl = s_act[lane] & ~__ldcg(&a.vis[v * K + lane]);
+                if (!__ballot_sync(0xffffffffu, cl != 0ull)) continue;
+                uint64_t nbl = 0ull;
                 const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
                 for (int64_t base = e0; base < e1; base += 32) {
                     const int64_t e = base + lane;
-                    int32_t u = 0;
-                    uint64_t fw = 0ull;
+                    uint64_t f[K];
                     if (e < e1) {
-                        u = a.icol[e];
-                        fw = __ldcg(&fcur[(int64_t)u * K + w]) & cw;
+                        load_words<K>(fcur + (int64_t)a.icol[e] * K, f);
+                    } else {
+#pragma unroll
+                        for (int w = 0; w < K; ++w) f[w] = 0ull;
                     }
-                    nbp |= fw;
-                    if (INSTR) n_sload += (unsigned long long)__popcll(fw);
-                    unsigned nz = __ballot_sync(0xffffffffu, fw != 0ull);
-                    while (nz) {
-                        // up to four parents per round so their count loads overlap
-                        const int j0 = __ffs(nz) - 1;
-                        nz &= nz - 1;
-                        const bool h1 = nz != 0u;
-                        const int j1 = h1 ? __ffs(nz) - 1 : j0;
-                        if (h1) nz &= nz - 1;
-                        const bool h2 = nz != 0u;
-                        const int j2 = h2 ? __ffs(nz) - 1 : j0;
-                        if (h2) nz &= nz - 1;
-                        const bool h3 = nz != 0u;
-                        const int j3 = h3 ? __ffs(nz) - 1 : j0;
-                        if (h3) nz &= nz - 1;
-                        const uint64_t f0 = shfl64(fw, j0);
-                        const uint64_t f1 = h1 ? shfl64(fw, j1) : 0ull;
-                        const uint64_t f2 = h2 ? shfl64(fw, j2) : 0ull;
-                        const uint64_t f3 = h3 ? shfl64(fw, j3) : 0ull;
-                        const ST *r0 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j0) * W + 64 * w;
-                        const ST *r1 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j1) * W + 64 * w;
-                        const ST *r2 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j2) * W + 64 * w;
-                        const ST *r3 = sig + (int64_t)__shfl_sync(0xffffffffu, u, j3) * W + 64 * w;
-                        S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0), b0 = S(0), b1 = S(0), b2 = S(0), b3 = S(0);
-                        if ((f0 >> lane) & 1ull) a0 = __ldcg(r0 + lane);
-                        if ((f1 >> lane) & 1ull) a1 = __ldcg(r1 + lane);
-                        if ((f2 >> lane) & 1ull) a2 = __ldcg(r2 + lane);
-                        if ((f3 >> lane) & 1ull) a3 = __ldcg(r3 + lane);
-                        if ((f0 >> (lane + 32)) & 1ull) b0 = __ldcg(r0 + lane + 32);
-                        if ((f1 >> (lane + 32)) & 1ull) b1 = __ldcg(r1 + lane + 32);
-                        if ((f2 >> (lane + 32)) & 1ull) b2 = __ldcg(r2 + lane + 32);
-                        if ((f3 >> (lane + 32)) & 1ull) b3 = __ldcg(r3 + lane + 32);
-                        if (FPSIG) {
-                            // keep the in-adjacency order of the additions
-                            acc0 += a0; acc0 += a1; acc0 += a2; acc0 += a3;
-                            acc1 += b0; acc1 += b1; acc1 += b2; acc1 += b3;
-                        } else {
-                            acc0 += (a0 + a1) + (a2 + a3);
-                            acc1 += (b0 + b1) + (b2 + b3);
-                            // flag before four more addends could wrap 2^64
-                            ovf |= (acc0 >= kLimit) | (acc1 >= kLimit);
-                        }
+#pragma unroll
+                    for (int w = 0; w < K; ++w) {
+                        const uint64_t r = warp_or64(f[w]);
+                        if (lane == w) nbl |= r & cl;
                     }
+                    if (__all_sync(0xffffffffu, nbl == cl)) break;
                 }
-                const uint64_t nb = warp_or64(nbp);
-                bool app = false;
-                if (lane == 0) {
-                    fnext[it] = nb;
-                    if (nb) app = atomicMax(&a.qstamp[v], stamp_next) < stamp_next;
-                }
-                if (app) qnext[atomicAdd(qn_next, 1)] = (int32_t)v;
-                if (nb) {
-                    ST *drow = sig + v * W + 64 * w;
-                    if ((nb >> lane) & 1ull) drow[lane] = (ST)acc0;
-                    if ((nb >> (lane + 32)) & 1ull) drow[lane + 32] = (ST)acc1;
+                if (lane < K && nbl) fnext[v * K + lane] = nbl;
+                if (__ballot_sync(0xffffffffu, nbl != 0ull) && lane == 0) {
+                    if (e1 - e0 > 32) qnext[n - 1 - atomicAdd(qh_next, 1)] = (int32_t)v;
+                    else qnext[atomicAdd(qn_next, 1)] = (int32_t)v;
                 }
             }
         }
-        if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(status, SigmaMode<SM>::flag);
-        ovf = false;
         if (!grid_sync(bar, status, a.budget_ns)) return;
         if (tid == 0 && L < 32) ctl->lvl_rec[L][4] = globaltimer_ns() - ctl->t_start;
 
@@ -350,28 +334,165 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                         for (int w = 0; w < K; ++w) any |= f[w] != 0ull;
                     }
                 }
-                const unsigned am = __ballot_sync(0xffffffffu, any);
+                const bool heavy = any && a.irp[v + 1] - a.irp[v] > 32;
+                const unsigned am = __ballot_sync(0xffffffffu, any && !heavy);
+                const unsigned hm = __ballot_sync(0xffffffffu, heavy);
                 if (am) {
                     const int leader = __ffs(am) - 1;
                     int pos = 0;
                     if (lane == leader) pos = atomicAdd(qn_next, __popc(am));
                     pos = __shfl_sync(0xffffffffu, pos, leader);
-                    if (any) qnext[pos + __popc(am & ((1u << lane) - 1u))] = (int32_t)v;
+                    if (any && !heavy) qnext[pos + __popc(am & ((1u << lane) - 1u))] = (int32_t)v;
+                }
+                if (hm) {
+                    const int leader = __ffs(hm) - 1;
+                    int pos = 0;
+                    if (lane == leader) pos = atomicAdd(qh_next, __popc(hm));
+                    pos = __shfl_sync(0xffffffffu, pos, leader);
+                    if (heavy) qnext[n - 1 - (pos + __popc(hm & ((1u << lane) - 1u)))] = (int32_t)v;
                 }
             }
-            if (!grid_sync(bar, status, a.budget_ns)) return;
         }
+        // mark settled targets
+        if (!a.full) {
+            for (long long p = p0 + tid; p < p1; p += nthreads) {
+                if (a.found[p] >= 0) continue;
+                const int32_t j = a.samp_lane[p] - a.lane_base;
+                const int32_t t = a.samp_t[p];
+                const int64_t q = (int64_t)t * K + (j >> 6);
+                if (((__ldcg(&a.vis[q]) | __ldcg(&fnext[q])) >> (j & 63)) & 1ull) {
+                    a.found[p] = L + 1;
+                    atomicSub(&a.remaining[j], 1);
+                }
+            }
+        }
+        if (!grid_sync(bar, status, a.budget_ns)) return;
         if (tid == 0 && L < 32) ctl->lvl_rec[L][5] = globaltimer_ns() - ctl->t_start;
 
-        // ---- phase B (1): settle the new frontier: visited bits, nonempty lanes,
-        // final counts checked against 2^53, next frontier's out-edges
+        // ---- phase A2: counts of level L+1.  A lane whose last targets were
+        // settled at this level retires after it, and of its level-(L+1)
+        // vertices only those targets are ever read (by the backtrack), so its
+        // counts are formed there alone.
+        if (a.full) {
+            if (threadIdx.x < K) s_cont[threadIdx.x] = s_act[threadIdx.x];
+        } else {
+            if (threadIdx.x < K) s_cont[threadIdx.x] = 0ull;
+            __syncthreads();
+            for (int j = threadIdx.x; j < W; j += blockDim.x) {
+                const bool c = ((s_act[j >> 6] >> (j & 63)) & 1ull) && __ldcg(&a.remaining[j]) > 0;
+                const unsigned bm = __ballot_sync(0xffffffffu, c);
+                if (lane == 0 && bm) atomicOr(&s_cont[j >> 6], (unsigned long long)bm << (j & 32));
+            }
+        }
+        __syncthreads();
+        const int64_t qn1 = (int64_t)ld_relaxed_u32((const uint32_t *)qn_next);
+        const int64_t qh1 = (int64_t)ld_relaxed_u32((const uint32_t *)qh_next);
+        for (int64_t it = gwarp; it < qn1 + qh1 * K; it += nwarps) {
+            if (it < qn1) {
+                // in-degree <= 32: one warp per new vertex, its parents and all
+                // their words loaded once; lane w < K holds the word's lanes to count
+                const int32_t v = __ldcg(&qnext[it]);
+                uint64_t nbl = 0ull;
+                if (lane < K) nbl = __ldcg(&fnext[(int64_t)v * K + lane]) & s_cont[lane];
+                const unsigned wm = __ballot_sync(0xffffffffu, nbl != 0ull);
+                if (!wm) continue;
+                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+                ST *drow = sig + (int64_t)v * W;
+                const int64_t e = e0 + lane;
+                int32_t u = 0;
+                uint64_t f[K];
+                if (e < e1) {
+                    u = a.icol[e];
+                    load_words<K>(fcur + (int64_t)u * K, f);
+                } else {
+#pragma unroll
+                    for (int w = 0; w < K; ++w) f[w] = 0ull;
+                }
+#pragma unroll
+                for (int w = 0; w < K; ++w) {
+                    if (!((wm >> w) & 1u)) continue;
+                    const uint64_t nbw = shfl64(nbl, w);
+                    const uint64_t fw = f[w] & nbw;
+                    if (INSTR) n_sload += (unsigned long long)__popcll(fw);
+                    S acc0 = S(0), acc1 = S(0);
+                    gather_chunk<SM, ST, S>(sig, W, w, fw, u, acc0, acc1, ovf);
+                    if (FPSIG) ovf |= (acc0 >= (S)kLimit) | (acc1 >= (S)kLimit);
+                    if ((nbw >> lane) & 1ull) drow[64 * w + lane] = (ST)acc0;
+                    if ((nbw >> (lane + 32)) & 1ull) drow[64 * w + lane + 32] = (ST)acc1;
+                    if (INSTR) n_swrite += lane == 0 ? (unsigned long long)__popcll(nbw) : 0ull;
+                }
+            } else {
+                // in-degree > 32: one warp per (vertex, word) over 32-edge chunks
+                const int64_t h = (it - qn1) / K;
+                const int w = (int)(it - qn1 - h * K);
+                const int32_t v = __ldcg(&qnext[n - 1 - h]);
+                const uint64_t nbw = __ldcg(&fnext[(int64_t)v * K + w]) & s_cont[w];
+                if (nbw == 0ull) continue;
+                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+                S acc0 = S(0), acc1 = S(0);
+                for (int64_t base = e0; base < e1; base += 32) {
+                    const int64_t e = base + lane;
+                    int32_t u = 0;
+                    uint64_t fw = 0ull;
+                    if (e < e1) {
+                        u = a.icol[e];
+                        fw = __ldcg(&fcur[(int64_t)u * K + w]) & nbw;
+                    }
+                    if (INSTR) n_sload += (unsigned long long)__popcll(fw);
+                    gather_chunk<SM, ST, S>(sig, W, w, fw, u, acc0, acc1, ovf);
+                }
+                if (FPSIG) ovf |= (acc0 >= (S)kLimit) | (acc1 >= (S)kLimit);
+                ST *drow = sig + (int64_t)v * W + 64 * w;
+                if ((nbw >> lane) & 1ull) drow[lane] = (ST)acc0;
+                if ((nbw >> (lane + 32)) & 1ull) drow[lane + 32] = (ST)acc1;
+                if (INSTR) n_swrite += lane == 0 ? (unsigned long long)__popcll(nbw) : 0ull;
+            }
+        }
+        if (!a.full) {
+            // targets of the retiring lanes: one warp per sample settled at L+1
+            for (long long p = p0 + gwarp; p < p1; p += nwarps) {
+                if (__ldcg(&a.found[p]) != L + 1) continue;
+                const int32_t j = a.samp_lane[p] - a.lane_base;
+                const int w = j >> 6;
+                const uint64_t bj = 1ull << (j & 63);
+                if (s_cont[w] & bj) continue;
+                const int32_t t = a.samp_t[p];
+                const int64_t e0 = a.irp[t], e1 = a.irp[t + 1];
+                S acc = S(0);
+                if (FPSIG) {
+                    // in-adjacency order
+                    if (lane == 0)
+                        for (int64_t e = e0; e < e1; ++e) {
+                            const int32_t u = a.icol[e];
+                            if (__ldcg(&fcur[(int64_t)u * K + w]) & bj) acc += (S)__ldcg(&sig[(int64_t)u * W + j]);
+                        }
+                } else {
+                    for (int64_t e = e0 + lane; e < e1; e += 32) {
+                        const int32_t u = a.icol[e];
+                        if (__ldcg(&fcur[(int64_t)u * K + w]) & bj) {
+                            acc += (S)__ldcg(&sig[(int64_t)u * W + j]);
+                            if (INSTR) ++n_sload;
+                        }
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                }
+                if (lane == 0) {
+                    ovf |= acc >= (S)kLimit;
+                    sig[(int64_t)t * W + j] = (ST)acc;
+                    if (INSTR) ++n_swrite;
+                }
+            }
+        }
+
+        // ---- phase B(1): settle the new frontier: visited bits, nonempty lanes,
+        // next frontier's out-edges (no reader of these runs in this interval)
         {
-            const int64_t qn1 = (int64_t)ld_relaxed_u32((const uint32_t *)qn_next);
             unsigned long long fe = 0ull;
-            for (int64_t it = tid; it < qn1 * K; it += nthreads) {
+            for (int64_t it = tid; it < (qn1 + qh1) * K; it += nthreads) {
                 const int64_t k = it / K;
                 const int w = (int)(it - k * K);
-                const int32_t v = __ldcg(&qnext[k]);
+                const int32_t v = __ldcg(&qnext[k < qn1 ? k : n - 1 - (k - qn1)]);
                 const uint64_t nb = __ldcg(&fnext[(int64_t)v * K + w]);
                 if (!nb) continue;
                 a.vis[(int64_t)v * K + w] = __ldcg(&a.vis[(int64_t)v * K + w]) | nb;
@@ -381,19 +502,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                     n_uv += 1;
                     n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
                 }
-                if (push && SM != 0) {
-                    // pushed counts are complete only now: check them against the
-                    // exact range (32-bit storage is covered by the wrap guard)
-                    uint64_t mm = nb;
-                    const ST *vrow = sig + (int64_t)v * W + 64 * w;
-                    while (mm) {
-                        const int b = __ffsll((long long)mm) - 1;
-                        mm &= mm - 1;
-                        if ((S)__ldcg(vrow + b) >= (S)kLimit) ovf = true;
-                    }
-                }
                 if (INSTR) {
-                    n_swrite += (unsigned long long)__popcll(nb);
                     const unsigned long long dg = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
                     uint64_t m2 = nb;
                     while (m2) {
@@ -412,8 +521,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             }
             if (a.policy == 2) {
                 // pull work of the next level: in-edges of every (vertex, word) that
-                // still has an unvisited active lane (visited bits now include level L+1
-                // except for the vertices this pass is still updating, a small excess)
+                // still has an unvisited active lane
                 unsigned long long ue = 0ull;
                 for (int64_t it = tid; it < nk; it += nthreads) {
                     const int64_t v = it / K;
@@ -430,20 +538,6 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         __syncthreads();
         if (threadIdx.x < K && s_nonempty[threadIdx.x])
             atomicOr(&ctl->nonempty[L & 1][threadIdx.x], s_nonempty[threadIdx.x]);
-
-        // ---- phase B: mark settled targets, then the last block retires lanes
-        if (!a.full) {
-            for (long long p = p0 + tid; p < p1; p += nthreads) {
-                if (a.found[p] >= 0) continue;
-                const int32_t j = a.samp_lane[p] - a.lane_base;
-                const int32_t t = a.samp_t[p];
-                const int64_t q = (int64_t)t * K + (j >> 6);
-                if (((__ldcg(&a.vis[q]) | __ldcg(&fnext[q])) >> (j & 63)) & 1ull) {
-                    a.found[p] = L + 1;
-                    atomicSub(&a.remaining[j], 1);
-                }
-            }
-        }
         __syncthreads();
         __shared__ int s_last;
         if (threadIdx.x == 0) {
@@ -473,10 +567,11 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 if (L < 32) {
                     ctl->lvl_rec[L][0] = globaltimer_ns() - ctl->t_start;
                     ctl->lvl_rec[L][1] = (push ? 1ull : 0ull) | (ctl->uedges[L & 1] << 1);
-                    ctl->lvl_rec[L][2] = (unsigned long long)ctl->qn[L & 1];
+                    ctl->lvl_rec[L][2] = (unsigned long long)(ctl->qn[L & 1] + ctl->qh[L & 1]);
                     ctl->lvl_rec[L][3] = ctl->fedges[L & 1];
                 }
                 ctl->qn[L & 1] = 0;  // the queue just consumed is refilled at level L+2
+                ctl->qh[L & 1] = 0;
                 const unsigned long long fe = ctl->fedges[(L + 1) & 1];
                 const unsigned long long ue = ctl->uedges[(L + 1) & 1];
                 ctl->fedges[L & 1] = 0ull;
@@ -793,9 +888,6 @@ void fill_common(percis_ctx *ctx, MsArgs &a, int Lcap) {
     a.qstamp = ctx->qstamp.as<int32_t>();
     a.policy = ctx->opt.direction;
     a.push_alpha = ctx->opt.push_alpha > 0.0 ? ctx->opt.push_alpha : 0.5;
-    // no vertex has more than max_indeg parents: counts below 2^63 / max_indeg cannot wrap 2^64
-    a.wrap_guard = (unsigned long long)(9223372036854775807LL / std::max<int64_t>(ctx->max_indeg, 1));
-    a.wrap_guard32 = (unsigned long long)(4294967295LL / std::max<int64_t>(ctx->max_indeg, 1));
 }
 
 // Each launch stamps its levels with fresh values, so the stamps never need clearing.
