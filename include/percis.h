@@ -219,6 +219,54 @@ percis_status percis_msbfs(percis_ctx *ctx, int32_t nsrc, const int32_t *sources
 percis_status percis_run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count, int32_t *s, int32_t *t,
                                int32_t *kind, int32_t *ilen, int64_t *cnt);
 
+/* ---- Many graphs in one context ----
+ * A batch of num_graphs independent graphs, each its own instance of the
+ * problem of Section II (own C, lambda_v, d^, vertex-diameter bound D, l1
+ * and l), as one block-diagonal CSR: graph g owns the vertices
+ * graph_vptr[g] .. graph_vptr[g+1]-1 (ids of the whole batch) and each of
+ * its edges stays inside that range.  Every graph runs its own state
+ * preprocessing, Algorithm 2 sampler and Algorithm 1 bounds; the
+ * sigma-counting BFS of all graphs shares the batched launches (lanes of
+ * several graphs in one launch over the vertex range of those graphs).
+ * (Not in the paper, whose method is per graph.)
+ * Sample numbering: in each phase, graph g's samples carry the indices
+ * off_g .. off_g + l_g - 1 (off_g = the sum of the sample counts of graphs
+ * 0 .. g-1) in the Philox counters of the pair and path draws; graph g's
+ * estimate equals a single-graph run whose samples start at off_g.
+ * All arrays are host memory (copied).  Errors: INVALID for a malformed
+ * batch (graph_vptr not running from 0 to n, a graph of fewer than two
+ * vertices, row_ptr not monotone, an edge leaving its graph).
+ * After this call, percis_set_states(ctx, x[n], ...) sets every graph's
+ * states (DEGENERATE names the graph), percis_estimate_graphs estimates, and
+ * percis_backward(ctx, grad_pc[n], grad_x[n], ...) differentiates every
+ * graph's estimate with its own frozen sample; percis_estimate refuses. */
+percis_status percis_load_graphs(percis_ctx *ctx, int32_t num_graphs, const int64_t *graph_vptr, int64_t n,
+                                 int64_t nnz, const int64_t *row_ptr, const int32_t *col, int directed);
+int32_t percis_num_graphs(percis_ctx *ctx);  /* 0 for a single-graph context */
+
+/* Algorithm 1 for every graph of a percis_load_graphs context at the same
+ * (eps, delta, seed).  pc_out[n]: estimates of all vertices (device or host
+ * memory per pc_on_device).  info: NULL or num_graphs entries, entry g for
+ * graph g; the launch counts, sources, batches and BFS times are shared by
+ * all graphs and every entry reports the totals.  Errors as percis_estimate;
+ * INVALID for the plain form. */
+percis_status percis_estimate_graphs(percis_ctx *ctx, double eps, double delta, uint64_t seed, double *pc_out,
+                                     int pc_on_device, percis_info *info);
+
+/* Autotuner (the batched form's batch width, frontier direction rule and
+ * lane order; not in the paper, whose results these options do not change).
+ * Coordinate descent: lane order {0, 1}, then lanes {64, 128, 256, 512},
+ * then direction {pull, push, work estimate with push_alpha 0.25, 0.5, 1, 2};
+ * each candidate is timed (CUDA events, best of two) on probe phases of
+ * probe_samples pairs drawn with `seed` from the loaded graph and states.
+ * The winner is stored in the context's options (other fields unchanged) and
+ * copied to *chosen when chosen is not NULL.  The probe replaces the last
+ * sample, so percis_backward needs a new percis_estimate first.
+ * Errors: STATE before percis_set_states; INVALID for probe_samples < 1 or the
+ * plain form; any error of the probe phases (options are then left as they
+ * were). */
+percis_status percis_autotune(percis_ctx *ctx, int64_t probe_samples, uint64_t seed, percis_options *chosen);
+
 /* Per-level profile of the last batched launch (measurement aid).  For each
  * level L < min(cap, 32) writes six int64 to out[6L..6L+5]: device time from
  * the launch's start to the end of level L (ns); direction in bit 0 (1 = push)

@@ -520,14 +520,17 @@ class Result:
 
 def percis(g: OGraph, x, eps: float, delta: float, seed: int, ell1: int | None = None, ell: int | None = None,
            D: int | None = None, prep: Prep | None = None, keep_paths: bool = True, allpaths: bool = False,
-           data_independent: bool = False) -> Result:
+           data_independent: bool = False, offsets: tuple[int, int] = (0, 0)) -> Result:
     """Algorithm 1 (PercIS): D, phase 1 (l1 samples, pair tag 0, path tag 2),
     rho^, v^, x^, l, then phase 2 (l fresh samples, pair tag 1, path tag 3).
     The phase-1 estimate uses 1/l1 (the 1/l printed in that line of
     Algorithm 1 is read as the phase-1 sample size).
 
     data_independent: PercIS-DI (Section V, sample-size experiment): no first
-    phase; rho^ = D and v^ = d^2/4 (its largest possible value)."""
+    phase; rho^ = D and v^ = d^2/4 (its largest possible value).
+
+    offsets: index of the first sample of phase 1 and of phase 2 in the
+    Philox counters (a graph of a batch whose samples follow other graphs')."""
     if prep is None:
         prep = prepare(x)
     if not np.all(prep.Cv > 0):
@@ -539,7 +542,7 @@ def percis(g: OGraph, x, eps: float, delta: float, seed: int, ell1: int | None =
         rh, vh = float(D), prep.dhat * prep.dhat / 4.0
     else:
         l1 = ell1 if ell1 is not None else ell1_default(eps, delta)
-        ph1 = run_samples(g, prep, seed, 0, 2, 0, l1, keep_paths=False, allpaths=allpaths)
+        ph1 = run_samples(g, prep, seed, 0, 2, offsets[0], l1, keep_paths=False, allpaths=allpaths)
         p1 = (ph1.acc_all if allpaths else ph1.acc) / l1
         p1_max = float(p1.max())
         rh, rt, Lam = rho_hat(ph1.ilen, D, delta)
@@ -547,7 +550,7 @@ def percis(g: OGraph, x, eps: float, delta: float, seed: int, ell1: int | None =
     xh = x_hat(vh, prep.dhat)
     if ell is None:
         ell, _ = ell_sup(eps, delta, prep.dhat, rh, xh)
-    ph2 = run_samples(g, prep, seed, 1, 3, 0, ell, keep_paths=keep_paths, allpaths=allpaths)
+    ph2 = run_samples(g, prep, seed, 1, 3, offsets[1], ell, keep_paths=keep_paths, allpaths=allpaths)
     pc = (ph2.acc_all if allpaths else ph2.acc) / ell
     pc_counts = prep.lam * ph2.cnt / ell
     return Result(pc, pc_counts, ph2.cnt, l1, ell, D, prep.dhat, rt, Lam, rh, vh, xh, p1_max, ph1, ph2, prep)

@@ -89,6 +89,10 @@ SIGNATURES = {
     "percis_run_phase": (_ST, [_P, _U64, ctypes.c_int, _I64, _P, _P, _P, _P, _P]),
     "percis_get_paths": (_ST, [_P, _P, _P, _P]),
     "percis_last_levels": (_I64, [_P, _P, _I64]),
+    "percis_autotune": (_ST, [_P, _I64, _U64, ctypes.POINTER(percis_options)]),
+    "percis_load_graphs": (_ST, [_P, _I32, _P, _I64, _I64, _P, _P, ctypes.c_int]),
+    "percis_num_graphs": (_I32, [_P]),
+    "percis_estimate_graphs": (_ST, [_P, _F64, _F64, _U64, _P, ctypes.c_int, _P]),
     "percis_bfs_noalloc": (_ST, [_I64, _P, _P, _P, _P, _I32, _I32, _P, _P, _P]),
 }
 
@@ -234,6 +238,34 @@ def percis_bfs_noalloc(n: int, row_ptr, col, in_row_ptr, in_col, source: int, ta
                                                  source, target, _ptr(dist), _ptr(sigma), stream))
 
 
+def percis_load_graphs(ctx, graph_vptr, row_ptr, col, directed: bool = False):
+    vp = np.ascontiguousarray(graph_vptr, dtype=np.int64)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    _check(ctx, load_library().percis_load_graphs(ctx, int(vp.shape[0]) - 1, _ptr(vp), int(rp.shape[0]) - 1,
+                                                  int(cl.shape[0]), _ptr(rp), _ptr(cl), int(directed)))
+
+
+def percis_num_graphs(ctx) -> int:
+    return int(load_library().percis_num_graphs(ctx))
+
+
+def percis_estimate_graphs(ctx, eps: float, delta: float, seed: int, pc_out,
+                           pc_on_device: int | None = None) -> list[dict]:
+    G = percis_num_graphs(ctx)
+    infos = (percis_info * max(G, 1))()
+    od = _on_device(pc_out) if pc_on_device is None else pc_on_device
+    _check(ctx, load_library().percis_estimate_graphs(ctx, eps, delta, seed, _ptr(pc_out), od,
+                                                      ctypes.cast(infos, ctypes.c_void_p)))
+    return [infos[g].as_dict() for g in range(G)]
+
+
+def percis_autotune(ctx, probe_samples: int, seed: int) -> percis_options:
+    o = percis_options()
+    _check(ctx, load_library().percis_autotune(ctx, probe_samples, seed, ctypes.byref(o)))
+    return o
+
+
 def percis_last_levels(ctx, cap: int = 32) -> list[tuple[int, ...]]:
     out = np.zeros(6 * cap, dtype=np.int64)
     k = int(load_library().percis_last_levels(ctx, out.ctypes.data, cap))
@@ -277,6 +309,13 @@ class PercIS:
             setattr(self.options, k, v)
         percis_set_options(self.ctx, self.options)
 
+    def autotune(self, probe_samples: int = 8192, seed: int = 0) -> dict:
+        """Pick lane width, lane order and direction rule by timing probe
+        phases; returns the chosen options."""
+        o = percis_autotune(self.ctx, probe_samples, seed)
+        self.options = o
+        return {name: getattr(o, name) for name, _ in o._fields_}
+
     def _sync_stream(self):
         percis_set_stream(self.ctx, self.torch.cuda.current_stream(self.device).cuda_stream)
 
@@ -304,6 +343,17 @@ class PercIS:
             out = t.empty(self.n, dtype=t.float64, device=self.device)
         info = percis_estimate(self.ctx, eps, delta, seed, out)
         return out, info
+
+    def load_graphs(self, graph_vptr, row_ptr, col, directed: bool = False):
+        """Many independent graphs as one block-diagonal CSR (host arrays)."""
+        percis_load_graphs(self.ctx, graph_vptr, row_ptr, col, directed)
+        self.n = int(np.asarray(row_ptr).shape[0]) - 1
+
+    def estimate_graphs(self, eps: float, delta: float, seed: int = 0, out=None):
+        t = self.torch
+        if out is None:
+            out = t.empty(self.n, dtype=t.float64, device=self.device)
+        return out, percis_estimate_graphs(self.ctx, eps, delta, seed, out)
 
     def exact(self):
         t = self.torch

@@ -178,13 +178,7 @@ void clear_status(percis_ctx *ctx) {
     if (ctx->plain_ctl.p) cudaMemsetAsync(ctx->plain_ctl.p, 0, sizeof(PlainCtl), ctx->stream);
 }
 
-struct PhaseOut {
-    int64_t sources = 0, batches = 0;
-    int32_t overflow = 0;
-    double bfs_ms = 0.0;
-    int64_t bfs_launches = 0;
-    int64_t work[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-};
+}  // namespace
 
 // One sampling phase (pair tag = phase, path tag = 2 + phase) of `count`
 // samples.  Leaves pairs, kinds, |I|, paths and cnt in the context.
@@ -221,8 +215,11 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->arena_top.p, 0, 64, ctx->stream));
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ilen.p, 0, sizeof(int32_t) * cap_count, ctx->stream));
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->path_off.p, 0, sizeof(long long) * cap_count, ctx->stream));
-        PERCIS_TRY(sample_pairs(ctx, seed, (uint32_t)phase, 0, count, ctx->pair_s.as<int32_t>(),
-                                ctx->pair_t.as<int32_t>(), ctx->kind.as<int32_t>()));
+        if (ctx->multi)
+            PERCIS_TRY(multi_sample_pairs(ctx, seed, (uint32_t)phase));
+        else
+            PERCIS_TRY(sample_pairs(ctx, seed, (uint32_t)phase, 0, count, ctx->pair_s.as<int32_t>(),
+                                    ctx->pair_t.as<int32_t>(), ctx->kind.as<int32_t>()));
         *sources = 0;
         *batches = 0;
         if (ctx->opt.form == PERCIS_FORM_PLAIN) {
@@ -280,6 +277,8 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
     }
     return set_err(ctx, PERCIS_E_TOO_LARGE, "phase could not be sized (levels/arena)");
 }
+
+namespace {
 
 percis_status phase_stats(percis_ctx *ctx, int64_t count, double ell, PhaseStats *hs) {
     PERCIS_TRY(ensure(ctx, ctx->red, sizeof(PhaseStats), "stats"));
@@ -367,6 +366,7 @@ void percis_destroy(percis_ctx *ctx) {
     if (ctx->counters.p) cudaFree(ctx->counters.p);
     if (ctx->levdeg.p) cudaFree(ctx->levdeg.p);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    multi_free(ctx);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -400,6 +400,7 @@ percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt) {
     if (opt->ell1 < 0 || opt->ell1 == 1 || opt->ell < 0 || !(opt->timeout_s > 0.0))
         return set_err(ctx, PERCIS_E_INVALID, "bad sample sizes or timeout");
     ctx->opt = *opt;
+    multi_set_options(ctx);
     return PERCIS_OK;
 }
 
@@ -409,6 +410,7 @@ percis_status percis_load_csr(percis_ctx *ctx, int64_t n, int64_t nnz, const int
     if (n < 2 || n > 0x7fffffffLL || nnz < 0 || !row_ptr || (nnz > 0 && !col))
         return set_err(ctx, PERCIS_E_INVALID, "need n >= 2 (int32 ids) and valid pointers");
     DeviceGuard g(ctx->device);
+    multi_free(ctx);
     ctx->have_graph = false;
     ctx->have_states = false;
     ctx->have_paths = false;
@@ -426,6 +428,10 @@ percis_status percis_load_csr(percis_ctx *ctx, int64_t n, int64_t nnz, const int
 }
 
 percis_status percis_set_states(percis_ctx *ctx, const double *x, int on_device) {
+    if (ctx && ctx->multi && x) {
+        DeviceGuard g(ctx->device);
+        return percis_multi_set_states(ctx, x, on_device);
+    }
     PERCIS_TRY(need_graph(ctx));
     if (!x) return set_err(ctx, PERCIS_E_INVALID, "x is NULL");
     DeviceGuard g(ctx->device);
@@ -442,6 +448,7 @@ percis_status percis_set_states(percis_ctx *ctx, const double *x, int on_device)
 percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_t seed, double *pc_out,
                               int pc_on_device, percis_info *info) {
     PERCIS_TRY(need_states(ctx));
+    if (ctx->multi) return set_err(ctx, PERCIS_E_INVALID, "a context of many graphs estimates with percis_estimate_graphs");
     if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0) || !pc_out)
         return set_err(ctx, PERCIS_E_INVALID, "eps and delta must lie in (0,1); pc_out must be non-NULL");
     DeviceGuard g(ctx->device);
@@ -538,6 +545,10 @@ percis_status percis_exact_small(percis_ctx *ctx, double *pc_out, int pc_on_devi
 percis_status percis_backward(percis_ctx *ctx, const double *grad_pc, double *grad_x, int on_device) {
     PERCIS_TRY(need_states(ctx));
     if (!grad_pc || !grad_x) return set_err(ctx, PERCIS_E_INVALID, "NULL gradient buffer");
+    if (ctx->multi) {
+        DeviceGuard g(ctx->device);
+        return percis_multi_backward(ctx, grad_pc, grad_x, on_device);
+    }
     if (!ctx->have_paths || ctx->last_phase != 1 || ctx->last_ell <= 0)
         return set_err(ctx, PERCIS_E_NO_SAMPLE, "backward needs a completed estimate of the one-path form");
     DeviceGuard g(ctx->device);
@@ -655,6 +666,85 @@ percis_status percis_run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_
         PERCIS_CHECK_LAUNCH(ctx, "cnt copy");
     }
     PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PERCIS_OK;
+}
+
+// Autotuner: coordinate descent over the options that change speed but not
+// results (lane order, lane width, direction rule), each candidate timed with
+// CUDA events on a probe phase of the current graph and states.
+percis_status percis_autotune(percis_ctx *ctx, int64_t probe_samples, uint64_t seed, percis_options *chosen) {
+    PERCIS_TRY(need_states(ctx));
+    if (probe_samples < 1) return set_err(ctx, PERCIS_E_INVALID, "probe_samples >= 1");
+    if (ctx->opt.form == PERCIS_FORM_PLAIN) return set_err(ctx, PERCIS_E_INVALID, "the autotuner tunes the batched form");
+    DeviceGuard g(ctx->device);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PERCIS_CUDA(ctx, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_err(ctx, cudaGetLastError(), "event");
+    }
+    percis_options best = ctx->opt;
+    const percis_options saved = ctx->opt;
+    percis_status st = PERCIS_OK;
+    auto time_opt = [&](const percis_options &o, float *ms) -> percis_status {
+        ctx->opt = o;
+        float bestms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            PhaseOut po;
+            PERCIS_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+            PERCIS_TRY(run_phase(ctx, seed + (uint64_t)rep, 0, probe_samples, &po));
+            PERCIS_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+            PERCIS_CUDA(ctx, cudaEventSynchronize(e1));
+            float t = 0.f;
+            PERCIS_CUDA(ctx, cudaEventElapsedTime(&t, e0, e1));
+            bestms = std::min(bestms, t);
+        }
+        *ms = bestms;
+        return PERCIS_OK;
+    };
+    float best_ms = 0.f;
+    st = time_opt(best, &best_ms);
+    // 1. lane order
+    for (int lo = 0; lo <= 1 && st == PERCIS_OK; ++lo) {
+        percis_options o = best;
+        o.lane_order = lo;
+        float ms = 0.f;
+        st = time_opt(o, &ms);
+        if (st == PERCIS_OK && ms < best_ms) best_ms = ms, best = o;
+    }
+    // 2. lane width
+    const int widths[4] = {64, 128, 256, 512};
+    for (int k = 0; k < 4 && st == PERCIS_OK; ++k) {
+        percis_options o = best;
+        o.lanes = widths[k];
+        float ms = 0.f;
+        st = time_opt(o, &ms);
+        if (st == PERCIS_OK && ms < best_ms) best_ms = ms, best = o;
+    }
+    // 3. direction: pull, push, or by work estimate with the push threshold
+    const double alphas[4] = {0.25, 0.5, 1.0, 2.0};
+    for (int k = 0; k < 6 && st == PERCIS_OK; ++k) {
+        percis_options o = best;
+        o.direction = k < 2 ? k : 2;
+        if (k >= 2) o.push_alpha = alphas[k - 2];
+        float ms = 0.f;
+        st = time_opt(o, &ms);
+        if (st == PERCIS_OK && ms < best_ms) best_ms = ms, best = o;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->have_paths = false;  // the probe phases replaced the last sample
+    if (st != PERCIS_OK) {
+        ctx->opt = saved;
+        return st;
+    }
+    // only the speed options change; everything else stays as the caller set it
+    ctx->opt = saved;
+    ctx->opt.lane_order = best.lane_order;
+    ctx->opt.lanes = best.lanes;
+    ctx->opt.direction = best.direction;
+    ctx->opt.push_alpha = best.push_alpha;
+    if (chosen) *chosen = ctx->opt;
     return PERCIS_OK;
 }
 

@@ -11,6 +11,8 @@
 
 namespace percis {
 
+struct MultiGraph;  // many independent graphs in one context (multi.cu)
+
 // Grow-only device buffer.
 struct DevBuf {
     void *p = nullptr;
@@ -107,6 +109,10 @@ struct percis_ctx {
     // scratch for reductions/scans
     percis::DevBuf scratch, red, status;
     percis::DevBuf pc_tmp, grad_tmp, host_pinned;
+
+    // many graphs: one sub-context per graph for everything but the batched BFS
+    percis::MultiGraph *multi = nullptr;
+    bool skip_diam = false;  // the union of many graphs takes the per-graph bounds
 };
 
 namespace percis {
@@ -173,6 +179,32 @@ percis_status backward_fixed(percis_ctx *ctx, const double *g, double *grad);
 
 // exact.cu
 percis_status exact_pc(percis_ctx *ctx, double *pc);
+
+// api.cu: one sampling phase (pair tag = phase, path tag = 2 + phase)
+struct PhaseOut {
+    int64_t sources = 0, batches = 0;
+    int32_t overflow = 0;
+    double bfs_ms = 0.0;
+    int64_t bfs_launches = 0;
+    int64_t work[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count, PhaseOut *po);
+
+// multi.cu
+void multi_free(percis_ctx *ctx);
+void multi_set_options(percis_ctx *ctx);  // the graphs' contexts follow the union's options
+percis_status percis_multi_set_states(percis_ctx *ctx, const double *x, int on_device);
+percis_status percis_multi_backward(percis_ctx *ctx, const double *grad_pc, double *grad_x, int on_device);
+// pairs of a phase of a many-graph context: graph g draws its counts[g]
+// samples with indices off_g.. from its own tables, as global vertex ids
+percis_status multi_sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag);
+// consecutive lanes from graphs whose vertex ranges fit the batch buffers
+struct LaneBatch {
+    int32_t lane_base, nlanes, vlo;
+    int64_t nr;
+};
+percis_status multi_plan_batches(percis_ctx *ctx, int64_t n_sources, int W, std::vector<LaneBatch> *out);
+int64_t multi_range(percis_ctx *ctx);  // vertex range of the batch buffers
 
 // bounds.cpp
 struct Bounds {

@@ -35,9 +35,18 @@ namespace percis {
 namespace {
 
 constexpr int kMsBlock = 256;
+#ifndef PERCIS_BLOCK_DEG
+#define PERCIS_BLOCK_DEG 256
+#endif
+constexpr int64_t kBlockDeg = PERCIS_BLOCK_DEG;  // in-degree above which a whole block counts one (vertex, word)
 
 struct MsArgs {
+    // A launch covers the vertex range [vlo, vlo + n) of the loaded graph (the
+    // whole graph, or the graphs of a multi-graph batch): rp / irp point at
+    // entry vlo, column entries and sample vertices are global ids, and the
+    // visited, frontier, count and queue arrays are indexed by id - vlo.
     int64_t n;
+    int32_t vlo;
     const int64_t *irp;
     const int32_t *icol;
     uint64_t *vis;
@@ -179,11 +188,13 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     GridBarrier *bar = reinterpret_cast<GridBarrier *>(ctl);
     uint32_t *status = &ctl->status;
     const int lane = threadIdx.x & 31;
+    const int warp_in_block = threadIdx.x >> 5;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t gwarp = tid >> 5;
     const int64_t nwarps = nthreads >> 5;
-    const int64_t n = a.n;
+    const int64_t n = a.n;  // vertices of the launch's range [vlo, vlo + n)
+    const int32_t vlo = a.vlo;
     const int64_t nk = n * K;
     const long long p0 = a.full ? 0 : a.lane_off[a.lane_base];
     const long long p1 = a.full ? 0 : a.lane_off[a.lane_base + a.nlanes];
@@ -219,7 +230,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     }
     if (!grid_sync(bar, status, a.budget_ns)) return;
     for (int64_t j = tid; j < a.nlanes; j += nthreads) {
-        const int32_t v = a.lane_src[a.lane_base + j];
+        const int32_t v = a.lane_src[a.lane_base + j] - vlo;
         const uint64_t bit = 1ull << (j & 63);
         atomicOr((unsigned long long *)&a.vis[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         atomicOr((unsigned long long *)&a.fh[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
@@ -236,6 +247,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     __shared__ unsigned long long s_nonempty[K];
     __shared__ unsigned long long s_act[K];
     __shared__ unsigned long long s_cont[K];
+    __shared__ S s_red[kMsBlock / 32][64];  // per-warp partial sums of a block-wide gather
     int L = 0;
     for (;;) {
         bool any_act = false;
@@ -262,8 +274,30 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         if (push) {
             const int64_t qn = (int64_t)ld_relaxed_u32((const uint32_t *)&ctl->qn[L & 1]);
             const int64_t qh = (int64_t)ld_relaxed_u32((const uint32_t *)&ctl->qh[L & 1]);
-            for (int64_t k = gwarp; k < qn + qh; k += nwarps) {
-                const int32_t u = __ldcg(&qcur[k < qn ? k : n - 1 - (k - qn)]);
+            // vertices of in-degree > 32 (the back of the queue) one block each,
+            // its warps splitting the edges; then one warp per light vertex
+            for (int64_t r = blockIdx.x; r < qh; r += gridDim.x) {
+                const int32_t u = __ldcg(&qcur[n - 1 - r]);
+                uint64_t fl = 0ull;
+                if (lane < K) fl = __ldcg(&fcur[(int64_t)u * K + lane]) & s_act[lane];
+                if (!__ballot_sync(0xffffffffu, fl != 0ull)) continue;
+                uint64_t fu[K];
+#pragma unroll
+                for (int w = 0; w < K; ++w) fu[w] = shfl64(fl, w);
+                const int64_t e0 = a.rp[u], e1 = a.rp[u + 1];
+                for (int64_t e = e0 + warp_in_block * 32 + lane; e < e1; e += kMsBlock) {
+                    const int32_t v = a.col[e] - vlo;
+                    uint64_t vv[K];
+                    load_words<K>(a.vis + (int64_t)v * K, vv);
+#pragma unroll
+                    for (int w = 0; w < K; ++w) {
+                        const uint64_t m = fu[w] & ~vv[w];
+                        if (m) atomicOr((unsigned long long *)&fnext[(int64_t)v * K + w], (unsigned long long)m);
+                    }
+                }
+            }
+            for (int64_t k = gwarp; k < qn; k += nwarps) {
+                const int32_t u = __ldcg(&qcur[k]);
                 uint64_t fl = 0ull;
                 if (lane < K) fl = __ldcg(&fcur[(int64_t)u * K + lane]) & s_act[lane];
                 if (!__ballot_sync(0xffffffffu, fl != 0ull)) continue;
@@ -272,7 +306,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 for (int w = 0; w < K; ++w) fu[w] = shfl64(fl, w);
                 const int64_t e0 = a.rp[u], e1 = a.rp[u + 1];
                 for (int64_t e = e0 + lane; e < e1; e += 32) {
-                    const int32_t v = a.col[e];
+                    const int32_t v = a.col[e] - vlo;
                     uint64_t vv[K];
                     load_words<K>(a.vis + (int64_t)v * K, vv);
 #pragma unroll
@@ -296,7 +330,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                     const int64_t e = base + lane;
                     uint64_t f[K];
                     if (e < e1) {
-                        load_words<K>(fcur + (int64_t)a.icol[e] * K, f);
+                        load_words<K>(fcur + (int64_t)(a.icol[e] - vlo) * K, f);
                     } else {
 #pragma unroll
                         for (int w = 0; w < K; ++w) f[w] = 0ull;
@@ -358,7 +392,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             for (long long p = p0 + tid; p < p1; p += nthreads) {
                 if (a.found[p] >= 0) continue;
                 const int32_t j = a.samp_lane[p] - a.lane_base;
-                const int32_t t = a.samp_t[p];
+                const int32_t t = a.samp_t[p] - vlo;
                 const int64_t q = (int64_t)t * K + (j >> 6);
                 if (((__ldcg(&a.vis[q]) | __ldcg(&fnext[q])) >> (j & 63)) & 1ull) {
                     a.found[p] = L + 1;
@@ -387,6 +421,49 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         __syncthreads();
         const int64_t qn1 = (int64_t)ld_relaxed_u32((const uint32_t *)qn_next);
         const int64_t qh1 = (int64_t)ld_relaxed_u32((const uint32_t *)qh_next);
+        if (!FPSIG) {
+            // in-degree > kBlockDeg: one block per (vertex, word), its warps
+            // splitting the edges; the partial sums meet in shared memory
+            // (integer sums, so the order does not matter)
+            for (int64_t hi = blockIdx.x; hi < qh1 * K; hi += gridDim.x) {
+                const int64_t h = hi / K;
+                const int w = (int)(hi - h * K);
+                const int32_t v = __ldcg(&qnext[n - 1 - h]);
+                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+                if (e1 - e0 <= kBlockDeg) continue;  // a warp item below; the same for the whole block
+                const uint64_t nbw = __ldcg(&fnext[(int64_t)v * K + w]) & s_cont[w];
+                if (nbw == 0ull) continue;
+                S acc0 = S(0), acc1 = S(0);
+                for (int64_t base = e0 + warp_in_block * 32; base < e1; base += kMsBlock) {
+                    const int64_t e = base + lane;
+                    int32_t u = 0;
+                    uint64_t fw = 0ull;
+                    if (e < e1) {
+                        u = a.icol[e] - vlo;
+                        fw = __ldcg(&fcur[(int64_t)u * K + w]) & nbw;
+                    }
+                    if (INSTR) n_sload += (unsigned long long)__popcll(fw);
+                    gather_chunk<SM, ST, S>(sig, W, w, fw, u, acc0, acc1, ovf);
+                }
+                s_red[warp_in_block][lane] = acc0;
+                s_red[warp_in_block][lane + 32] = acc1;
+                __syncthreads();
+                if (warp_in_block == 0) {
+                    S t0 = S(0), t1 = S(0);
+#pragma unroll
+                    for (int q = 0; q < kMsBlock / 32; ++q) {
+                        t0 += s_red[q][lane];
+                        t1 += s_red[q][lane + 32];
+                    }
+                    ovf |= (t0 >= (S)kLimit) | (t1 >= (S)kLimit);
+                    ST *drow = sig + (int64_t)v * W + 64 * w;
+                    if ((nbw >> lane) & 1ull) drow[lane] = (ST)t0;
+                    if ((nbw >> (lane + 32)) & 1ull) drow[lane + 32] = (ST)t1;
+                    if (INSTR) n_swrite += lane == 0 ? (unsigned long long)__popcll(nbw) : 0ull;
+                }
+                __syncthreads();
+            }
+        }
         for (int64_t it = gwarp; it < qn1 + qh1 * K; it += nwarps) {
             if (it < qn1) {
                 // in-degree <= 32: one warp per new vertex, its parents and all
@@ -402,7 +479,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 int32_t u = 0;
                 uint64_t f[K];
                 if (e < e1) {
-                    u = a.icol[e];
+                    u = a.icol[e] - vlo;
                     load_words<K>(fcur + (int64_t)u * K, f);
                 } else {
 #pragma unroll
@@ -422,20 +499,23 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                     if (INSTR) n_swrite += lane == 0 ? (unsigned long long)__popcll(nbw) : 0ull;
                 }
             } else {
-                // in-degree > 32: one warp per (vertex, word) over 32-edge chunks
+                // in-degree in (32, kBlockDeg] (any, for FP64 counts, whose
+                // additions keep the in-adjacency order): one warp per
+                // (vertex, word) over 32-edge chunks
                 const int64_t h = (it - qn1) / K;
                 const int w = (int)(it - qn1 - h * K);
                 const int32_t v = __ldcg(&qnext[n - 1 - h]);
+                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+                if (!FPSIG && e1 - e0 > kBlockDeg) continue;
                 const uint64_t nbw = __ldcg(&fnext[(int64_t)v * K + w]) & s_cont[w];
                 if (nbw == 0ull) continue;
-                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
                 S acc0 = S(0), acc1 = S(0);
                 for (int64_t base = e0; base < e1; base += 32) {
                     const int64_t e = base + lane;
                     int32_t u = 0;
                     uint64_t fw = 0ull;
                     if (e < e1) {
-                        u = a.icol[e];
+                        u = a.icol[e] - vlo;
                         fw = __ldcg(&fcur[(int64_t)u * K + w]) & nbw;
                     }
                     if (INSTR) n_sload += (unsigned long long)__popcll(fw);
@@ -456,19 +536,19 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 const int w = j >> 6;
                 const uint64_t bj = 1ull << (j & 63);
                 if (s_cont[w] & bj) continue;
-                const int32_t t = a.samp_t[p];
+                const int32_t t = a.samp_t[p] - vlo;
                 const int64_t e0 = a.irp[t], e1 = a.irp[t + 1];
                 S acc = S(0);
                 if (FPSIG) {
                     // in-adjacency order
                     if (lane == 0)
                         for (int64_t e = e0; e < e1; ++e) {
-                            const int32_t u = a.icol[e];
+                            const int32_t u = a.icol[e] - vlo;
                             if (__ldcg(&fcur[(int64_t)u * K + w]) & bj) acc += (S)__ldcg(&sig[(int64_t)u * W + j]);
                         }
                 } else {
                     for (int64_t e = e0 + lane; e < e1; e += 32) {
-                        const int32_t u = a.icol[e];
+                        const int32_t u = a.icol[e] - vlo;
                         if (__ldcg(&fcur[(int64_t)u * K + w]) & bj) {
                             acc += (S)__ldcg(&sig[(int64_t)u * W + j]);
                             if (INSTR) ++n_sload;
@@ -622,7 +702,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         for (long long p = p0 + gwarp; p < p1; p += a.ap_warps) {
             const int32_t i = a.sorted_samples[p];
             const int32_t j = a.samp_lane[p] - a.lane_base;
-            const int32_t t = a.samp_t[p];
+            const int32_t t = a.samp_t[p] - vlo;
             const int32_t d = __ldcg(&a.found[p]);
             if (lane == 0) {
                 if (d < 0) a.kind[i] = 2;
@@ -653,7 +733,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                         bool mine = false;
                         int32_t pv = 0;
                         if (ee < e1) {
-                            pv = a.icol[ee];
+                            pv = a.icol[ee] - vlo;
                             if (__ldcg(&fL[(int64_t)pv * K + wj]) & bj) {
                                 mine = atomicExch(&stamp[pv], ep) != ep;
                                 if (mine) tau[pv] = S(0);
@@ -671,7 +751,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                     const S tw = __ldcg(&tau[w]);
                     const int64_t e0 = a.irp[w], e1 = a.irp[w + 1];
                     for (int64_t ee = e0 + lane; ee < e1; ee += 32) {
-                        const int32_t pv = a.icol[ee];
+                        const int32_t pv = a.icol[ee] - vlo;
                         if (__ldcg(&fL[(int64_t)pv * K + wj]) & bj) atomicAdd(&tau[pv], tw);
                     }
                 }
@@ -679,7 +759,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 for (int q = lane; q < nb; q += 32) {
                     const int32_t v = __ldcg(&lb[q]);
                     const double f = (double)(S)__ldcg(&sig[(int64_t)v * W + j]) * (double)__ldcg(&tau[v]) / sst;
-                    atomicAdd(&a.acc_ap[v], f);
+                    atomicAdd(&a.acc_ap[v + vlo], f);
                 }
                 __syncwarp();
                 int32_t *tmp = la;
@@ -695,8 +775,8 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     for (long long p = p0 + gwarp; p < p1; p += nwarps) {
         const int32_t i = a.sorted_samples[p];
         const int32_t j = a.samp_lane[p] - a.lane_base;
-        const int32_t t = a.samp_t[p];
-        const int32_t s = a.lane_src[a.lane_base + j];
+        const int32_t t = a.samp_t[p] - vlo;
+        const int32_t s = a.lane_src[a.lane_base + j] - vlo;
         const int32_t d = __ldcg(&a.found[p]);
         if (INSTR) {
             // edges a top-down truncated BFS from s scans before settling t
@@ -745,7 +825,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 int32_t pv = -1;
                 S val = S(0);
                 if (e < e1) {
-                    pv = a.icol[e];
+                    pv = a.icol[e] - vlo;
                     if (__ldcg(&fprev[(int64_t)pv * K + wj]) & bj) val = (S)__ldcg(&sig[(int64_t)pv * W + j]);
                 }
                 // running sums are exact (integers; FP64 sums of integers below 2^53)
@@ -760,8 +840,8 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             }
             if (pick != s) {
                 if (lane == 0) {
-                    if (store) a.arena[off + k] = pick;
-                    atomicAdd(&a.cnt[pick], 1ULL);
+                    if (store) a.arena[off + k] = pick + vlo;
+                    atomicAdd(&a.cnt[pick + vlo], 1ULL);
                 }
                 ++k;
             }
@@ -850,8 +930,8 @@ percis_status launch_ms_k(percis_ctx *ctx, int K, MsArgs &a) {
     }
 }
 
-percis_status ensure_ms(percis_ctx *ctx, int W, int Lcap) {
-    const int64_t n = ctx->n;
+percis_status ensure_ms(percis_ctx *ctx, int W, int Lcap, int64_t nr) {
+    const int64_t n = nr;  // vertices of the largest launch range
     const int K = W / 64;
     const bool fresh_stamps = ctx->qstamp.bytes < sizeof(int32_t) * (size_t)n;
     PERCIS_TRY(ensure(ctx, ctx->fq0, sizeof(int32_t) * n, "frontier queue"));
@@ -906,7 +986,8 @@ int choose_lanes(percis_ctx *ctx, int64_t n_sources) {
         // keep the lane sigma array within a modest share of device memory
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-            while (W > 64 && (double)ctx->n * W * 8.0 > 0.25 * (double)total_b) W /= 2;
+            const double nv = (double)(ctx->multi ? multi_range(ctx) : ctx->n);
+            while (W > 64 && nv * W * 8.0 > 0.25 * (double)total_b) W /= 2;
         }
     }
     return W;
@@ -917,12 +998,28 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
     const int W = choose_lanes(ctx, n_sources);
     const int K = W / 64;
     int Lcap = std::max(ctx->levels_alloc, 32);
-    PERCIS_TRY(ensure_ms(ctx, W, Lcap));
+    std::vector<LaneBatch> plan;
+    if (ctx->multi) {
+        PERCIS_TRY(multi_plan_batches(ctx, n_sources, W, &plan));
+    } else {
+        for (int64_t b = 0; b * W < n_sources; ++b)
+            plan.push_back({(int32_t)(b * W), (int32_t)std::min<int64_t>(W, n_sources - b * W), 0, ctx->n});
+    }
+    int64_t nr_max = 1;
+    for (const LaneBatch &lb : plan) nr_max = std::max(nr_max, lb.nr);
+    if (!ctx->directed && ctx->vertex_diam > 0) {
+        // no undirected shortest path has more than D + 1 edges: enough levels
+        // up front (within a 16 GiB frontier history), so deep graphs need no
+        // re-runs with a longer history
+        const int64_t lmem = (16ll << 30) / std::max<int64_t>(1, nr_max * K * 8) - 1;
+        Lcap = (int)std::max<int64_t>(Lcap, std::min<int64_t>(ctx->vertex_diam + 3, std::min<int64_t>(lmem, 1 << 20)));
+    }
+    PERCIS_TRY(ensure_ms(ctx, W, Lcap, nr_max));
     ctx->levels_alloc = Lcap;
     ctx->lanes_alloc = W;
     PERCIS_TRY(ensure(ctx, ctx->found, sizeof(int32_t) * (count + 1), "found"));
     PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ms_ctl.p, 0, sizeof(MsCtl), ctx->stream));
-    const int64_t B = (n_sources + W - 1) / W;
+    const int64_t B = (int64_t)plan.size();
     *batches = B;
     MsArgs a{};
     fill_common(ctx, a, Lcap);
@@ -951,7 +1048,7 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
     a.allpaths = ctx->opt.estimator == 1;
     if (a.allpaths) {
         // per-warp scratch of 20 n bytes, within a 8 GiB budget
-        const int64_t n = ctx->n;
+        const int64_t n = nr_max;
         const int64_t per_warp = 20 * n;
         const int64_t warps = (int64_t)ms_grid_for(ctx, K) * (kMsBlock / 32);
         const int64_t ap_warps = std::max<int64_t>(1, std::min<int64_t>(warps, (8ll << 30) / per_warp));
@@ -974,9 +1071,14 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
         a.ap_stamp = ctx->ap_stamp.as<int32_t>();
         a.ap_list = ctx->ap_list.as<int32_t>();
     }
+    const int64_t *irp0 = a.irp, *rp0 = a.rp;
     for (int64_t b = 0; b < B; ++b) {
-        a.lane_base = (int32_t)(b * W);
-        a.nlanes = (int32_t)std::min<int64_t>(W, n_sources - b * W);
+        a.lane_base = plan[b].lane_base;
+        a.nlanes = plan[b].nlanes;
+        a.vlo = plan[b].vlo;
+        a.n = plan[b].nr;
+        a.irp = irp0 + a.vlo;
+        a.rp = rp0 + a.vlo;
         cudaEvent_t e0 = next_event(ctx), e1 = next_event(ctx);
         if (e0) cudaEventRecord(e0, ctx->stream);
         next_stamps(ctx, a);
@@ -998,7 +1100,7 @@ percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, 
     const int K = W / 64;
     int Lcap = std::max(ctx->levels_alloc, 32);
     for (int attempt = 0; attempt < 12; ++attempt) {
-        PERCIS_TRY(ensure_ms(ctx, W, Lcap));
+        PERCIS_TRY(ensure_ms(ctx, W, Lcap, ctx->n));
         ctx->levels_alloc = Lcap;
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ms_ctl.p, 0, sizeof(MsCtl), ctx->stream));
         MsArgs a{};

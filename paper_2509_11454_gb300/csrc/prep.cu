@@ -177,6 +177,12 @@ __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, dou
                 const int slot = (int)(sw % kRing);
                 const int cnt = (int)min((int64_t)kTile, n - sw * kTile);
                 int k = cnt - 1;
+                // x is non-increasing in i, so a tile whose largest state (k = 0)
+                // is zero holds only zeros; while w is still zero, each sum is
+                // exactly +0 and the dependent adds can be skipped
+                if (wn == 0.0 && S.x[slot][0] == 0.0) {
+                    for (; k >= 0; --k) S.w[slot][k] = 0.0;
+                }
                 for (; k >= 7; k -= 8) {  // operands loaded ahead of the dependent adds
                     double v[8];
 #pragma unroll
@@ -198,6 +204,10 @@ __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, dou
                 const int slot = (int)(sr % kRing);
                 const int cnt = (int)min((int64_t)kTile, n - sr * kTile);
                 int k = cnt - 1;
+                // an all-zero tile of states has w = 0 and so c = 0 throughout
+                if (rn == 0.0 && S.x[slot][0] == 0.0) {
+                    for (; k >= 0; --k) S.r[slot][k] = 0.0;
+                }
                 for (; k >= 7; k -= 8) {
                     double v[8];
 #pragma unroll
@@ -439,9 +449,11 @@ percis_status prep_graph(percis_ctx *ctx) {
         PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         ctx->max_indeg = (int64_t)md;
     }
-    int64_t D = 0;
-    PERCIS_TRY(vertex_diam_ub(ctx, &D));
-    ctx->vertex_diam = D;
+    if (!ctx->skip_diam) {
+        int64_t D = 0;
+        PERCIS_TRY(vertex_diam_ub(ctx, &D));
+        ctx->vertex_diam = D;
+    }
     return PERCIS_OK;
 }
 

@@ -239,6 +239,37 @@ def workload(name: str, seed: int = 0):
     raise KeyError(name)
 
 
+def graph_batch(sizes, seed: int) -> list[Graph]:
+    """Independent graphs of the given vertex counts, the type taken in turn:
+    Watts-Strogatz (k=10, p=0.05), Barabasi-Albert (m=3), square grid with 5%
+    of its edges deleted (side round(sqrt(n)), so its size is close to n)."""
+    out = []
+    for g, n in enumerate(sizes):
+        n = int(n)
+        sub = seed * 100_003 + g
+        if g % 3 == 0:
+            out.append(watts_strogatz(n, 10, 0.05, sub))
+        elif g % 3 == 1:
+            out.append(barabasi_albert(n, 3, sub))
+        else:
+            out.append(grid_2d(max(2, int(round(math.sqrt(n)))), 0.05, sub))
+    return out
+
+
+def union_csr(graphs) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Block-diagonal CSR of independent graphs: (graph_vptr, row_ptr, col)."""
+    vptr = np.zeros(len(graphs) + 1, dtype=np.int64)
+    vptr[1:] = np.cumsum([g.n for g in graphs])
+    eptr = np.zeros(len(graphs) + 1, dtype=np.int64)
+    eptr[1:] = np.cumsum([g.nnz for g in graphs])
+    row_ptr = np.zeros(int(vptr[-1]) + 1, dtype=np.int64)
+    col = np.zeros(int(eptr[-1]), dtype=np.int32)
+    for k, g in enumerate(graphs):
+        row_ptr[vptr[k]:vptr[k + 1] + 1] = g.row_ptr + eptr[k]
+        col[eptr[k]:eptr[k + 1]] = g.col + np.int32(vptr[k])
+    return vptr, row_ptr, col
+
+
 def uneven_batch_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """Vertex counts log-uniform in [lo, hi]."""
     rng = np.random.default_rng([seed, 19])

@@ -244,6 +244,24 @@ def test_percis_di_matches_oracle(binding):
     eng.close()
 
 
+def test_autotune_keeps_results(binding):
+    """The autotuner only picks speed options: the estimate after tuning is
+    bit-identical to the default one and to the oracle's."""
+    g, x, eps, delta = synth.workload("er1000")
+    og = oracle.from_synth(g)
+    ref_eng = _engine(binding, g, x)
+    ref, _ = ref_eng.estimate(eps, delta, seed=8)
+    eng = _engine(binding, g, x)
+    o = eng.autotune(probe_samples=3000, seed=1)
+    assert o["lanes"] in (0, 64, 128, 256, 512) and o["lane_order"] in (0, 1) and o["direction"] in (0, 1, 2)
+    pc, info = eng.estimate(eps, delta, seed=8)
+    assert np.array_equal(_np(pc), _np(ref))
+    res = oracle.percis(og, x, eps, delta, 8, ell=info["ell"], keep_paths=False)
+    assert np.max(np.abs(_np(pc) - res.pc)) <= 1e-9
+    ref_eng.close()
+    eng.close()
+
+
 def test_backward_matches_oracle_and_fd(binding):
     g = synth.barabasi_albert(2000, 4, 0)
     og = oracle.from_synth(g)
@@ -312,6 +330,24 @@ def test_epsilon_guarantee_gpu(binding):
     for seed in range(20):
         pc, _ = eng.estimate(eps, delta, seed=seed)
         ok += int(np.max(np.abs(_np(pc) - exact)) <= eps)
+    assert ok >= 18
+    eng.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["ba100k_outbreak", "ba200k_uniform"])
+def test_epsilon_guarantee_full_size_gpu_exact(binding, name):
+    """Proposition 4 at full size: the exact centrality from the GPU
+    (all-sources batched sigma-BFS + the extended Brandes dependencies,
+    parity-tested against the oracle on small graphs) as ground truth;
+    max_v |p~(v) - p(v)| <= eps in at least 18 of 20 seeds."""
+    g, x, eps, delta = synth.workload(name)
+    eng = _engine(binding, g, x)
+    exact = eng.exact()
+    ok = 0
+    for seed in range(20):
+        pc, _ = eng.estimate(eps, delta, seed=seed)
+        ok += int(float(torch.max(torch.abs(pc - exact))) <= eps)
     assert ok >= 18
     eng.close()
 
