@@ -360,7 +360,7 @@ void percis_destroy(percis_ctx *ctx) {
                       &ctx->samp_t, &ctx->lane_src, &ctx->lane_off, &ctx->scratch, &ctx->red, &ctx->status,
                       &ctx->pc_tmp, &ctx->grad_tmp, &ctx->host_pinned, &ctx->vorder,
                       &ctx->fq0, &ctx->fq1, &ctx->qstamp, &ctx->acc_ap,
-                      &ctx->ap_tau, &ctx->ap_stamp, &ctx->ap_list};
+                      &ctx->ap_tau, &ctx->ap_stamp, &ctx->ap_list, &ctx->plan_dev};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->counters.p) cudaFree(ctx->counters.p);

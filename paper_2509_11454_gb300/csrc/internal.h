@@ -86,6 +86,7 @@ struct percis_ctx {
     int sigma_mode = 0;  // batched sigma storage: 0 = 32-bit, 1 = 64-bit integers, 2 = FP64
     percis::DevBuf fq0, fq1, qstamp;  // frontier queues and per-vertex level stamps
     percis::DevBuf acc_ap, ap_tau, ap_stamp, ap_list;  // all-paths estimator
+    percis::DevBuf plan_dev;                           // lane batches of a many-graph phase
     int64_t ap_warps = 0, ap_n = 0;
     int32_t ap_epoch = 0;
     int32_t stamp_base = 1;

@@ -41,6 +41,11 @@ constexpr int kMsBlock = 256;
 constexpr int64_t kBlockDeg = PERCIS_BLOCK_DEG;  // in-degree above which a whole block counts one (vertex, word)
 
 struct MsArgs {
+    // batches of the persistent launch: a host plan, or W-lane batches over the
+    // device-resident lane count *u_dev, or the single batch below
+    const LaneBatch *plan;
+    int32_t nplan;
+    const long long *u_dev;
     // A launch covers the vertex range [vlo, vlo + n) of the loaded graph (the
     // whole graph, or the graphs of a multi-graph batch): rp / irp point at
     // entry vlo, column entries and sample vertices are global ids, and the
@@ -174,8 +179,14 @@ __device__ __forceinline__ void gather_chunk(const ST *sig, int W, int w, uint64
     }
 }
 
+// One batch of lanes: levels, counts and the backtrack of its samples.  The
+// batch covers lanes lane_base .. lane_base + nlanes - 1 and the vertex range
+// [vlo, vlo + n); rp / irp point at entry vlo.  Returns false when the launch
+// must stop (a bounded wait ran out, or the frontier history is too short).
 template <int K, bool INSTR, int SM>
-__global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
+__device__ __forceinline__ bool ms_batch(const MsArgs &a, const int32_t lane_base, const int32_t nlanes,
+                                         const int32_t vlo, const int64_t n, const int64_t *rp, const int64_t *irp,
+                                         const int32_t ap_epoch) {
     constexpr int W = 64 * K;
     constexpr bool FPSIG = SM == 2;
     using S = typename SigmaMode<SM>::S;
@@ -193,11 +204,9 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t gwarp = tid >> 5;
     const int64_t nwarps = nthreads >> 5;
-    const int64_t n = a.n;  // vertices of the launch's range [vlo, vlo + n)
-    const int32_t vlo = a.vlo;
     const int64_t nk = n * K;
-    const long long p0 = a.full ? 0 : a.lane_off[a.lane_base];
-    const long long p1 = a.full ? 0 : a.lane_off[a.lane_base + a.nlanes];
+    const long long p0 = a.full ? 0 : a.lane_off[lane_base];
+    const long long p1 = a.full ? 0 : a.lane_off[lane_base + nlanes];
 
     // ---- prologue: clear visited, frontiers 0 and 1, (push) sigma; reset lane state
     for (int64_t i = tid; i < nk; i += nthreads) {
@@ -212,7 +221,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         for (int j = threadIdx.x; j < W; j += blockDim.x) a.remaining[j] = 0;
         if (threadIdx.x < K) {
             const int lo = threadIdx.x * 64;
-            const int cntl = max(0, min(64, a.nlanes - lo));
+            const int cntl = max(0, min(64, nlanes - lo));
             ctl->active[threadIdx.x] = cntl == 64 ? ~0ull : ((1ull << cntl) - 1ull);
             ctl->nonempty[0][threadIdx.x] = 0ull;
             ctl->nonempty[1][threadIdx.x] = 0ull;
@@ -220,7 +229,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         if (threadIdx.x == 0) {
             ctl->ticket = 0;
             ctl->level = 0;
-            ctl->qn[0] = a.nlanes;
+            ctl->qn[0] = nlanes;
             ctl->qn[1] = 0;
             ctl->qh[0] = 0;
             ctl->qh[1] = 0;
@@ -228,21 +237,21 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             ctl->t_start = globaltimer_ns();
         }
     }
-    if (!grid_sync(bar, status, a.budget_ns)) return;
-    for (int64_t j = tid; j < a.nlanes; j += nthreads) {
-        const int32_t v = a.lane_src[a.lane_base + j] - vlo;
+    if (!grid_sync(bar, status, a.budget_ns)) return false;
+    for (int64_t j = tid; j < nlanes; j += nthreads) {
+        const int32_t v = a.lane_src[lane_base + j] - vlo;
         const uint64_t bit = 1ull << (j & 63);
         atomicOr((unsigned long long *)&a.vis[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         atomicOr((unsigned long long *)&a.fh[(int64_t)v * K + (j >> 6)], (unsigned long long)bit);
         sig[(int64_t)v * W + j] = ST(1);
         a.fq0[j] = v;
-        if (INSTR) a.levdeg[(int64_t)j * (a.Lcap + 1)] = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
+        if (INSTR) a.levdeg[(int64_t)j * (a.Lcap + 1)] = (unsigned long long)(rp[v + 1] - rp[v]);
         if (!a.full) {
-            const long long q0 = a.lane_off[a.lane_base + j], q1 = a.lane_off[a.lane_base + j + 1];
+            const long long q0 = a.lane_off[lane_base + j], q1 = a.lane_off[lane_base + j + 1];
             a.remaining[j] = (int32_t)(q1 - q0);
         }
     }
-    if (!grid_sync(bar, status, a.budget_ns)) return;
+    if (!grid_sync(bar, status, a.budget_ns)) return false;
 
     __shared__ unsigned long long s_nonempty[K];
     __shared__ unsigned long long s_act[K];
@@ -284,7 +293,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 uint64_t fu[K];
 #pragma unroll
                 for (int w = 0; w < K; ++w) fu[w] = shfl64(fl, w);
-                const int64_t e0 = a.rp[u], e1 = a.rp[u + 1];
+                const int64_t e0 = rp[u], e1 = rp[u + 1];
                 for (int64_t e = e0 + warp_in_block * 32 + lane; e < e1; e += kMsBlock) {
                     const int32_t v = a.col[e] - vlo;
                     uint64_t vv[K];
@@ -304,7 +313,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 uint64_t fu[K];
 #pragma unroll
                 for (int w = 0; w < K; ++w) fu[w] = shfl64(fl, w);
-                const int64_t e0 = a.rp[u], e1 = a.rp[u + 1];
+                const int64_t e0 = rp[u], e1 = rp[u + 1];
                 for (int64_t e = e0 + lane; e < e1; e += 32) {
                     const int32_t v = a.col[e] - vlo;
                     uint64_t vv[K];
@@ -325,7 +334,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 if (lane < K) cl = s_act[lane] & ~__ldcg(&a.vis[v * K + lane]);
                 if (!__ballot_sync(0xffffffffu, cl != 0ull)) continue;
                 uint64_t nbl = 0ull;
-                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+                const int64_t e0 = irp[v], e1 = irp[v + 1];
                 for (int64_t base = e0; base < e1; base += 32) {
                     const int64_t e = base + lane;
                     uint64_t f[K];
@@ -349,7 +358,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 }
             }
         }
-        if (!grid_sync(bar, status, a.budget_ns)) return;
+        if (!grid_sync(bar, status, a.budget_ns)) return false;
         if (tid == 0 && L < 32) ctl->lvl_rec[L][4] = globaltimer_ns() - ctl->t_start;
 
         if (push) {
@@ -368,7 +377,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                         for (int w = 0; w < K; ++w) any |= f[w] != 0ull;
                     }
                 }
-                const bool heavy = any && a.irp[v + 1] - a.irp[v] > 32;
+                const bool heavy = any && irp[v + 1] - irp[v] > 32;
                 const unsigned am = __ballot_sync(0xffffffffu, any && !heavy);
                 const unsigned hm = __ballot_sync(0xffffffffu, heavy);
                 if (am) {
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         if (!a.full) {
             for (long long p = p0 + tid; p < p1; p += nthreads) {
                 if (a.found[p] >= 0) continue;
-                const int32_t j = a.samp_lane[p] - a.lane_base;
+                const int32_t j = a.samp_lane[p] - lane_base;
                 const int32_t t = a.samp_t[p] - vlo;
                 const int64_t q = (int64_t)t * K + (j >> 6);
                 if (((__ldcg(&a.vis[q]) | __ldcg(&fnext[q])) >> (j & 63)) & 1ull) {
@@ -400,7 +409,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 }
             }
         }
-        if (!grid_sync(bar, status, a.budget_ns)) return;
+        if (!grid_sync(bar, status, a.budget_ns)) return false;
         if (tid == 0 && L < 32) ctl->lvl_rec[L][5] = globaltimer_ns() - ctl->t_start;
 
         // ---- phase A2: counts of level L+1.  A lane whose last targets were
@@ -429,7 +438,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 const int64_t h = hi / K;
                 const int w = (int)(hi - h * K);
                 const int32_t v = __ldcg(&qnext[n - 1 - h]);
-                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+                const int64_t e0 = irp[v], e1 = irp[v + 1];
                 if (e1 - e0 <= kBlockDeg) continue;  // a warp item below; the same for the whole block
                 const uint64_t nbw = __ldcg(&fnext[(int64_t)v * K + w]) & s_cont[w];
                 if (nbw == 0ull) continue;
@@ -473,7 +482,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 if (lane < K) nbl = __ldcg(&fnext[(int64_t)v * K + lane]) & s_cont[lane];
                 const unsigned wm = __ballot_sync(0xffffffffu, nbl != 0ull);
                 if (!wm) continue;
-                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+                const int64_t e0 = irp[v], e1 = irp[v + 1];
                 ST *drow = sig + (int64_t)v * W;
                 const int64_t e = e0 + lane;
                 int32_t u = 0;
@@ -505,7 +514,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 const int64_t h = (it - qn1) / K;
                 const int w = (int)(it - qn1 - h * K);
                 const int32_t v = __ldcg(&qnext[n - 1 - h]);
-                const int64_t e0 = a.irp[v], e1 = a.irp[v + 1];
+                const int64_t e0 = irp[v], e1 = irp[v + 1];
                 if (!FPSIG && e1 - e0 > kBlockDeg) continue;
                 const uint64_t nbw = __ldcg(&fnext[(int64_t)v * K + w]) & s_cont[w];
                 if (nbw == 0ull) continue;
@@ -532,12 +541,12 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             // targets of the retiring lanes: one warp per sample settled at L+1
             for (long long p = p0 + gwarp; p < p1; p += nwarps) {
                 if (__ldcg(&a.found[p]) != L + 1) continue;
-                const int32_t j = a.samp_lane[p] - a.lane_base;
+                const int32_t j = a.samp_lane[p] - lane_base;
                 const int w = j >> 6;
                 const uint64_t bj = 1ull << (j & 63);
                 if (s_cont[w] & bj) continue;
                 const int32_t t = a.samp_t[p] - vlo;
-                const int64_t e0 = a.irp[t], e1 = a.irp[t + 1];
+                const int64_t e0 = irp[t], e1 = irp[t + 1];
                 S acc = S(0);
                 if (FPSIG) {
                     // in-adjacency order
@@ -577,13 +586,13 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 if (!nb) continue;
                 a.vis[(int64_t)v * K + w] = __ldcg(&a.vis[(int64_t)v * K + w]) | nb;
                 atomicOr(&s_nonempty[w], (unsigned long long)nb);
-                fe += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
+                fe += (unsigned long long)(rp[v + 1] - rp[v]);
                 if (INSTR && w == 0) {
                     n_uv += 1;
-                    n_ue += (unsigned long long)(a.rp[v + 1] - a.rp[v]);
+                    n_ue += (unsigned long long)(rp[v + 1] - rp[v]);
                 }
                 if (INSTR) {
-                    const unsigned long long dg = (unsigned long long)(a.rp[v + 1] - a.rp[v]);
+                    const unsigned long long dg = (unsigned long long)(rp[v + 1] - rp[v]);
                     uint64_t m2 = nb;
                     while (m2) {
                         const int b = __ffsll((long long)m2) - 1;
@@ -607,7 +616,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                     const int64_t v = it / K;
                     const int w = (int)(it - v * K);
                     const uint64_t vw = __ldcg(&a.vis[it]) | __ldcg(&fnext[it]);
-                    if (s_act[w] & ~vw) ue += (unsigned long long)(a.irp[v + 1] - a.irp[v]);
+                    if (s_act[w] & ~vw) ue += (unsigned long long)(irp[v + 1] - irp[v]);
                 }
                 for (int off = 16; off > 0; off >>= 1) ue += __shfl_xor_sync(0xffffffffu, ue, off);
                 if (lane == 0 && ue) atomicAdd(&ctl->uedges[(L + 1) & 1], ue);
@@ -659,7 +668,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 ctl->push_next = a.policy == 1 || (a.policy == 2 && a.push_alpha * (double)fe < (double)ue);
             }
         }
-        if (!grid_sync(bar, status, a.budget_ns)) return;
+        if (!grid_sync(bar, status, a.budget_ns)) return false;
         ++L;
         bool more = false;
 #pragma unroll
@@ -667,7 +676,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         if (!more) break;
         if (L + 1 > a.Lcap) {
             if (tid == 0) atomicOr(status, DEV_NEED_LEVELS);
-            return;
+            return false;
         }
     }
     if (INSTR) {
@@ -685,7 +694,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         }
         if (tid == 0) atomicAdd(&a.counters[5], (unsigned long long)L);
     }
-    if (a.full) return;
+    if (a.full) return true;
 
     if (a.allpaths) {
         // ---- all-paths form (warp per sample): reverse sweep from t over the
@@ -693,7 +702,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         // (exact integers), and every internal v receives
         // f(v) = sigma_sv tau_v / sigma_st.  Scratch is per warp; entries are
         // valid only where the claim stamp equals this sample's epoch.
-        if (gwarp >= a.ap_warps) return;
+        if (gwarp >= a.ap_warps) return true;
         S *tau = reinterpret_cast<S *>(a.ap_tau) + gwarp * n;  // integers, or FP64 beyond 2^53
         int32_t *stamp = a.ap_stamp + gwarp * n;
         int32_t *la = a.ap_list + gwarp * 2 * n;
@@ -701,7 +710,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
         const unsigned lt = (1u << lane) - 1u;
         for (long long p = p0 + gwarp; p < p1; p += a.ap_warps) {
             const int32_t i = a.sorted_samples[p];
-            const int32_t j = a.samp_lane[p] - a.lane_base;
+            const int32_t j = a.samp_lane[p] - lane_base;
             const int32_t t = a.samp_t[p] - vlo;
             const int32_t d = __ldcg(&a.found[p]);
             if (lane == 0) {
@@ -710,7 +719,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 a.path_off[i] = 0;
             }
             if (d < 2) continue;
-            const int32_t ep = a.ap_epoch + (int32_t)(p - p0) + 1;
+            const int32_t ep = ap_epoch + (int32_t)p + 1;  // sample positions are unique in a phase
             const int wj = j >> 6;
             const uint64_t bj = 1ull << (j & 63);
             const double sst = (double)(S)__ldcg(&sig[(int64_t)t * W + j]);
@@ -727,7 +736,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 // claim the predecessors at level L (first claimer zeroes tau)
                 for (int q = 0; q < na; ++q) {
                     const int32_t w = __ldcg(&la[q]);
-                    const int64_t e0 = a.irp[w], e1 = a.irp[w + 1];
+                    const int64_t e0 = irp[w], e1 = irp[w + 1];
                     for (int64_t base = e0; base < e1; base += 32) {
                         const int64_t ee = base + lane;
                         bool mine = false;
@@ -749,7 +758,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 for (int q = 0; q < na; ++q) {
                     const int32_t w = __ldcg(&la[q]);
                     const S tw = __ldcg(&tau[w]);
-                    const int64_t e0 = a.irp[w], e1 = a.irp[w + 1];
+                    const int64_t e0 = irp[w], e1 = irp[w + 1];
                     for (int64_t ee = e0 + lane; ee < e1; ee += 32) {
                         const int32_t pv = a.icol[ee] - vlo;
                         if (__ldcg(&fL[(int64_t)pv * K + wj]) & bj) atomicAdd(&tau[pv], tw);
@@ -768,15 +777,15 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
                 na = nb;
             }
         }
-        return;
+        return true;
     }
 
     // ---- backtrack every sample of the batch (warp per sample)
     for (long long p = p0 + gwarp; p < p1; p += nwarps) {
         const int32_t i = a.sorted_samples[p];
-        const int32_t j = a.samp_lane[p] - a.lane_base;
+        const int32_t j = a.samp_lane[p] - lane_base;
         const int32_t t = a.samp_t[p] - vlo;
-        const int32_t s = a.lane_src[a.lane_base + j] - vlo;
+        const int32_t s = a.lane_src[lane_base + j] - vlo;
         const int32_t d = __ldcg(&a.found[p]);
         if (INSTR) {
             // edges a top-down truncated BFS from s scans before settling t
@@ -817,7 +826,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step),
                                             (double)(S)__ldcg(&sig[(int64_t)w * W + j]));
             const uint64_t *fprev = a.fh + (int64_t)(lw - 1) * nk;
-            const int64_t e0 = a.irp[w], e1 = a.irp[w + 1];
+            const int64_t e0 = irp[w], e1 = irp[w + 1];
             S carry = S(0);
             int32_t pick = -1;
             for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
@@ -849,6 +858,43 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
             --lw;
             ++step;
         }
+    }
+    return true;
+}
+
+// The persistent launch: every batch of a phase in turn, separated by grid
+// barriers.  Batches come from a host plan (many graphs), from the lane count
+// the grouping left in device memory (W lanes each, so a phase needs no host
+// round trip), or are the single batch given in the arguments.
+template <int K, bool INSTR, int SM>
+__global__ void __launch_bounds__(kMsBlock, 4) k_msbfs(MsArgs a) {
+    constexpr int W = 64 * K;
+    MsCtl *ctl = a.ctl;
+    GridBarrier *bar = reinterpret_cast<GridBarrier *>(ctl);
+    uint32_t *status = &ctl->status;
+    int64_t B = 1;
+    long long U = 0;
+    if (a.plan) {
+        B = a.nplan;
+    } else if (a.u_dev) {
+        U = *a.u_dev;
+        B = (U + W - 1) / W;
+    }
+    for (int64_t b = 0; b < B; ++b) {
+        int32_t lane_base = a.lane_base, nlanes = a.nlanes, vlo = a.vlo;
+        int64_t n = a.n;
+        if (a.plan) {
+            lane_base = a.plan[b].lane_base;
+            nlanes = a.plan[b].nlanes;
+            vlo = a.plan[b].vlo;
+            n = a.plan[b].nr;
+        } else if (a.u_dev) {
+            lane_base = (int32_t)(b * W);
+            nlanes = (int32_t)min((long long)W, U - b * W);
+        }
+        // the previous batch's backtrack reads what this batch's prologue clears
+        if (b > 0 && !grid_sync(bar, status, a.budget_ns)) return;
+        if (!ms_batch<K, INSTR, SM>(a, lane_base, nlanes, vlo, n, a.rp + vlo, a.irp + vlo, a.ap_epoch)) return;
     }
 }
 
@@ -998,15 +1044,15 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
     const int W = choose_lanes(ctx, n_sources);
     const int K = W / 64;
     int Lcap = std::max(ctx->levels_alloc, 32);
+    // many graphs: a host plan of lane batches over vertex ranges; one graph:
+    // W-lane batches over the lane count the grouping left on the device
     std::vector<LaneBatch> plan;
+    int64_t nr_max = ctx->n;
     if (ctx->multi) {
         PERCIS_TRY(multi_plan_batches(ctx, n_sources, W, &plan));
-    } else {
-        for (int64_t b = 0; b * W < n_sources; ++b)
-            plan.push_back({(int32_t)(b * W), (int32_t)std::min<int64_t>(W, n_sources - b * W), 0, ctx->n});
+        nr_max = 1;
+        for (const LaneBatch &lb : plan) nr_max = std::max(nr_max, lb.nr);
     }
-    int64_t nr_max = 1;
-    for (const LaneBatch &lb : plan) nr_max = std::max(nr_max, lb.nr);
     if (!ctx->directed && ctx->vertex_diam > 0) {
         // no undirected shortest path has more than D + 1 edges: enough levels
         // up front (within a 16 GiB frontier history), so deep graphs need no
@@ -1019,7 +1065,7 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
     ctx->lanes_alloc = W;
     PERCIS_TRY(ensure(ctx, ctx->found, sizeof(int32_t) * (count + 1), "found"));
     PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ms_ctl.p, 0, sizeof(MsCtl), ctx->stream));
-    const int64_t B = (int64_t)plan.size();
+    const int64_t B = ctx->multi ? (int64_t)plan.size() : (n_sources + W - 1) / W;
     *batches = B;
     MsArgs a{};
     fill_common(ctx, a, Lcap);
@@ -1071,24 +1117,24 @@ percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, i
         a.ap_stamp = ctx->ap_stamp.as<int32_t>();
         a.ap_list = ctx->ap_list.as<int32_t>();
     }
-    const int64_t *irp0 = a.irp, *rp0 = a.rp;
-    for (int64_t b = 0; b < B; ++b) {
-        a.lane_base = plan[b].lane_base;
-        a.nlanes = plan[b].nlanes;
-        a.vlo = plan[b].vlo;
-        a.n = plan[b].nr;
-        a.irp = irp0 + a.vlo;
-        a.rp = rp0 + a.vlo;
-        cudaEvent_t e0 = next_event(ctx), e1 = next_event(ctx);
-        if (e0) cudaEventRecord(e0, ctx->stream);
-        next_stamps(ctx, a);
-        if (a.allpaths) {
-            a.ap_epoch = ctx->ap_epoch;
-            ctx->ap_epoch += (int32_t)std::min<int64_t>(count, 1 << 30) + 1;
-        }
-        PERCIS_TRY(launch_ms_k(ctx, K, a));
-        if (e1) cudaEventRecord(e1, ctx->stream);
+    if (ctx->multi) {
+        PERCIS_TRY(ensure(ctx, ctx->plan_dev, sizeof(LaneBatch) * std::max<size_t>(plan.size(), 1), "batch plan"));
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(ctx->plan_dev.p, plan.data(), sizeof(LaneBatch) * plan.size(),
+                                         cudaMemcpyHostToDevice, ctx->stream));
+        a.plan = ctx->plan_dev.as<LaneBatch>();
+        a.nplan = (int32_t)plan.size();
+    } else {
+        a.u_dev = ctx->lane_of_v.as<long long>() + ctx->n;  // number of lanes
     }
+    if (a.allpaths) {
+        a.ap_epoch = ctx->ap_epoch;
+        ctx->ap_epoch += (int32_t)std::min<int64_t>(count, 1 << 30) + 1;
+    }
+    // every batch of the phase in one persistent launch
+    cudaEvent_t e0 = next_event(ctx), e1 = next_event(ctx);
+    if (e0) cudaEventRecord(e0, ctx->stream);
+    PERCIS_TRY(launch_ms_k(ctx, K, a));
+    if (e1) cudaEventRecord(e1, ctx->stream);
     return PERCIS_OK;
 }
 
