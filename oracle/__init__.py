@@ -84,7 +84,9 @@ def _declare(L):
     L.orc_backtrack.argtypes = [P, P, P, P, I32, I32, U64, U32, U64, P]
     L.orc_backtrack.restype = I32
     L.orc_run_samples.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, F64, P, U64, U32, U32, I64, I64,
-                                  P, P, P, P, P, P, P, P, I64, P, P, P]
+                                  P, P, P, P, P, P, P, P, I64, P, P, P, ctypes.c_int]
+    L.orc_bibfs.argtypes = [I64, P, P, P, P, I32, I32, U64, U32, U64, P, P, P, P, P]
+    L.orc_bibfs.restype = I32
     L.orc_allpaths.argtypes = [I64, P, P, P, P, I32, I32, P, P]
     L.orc_allpaths.restype = I32
     L.orc_run_samples.restype = ctypes.c_int
@@ -270,8 +272,13 @@ class Phase:
 
 
 def run_samples(g: OGraph, prep: Prep, seed: int, tag_pair: int, tag_path: int, i0: int, count: int,
-                keep_paths: bool = True, path_cap: int | None = None, allpaths: bool = False) -> Phase:
-    """One sampling phase: Algorithm 2 pairs, RandomSP paths, estimator sums."""
+                keep_paths: bool = True, path_cap: int | None = None, allpaths: bool = False,
+                bidir: bool = False) -> Phase:
+    """One sampling phase: Algorithm 2 pairs, RandomSP paths, estimator sums.
+    bidir: RandomSP by the balanced bidirectional BFS (see bibfs); the
+    edges then count what both sides scanned."""
+    if bidir and allpaths:
+        raise ValueError("the all-paths form uses the one-sided BFS")
     n = g.n
     s = np.zeros(count, dtype=np.int32)
     t = np.zeros(count, dtype=np.int32)
@@ -294,7 +301,8 @@ def run_samples(g: OGraph, prep: Prep, seed: int, tag_pair: int, tag_path: int, 
             rc = lib().orc_run_samples(n, _p(g.rp), _p(g.col), _p(g.irp), _p(g.icol), _p(prep.x), _p(prep.xs),
                                        _p(prep.perm), _p(prep.w), _p(prep.ci), _p(prep.r), prep.c, _p(prep.Cv),
                                        seed, tag_pair, tag_path, i0, count, _p(s), _p(t), _p(kind), _p(ilen),
-                                       _p(cnt), _p(acc), _p(pp), _p(pn), cap, _p(edges), _p(ovf), _p(acc_all))
+                                       _p(cnt), _p(acc), _p(pp), _p(pn), cap, _p(edges), _p(ovf), _p(acc_all),
+                                       int(bidir))
             if rc == -1:
                 cap = int(pp[-1]) + 1
                 continue
@@ -306,10 +314,25 @@ def run_samples(g: OGraph, prep: Prep, seed: int, tag_pair: int, tag_path: int, 
         rc = lib().orc_run_samples(n, _p(g.rp), _p(g.col), _p(g.irp), _p(g.icol), _p(prep.x), _p(prep.xs),
                                    _p(prep.perm), _p(prep.w), _p(prep.ci), _p(prep.r), prep.c, _p(prep.Cv),
                                    seed, tag_pair, tag_path, i0, count, _p(s), _p(t), _p(kind), _p(ilen),
-                                   _p(cnt), _p(acc), None, None, 0, _p(edges), _p(ovf), _p(acc_all))
+                                   _p(cnt), _p(acc), None, None, 0, _p(edges), _p(ovf), _p(acc_all), int(bidir))
     if rc == -2:
         raise RuntimeError("oracle backtrack failed (sigma not exact?)")
     return Phase(s, t, kind, ilen, cnt, acc, pp, pn, edges, bool(ovf[0]), acc_all)
+
+
+def bibfs(g: OGraph, s: int, t: int, seed: int, tag: int, i: int):
+    """Balanced bidirectional RandomSP of sample i: (d(s,t) or -1, internal
+    nodes, sigma_st, edges scanned)."""
+    path = np.zeros(g.n + 1, dtype=np.int32)
+    plen = np.zeros(1, dtype=np.int32)
+    sst = np.zeros(1)
+    edges = np.zeros(1, dtype=np.int64)
+    ovf = np.zeros(1, dtype=np.int32)
+    d = lib().orc_bibfs(g.n, _p(g.rp), _p(g.col), _p(g.irp), _p(g.icol), s, t, seed, tag, i, _p(path), _p(plen),
+                        _p(sst), _p(edges), _p(ovf))
+    if d == -2:
+        raise RuntimeError("oracle bidirectional backtrack failed")
+    return int(d), path[: int(plen[0])].copy(), float(sst[0]), int(edges[0])
 
 
 def allpaths(g: OGraph, dist, sigma, s: int, t: int):
@@ -520,7 +543,7 @@ class Result:
 
 def percis(g: OGraph, x, eps: float, delta: float, seed: int, ell1: int | None = None, ell: int | None = None,
            D: int | None = None, prep: Prep | None = None, keep_paths: bool = True, allpaths: bool = False,
-           data_independent: bool = False, offsets: tuple[int, int] = (0, 0)) -> Result:
+           data_independent: bool = False, offsets: tuple[int, int] = (0, 0), bidir: bool = False) -> Result:
     """Algorithm 1 (PercIS): D, phase 1 (l1 samples, pair tag 0, path tag 2),
     rho^, v^, x^, l, then phase 2 (l fresh samples, pair tag 1, path tag 3).
     The phase-1 estimate uses 1/l1 (the 1/l printed in that line of
@@ -542,7 +565,7 @@ def percis(g: OGraph, x, eps: float, delta: float, seed: int, ell1: int | None =
         rh, vh = float(D), prep.dhat * prep.dhat / 4.0
     else:
         l1 = ell1 if ell1 is not None else ell1_default(eps, delta)
-        ph1 = run_samples(g, prep, seed, 0, 2, offsets[0], l1, keep_paths=False, allpaths=allpaths)
+        ph1 = run_samples(g, prep, seed, 0, 2, offsets[0], l1, keep_paths=False, allpaths=allpaths, bidir=bidir)
         p1 = (ph1.acc_all if allpaths else ph1.acc) / l1
         p1_max = float(p1.max())
         rh, rt, Lam = rho_hat(ph1.ilen, D, delta)
@@ -550,7 +573,7 @@ def percis(g: OGraph, x, eps: float, delta: float, seed: int, ell1: int | None =
     xh = x_hat(vh, prep.dhat)
     if ell is None:
         ell, _ = ell_sup(eps, delta, prep.dhat, rh, xh)
-    ph2 = run_samples(g, prep, seed, 1, 3, offsets[1], ell, keep_paths=keep_paths, allpaths=allpaths)
+    ph2 = run_samples(g, prep, seed, 1, 3, offsets[1], ell, keep_paths=keep_paths, allpaths=allpaths, bidir=bidir)
     pc = (ph2.acc_all if allpaths else ph2.acc) / ell
     pc_counts = prep.lam * ph2.cnt / ell
     return Result(pc, pc_counts, ph2.cnt, l1, ell, D, prep.dhat, rt, Lam, rh, vh, xh, p1_max, ph1, ph2, prep)

@@ -256,6 +256,161 @@ int32_t orc_backtrack(const int64_t *irp, const int32_t *icol, const int32_t *di
     return k;
 }
 
+/* RandomSP by a balanced bidirectional BFS (Section III-B).  The paper names
+ * the traversal but not its details; this follows the reading stated here.
+ * Forward side from s over out-edges, backward side from t over in-edges,
+ * each with its own distance and path counts (sigma_s, sigma_t).  While both
+ * frontiers are non-empty, expand one level of the side whose frontier has
+ * the smaller sum of degrees in its direction (the forward side on a tie).
+ * The first level L_a of a side that contains vertices the other side has
+ * reached ends the search: with a the expanded side's new level and b the
+ * other side's last level, every such vertex lies at distance b from the
+ * other end, d(s,t) = a + b, and every shortest path crosses the layer
+ * M = {v : d(s,v) = a_F} exactly once, so sigma_st = sum over M of
+ * sigma_s(v) sigma_t(v).  The path: v in M with probability
+ * sigma_s(v) sigma_t(v) / sigma_st (first v in vertex-id order whose running
+ * sum reaches u_0 sigma_st), then the forward side backtracked from v to s and
+ * the backward side from v to t, each step choosing among the next vertices
+ * towards the end (in-CSR order towards s, out-CSR order towards t) the first
+ * whose running count reaches u sigma(w) (uniform steps 1, 2, ...).
+ * Internal nodes are written v first (unless v is s or t), then the s side
+ * from v, then the t side from v.  Returns d(s,t), or -1 when a frontier
+ * empties first (t unreachable).  *sst = sigma_st; *edges_out = edges scanned
+ * by both sides. */
+int32_t orc_bibfs(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *irp, const int32_t *icol,
+                  int32_t s, int32_t t, uint64_t seed, uint32_t tag, uint64_t i, int32_t *path, int32_t *plen,
+                  double *sst, int64_t *edges_out, int32_t *overflow) {
+    int32_t *dist[2];
+    double *sig[2];
+    int32_t *queue[2];
+    for (int x = 0; x < 2; x++) {
+        dist[x] = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+        sig[x] = (double *)calloc((size_t)n, sizeof(double));
+        queue[x] = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+        for (int64_t v = 0; v < n; v++) dist[x][v] = -1;
+    }
+    const int64_t *ptr[2] = {rp, irp};  /* forward: out-edges; backward: in-edges */
+    const int32_t *adj[2] = {col, icol};
+    int32_t end[2] = {s, t};
+    int64_t lo[2] = {0, 0}, hi[2] = {1, 1}; /* current frontier = queue[x][lo..hi) */
+    int32_t lev[2] = {0, 0};
+    int64_t cost[2];
+    int64_t edges = 0;
+    int32_t d = -1;
+    *plen = 0;
+    *sst = 0.0;
+    for (int x = 0; x < 2; x++) {
+        dist[x][end[x]] = 0;
+        sig[x][end[x]] = 1.0;
+        queue[x][0] = end[x];
+        cost[x] = ptr[x][end[x] + 1] - ptr[x][end[x]];
+    }
+    int32_t *meet = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t nm = 0;
+    if (s != t) {
+        while (hi[0] > lo[0] && hi[1] > lo[1]) {
+            const int x = cost[0] <= cost[1] ? 0 : 1, y = 1 - x;
+            int64_t top = hi[x];
+            /* discover level lev+1 */
+            for (int64_t q = lo[x]; q < hi[x]; q++) {
+                const int32_t u = queue[x][q];
+                for (int64_t e = ptr[x][u]; e < ptr[x][u + 1]; e++) {
+                    const int32_t v = adj[x][e];
+                    edges++;
+                    if (dist[x][v] < 0) {
+                        dist[x][v] = lev[x] + 1;
+                        queue[x][top++] = v;
+                    }
+                    if (dist[x][v] == lev[x] + 1) sig[x][v] += sig[x][u];
+                }
+            }
+            lo[x] = hi[x];
+            hi[x] = top;
+            lev[x]++;
+            cost[x] = 0;
+            for (int64_t q = lo[x]; q < hi[x]; q++) {
+                const int32_t v = queue[x][q];
+                cost[x] += ptr[x][v + 1] - ptr[x][v];
+                if (sig[x][v] >= 9007199254740992.0) *overflow = 1;
+                if (dist[y][v] >= 0) meet[nm++] = v;
+            }
+            if (nm > 0) {
+                d = lev[x] + dist[y][meet[0]];
+                break;
+            }
+        }
+    }
+    if (d >= 0) {
+        /* the meeting layer in vertex-id order (insertion sort of a small set) */
+        for (int64_t a = 1; a < nm; a++) {
+            const int32_t key = meet[a];
+            int64_t b = a - 1;
+            while (b >= 0 && meet[b] > key) {
+                meet[b + 1] = meet[b];
+                b--;
+            }
+            meet[b + 1] = key;
+        }
+        double total = 0.0;
+        for (int64_t a = 0; a < nm; a++) total += sig[0][meet[a]] * sig[1][meet[a]];
+        *sst = total;
+        double u[2];
+        orc_uniforms(seed, i, tag, 0, u);
+        const double target = u[0] * total;
+        double cum = 0.0;
+        int32_t v = meet[nm - 1];
+        for (int64_t a = 0; a < nm; a++) {
+            cum += sig[0][meet[a]] * sig[1][meet[a]];
+            if (cum >= target) {
+                v = meet[a];
+                break;
+            }
+        }
+        int32_t k = 0;
+        if (v != s && v != t) path[k++] = v;
+        uint32_t step = 1;
+        for (int x = 0; x < 2; x++) {
+            /* towards s: predecessors over in-edges; towards t: successors over out-edges */
+            const int64_t *bp = x == 0 ? irp : rp;
+            const int32_t *bc = x == 0 ? icol : col;
+            int32_t w = v;
+            while (w != end[x]) {
+                orc_uniforms(seed, i, tag, step >> 1, u);
+                const double tg = u[step & 1] * sig[x][w];
+                double c2 = 0.0;
+                int32_t pick = -1;
+                for (int64_t e = bp[w]; e < bp[w + 1]; e++) {
+                    const int32_t p2 = bc[e];
+                    if (dist[x][p2] >= 0 && dist[x][p2] == dist[x][w] - 1) {
+                        c2 += sig[x][p2];
+                        if (c2 >= tg) {
+                            pick = p2;
+                            break;
+                        }
+                    }
+                }
+                if (pick < 0) {
+                    d = -2;
+                    break;
+                }
+                if (pick != end[x]) path[k++] = pick;
+                w = pick;
+                step++;
+            }
+            if (d < 0) break;
+        }
+        *plen = k;
+    }
+    *edges_out = edges;
+    for (int x = 0; x < 2; x++) {
+        free(dist[x]);
+        free(sig[x]);
+        free(queue[x]);
+    }
+    free(meet);
+    return d;
+}
+
 /* All shortest paths at once (the Rao-Blackwellised form of the Section III-A
  * estimator: E over the uniform path of 1[v in I] is sigma_st(v)/sigma_st).
  * After the truncated BFS from s to t, tau_w = number of shortest w-t paths by
@@ -325,7 +480,7 @@ int orc_run_samples(int64_t n, const int64_t *rp, const int32_t *col, const int6
                     const double *r, double c, const double *Cv, uint64_t seed, uint32_t tag_pair, uint32_t tag_path,
                     int64_t i0, int64_t count, int32_t *s_out, int32_t *t_out, int32_t *kind, int32_t *ilen,
                     int64_t *cnt, double *acc, int64_t *path_ptr, int32_t *path_nodes, int64_t path_cap,
-                    int64_t *edges, int32_t *overflow, double *acc_all) {
+                    int64_t *edges, int32_t *overflow, double *acc_all, int bidir) {
     int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     double *sigma = (double *)malloc(sizeof(double) * (size_t)n);
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
@@ -348,11 +503,23 @@ int orc_run_samples(int64_t n, const int64_t *rp, const int32_t *col, const int6
             kind[k] = 1;
         } else {
             int64_t no;
-            int64_t d = orc_bfs(n, rp, col, irp, icol, s, t, dist, sigma, order, &no, &e_scanned, overflow);
+            int64_t d;
+            int32_t got = 0;
+            if (bidir) {
+                double sst;
+                d = orc_bibfs(n, rp, col, irp, icol, s, t, seed, tag_path, i, path, &got, &sst, &e_scanned,
+                              overflow);
+                if (d == -2) {
+                    rc = -2;
+                    d = -1;
+                }
+            } else {
+                d = orc_bfs(n, rp, col, irp, icol, s, t, dist, sigma, order, &no, &e_scanned, overflow);
+            }
             if (d < 0) {
                 kind[k] = 2;
             } else {
-                int32_t got = orc_backtrack(irp, icol, dist, sigma, s, t, seed, tag_path, i, path);
+                if (!bidir) got = orc_backtrack(irp, icol, dist, sigma, s, t, seed, tag_path, i, path);
                 if (got < 0) {
                     rc = -2;
                     got = 0;

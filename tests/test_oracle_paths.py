@@ -276,3 +276,77 @@ def test_allpaths_estimator_lower_error():
         e1 += float(((r1.pc - ex) ** 2).sum())
         e2 += float(((r2.pc - ex) ** 2).sum())
     assert e2 < 0.6 * e1
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_bidirectional_distance_and_count_match_bfs(directed):
+    """The balanced bidirectional search meets at d(s,t) with sigma_st equal
+    to the one-sided BFS count (scipy-pinned distances, walk-pinned counts);
+    unreachable targets give -1 on both."""
+    g = _rand_graph(200, 420 if directed else 260, directed, 31)
+    og = oracle.from_synth(g)
+    rng = np.random.default_rng(5)
+    seen_unreach = False
+    for k in range(120):
+        s, t = (int(v) for v in rng.integers(0, g.n, 2))
+        if s == t:
+            continue
+        d, path, sst, _ = oracle.bibfs(og, s, t, 7, 3, k)
+        ret, dist, sigma, _, _, _ = oracle.bfs(og, s, t)
+        if dist[t] < 0:
+            assert d == -1
+            seen_unreach = True
+            continue
+        assert d == dist[t] and sst == sigma[t]
+        assert len(path) == d - 1
+    assert seen_unreach or not directed
+
+
+def test_bidirectional_path_is_a_shortest_path():
+    g = synth.barabasi_albert(400, 2, 1)
+    og = oracle.from_synth(g)
+    adj = _dense(g)
+    rng = np.random.default_rng(0)
+    for i in range(60):
+        s, t = (int(v) for v in rng.integers(0, 400, 2))
+        if s == t:
+            continue
+        d, path, _, _ = oracle.bibfs(og, s, t, 5, 2, i)
+        ret, dist, _, _, _, _ = oracle.bfs(og, s, t)
+        assert d == dist[t]
+        # the internal nodes are v, then the s side from v, then the t side from v
+        assert len(path) == d - 1 and len(set(path.tolist()) | {s, t}) == d + 1
+        ds = {int(v): int(dist[v]) for v in path}
+        order = sorted(path.tolist(), key=lambda v: ds[v])
+        full = [s] + order + [t]
+        for a, b in zip(full[:-1], full[1:]):
+            assert adj[a, b] == 1
+
+
+def test_bidirectional_randomsp_uniform_over_shortest_paths():
+    """Each of the 70 corner-to-corner paths of a 5x5 grid with probability 1/70."""
+    g = synth.grid_2d(5, 0.0, 0)
+    og = oracle.from_synth(g)
+    counts = {}
+    for i in range(70 * 300):
+        d, path, sst, _ = oracle.bibfs(og, 0, 24, 99, 3, i)
+        assert d == 8 and sst == 70.0
+        key = tuple(sorted(path.tolist()))
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 70
+    assert stats.chisquare(np.array(list(counts.values()))).pvalue > 1e-4
+
+
+def test_bidirectional_estimator_unbiased():
+    g = synth.barabasi_albert(14, 2, 11)
+    og = oracle.from_synth(g)
+    x = np.random.default_rng(11).random(14)
+    prep = oracle.prepare(x)
+    pe = oracle.exact_pc(og, x, prep.Cv)
+    ell, reps = 200, 150
+    est = np.zeros(14)
+    for k in range(reps):
+        ph = oracle.run_samples(og, prep, 50 + k, 1, 3, 0, ell, keep_paths=False, bidir=True)
+        est += ph.acc / ell
+    sd = np.sqrt(np.maximum(pe * (prep.dhat - pe), 1e-30) / (ell * reps))
+    assert np.all(np.abs(est / reps - pe) <= 5 * sd + 1e-12)
