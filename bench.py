@@ -43,8 +43,9 @@ WORKLOAD_DESC = {
 }
 # DRAM traffic of one batched sigma-BFS launch from an ncu capture, valid only
 # for the kernel source it was taken on (sha256 of csrc/msbfs.cu).
-NCU_TRAFFIC = {"msbfs_sha256": "fda36146203be3fa0e82ab030f18e6640c606aad1f28fbb043888e7069da9660",
-               "bytes_per_launch": 818932736 + 962884096}  # profiles/k_msbfs_ba100k_outbreak.md
+NCU_TRAFFIC = {"msbfs_sha256": "ca2e6806ea9f3f5243f765b02c21eecae307c332c69e267183886b9109460557",
+               # DRAM read + write of one phase-2 launch (20 batches) / 20: bytes per batch of lanes
+               "bytes_per_launch": (10704329000 + 6086044000) / 20}  # the ncu capture summarised under profiles/
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
 
@@ -307,7 +308,8 @@ def main():
             traffic = NCU_TRAFFIC["bytes_per_launch"]
         extras["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                              "kernel": "k_msbfs (batched sigma-BFS + backtrack, one launch per lane batch)",
+                              "kernel": "k_msbfs (batched sigma-BFS + backtrack; one persistent launch per phase, "
+                                        "figures per batch of W lanes)",
                               "peak_source": f"{peak_kind} HBM copy bandwidth",
                               "algorithmic_bytes_per_launch": per_launch_bytes,
                               "avg_launch_ms": per_launch_s * 1000.0, "launches_per_step": bfs_launches / len(infos)}
