@@ -47,14 +47,23 @@ typedef enum {
     PERCIS_E_STATE = 8        /* call order: graph or states not loaded yet */
 } percis_status;
 
-/* How sampled paths are produced (same samples, same results):
+/* How sampled paths are produced:
  *  BATCHED: samples are grouped by source; up to `lanes` distinct sources
- *           share one persistent multi-source sigma-BFS launch (bitset
- *           frontiers, one bit per source per vertex), followed in the same
- *           launch by the per-sample backtrack.
+ *           share one persistent multi-source sigma-BFS (bitset frontiers,
+ *           one bit per source per vertex), followed in the same launch by
+ *           the per-sample backtrack from t.
  *  PLAIN:   one single-source sigma-BFS launch plus one backtrack launch per
- *           sampled pair (the baseline form). */
-enum { PERCIS_FORM_BATCHED = 0, PERCIS_FORM_PLAIN = 1 };
+ *           sampled pair (the baseline form).  Same paths as BATCHED.
+ *  BIDIR:   RandomSP by a balanced bidirectional BFS (Section III-B), one
+ *           block per sample: the side with the smaller frontier degree sum
+ *           expands until the sides meet; the meeting vertex is drawn with
+ *           probability sigma_s(v) sigma_t(v) / sigma_st (first in vertex-id
+ *           order whose running sum reaches u_0 sigma_st) and both sides are
+ *           backtracked from it.  Same pairs and the same path distribution,
+ *           other paths than BATCHED (each path uniform over the shortest
+ *           paths); paths list the meeting vertex, then the s side, then the
+ *           t side.  No all-paths estimator, no many-graph contexts. */
+enum { PERCIS_FORM_BATCHED = 0, PERCIS_FORM_PLAIN = 1, PERCIS_FORM_BIDIR = 2 };
 
 typedef struct {
     int32_t form;             /* PERCIS_FORM_*; default BATCHED */

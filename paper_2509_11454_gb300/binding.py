@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "DEGENERATE", 3: "OOM", 4: "CUDA", 5: 
                 7: "NO_SAMPLE", 8: "STATE"}
 FORM_BATCHED = 0
 FORM_PLAIN = 1
+FORM_BIDIR = 2
 
 
 class PercisError(RuntimeError):
@@ -303,7 +304,7 @@ class PercIS:
     def set_options(self, **kw):
         for k, v in kw.items():
             if k == "form" and isinstance(v, str):
-                v = {"batched": FORM_BATCHED, "plain": FORM_PLAIN}[v]
+                v = {"batched": FORM_BATCHED, "plain": FORM_PLAIN, "bidir": FORM_BIDIR}[v]
             if k == "estimator" and isinstance(v, str):
                 v = {"path": 0, "allpaths": 1}[v]
             setattr(self.options, k, v)

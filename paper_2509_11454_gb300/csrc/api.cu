@@ -228,6 +228,12 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
             PERCIS_TRY(plain_phase(ctx, seed, (uint32_t)(2 + phase), count));
             if (e1) cudaEventRecord(e1, ctx->stream);
             *batches = count;
+        } else if (ctx->opt.form == PERCIS_FORM_BIDIR) {
+            cudaEvent_t e0 = next_event(ctx), e1 = next_event(ctx);
+            if (e0) cudaEventRecord(e0, ctx->stream);
+            PERCIS_TRY(bidir_phase(ctx, seed, (uint32_t)(2 + phase), count));
+            if (e1) cudaEventRecord(e1, ctx->stream);
+            *batches = 1;
         } else {
             int64_t U = 0, valid = 0;
             PERCIS_TRY(group_by_source(ctx, count, &U, &valid));
@@ -360,7 +366,8 @@ void percis_destroy(percis_ctx *ctx) {
                       &ctx->samp_t, &ctx->lane_src, &ctx->lane_off, &ctx->scratch, &ctx->red, &ctx->status,
                       &ctx->pc_tmp, &ctx->grad_tmp, &ctx->host_pinned, &ctx->vorder,
                       &ctx->fq0, &ctx->fq1, &ctx->qstamp, &ctx->acc_ap,
-                      &ctx->ap_tau, &ctx->ap_stamp, &ctx->ap_list, &ctx->plan_dev};
+                      &ctx->ap_tau, &ctx->ap_stamp, &ctx->ap_list, &ctx->plan_dev, &ctx->bi_info,
+                      &ctx->bi_sig, &ctx->bi_queue};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->counters.p) cudaFree(ctx->counters.p);
@@ -387,7 +394,7 @@ int64_t percis_launch_count(const percis_ctx *ctx) { return ctx ? ctx->launches 
 
 percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt) {
     if (!ctx || !opt) return PERCIS_E_INVALID;
-    if (opt->form != PERCIS_FORM_BATCHED && opt->form != PERCIS_FORM_PLAIN)
+    if (opt->form != PERCIS_FORM_BATCHED && opt->form != PERCIS_FORM_PLAIN && opt->form != PERCIS_FORM_BIDIR)
         return set_err(ctx, PERCIS_E_INVALID, "unknown form");
     if (opt->lanes != 0 && opt->lanes != 64 && opt->lanes != 128 && opt->lanes != 256 && opt->lanes != 512)
         return set_err(ctx, PERCIS_E_INVALID, "lanes must be 0, 64, 128, 256 or 512");
@@ -395,7 +402,7 @@ percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt) {
     if (opt->direction < 0 || opt->direction > 2) return set_err(ctx, PERCIS_E_INVALID, "direction must be 0, 1 or 2");
     if (!(opt->push_alpha >= 0.0)) return set_err(ctx, PERCIS_E_INVALID, "push_alpha must be >= 0");
     if (opt->estimator != 0 && opt->estimator != 1) return set_err(ctx, PERCIS_E_INVALID, "estimator must be 0 or 1");
-    if (opt->estimator == 1 && opt->form == PERCIS_FORM_PLAIN)
+    if (opt->estimator == 1 && opt->form != PERCIS_FORM_BATCHED)
         return set_err(ctx, PERCIS_E_INVALID, "the all-paths estimator runs in the batched form");
     if (opt->ell1 < 0 || opt->ell1 == 1 || opt->ell < 0 || !(opt->timeout_s > 0.0))
         return set_err(ctx, PERCIS_E_INVALID, "bad sample sizes or timeout");

@@ -1,0 +1,362 @@
+// RandomSP by a balanced bidirectional BFS (Section III-B), one block per
+// sample.  The paper names the traversal but not its details; the reading
+// (the same one the oracle follows):
+//   * forward side from s over out-edges, backward side from t over in-edges,
+//     each with its own levels and exact integer path counts;
+//   * while both frontiers are non-empty, the side whose frontier has the
+//     smaller sum of degrees (in its direction; forward on a tie) expands one
+//     level;
+//   * the first new level that holds vertices the other side has reached ends
+//     the search: those vertices all sit at the other side's last level b, so
+//     d(s,t) = a + b and sigma_st = sum over them of sigma_s(v) sigma_t(v);
+//   * the meeting vertex is the first, in vertex-id order, whose running sum of
+//     sigma_s sigma_t reaches u_0 sigma_st; both sides are then backtracked
+//     from it (towards s over in-edges, towards t over out-edges), each step
+//     taking the first candidate whose running count reaches u sigma(w).
+// Samples are independent, so blocks take them from a shared counter and
+// never wait on one another.  Each block owns a slot of scratch arrays
+// (level + epoch word, count and queue per vertex and side); a vertex belongs
+// to the current sample only while its word carries the sample's epoch, so the
+// arrays are never cleared between samples.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace percis {
+
+namespace {
+
+constexpr int kBiBlock = 256;
+
+struct BiArgs {
+    int64_t n;
+    const int64_t *rp, *irp;
+    const int32_t *col, *icol;
+    int64_t count;
+    const int32_t *pair_s, *pair_t;
+    int32_t *kind, *ilen;
+    long long *path_off;
+    int32_t *arena;
+    unsigned long long *arena_top;
+    int64_t arena_cap;
+    unsigned long long *cnt;
+    uint64_t seed;
+    uint32_t tag;
+    uint32_t epoch_base;
+    unsigned long long *info;   // [slots][2][n]: epoch << 32 | level
+    unsigned long long *sig;    // [slots][2][n]
+    int32_t *queue;             // [slots][2][n]: visited vertices of each side in level order
+    int32_t slots;
+    unsigned long long *next;   // next sample to take
+    uint32_t *status;
+    unsigned long long *edges;  // optional: edges scanned (both sides)
+};
+
+__device__ __forceinline__ unsigned long long pack(uint32_t ep, uint32_t lev) {
+    return ((unsigned long long)ep << 32) | lev;
+}
+
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T t = T(0);
+    for (int q = 0; q < kBiBlock / 32; ++q) t += red[q];
+    return t;
+}
+
+__global__ void __launch_bounds__(kBiBlock) k_bibfs(BiArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nw = kBiBlock / 32;
+    const int64_t n = a.n;
+    const size_t slot = blockIdx.x;
+    unsigned long long *info[2] = {a.info + (slot * 2) * n, a.info + (slot * 2 + 1) * n};
+    unsigned long long *sig[2] = {a.sig + (slot * 2) * n, a.sig + (slot * 2 + 1) * n};
+    int32_t *queue[2] = {a.queue + (slot * 2) * n, a.queue + (slot * 2 + 1) * n};
+    const int64_t *ptr[2] = {a.rp, a.irp};  // expansion: forward over out-edges, backward over in-edges
+    const int32_t *adj[2] = {a.col, a.icol};
+
+    __shared__ long long s_i;
+    __shared__ long long s_lo[2], s_hi[2];
+    __shared__ uint32_t s_lev[2];
+    __shared__ unsigned long long s_cost[2], s_newcost;
+    __shared__ int s_new, s_meet;
+    __shared__ unsigned long long s_red[nw];
+    __shared__ unsigned long long s_edges;
+    if (threadIdx.x == 0) s_edges = 0ull;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_i = (long long)atomicAdd(a.next, 1ull);
+        __syncthreads();
+        const long long i = s_i;
+        if (i >= a.count) break;
+        if (a.kind[i] != 0) {  // zero weight: no path (block-uniform)
+            if (threadIdx.x == 0) {
+                a.ilen[i] = 0;
+                a.path_off[i] = 0;
+            }
+            continue;
+        }
+        const int32_t end[2] = {a.pair_s[i], a.pair_t[i]};
+        const uint32_t ep = a.epoch_base + (uint32_t)i + 1u;
+        if (threadIdx.x == 0) {
+            for (int x = 0; x < 2; ++x) {
+                info[x][end[x]] = pack(ep, 0);
+                sig[x][end[x]] = 1ull;
+                queue[x][0] = end[x];
+                s_lo[x] = 0;
+                s_hi[x] = 1;
+                s_lev[x] = 0;
+                s_cost[x] = (unsigned long long)(ptr[x][end[x] + 1] - ptr[x][end[x]]);
+            }
+            s_new = 0;
+            s_newcost = 0ull;
+            s_meet = 0;
+        }
+        __syncthreads();
+        int x = 0;
+        bool met = end[0] != end[1];
+        if (met) {
+            met = false;
+            for (;;) {
+                if (s_hi[0] == s_lo[0] || s_hi[1] == s_lo[1]) break;  // a side ran dry: t unreachable
+                x = s_cost[0] <= s_cost[1] ? 0 : 1;
+                const int y = 1 - x;
+                const long long lo = s_lo[x], hi = s_hi[x];
+                const uint32_t nl = s_lev[x] + 1;
+                const unsigned long long want = pack(ep, nl);
+                unsigned long long ne = 0ull;
+                // claim level nl
+                for (long long q = lo + warp; q < hi; q += nw) {
+                    const int32_t u = queue[x][q];
+                    const int64_t e0 = ptr[x][u], e1 = ptr[x][u + 1];
+                    ne += (unsigned long long)(e1 - e0);
+                    for (int64_t e = e0 + lane; e < e1; e += 32) {
+                        const int32_t v = adj[x][e];
+                        const unsigned long long old = __ldcg(&info[x][v]);
+                        if ((uint32_t)(old >> 32) != ep && atomicCAS(&info[x][v], old, want) == old) {
+                            sig[x][v] = 0ull;
+                            queue[x][hi + atomicAdd(&s_new, 1)] = v;
+                            atomicAdd(&s_newcost, (unsigned long long)(ptr[x][v + 1] - ptr[x][v]));
+                            if ((uint32_t)(__ldcg(&info[y][v]) >> 32) == ep) s_meet = 1;
+                        }
+                    }
+                }
+                __syncthreads();
+                // counts of level nl: every edge from level nl-1 into it
+                for (long long q = lo + warp; q < hi; q += nw) {
+                    const int32_t u = queue[x][q];
+                    const unsigned long long su = __ldcg(&sig[x][u]);
+                    for (int64_t e = ptr[x][u] + lane; e < ptr[x][u + 1]; e += 32) {
+                        const int32_t v = adj[x][e];
+                        if (__ldcg(&info[x][v]) == want) {
+                            const unsigned long long o = atomicAdd(&sig[x][v], su);
+                            if (o + su >= (1ull << 53)) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                        }
+                    }
+                }
+                if (a.edges && lane == 0) atomicAdd(&s_edges, ne);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    s_lo[x] = hi;
+                    s_hi[x] = hi + s_new;
+                    s_lev[x] = nl;
+                    s_cost[x] = s_newcost;
+                    s_new = 0;
+                    s_newcost = 0ull;
+                }
+                __syncthreads();
+                if (s_meet) {
+                    met = true;
+                    break;
+                }
+            }
+        }
+        if (!met) {
+            if (threadIdx.x == 0) {
+                a.kind[i] = 2;
+                a.ilen[i] = 0;
+                a.path_off[i] = 0;
+            }
+            continue;
+        }
+        // meeting layer: level s_lev[x] of side x reached by the other side
+        const int y = 1 - x;
+        const long long mlo = s_lo[x], mhi = s_hi[x];
+        unsigned long long part = 0ull;
+        for (long long q = mlo + threadIdx.x; q < mhi; q += kBiBlock) {
+            const int32_t v = queue[x][q];
+            if ((uint32_t)(__ldcg(&info[y][v]) >> 32) == ep) {
+                const unsigned long long p = __ldcg(&sig[0][v]) * __ldcg(&sig[1][v]);
+                if (__umul64hi(__ldcg(&sig[0][v]), __ldcg(&sig[1][v])) != 0ull || p >= (1ull << 53))
+                    atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                part += p;
+            }
+        }
+        const unsigned long long sst = block_sum(part, s_red);
+        const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, 0), (double)sst);
+        // first vertex id T with sum over the layer of sigma_s sigma_t for ids <= T reaching the target
+        int32_t blo = 0, bhi = (int32_t)(n - 1);
+        while (blo < bhi) {
+            const int32_t mid = blo + (bhi - blo) / 2;
+            unsigned long long pm = 0ull;
+            for (long long q = mlo + threadIdx.x; q < mhi; q += kBiBlock) {
+                const int32_t v = queue[x][q];
+                if (v <= mid && (uint32_t)(__ldcg(&info[y][v]) >> 32) == ep)
+                    pm += __ldcg(&sig[0][v]) * __ldcg(&sig[1][v]);
+            }
+            const unsigned long long sm = block_sum(pm, s_red);
+            if ((double)sm >= target) bhi = mid;
+            else blo = mid + 1;
+        }
+        const int32_t vm = blo;
+        if (warp == 0) {
+            const uint32_t la = (uint32_t)(__ldcg(&info[0][vm]) & 0xffffffffu);
+            const uint32_t lb = (uint32_t)(__ldcg(&info[1][vm]) & 0xffffffffu);
+            const int32_t len = (int32_t)(la + lb) - 1;
+            unsigned long long off = 0ull;
+            if (lane == 0) {
+                off = atomicAdd(a.arena_top, (unsigned long long)len);
+                if ((int64_t)(off + len) > a.arena_cap) atomicOr(a.status, DEV_ARENA_OVERFLOW);
+                a.ilen[i] = len;
+                a.path_off[i] = (long long)off;
+            }
+            off = __shfl_sync(0xffffffffu, off, 0);
+            const bool store = (int64_t)(off + len) <= a.arena_cap;
+            int32_t k = 0;
+            if (vm != end[0] && vm != end[1]) {
+                if (lane == 0) {
+                    if (store) a.arena[off] = vm;
+                    atomicAdd(&a.cnt[vm], 1ull);
+                }
+                k = 1;
+            }
+            uint32_t step = 1;
+            for (int z = 0; z < 2; ++z) {
+                // towards s: predecessors over in-edges; towards t: successors over out-edges
+                const int64_t *bp = z == 0 ? a.irp : a.rp;
+                const int32_t *bc = z == 0 ? a.icol : a.col;
+                int32_t w = vm;
+                while (w != end[z]) {
+                    const uint32_t lw = (uint32_t)(__ldcg(&info[z][w]) & 0xffffffffu);
+                    const unsigned long long prev = pack(ep, lw - 1);
+                    const double tg = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step),
+                                                (double)__ldcg(&sig[z][w]));
+                    const int64_t e0 = bp[w], e1 = bp[w + 1];
+                    unsigned long long carry = 0ull;
+                    int32_t pick = -1;
+                    for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
+                        const int64_t e = base + lane;
+                        int32_t pv = -1;
+                        unsigned long long val = 0ull;
+                        if (e < e1) {
+                            pv = bc[e];
+                            if (__ldcg(&info[z][pv]) == prev) val = __ldcg(&sig[z][pv]);
+                        }
+                        unsigned long long cum = val;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const unsigned long long t2 = __shfl_up_sync(0xffffffffu, cum, o);
+                            if (lane >= o) cum += t2;
+                        }
+                        cum += carry;
+                        const unsigned hit = __ballot_sync(0xffffffffu, val > 0ull && (double)cum >= tg);
+                        if (hit) pick = __shfl_sync(0xffffffffu, pv, __ffs(hit) - 1);
+                        carry = __shfl_sync(0xffffffffu, cum, 31);
+                    }
+                    if (pick < 0) {
+                        if (lane == 0) atomicOr(a.status, DEV_BAD_PATH);
+                        break;
+                    }
+                    if (pick != end[z]) {
+                        if (lane == 0) {
+                            if (store && k < len) a.arena[off + k] = pick;
+                            atomicAdd(&a.cnt[pick], 1ull);
+                        }
+                        ++k;
+                    }
+                    w = pick;
+                    ++step;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (a.edges && threadIdx.x == 0 && s_edges) atomicAdd(a.edges, s_edges);
+}
+
+}  // namespace
+
+// All samples of a phase (pairs, kinds already drawn): kinds of unreachable
+// targets, |I|, paths and counts, as the batched form leaves them.
+percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count) {
+    const int64_t n = ctx->n;
+    const size_t per_slot = (size_t)n * 2 * (sizeof(unsigned long long) * 2 + sizeof(int32_t));
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs, kBiBlock, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    // at most 8 GiB of scratch
+    int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, (8ll << 30) / per_slot));
+    slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
+    if (ctx->bi_slots < slots || ctx->bi_n != n) {
+        PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 2 * n * slots, "bidirectional levels"));
+        PERCIS_TRY(ensure(ctx, ctx->bi_sig, sizeof(unsigned long long) * 2 * n * slots, "bidirectional counts"));
+        PERCIS_TRY(ensure(ctx, ctx->bi_queue, sizeof(int32_t) * 2 * n * slots, "bidirectional queues"));
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 2 * n * slots, ctx->stream));
+        ctx->bi_slots = slots;
+        ctx->bi_n = n;
+        ctx->bi_epoch = 0;
+    }
+    if ((uint64_t)ctx->bi_epoch + (uint64_t)count + 2 > 0xffffffffull) {
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 2 * n * ctx->bi_slots,
+                                         ctx->stream));
+        ctx->bi_epoch = 0;
+    }
+    PERCIS_TRY(ensure(ctx, ctx->ms_ctl, sizeof(MsCtl), "ms ctl"));
+    // the status word may be freshly allocated: it must start at zero
+    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ms_ctl.p, 0, sizeof(MsCtl), ctx->stream));
+    PERCIS_TRY(ensure(ctx, ctx->red, 64, "sample counter"));
+    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(unsigned long long), ctx->stream));
+    BiArgs a{};
+    a.n = n;
+    a.rp = ctx->rp.as<int64_t>();
+    a.col = ctx->col.as<int32_t>();
+    a.irp = ctx->directed ? ctx->irp.as<int64_t>() : ctx->rp.as<int64_t>();
+    a.icol = ctx->directed ? ctx->icol.as<int32_t>() : ctx->col.as<int32_t>();
+    a.count = count;
+    a.pair_s = ctx->pair_s.as<int32_t>();
+    a.pair_t = ctx->pair_t.as<int32_t>();
+    a.kind = ctx->kind.as<int32_t>();
+    a.ilen = ctx->ilen.as<int32_t>();
+    a.path_off = ctx->path_off.as<long long>();
+    a.arena = ctx->arena.as<int32_t>();
+    a.arena_top = ctx->arena_top.as<unsigned long long>();
+    a.arena_cap = ctx->arena_cap;
+    a.cnt = ctx->cnt.as<unsigned long long>();
+    a.seed = seed;
+    a.tag = tag_path;
+    a.epoch_base = (uint32_t)ctx->bi_epoch;
+    ctx->bi_epoch += count + 1;
+    a.info = ctx->bi_info.as<unsigned long long>();
+    a.sig = ctx->bi_sig.as<unsigned long long>();
+    a.queue = ctx->bi_queue.as<int32_t>();
+    a.slots = (int32_t)ctx->bi_slots;
+    a.next = ctx->red.as<unsigned long long>();
+    a.status = &ctx->ms_ctl.as<MsCtl>()->status;
+    a.edges = ctx->opt.instrument ? ctx->counters.as<unsigned long long>() + 4 : nullptr;
+    k_bibfs<<<(int)ctx->bi_slots, kBiBlock, 0, ctx->stream>>>(a);
+    PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS");
+    return PERCIS_OK;
+}
+
+}  // namespace percis

@@ -87,6 +87,8 @@ struct percis_ctx {
     percis::DevBuf fq0, fq1, qstamp;  // frontier queues and per-vertex level stamps
     percis::DevBuf acc_ap, ap_tau, ap_stamp, ap_list;  // all-paths estimator
     percis::DevBuf plan_dev;                           // lane batches of a many-graph phase
+    percis::DevBuf bi_info, bi_sig, bi_queue;          // bidirectional form: per-slot scratch
+    int64_t bi_slots = 0, bi_n = 0, bi_epoch = 0;
     int64_t ap_warps = 0, ap_n = 0;
     int32_t ap_epoch = 0;
     int32_t stamp_base = 1;
@@ -168,6 +170,9 @@ percis_status plain_backtrack(percis_ctx *ctx, uint64_t seed, uint32_t tag, int6
 percis_status plain_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count);
 percis_status plain_dist_sigma(percis_ctx *ctx, int32_t *dist, double *sigma);
 percis_status vertex_diam_ub(percis_ctx *ctx, int64_t *D);
+
+// bibfs.cu
+percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count);
 
 // msbfs.cu
 percis_status batched_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count, int64_t n_sources,

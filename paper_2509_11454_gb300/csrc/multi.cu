@@ -346,7 +346,7 @@ extern "C" percis_status percis_estimate_graphs(percis_ctx *ctx, double eps, dou
     PERCIS_TRY(need_multi(ctx, true));
     if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0) || !pc_out)
         return set_err(ctx, PERCIS_E_INVALID, "eps and delta must lie in (0,1); pc_out must be non-NULL");
-    if (ctx->opt.form == PERCIS_FORM_PLAIN)
+    if (ctx->opt.form != PERCIS_FORM_BATCHED)
         return set_err(ctx, PERCIS_E_INVALID, "many graphs run in the batched form");
     MultiGraph *m = ctx->multi;
     const int32_t G = m->G;

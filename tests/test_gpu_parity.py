@@ -135,7 +135,8 @@ def test_msbfs_bitexact(binding, gcase, nsrc, direction):
     eng.close()
 
 
-@pytest.mark.parametrize("form,direction", [("batched", 0), ("batched", 1), ("batched", 2), ("plain", 2)])
+@pytest.mark.parametrize("form,direction", [("batched", 0), ("batched", 1), ("batched", 2), ("plain", 2),
+                                            ("bidir", 2)])
 def test_phase_bitexact(binding, gcase, form, direction):
     name, g, og = gcase
     x = _states(name, g.n)
@@ -143,7 +144,7 @@ def test_phase_bitexact(binding, gcase, form, direction):
     eng = _engine(binding, g, x, form=form, direction=direction)
     prep = oracle.prepare(x)
     got = eng.run_phase(seed=11, phase=1, count=count)
-    ph = oracle.run_samples(og, prep, 11, 1, 3, 0, count, keep_paths=True)
+    ph = oracle.run_samples(og, prep, 11, 1, 3, 0, count, keep_paths=True, bidir=form == "bidir")
     assert np.array_equal(_np(got["s"]), ph.s)
     assert np.array_equal(_np(got["t"]), ph.t)
     assert np.array_equal(_np(got["kind"]), ph.kind)
@@ -204,6 +205,51 @@ def test_allpaths_estimate_matches_oracle(binding, name):
     assert tot == pytest.approx(float(res.phase2.ilen.sum()), rel=1e-10)
     with pytest.raises(binding.PercisError):
         eng.backward(torch.ones(g.n, dtype=torch.float64, device="cuda"))
+    eng.close()
+
+
+@pytest.mark.parametrize("name", ["er1000", "ba3000", "rmat12", "grid30"])
+def test_bidir_estimate_matches_oracle(binding, name):
+    """The bidirectional form through Algorithm 1: l, rho~ and the estimate
+    as the oracle's bidirectional replica computes them; its backward equals
+    the oracle's VJP on the same sample."""
+    g = GRAPHS[name]()
+    og = oracle.from_synth(g)
+    x = _states(name, g.n)
+    eng = _engine(binding, g, x, form="bidir")
+    pc, info = eng.estimate(0.05, 0.1, seed=6)
+    res = oracle.percis(og, x, 0.05, 0.1, 6, keep_paths=True, bidir=True)
+    assert info["rho_tilde"] == res.rho_tilde
+    assert abs(info["ell"] - res.ell) <= 1
+    if info["ell"] != res.ell:
+        res = oracle.percis(og, x, 0.05, 0.1, 6, ell=info["ell"], keep_paths=True, bidir=True)
+    assert np.max(np.abs(_np(pc) - res.pc)) <= 1e-9
+    prep = oracle.prepare(x, cv_method="sorted")
+    gvec = np.random.default_rng(4).standard_normal(g.n)
+    gx = _np(eng.backward(torch.as_tensor(gvec, device="cuda")))
+    F = prep.lam * res.phase2.cnt / info["ell"]
+    ref = oracle.vjp_fixed(prep, info["ell"], res.phase2, F, gvec)
+    assert np.linalg.norm(gx - ref) <= 1e-10 * np.linalg.norm(ref)
+    eng.close()
+
+
+@pytest.mark.slow
+def test_bidir_full_size_outbreak_sampled(binding):
+    """BA n=100,000 outbreak, eps=0.005, bidirectional form: every phase-2
+    pair, sampled paths against the oracle one by one, estimate = lambda cnt / l."""
+    g, x, eps, delta = synth.workload("ba100k_outbreak")
+    og = oracle.from_synth(g)
+    eng = _engine(binding, g, x, form="bidir")
+    pc, info = eng.estimate(eps, delta, seed=0)
+    ell = info["ell"]
+    prep = oracle.prepare(x)
+    ptr, nodes = eng.get_paths(ell)
+    ptr, nodes = _np(ptr), _np(nodes)
+    cnt = np.bincount(nodes, minlength=g.n)
+    assert np.max(np.abs(_np(pc) - prep.lam * cnt / ell)) <= 1e-12
+    for i in np.random.default_rng(0).choice(ell, 40, replace=False):
+        ph = oracle.run_samples(og, prep, 0, 1, 3, int(i), 1, keep_paths=True, bidir=True)
+        assert np.array_equal(nodes[ptr[i]:ptr[i + 1]], ph.path_nodes), i
     eng.close()
 
 
