@@ -43,9 +43,10 @@ WORKLOAD_DESC = {
 }
 # DRAM traffic of one batched sigma-BFS launch from an ncu capture, valid only
 # for the kernel source it was taken on (sha256 of csrc/msbfs.cu).
-NCU_TRAFFIC = {"msbfs_sha256": "ca2e6806ea9f3f5243f765b02c21eecae307c332c69e267183886b9109460557",
+NCU_TRAFFIC = {"sha256": "ca2e6806ea9f3f5243f765b02c21eecae307c332c69e267183886b9109460557",
                # DRAM read + write of one phase-2 launch (20 batches) / 20: bytes per batch of lanes
                "bytes_per_launch": (10704329000 + 6086044000) / 20}  # the ncu capture summarised under profiles/
+NCU_TRAFFIC_BIDIR = {"sha256": None, "bytes_per_launch": None}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
 
@@ -209,6 +210,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-pairs", type=int, default=300)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/differentiated/e2e/cpu legs")
+    ap.add_argument("--form", default="bidir", choices=["bidir", "batched"],
+                    help="form of the timed step: bidirectional BFS per sample, or the batched multi-source BFS")
     ap.add_argument("--lanes", type=int, default=0, help="batched lane width (0 = library default)")
     ap.add_argument("--lane-order", type=int, default=-1, help="0 = by vertex id, 1 = by hub neighbour")
     ap.add_argument("--direction", type=int, default=-1, help="0 = pull, 1 = push, 2 = by work estimate")
@@ -237,6 +240,7 @@ def main():
     stream = torch.cuda.Stream(device=local)
     torch.cuda.set_stream(stream)
     eng = binding.PercIS(local)
+    eng.set_options(form=args.form)
     if args.lanes:
         eng.set_options(lanes=args.lanes)
     if args.lane_order >= 0:
@@ -289,35 +293,47 @@ def main():
     if rank == 0:
         peaks, peak_kind = _peaks()
         # algorithmic work of the same estimates, counted in an untimed instrumented replay
-        eng.set_options(instrument=1)
-        work = np.zeros((2, 8))
-        for k in range(args.steps):
-            inf = step(seed_base + k)
-            work += np.array(inf["work"], dtype=np.float64)
-        eng.set_options(instrument=0)
+        # (the batched replay also gives the one-sided BFS edges of the same pairs, for GTEPS)
+        def replay(form):
+            eng.set_options(instrument=1, form=form)
+            work = np.zeros((2, 8))
+            for k in range(args.steps):
+                inf = step(seed_base + k)
+                work += np.array(inf["work"], dtype=np.float64)
+            eng.set_options(instrument=0, form=args.form)
+            return work.sum(axis=0)
+
+        w = replay(args.form)
+        wb = w if args.form == "batched" else replay("batched")
         bfs_ms = sum(sum(i["bfs_ms"]) for i in infos)
         bfs_launches = sum(sum(i["bfs_launches"]) for i in infos)
-        w = work.sum(axis=0)
-        algo_bytes = 8.0 * w[0] + 8.0 * w[1] + 8.0 * w[2] + 4.0 * w[3]
+        if args.form == "batched":
+            kernel, src_name, ncu = ("k_msbfs (batched sigma-BFS + backtrack; one persistent launch per phase, "
+                                     "figures per batch of W lanes)", "msbfs.cu", NCU_TRAFFIC)
+            algo_bytes = 8.0 * w[0] + 8.0 * w[1] + 8.0 * w[2] + 4.0 * w[3]
+            work_step = {"sigma_dag_reads": w[0], "sigma_writes": w[1], "union_frontier_rows": w[2],
+                         "union_frontier_edges": w[3], "truncated_bfs_edges": w[4], "bfs_samples": w[6]}
+        else:
+            kernel, src_name, ncu = ("k_bibfs (bidirectional sigma-BFS + backtrack, one block per sample; "
+                                     "one launch per phase)", "bibfs.cu", NCU_TRAFFIC_BIDIR)
+            # per edge scanned: column 4 B + level word 8 B; per count addition 8 B; per vertex reached:
+            # claim 8 B, queue 4 B, count read, write and clear 3 x 8 B
+            algo_bytes = 12.0 * w[0] + 8.0 * w[1] + 36.0 * w[2]
+            work_step = {"edges_scanned": w[0], "count_additions": w[1], "vertices_reached": w[2],
+                         "bfs_samples": w[3], "one_sided_bfs_edges": wb[4]}
         per_launch_bytes = algo_bytes / max(bfs_launches, 1)
         per_launch_s = bfs_ms / 1000.0 / max(bfs_launches, 1)
         achieved = per_launch_bytes / per_launch_s / 1e9
         traffic = None
-        msbfs_src = os.path.join(ROOT, "paper_2509_11454_gb300", "csrc", "msbfs.cu")
-        if NCU_TRAFFIC["msbfs_sha256"] == _sha(msbfs_src):
-            traffic = NCU_TRAFFIC["bytes_per_launch"]
+        if ncu["sha256"] == _sha(os.path.join(ROOT, "paper_2509_11454_gb300", "csrc", src_name)):
+            traffic = ncu["bytes_per_launch"]
         extras["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                              "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                              "kernel": "k_msbfs (batched sigma-BFS + backtrack; one persistent launch per phase, "
-                                        "figures per batch of W lanes)",
+                              "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
                               "peak_source": f"{peak_kind} HBM copy bandwidth",
                               "algorithmic_bytes_per_launch": per_launch_bytes,
                               "avg_launch_ms": per_launch_s * 1000.0, "launches_per_step": bfs_launches / len(infos)}
-        extras["gteps"] = w[4] / t_total / 1e9 if w[4] else None
-        extras["work_per_step"] = {"sigma_dag_reads": w[0] / len(infos), "sigma_writes": w[1] / len(infos),
-                                   "union_frontier_rows": w[2] / len(infos),
-                                   "union_frontier_edges": w[3] / len(infos),
-                                   "truncated_bfs_edges": w[4] / len(infos), "bfs_samples": w[6] / len(infos)}
+        extras["gteps"] = wb[4] / t_total / 1e9 if wb[4] else None
+        extras["work_per_step"] = {k: v / len(infos) for k, v in work_step.items()}
         extras["bfs_share_of_step"] = bfs_ms / sum(times)
 
         if not args.no_extras:
@@ -334,7 +350,27 @@ def main():
             eng.set_options(form="batched")
             extras["plain"] = {"value": (inf_p["ell1"] + inf_p["ell"]) / t_p, "unit": "pairs/s",
                                "ms_per_step": t_p * 1000.0, "steps": 1}
-            extras["batched_over_plain"] = value / world / extras["plain"]["value"]
+
+            # the other sampling form on the same seeds
+            other = "batched" if args.form == "bidir" else "bidir"
+            eng.set_options(form=other)
+            to, po = [], 0
+            for k in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                inf = step(seed_base + k)
+                e1.record(stream)
+                e1.synchronize()
+                to.append(e0.elapsed_time(e1) / 1000.0)
+                po += inf["ell1"] + inf["ell"]
+            eng.set_options(form=args.form)
+            extras["batched" if other == "batched" else "bidirectional"] = {
+                "value": po / sum(to), "unit": "pairs/s", "ms_per_step": 1000.0 * sum(to) / len(to)}
+            b_val = value / world if args.form == "batched" else extras["batched"]["value"]
+            extras["batched_over_plain"] = b_val / extras["plain"]["value"]
+            extras["headline_over_plain"] = value / world / extras["plain"]["value"]
 
             # differentiated form: forward + backward (dPC/dx) per step
             gvec = torch.randn(g.n, dtype=torch.float64, device="cuda")
@@ -397,7 +433,9 @@ def main():
     if rank == 0:
         i0 = infos[0]
         cfg = dict(WORKLOAD_DESC)
-        cfg.update({"n": g.n, "nnz": g.nnz, "form": "batched", "lanes": i0["lanes"],
+        cfg.update({"n": g.n, "nnz": g.nnz,
+                    "form": {"bidir": "bidirectional BFS per sample", "batched": "batched multi-source BFS"}[args.form],
+                    "lanes": i0["lanes"],
                     "lane_order": ["vertex id", "hub neighbour"][eng.options.lane_order],
                     "direction": ["pull", "push", "per level by work estimate"][eng.options.direction],
                     "push_alpha": eng.options.push_alpha or 0.5,

@@ -119,7 +119,11 @@ typedef struct {
      *            settle t (whole reachable set when t is unreachable)
      * work[p][5] levels run, summed over launches
      * work[p][6] sampled pairs that reached a BFS (R(x_s - x_t) > 0)
-     * work[p][7] reserved */
+     * work[p][7] reserved
+     * Bidirectional form instead: [0] edges scanned by both sides, [1] count
+     * additions (edges into a new level), [2] vertices reached by both
+     * sides, [3] samples traversed; the rest 0.  bfs_launches is then the
+     * number of bidirectional launches (one per phase). */
     int64_t work[2][8];
 } percis_info;
 

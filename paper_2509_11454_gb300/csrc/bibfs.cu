@@ -16,8 +16,10 @@
 // Samples are independent, so blocks take them from a shared counter and
 // never wait on one another.  Each block owns a slot of scratch arrays
 // (level + epoch word, count and queue per vertex and side); a vertex belongs
-// to the current sample only while its word carries the sample's epoch, so the
-// arrays are never cleared between samples.
+// to the current sample only while its word carries the sample's epoch, so
+// the level words are never cleared, and each sample zeroes the counts of the
+// vertices it reached (its queues list them), so a level's claims and count
+// additions go in one pass over its edges.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,7 +31,17 @@ namespace percis {
 
 namespace {
 
-constexpr int kBiBlock = 256;
+#ifndef PERCIS_BI_BLOCK
+#define PERCIS_BI_BLOCK 128
+#endif
+constexpr int kBiBlock = PERCIS_BI_BLOCK;
+#ifndef PERCIS_MEET_CAP
+#define PERCIS_MEET_CAP 256
+#endif
+constexpr int kMeetCap = PERCIS_MEET_CAP;  // meeting-layer members kept in shared memory
+#ifndef PERCIS_BI_MINB
+#define PERCIS_BI_MINB 12
+#endif
 
 struct BiArgs {
     int64_t n;
@@ -52,7 +64,8 @@ struct BiArgs {
     int32_t slots;
     unsigned long long *next;   // next sample to take
     uint32_t *status;
-    unsigned long long *edges;  // optional: edges scanned (both sides)
+    unsigned long long *work;   // optional work counters: [0] edges scanned, [1] count additions,
+                                // [2] vertices reached (both sides), [3] samples traversed
 };
 
 __device__ __forceinline__ unsigned long long pack(uint32_t ep, uint32_t lev) {
@@ -72,16 +85,15 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
     return t;
 }
 
-__global__ void __launch_bounds__(kBiBlock) k_bibfs(BiArgs a) {
+__global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nw = kBiBlock / 32;
     const int64_t n = a.n;
     const size_t slot = blockIdx.x;
-    unsigned long long *info[2] = {a.info + (slot * 2) * n, a.info + (slot * 2 + 1) * n};
-    unsigned long long *sig[2] = {a.sig + (slot * 2) * n, a.sig + (slot * 2 + 1) * n};
-    int32_t *queue[2] = {a.queue + (slot * 2) * n, a.queue + (slot * 2 + 1) * n};
-    const int64_t *ptr[2] = {a.rp, a.irp};  // expansion: forward over out-edges, backward over in-edges
-    const int32_t *adj[2] = {a.col, a.icol};
+    // side 0 = forward from s over out-edges, side 1 = backward from t over in-edges
+    unsigned long long *const info0 = a.info + (slot * 2) * n, *const info1 = info0 + n;
+    unsigned long long *const sig0 = a.sig + (slot * 2) * n, *const sig1 = sig0 + n;
+    int32_t *const queue0 = a.queue + (slot * 2) * n, *const queue1 = queue0 + n;
 
     __shared__ long long s_i;
     __shared__ long long s_lo[2], s_hi[2];
@@ -89,8 +101,13 @@ __global__ void __launch_bounds__(kBiBlock) k_bibfs(BiArgs a) {
     __shared__ unsigned long long s_cost[2], s_newcost;
     __shared__ int s_new, s_meet;
     __shared__ unsigned long long s_red[nw];
-    __shared__ unsigned long long s_edges;
-    if (threadIdx.x == 0) s_edges = 0ull;
+    __shared__ int s_nm;
+    __shared__ int32_t s_mv[kMeetCap];
+    __shared__ unsigned long long s_mw[kMeetCap];
+    __shared__ int32_t s_best[nw];
+    __shared__ unsigned long long s_work[4];
+    if (threadIdx.x < 4) s_work[threadIdx.x] = 0ull;
+    unsigned long long n_add = 0ull;
 
     for (;;) {
         __syncthreads();
@@ -105,17 +122,21 @@ __global__ void __launch_bounds__(kBiBlock) k_bibfs(BiArgs a) {
             }
             continue;
         }
-        const int32_t end[2] = {a.pair_s[i], a.pair_t[i]};
+        const int32_t s = a.pair_s[i], t = a.pair_t[i];
         const uint32_t ep = a.epoch_base + (uint32_t)i + 1u;
         if (threadIdx.x == 0) {
+            info0[s] = pack(ep, 0);
+            sig0[s] = 1ull;
+            queue0[0] = s;
+            info1[t] = pack(ep, 0);
+            sig1[t] = 1ull;
+            queue1[0] = t;
+            s_cost[0] = (unsigned long long)(a.rp[s + 1] - a.rp[s]);
+            s_cost[1] = (unsigned long long)(a.irp[t + 1] - a.irp[t]);
             for (int x = 0; x < 2; ++x) {
-                info[x][end[x]] = pack(ep, 0);
-                sig[x][end[x]] = 1ull;
-                queue[x][0] = end[x];
                 s_lo[x] = 0;
                 s_hi[x] = 1;
                 s_lev[x] = 0;
-                s_cost[x] = (unsigned long long)(ptr[x][end[x] + 1] - ptr[x][end[x]]);
             }
             s_new = 0;
             s_newcost = 0ull;
@@ -123,47 +144,53 @@ __global__ void __launch_bounds__(kBiBlock) k_bibfs(BiArgs a) {
         }
         __syncthreads();
         int x = 0;
-        bool met = end[0] != end[1];
+        bool met = s != t;
         if (met) {
             met = false;
             for (;;) {
                 if (s_hi[0] == s_lo[0] || s_hi[1] == s_lo[1]) break;  // a side ran dry: t unreachable
                 x = s_cost[0] <= s_cost[1] ? 0 : 1;
-                const int y = 1 - x;
                 const long long lo = s_lo[x], hi = s_hi[x];
                 const uint32_t nl = s_lev[x] + 1;
                 const unsigned long long want = pack(ep, nl);
                 unsigned long long ne = 0ull;
-                // claim level nl
+                // level nl: claim unreached neighbours and add the counts over
+                // every edge into the level in one pass (counts of unreached
+                // vertices are zero: each sample clears the ones it touched)
+                unsigned long long *infx = x ? info1 : info0;
+                unsigned long long *sigx = x ? sig1 : sig0;
+                const unsigned long long *infy = x ? info0 : info1;
+                int32_t *qx = x ? queue1 : queue0;
+                const int64_t *px = x ? a.irp : a.rp;
+                const int32_t *ax = x ? a.icol : a.col;
                 for (long long q = lo + warp; q < hi; q += nw) {
-                    const int32_t u = queue[x][q];
-                    const int64_t e0 = ptr[x][u], e1 = ptr[x][u + 1];
+                    const int32_t u = qx[q];
+                    const unsigned long long su = __ldcg(&sigx[u]);
+                    const int64_t e0 = px[u], e1 = px[u + 1];
                     ne += (unsigned long long)(e1 - e0);
                     for (int64_t e = e0 + lane; e < e1; e += 32) {
-                        const int32_t v = adj[x][e];
-                        const unsigned long long old = __ldcg(&info[x][v]);
-                        if ((uint32_t)(old >> 32) != ep && atomicCAS(&info[x][v], old, want) == old) {
-                            sig[x][v] = 0ull;
-                            queue[x][hi + atomicAdd(&s_new, 1)] = v;
-                            atomicAdd(&s_newcost, (unsigned long long)(ptr[x][v + 1] - ptr[x][v]));
-                            if ((uint32_t)(__ldcg(&info[y][v]) >> 32) == ep) s_meet = 1;
+                        const int32_t v = ax[e];
+                        const unsigned long long old = __ldcg(&infx[v]);
+                        bool at = old == want;
+                        if ((uint32_t)(old >> 32) != ep) {
+                            const unsigned long long prev = atomicCAS(&infx[v], old, want);
+                            if (prev == old) {
+                                at = true;
+                                qx[hi + atomicAdd(&s_new, 1)] = v;
+                                atomicAdd(&s_newcost, (unsigned long long)(px[v + 1] - px[v]));
+                                if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) s_meet = 1;
+                            } else {
+                                at = prev == want;  // claimed in this level by another thread
+                            }
                         }
-                    }
-                }
-                __syncthreads();
-                // counts of level nl: every edge from level nl-1 into it
-                for (long long q = lo + warp; q < hi; q += nw) {
-                    const int32_t u = queue[x][q];
-                    const unsigned long long su = __ldcg(&sig[x][u]);
-                    for (int64_t e = ptr[x][u] + lane; e < ptr[x][u + 1]; e += 32) {
-                        const int32_t v = adj[x][e];
-                        if (__ldcg(&info[x][v]) == want) {
-                            const unsigned long long o = atomicAdd(&sig[x][v], su);
+                        if (at) {
+                            if (a.work) ++n_add;
+                            const unsigned long long o = atomicAdd(&sigx[v], su);
                             if (o + su >= (1ull << 53)) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
                         }
                     }
                 }
-                if (a.edges && lane == 0) atomicAdd(&s_edges, ne);
+                if (a.work && lane == 0) atomicAdd(&s_work[0], ne);
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     s_lo[x] = hi;
@@ -186,111 +213,161 @@ __global__ void __launch_bounds__(kBiBlock) k_bibfs(BiArgs a) {
                 a.ilen[i] = 0;
                 a.path_off[i] = 0;
             }
-            continue;
-        }
-        // meeting layer: level s_lev[x] of side x reached by the other side
-        const int y = 1 - x;
-        const long long mlo = s_lo[x], mhi = s_hi[x];
-        unsigned long long part = 0ull;
-        for (long long q = mlo + threadIdx.x; q < mhi; q += kBiBlock) {
-            const int32_t v = queue[x][q];
-            if ((uint32_t)(__ldcg(&info[y][v]) >> 32) == ep) {
-                const unsigned long long p = __ldcg(&sig[0][v]) * __ldcg(&sig[1][v]);
-                if (__umul64hi(__ldcg(&sig[0][v]), __ldcg(&sig[1][v])) != 0ull || p >= (1ull << 53))
-                    atomicOr(a.status, DEV_SIGMA_OVERFLOW);
-                part += p;
-            }
-        }
-        const unsigned long long sst = block_sum(part, s_red);
-        const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, 0), (double)sst);
-        // first vertex id T with sum over the layer of sigma_s sigma_t for ids <= T reaching the target
-        int32_t blo = 0, bhi = (int32_t)(n - 1);
-        while (blo < bhi) {
-            const int32_t mid = blo + (bhi - blo) / 2;
-            unsigned long long pm = 0ull;
+        } else {
+            // meeting layer: level s_lev[x] of side x reached by the other side
+            const unsigned long long *infy = x ? info0 : info1;
+            const int32_t *qx = x ? queue1 : queue0;
+            const long long mlo = s_lo[x], mhi = s_hi[x];
+            // the layer's members with their weights sigma_s sigma_t, kept in
+            // shared memory when they fit
+            if (threadIdx.x == 0) s_nm = 0;
+            __syncthreads();
+            unsigned long long part = 0ull;
             for (long long q = mlo + threadIdx.x; q < mhi; q += kBiBlock) {
-                const int32_t v = queue[x][q];
-                if (v <= mid && (uint32_t)(__ldcg(&info[y][v]) >> 32) == ep)
-                    pm += __ldcg(&sig[0][v]) * __ldcg(&sig[1][v]);
-            }
-            const unsigned long long sm = block_sum(pm, s_red);
-            if ((double)sm >= target) bhi = mid;
-            else blo = mid + 1;
-        }
-        const int32_t vm = blo;
-        if (warp == 0) {
-            const uint32_t la = (uint32_t)(__ldcg(&info[0][vm]) & 0xffffffffu);
-            const uint32_t lb = (uint32_t)(__ldcg(&info[1][vm]) & 0xffffffffu);
-            const int32_t len = (int32_t)(la + lb) - 1;
-            unsigned long long off = 0ull;
-            if (lane == 0) {
-                off = atomicAdd(a.arena_top, (unsigned long long)len);
-                if ((int64_t)(off + len) > a.arena_cap) atomicOr(a.status, DEV_ARENA_OVERFLOW);
-                a.ilen[i] = len;
-                a.path_off[i] = (long long)off;
-            }
-            off = __shfl_sync(0xffffffffu, off, 0);
-            const bool store = (int64_t)(off + len) <= a.arena_cap;
-            int32_t k = 0;
-            if (vm != end[0] && vm != end[1]) {
-                if (lane == 0) {
-                    if (store) a.arena[off] = vm;
-                    atomicAdd(&a.cnt[vm], 1ull);
+                const int32_t v = qx[q];
+                if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) {
+                    const unsigned long long a0 = __ldcg(&sig0[v]), a1 = __ldcg(&sig1[v]);
+                    const unsigned long long p = a0 * a1;
+                    if (__umul64hi(a0, a1) != 0ull || p >= (1ull << 53)) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                    part += p;
+                    const int slot_m = atomicAdd(&s_nm, 1);
+                    if (slot_m < kMeetCap) {
+                        s_mv[slot_m] = v;
+                        s_mw[slot_m] = p;
+                    }
                 }
-                k = 1;
             }
-            uint32_t step = 1;
-            for (int z = 0; z < 2; ++z) {
-                // towards s: predecessors over in-edges; towards t: successors over out-edges
-                const int64_t *bp = z == 0 ? a.irp : a.rp;
-                const int32_t *bc = z == 0 ? a.icol : a.col;
-                int32_t w = vm;
-                while (w != end[z]) {
-                    const uint32_t lw = (uint32_t)(__ldcg(&info[z][w]) & 0xffffffffu);
-                    const unsigned long long prev = pack(ep, lw - 1);
-                    const double tg = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step),
-                                                (double)__ldcg(&sig[z][w]));
-                    const int64_t e0 = bp[w], e1 = bp[w + 1];
-                    unsigned long long carry = 0ull;
-                    int32_t pick = -1;
-                    for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
-                        const int64_t e = base + lane;
-                        int32_t pv = -1;
-                        unsigned long long val = 0ull;
-                        if (e < e1) {
-                            pv = bc[e];
-                            if (__ldcg(&info[z][pv]) == prev) val = __ldcg(&sig[z][pv]);
-                        }
-                        unsigned long long cum = val;
+            const unsigned long long sst = block_sum(part, s_red);
+            const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, 0), (double)sst);
+            const int nm = s_nm;
+            if (a.work && threadIdx.x == 0 && nm > kMeetCap) s_work[3] += 1ull << 32;  // large layers (high word)
+            int32_t vm;
+            if (nm <= kMeetCap) {
+                // member j qualifies when the weights of the members with ids <= its
+                // own reach the target; the meeting vertex is the smallest such id
+                int32_t best = 0x7fffffff;
+                for (int j = threadIdx.x; j < nm; j += kBiBlock) {
+                    const int32_t vj = s_mv[j];
+                    unsigned long long pre = 0ull;
+                    for (int k2 = 0; k2 < nm; ++k2)
+                        if (s_mv[k2] <= vj) pre += s_mw[k2];
+                    if ((double)pre >= target) best = min(best, vj);
+                }
 #pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const unsigned long long t2 = __shfl_up_sync(0xffffffffu, cum, o);
-                            if (lane >= o) cum += t2;
+                for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
+                __syncthreads();
+                if (lane == 0) s_best[warp] = best;
+                __syncthreads();
+                vm = s_best[0];
+                for (int q = 1; q < nw; ++q) vm = min(vm, s_best[q]);
+            } else {
+                // a large layer: the first vertex id T whose layer prefix sum
+                // reaches the target, by bisection over the ids
+                int32_t blo = 0, bhi = (int32_t)(n - 1);
+                while (blo < bhi) {
+                    const int32_t mid = blo + (bhi - blo) / 2;
+                    unsigned long long pm = 0ull;
+                    for (long long q = mlo + threadIdx.x; q < mhi; q += kBiBlock) {
+                        const int32_t v = qx[q];
+                        if (v <= mid && (uint32_t)(__ldcg(&infy[v]) >> 32) == ep)
+                            pm += __ldcg(&sig0[v]) * __ldcg(&sig1[v]);
+                    }
+                    const unsigned long long sm = block_sum(pm, s_red);
+                    if ((double)sm >= target) bhi = mid;
+                    else blo = mid + 1;
+                }
+                vm = blo;
+            }
+            if (warp == 0) {
+                const uint32_t la = (uint32_t)(__ldcg(&info0[vm]) & 0xffffffffu);
+                const uint32_t lb = (uint32_t)(__ldcg(&info1[vm]) & 0xffffffffu);
+                const int32_t len = (int32_t)(la + lb) - 1;
+                unsigned long long off = 0ull;
+                if (lane == 0) {
+                    off = atomicAdd(a.arena_top, (unsigned long long)len);
+                    if ((int64_t)(off + len) > a.arena_cap) atomicOr(a.status, DEV_ARENA_OVERFLOW);
+                    a.ilen[i] = len;
+                    a.path_off[i] = (long long)off;
+                }
+                off = __shfl_sync(0xffffffffu, off, 0);
+                const bool store = (int64_t)(off + len) <= a.arena_cap;
+                int32_t k = 0;
+                if (vm != s && vm != t) {
+                    if (lane == 0) {
+                        if (store) a.arena[off] = vm;
+                        atomicAdd(&a.cnt[vm], 1ull);
+                    }
+                    k = 1;
+                }
+                uint32_t step = 1;
+                for (int z = 0; z < 2; ++z) {
+                    // towards s: predecessors over in-edges; towards t: successors over out-edges
+                    const int64_t *bp = z == 0 ? a.irp : a.rp;
+                    const int32_t *bc = z == 0 ? a.icol : a.col;
+                    const unsigned long long *infz = z == 0 ? info0 : info1;
+                    const unsigned long long *sigz = z == 0 ? sig0 : sig1;
+                    const int32_t endz = z == 0 ? s : t;
+                    int32_t w = vm;
+                    while (w != endz) {
+                        const uint32_t lw = (uint32_t)(__ldcg(&infz[w]) & 0xffffffffu);
+                        const unsigned long long prev = pack(ep, lw - 1);
+                        const double tg = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step),
+                                                    (double)__ldcg(&sigz[w]));
+                        const int64_t e0 = bp[w], e1 = bp[w + 1];
+                        unsigned long long carry = 0ull;
+                        int32_t pick = -1;
+                        for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
+                            const int64_t e = base + lane;
+                            int32_t pv = -1;
+                            unsigned long long val = 0ull;
+                            if (e < e1) {
+                                pv = bc[e];
+                                if (__ldcg(&infz[pv]) == prev) val = __ldcg(&sigz[pv]);
+                            }
+                            unsigned long long cum = val;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const unsigned long long t2 = __shfl_up_sync(0xffffffffu, cum, o);
+                                if (lane >= o) cum += t2;
+                            }
+                            cum += carry;
+                            const unsigned hit = __ballot_sync(0xffffffffu, val > 0ull && (double)cum >= tg);
+                            if (hit) pick = __shfl_sync(0xffffffffu, pv, __ffs(hit) - 1);
+                            carry = __shfl_sync(0xffffffffu, cum, 31);
                         }
-                        cum += carry;
-                        const unsigned hit = __ballot_sync(0xffffffffu, val > 0ull && (double)cum >= tg);
-                        if (hit) pick = __shfl_sync(0xffffffffu, pv, __ffs(hit) - 1);
-                        carry = __shfl_sync(0xffffffffu, cum, 31);
-                    }
-                    if (pick < 0) {
-                        if (lane == 0) atomicOr(a.status, DEV_BAD_PATH);
-                        break;
-                    }
-                    if (pick != end[z]) {
-                        if (lane == 0) {
-                            if (store && k < len) a.arena[off + k] = pick;
-                            atomicAdd(&a.cnt[pick], 1ull);
+                        if (pick < 0) {
+                            if (lane == 0) atomicOr(a.status, DEV_BAD_PATH);
+                            break;
                         }
-                        ++k;
+                        if (pick != endz) {
+                            if (lane == 0) {
+                                if (store && k < len) a.arena[off + k] = pick;
+                                atomicAdd(&a.cnt[pick], 1ull);
+                            }
+                            ++k;
+                        }
+                        w = pick;
+                        ++step;
                     }
-                    w = pick;
-                    ++step;
                 }
             }
         }
+        // clear the counts this sample touched (every vertex either side reached)
+        __syncthreads();
+        if (a.work && threadIdx.x == 0) {
+            s_work[2] += (unsigned long long)(s_hi[0] + s_hi[1]);
+            s_work[3] += 1ull;
+        }
+        for (long long q = threadIdx.x; q < s_hi[0]; q += kBiBlock) sig0[queue0[q]] = 0ull;
+        for (long long q = threadIdx.x; q < s_hi[1]; q += kBiBlock) sig1[queue1[q]] = 0ull;
+    }
+    if (a.work) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) n_add += __shfl_xor_sync(0xffffffffu, n_add, off);
+        if (lane == 0 && n_add) atomicAdd(&s_work[1], n_add);
     }
     __syncthreads();
-    if (a.edges && threadIdx.x == 0 && s_edges) atomicAdd(a.edges, s_edges);
+    if (a.work && threadIdx.x < 4 && s_work[threadIdx.x]) atomicAdd(&a.work[threadIdx.x], s_work[threadIdx.x]);
 }
 
 }  // namespace
@@ -305,14 +382,16 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs, kBiBlock, 0) != cudaSuccess || per_sm < 1)
             per_sm = 1;
     }
-    // at most 8 GiB of scratch
-    int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, (8ll << 30) / per_slot));
+    // at most 16 GiB of scratch
+    int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, (16ll << 30) / per_slot));
     slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
     if (ctx->bi_slots < slots || ctx->bi_n != n) {
         PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 2 * n * slots, "bidirectional levels"));
         PERCIS_TRY(ensure(ctx, ctx->bi_sig, sizeof(unsigned long long) * 2 * n * slots, "bidirectional counts"));
         PERCIS_TRY(ensure(ctx, ctx->bi_queue, sizeof(int32_t) * 2 * n * slots, "bidirectional queues"));
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 2 * n * slots, ctx->stream));
+        // counts start at zero; every sample clears the ones it touched
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_sig.p, 0, sizeof(unsigned long long) * 2 * n * slots, ctx->stream));
         ctx->bi_slots = slots;
         ctx->bi_n = n;
         ctx->bi_epoch = 0;
@@ -353,7 +432,7 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     a.slots = (int32_t)ctx->bi_slots;
     a.next = ctx->red.as<unsigned long long>();
     a.status = &ctx->ms_ctl.as<MsCtl>()->status;
-    a.edges = ctx->opt.instrument ? ctx->counters.as<unsigned long long>() + 4 : nullptr;
+    a.work = ctx->opt.instrument ? ctx->counters.as<unsigned long long>() : nullptr;
     k_bibfs<<<(int)ctx->bi_slots, kBiBlock, 0, ctx->stream>>>(a);
     PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS");
     return PERCIS_OK;
