@@ -39,6 +39,7 @@ constexpr int kBiBlock = PERCIS_BI_BLOCK;
 #define PERCIS_MEET_CAP 256
 #endif
 constexpr int kMeetCap = PERCIS_MEET_CAP;  // meeting-layer members kept in shared memory
+constexpr int kFlat = 512;  // frontiers up to this size have their edges spread over the block
 #ifndef PERCIS_BI_MINB
 #define PERCIS_BI_MINB 12
 #endif
@@ -105,6 +106,9 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
     __shared__ int32_t s_mv[kMeetCap];
     __shared__ unsigned long long s_mw[kMeetCap];
     __shared__ int32_t s_best[nw];
+    __shared__ int32_t s_fu[kFlat];
+    __shared__ unsigned long long s_fs[kFlat];
+    __shared__ int32_t s_pre[kFlat + 1];
     __shared__ unsigned long long s_work[4];
     if (threadIdx.x < 4) s_work[threadIdx.x] = 0ull;
     unsigned long long n_add = 0ull;
@@ -163,34 +167,88 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 int32_t *qx = x ? queue1 : queue0;
                 const int64_t *px = x ? a.irp : a.rp;
                 const int32_t *ax = x ? a.icol : a.col;
-                for (long long q = lo + warp; q < hi; q += nw) {
-                    const int32_t u = qx[q];
-                    const unsigned long long su = __ldcg(&sigx[u]);
-                    const int64_t e0 = px[u], e1 = px[u + 1];
-                    ne += (unsigned long long)(e1 - e0);
-                    for (int64_t e = e0 + lane; e < e1; e += 32) {
-                        const int32_t v = ax[e];
-                        const unsigned long long old = __ldcg(&infx[v]);
-                        bool at = old == want;
-                        if ((uint32_t)(old >> 32) != ep) {
-                            const unsigned long long prev = atomicCAS(&infx[v], old, want);
-                            if (prev == old) {
-                                at = true;
-                                qx[hi + atomicAdd(&s_new, 1)] = v;
-                                atomicAdd(&s_newcost, (unsigned long long)(px[v + 1] - px[v]));
-                                if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) s_meet = 1;
-                            } else {
-                                at = prev == want;  // claimed in this level by another thread
-                            }
-                        }
-                        if (at) {
-                            if (a.work) ++n_add;
-                            const unsigned long long o = atomicAdd(&sigx[v], su);
-                            if (o + su >= (1ull << 53)) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                const long long f = hi - lo;
+                // one edge: claim the neighbour if unreached, add the parent's count if
+                // it lies on the new level
+                auto visit = [&](const int32_t v, const unsigned long long su) {
+                    const unsigned long long old = __ldcg(&infx[v]);
+                    bool at = old == want;
+                    if ((uint32_t)(old >> 32) != ep) {
+                        const unsigned long long prev = atomicCAS(&infx[v], old, want);
+                        if (prev == old) {
+                            at = true;
+                            qx[hi + atomicAdd(&s_new, 1)] = v;
+                            atomicAdd(&s_newcost, (unsigned long long)(px[v + 1] - px[v]));
+                            if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) s_meet = 1;
+                        } else {
+                            at = prev == want;  // claimed in this level by another thread
                         }
                     }
+                    if (at) {
+                        if (a.work) ++n_add;
+                        const unsigned long long o = atomicAdd(&sigx[v], su);
+                        if (o + su >= (1ull << 53)) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                    }
+                };
+                if (f <= kFlat) {
+                    // the level's edges spread evenly over the block (a hub's
+                    // adjacency is not left to one warp): degree prefix sums of the
+                    // frontier in shared memory, each edge finds its vertex by bisection
+                    for (long long k = threadIdx.x; k < f; k += kBiBlock) {
+                        const int32_t u = qx[lo + k];
+                        s_fu[k] = u;
+                        s_fs[k] = __ldcg(&sigx[u]);
+                        s_pre[k] = (int32_t)(px[u + 1] - px[u]);
+                    }
+                    __syncthreads();
+                    if (warp == 0) {
+                        constexpr int per = kFlat / 32;
+                        int32_t loc[per];
+                        int32_t tot = 0;
+#pragma unroll
+                        for (int r = 0; r < per; ++r) {
+                            const long long k = (long long)lane * per + r;
+                            loc[r] = tot;
+                            tot += k < f ? s_pre[k] : 0;
+                        }
+                        int32_t incl = tot;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int32_t t2 = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += t2;
+                        }
+                        const int32_t base = incl - tot;
+                        __syncwarp();
+#pragma unroll
+                        for (int r = 0; r < per; ++r) {
+                            const long long k = (long long)lane * per + r;
+                            if (k < f) s_pre[k] = base + loc[r];
+                        }
+                        if (lane == 31) s_pre[f] = incl;
+                    }
+                    __syncthreads();
+                    const int32_t E = s_pre[f];
+                    ne = threadIdx.x == 0 ? (unsigned long long)E : 0ull;
+                    for (int32_t j = threadIdx.x; j < E; j += kBiBlock) {
+                        int32_t klo = 0, khi = (int32_t)f - 1;  // last k with s_pre[k] <= j
+                        while (klo < khi) {
+                            const int32_t mid = (klo + khi + 1) >> 1;
+                            if (s_pre[mid] <= j) klo = mid;
+                            else khi = mid - 1;
+                        }
+                        const int32_t u = s_fu[klo];
+                        visit(ax[px[u] + (j - s_pre[klo])], s_fs[klo]);
+                    }
+                } else {
+                    for (long long q = lo + warp; q < hi; q += nw) {
+                        const int32_t u = qx[q];
+                        const unsigned long long su = __ldcg(&sigx[u]);
+                        const int64_t e0 = px[u], e1 = px[u + 1];
+                        if (lane == 0) ne += (unsigned long long)(e1 - e0);
+                        for (int64_t e = e0 + lane; e < e1; e += 32) visit(ax[e], su);
+                    }
                 }
-                if (a.work && lane == 0) atomicAdd(&s_work[0], ne);
+                if (a.work && ne) atomicAdd(&s_work[0], ne);
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     s_lo[x] = hi;
