@@ -89,6 +89,11 @@ typedef struct {
                                  gets sigma_sv sigma_vt / sigma_st (same expectation; the
                                  Rao-Blackwellised form; batched form only; no backward) */
     double push_alpha;        /* direction 2 threshold; 0 = default (0.5) */
+    int32_t cuda_graphs;      /* 1: a many-graph context records the per-graph pair-sampling
+                                 launches of a phase once in a CUDA graph and replays it while
+                                 the per-graph sample counts repeat (phase 1 always does);
+                                 the seed is read from device memory, results are unchanged */
+    int32_t reserved;
 } percis_options;
 
 typedef struct {

@@ -367,7 +367,7 @@ void percis_destroy(percis_ctx *ctx) {
                       &ctx->pc_tmp, &ctx->grad_tmp, &ctx->host_pinned, &ctx->vorder,
                       &ctx->fq0, &ctx->fq1, &ctx->qstamp, &ctx->acc_ap,
                       &ctx->ap_tau, &ctx->ap_stamp, &ctx->ap_list, &ctx->plan_dev, &ctx->bi_info,
-                      &ctx->bi_sig, &ctx->bi_queue};
+                      &ctx->bi_queue};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->counters.p) cudaFree(ctx->counters.p);

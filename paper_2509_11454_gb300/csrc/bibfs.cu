@@ -59,14 +59,21 @@ struct BiArgs {
     uint64_t seed;
     uint32_t tag;
     uint32_t epoch_base;
-    unsigned long long *info;   // [slots][2][n]: epoch << 32 | level
-    unsigned long long *sig;    // [slots][2][n]
+    unsigned long long *vs;     // [slots][n][4]: per vertex the level words of the two sides
+                                // (epoch << 32 | level), then their path counts: one 32-byte
+                                // sector holds everything a visit touches
     int32_t *queue;             // [slots][2][n]: visited vertices of each side in level order
     int32_t slots;
     unsigned long long *next;   // next sample to take
     uint32_t *status;
     unsigned long long *work;   // optional work counters: [0] edges scanned, [1] count additions,
                                 // [2] vertices reached (both sides), [3] samples traversed
+};
+
+// one field of the per-vertex records, indexed by vertex
+struct Strided {
+    unsigned long long *p;
+    __device__ __forceinline__ unsigned long long &operator[](int64_t v) const { return p[4 * v]; }
 };
 
 __device__ __forceinline__ unsigned long long pack(uint32_t ep, uint32_t lev) {
@@ -92,8 +99,8 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
     const int64_t n = a.n;
     const size_t slot = blockIdx.x;
     // side 0 = forward from s over out-edges, side 1 = backward from t over in-edges
-    unsigned long long *const info0 = a.info + (slot * 2) * n, *const info1 = info0 + n;
-    unsigned long long *const sig0 = a.sig + (slot * 2) * n, *const sig1 = sig0 + n;
+    unsigned long long *const vrec = a.vs + slot * (size_t)n * 4;
+    const Strided info0{vrec}, info1{vrec + 1}, sig0{vrec + 2}, sig1{vrec + 3};
     int32_t *const queue0 = a.queue + (slot * 2) * n, *const queue1 = queue0 + n;
 
     __shared__ long long s_i;
@@ -161,9 +168,9 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 // level nl: claim unreached neighbours and add the counts over
                 // every edge into the level in one pass (counts of unreached
                 // vertices are zero: each sample clears the ones it touched)
-                unsigned long long *infx = x ? info1 : info0;
-                unsigned long long *sigx = x ? sig1 : sig0;
-                const unsigned long long *infy = x ? info0 : info1;
+                const Strided infx = x ? info1 : info0;
+                const Strided sigx = x ? sig1 : sig0;
+                const Strided infy = x ? info0 : info1;
                 int32_t *qx = x ? queue1 : queue0;
                 const int64_t *px = x ? a.irp : a.rp;
                 const int32_t *ax = x ? a.icol : a.col;
@@ -273,7 +280,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
             }
         } else {
             // meeting layer: level s_lev[x] of side x reached by the other side
-            const unsigned long long *infy = x ? info0 : info1;
+            const Strided infy = x ? info0 : info1;
             const int32_t *qx = x ? queue1 : queue0;
             const long long mlo = s_lo[x], mhi = s_hi[x];
             // the layer's members with their weights sigma_s sigma_t, kept in
@@ -362,8 +369,8 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                     // towards s: predecessors over in-edges; towards t: successors over out-edges
                     const int64_t *bp = z == 0 ? a.irp : a.rp;
                     const int32_t *bc = z == 0 ? a.icol : a.col;
-                    const unsigned long long *infz = z == 0 ? info0 : info1;
-                    const unsigned long long *sigz = z == 0 ? sig0 : sig1;
+                    const Strided infz = z == 0 ? info0 : info1;
+                    const Strided sigz = z == 0 ? sig0 : sig1;
                     const int32_t endz = z == 0 ? s : t;
                     int32_t w = vm;
                     while (w != endz) {
@@ -434,7 +441,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
 // targets, |I|, paths and counts, as the batched form leaves them.
 percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count) {
     const int64_t n = ctx->n;
-    const size_t per_slot = (size_t)n * 2 * (sizeof(unsigned long long) * 2 + sizeof(int32_t));
+    const size_t per_slot = (size_t)n * (sizeof(unsigned long long) * 4 + sizeof(int32_t) * 2);
     static int per_sm = 0;
     if (!per_sm) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs, kBiBlock, 0) != cudaSuccess || per_sm < 1)
@@ -444,18 +451,16 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, (16ll << 30) / per_slot));
     slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
     if (ctx->bi_slots < slots || ctx->bi_n != n) {
-        PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 2 * n * slots, "bidirectional levels"));
-        PERCIS_TRY(ensure(ctx, ctx->bi_sig, sizeof(unsigned long long) * 2 * n * slots, "bidirectional counts"));
+        PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 4 * n * slots, "bidirectional records"));
         PERCIS_TRY(ensure(ctx, ctx->bi_queue, sizeof(int32_t) * 2 * n * slots, "bidirectional queues"));
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 2 * n * slots, ctx->stream));
-        // counts start at zero; every sample clears the ones it touched
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_sig.p, 0, sizeof(unsigned long long) * 2 * n * slots, ctx->stream));
+        // level words of no sample, counts zero (every sample clears the counts it touched)
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * n * slots, ctx->stream));
         ctx->bi_slots = slots;
         ctx->bi_n = n;
         ctx->bi_epoch = 0;
     }
     if ((uint64_t)ctx->bi_epoch + (uint64_t)count + 2 > 0xffffffffull) {
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 2 * n * ctx->bi_slots,
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * n * ctx->bi_slots,
                                          ctx->stream));
         ctx->bi_epoch = 0;
     }
@@ -484,8 +489,7 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     a.tag = tag_path;
     a.epoch_base = (uint32_t)ctx->bi_epoch;
     ctx->bi_epoch += count + 1;
-    a.info = ctx->bi_info.as<unsigned long long>();
-    a.sig = ctx->bi_sig.as<unsigned long long>();
+    a.vs = ctx->bi_info.as<unsigned long long>();
     a.queue = ctx->bi_queue.as<int32_t>();
     a.slots = (int32_t)ctx->bi_slots;
     a.next = ctx->red.as<unsigned long long>();

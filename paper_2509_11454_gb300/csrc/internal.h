@@ -87,7 +87,7 @@ struct percis_ctx {
     percis::DevBuf fq0, fq1, qstamp;  // frontier queues and per-vertex level stamps
     percis::DevBuf acc_ap, ap_tau, ap_stamp, ap_list;  // all-paths estimator
     percis::DevBuf plan_dev;                           // lane batches of a many-graph phase
-    percis::DevBuf bi_info, bi_sig, bi_queue;          // bidirectional form: per-slot scratch
+    percis::DevBuf bi_info, bi_queue;                  // bidirectional form: per-slot scratch
     int64_t bi_slots = 0, bi_n = 0, bi_epoch = 0;
     int64_t ap_warps = 0, ap_n = 0;
     int32_t ap_epoch = 0;
@@ -160,7 +160,8 @@ percis_status prep_states(percis_ctx *ctx);  // sort, tables, C_v, lambda, d^
 
 // sampler.cu
 percis_status sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag, int64_t i0, int64_t count, int32_t *s,
-                           int32_t *t, int32_t *kind);
+                           int32_t *t, int32_t *kind, const uint64_t *seed_dev = nullptr,
+                           cudaStream_t stream = nullptr);
 percis_status group_by_source(percis_ctx *ctx, int64_t count, int64_t *n_sources, int64_t *n_valid);
 
 // bfs_plain.cu

@@ -33,9 +33,21 @@ struct MultiGraph {
     DevBuf gid;                         // graph of every vertex
     DevBuf soff_dev, ell_dev, stats, pmax;
     bool paths_scattered = false;
+    // recorded per-graph sampling launches of each phase (pair tag 0 / 1), the
+    // counts they were recorded for, and the device word they read the seed from
+    cudaGraphExec_t samp_exec[2] = {nullptr, nullptr};
+    std::vector<int64_t> samp_key[2];
+    DevBuf seed_dev;
+    int64_t graph_launches = 0, graph_records = 0;
 };
 
 namespace {
+
+void drop_graph(MultiGraph *m, int k) {
+    if (m->samp_exec[k]) cudaGraphExecDestroy(m->samp_exec[k]);
+    m->samp_exec[k] = nullptr;
+    m->samp_key[k].clear();
+}
 
 __global__ void k_offset_ids(int32_t *s, int32_t *t, int64_t count, int32_t delta) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -116,8 +128,10 @@ __global__ void k_ilen64(const int32_t *ilen, int64_t count, long long *out) {
 void multi_free(percis_ctx *ctx) {
     if (!ctx->multi) return;
     MultiGraph *m = ctx->multi;
+    drop_graph(m, 0);
+    drop_graph(m, 1);
     for (percis_ctx *sub : m->subs) percis_destroy(sub);
-    DevBuf *bufs[] = {&m->gid, &m->soff_dev, &m->ell_dev, &m->stats, &m->pmax};
+    DevBuf *bufs[] = {&m->gid, &m->soff_dev, &m->ell_dev, &m->stats, &m->pmax, &m->seed_dev};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete m;
@@ -131,7 +145,10 @@ void multi_set_options(percis_ctx *ctx) {
     for (percis_ctx *sub : ctx->multi->subs) sub->opt = ctx->opt;
 }
 
-percis_status multi_sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag) {
+namespace {
+
+// the per-graph launches of one phase's pair sampling
+percis_status issue_sampling(percis_ctx *ctx, uint64_t seed, uint32_t tag, const uint64_t *seed_dev) {
     MultiGraph *m = ctx->multi;
     for (int32_t g = 0; g < m->G; ++g) {
         const int64_t c = m->counts[g];
@@ -140,11 +157,51 @@ percis_status multi_sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag) {
         int32_t *t = ctx->pair_t.as<int32_t>() + m->soff[g];
         int32_t *kd = ctx->kind.as<int32_t>() + m->soff[g];
         percis_ctx *sub = m->subs[g];
-        const percis_status st = sample_pairs(sub, seed, tag, m->soff[g], c, s, t, kd);
+        const percis_status st = sample_pairs(sub, seed, tag, m->soff[g], c, s, t, kd, seed_dev, ctx->stream);
         if (st != PERCIS_OK) return set_err(ctx, st, "graph " + std::to_string(g) + ": " + sub->err);
         k_offset_ids<<<grid_for(ctx, c, 256), 256, 0, ctx->stream>>>(s, t, c, (int32_t)m->vptr[g]);
         PERCIS_CHECK_LAUNCH(ctx, "offset ids");
     }
+    return PERCIS_OK;
+}
+
+}  // namespace
+
+percis_status multi_sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag) {
+    MultiGraph *m = ctx->multi;
+    if (!ctx->opt.cuda_graphs || tag > 1) return issue_sampling(ctx, seed, tag, nullptr);
+    // CUDA graph: the G sampling launches (and their id offsets) recorded once per
+    // count vector and replayed; the seed travels through a device word
+    PERCIS_TRY(ensure(ctx, m->seed_dev, 64, "seed word"));
+    PERCIS_CUDA(ctx, cudaMemcpyAsync(m->seed_dev.p, &seed, sizeof(seed), cudaMemcpyHostToDevice, ctx->stream));
+    const int k = (int)tag;
+    // the recorded launches bake in the buffers' addresses: re-record when counts or buffers change
+    std::vector<int64_t> key = m->counts;
+    key.push_back((int64_t)(uintptr_t)ctx->pair_s.p);
+    key.push_back((int64_t)(uintptr_t)ctx->pair_t.p);
+    key.push_back((int64_t)(uintptr_t)ctx->kind.p);
+    if (!m->samp_exec[k] || m->samp_key[k] != key) {
+        drop_graph(m, k);
+        cudaGraph_t graph = nullptr;
+        PERCIS_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const percis_status st = issue_sampling(ctx, seed, tag, m->seed_dev.as<uint64_t>());
+        const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+        if (st != PERCIS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ec != cudaSuccess) return cuda_err(ctx, ec, "end of the sampling capture");
+        const cudaError_t ei = cudaGraphInstantiate(&m->samp_exec[k], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            m->samp_exec[k] = nullptr;
+            return cuda_err(ctx, ei, "instantiating the sampling graph");
+        }
+        m->samp_key[k] = key;
+        m->graph_records++;
+    }
+    PERCIS_CUDA(ctx, cudaGraphLaunch(m->samp_exec[k], ctx->stream));
+    m->graph_launches++;
     return PERCIS_OK;
 }
 

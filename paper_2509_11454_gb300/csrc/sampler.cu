@@ -13,9 +13,10 @@ namespace {
 __global__ void k_sample_pairs(int64_t n, const double *__restrict__ xs, const int32_t *__restrict__ perm,
                                const double *__restrict__ w, const double *__restrict__ ci,
                                const double *__restrict__ r, const double *__restrict__ dscal,
-                               const double *__restrict__ x, uint64_t seed, uint32_t tag, int64_t i0, int64_t count,
-                               int32_t *s_out, int32_t *t_out, int32_t *kind) {
+                               const double *__restrict__ x, uint64_t seed, const uint64_t *seed_dev, uint32_t tag,
+                               int64_t i0, int64_t count, int32_t *s_out, int32_t *t_out, int32_t *kind) {
     const double c = dscal[0];
+    if (seed_dev) seed = *seed_dev;  // a recorded launch reads the seed of the current call
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
         double us, ut;
@@ -103,12 +104,13 @@ __global__ void k_lane_tables(const long long *src_count, const long long *src_o
 }  // namespace
 
 percis_status sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag, int64_t i0, int64_t count, int32_t *s,
-                           int32_t *t, int32_t *kind) {
+                           int32_t *t, int32_t *kind, const uint64_t *seed_dev, cudaStream_t stream) {
     if (count <= 0) return PERCIS_OK;
     const int block = 256;
-    k_sample_pairs<<<grid_for(ctx, count, block), block, 0, ctx->stream>>>(
+    k_sample_pairs<<<grid_for(ctx, count, block), block, 0, stream ? stream : ctx->stream>>>(
         ctx->n, ctx->xs.as<double>(), ctx->perm.as<int32_t>(), ctx->w.as<double>(), ctx->ci.as<double>(),
-        ctx->r.as<double>(), ctx->dscal.as<double>(), ctx->x.as<double>(), seed, tag, i0, count, s, t, kind);
+        ctx->r.as<double>(), ctx->dscal.as<double>(), ctx->x.as<double>(), seed, seed_dev, tag, i0, count, s, t,
+        kind);
     PERCIS_CHECK_LAUNCH(ctx, "sample pairs");
     return PERCIS_OK;
 }
