@@ -353,6 +353,9 @@ int32_t orc_bibfs(int64_t n, const int64_t *rp, const int32_t *col, const int64_
         }
         double total = 0.0;
         for (int64_t a = 0; a < nm; a++) total += sig[0][meet[a]] * sig[1][meet[a]];
+        /* sigma_st (and each term sigma_s(v) sigma_t(v)) is a path count too: past
+         * 2^53 the FP64 values are no longer exact */
+        if (total >= 9007199254740992.0) *overflow = 1;
         *sst = total;
         double u[2];
         orc_uniforms(seed, i, tag, 0, u);
