@@ -62,7 +62,8 @@ typedef enum {
  *           backtracked from it.  Same pairs and the same path distribution,
  *           other paths than BATCHED (each path uniform over the shortest
  *           paths); paths list the meeting vertex, then the s side, then the
- *           t side.  No all-paths estimator, no many-graph contexts. */
+ *           t side.  No all-paths estimator.  Scratch per block: 40 bytes per
+ *           vertex of the graph (of the largest graph in a many-graph context). */
 enum { PERCIS_FORM_BATCHED = 0, PERCIS_FORM_PLAIN = 1, PERCIS_FORM_BIDIR = 2 };
 
 typedef struct {

@@ -255,7 +255,11 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
             ctx->arena_cap = cap;
             continue;
         }
-        if (ctx->opt.form != PERCIS_FORM_PLAIN) {
+        if (ctx->opt.form == PERCIS_FORM_BIDIR && (st & DEV_SIGMA_OVERFLOW) && ctx->sigma_mode != 2) {
+            ctx->sigma_mode = 2;  // counts reached 2^53: redo with FP64 counts
+            continue;
+        }
+        if (ctx->opt.form == PERCIS_FORM_BATCHED) {
             if ((st & DEV_SIGMA_WIDE) && ctx->sigma_mode == 0) {
                 ctx->sigma_mode = 1;  // a count reached 2^32: redo with 64-bit storage
                 continue;

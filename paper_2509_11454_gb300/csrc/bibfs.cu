@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -66,6 +67,11 @@ struct BiArgs {
     int32_t slots;
     unsigned long long *next;   // next sample to take
     uint32_t *status;
+    // many graphs: records are indexed within the sample's graph (vertex - its
+    // first id), so a slot holds nslot records (the largest graph)
+    const int32_t *gid;         // graph of every vertex, or null for one graph
+    const int64_t *vbase;       // first vertex id of every graph
+    int64_t nslot;
     unsigned long long *work;   // optional work counters: [0] edges scanned, [1] count additions,
                                 // [2] vertices reached (both sides), [3] samples traversed
 };
@@ -74,6 +80,13 @@ struct BiArgs {
 struct Strided {
     unsigned long long *p;
     __device__ __forceinline__ unsigned long long &operator[](int64_t v) const { return p[4 * v]; }
+};
+
+// the path-count fields, as exact integers or (past 2^53) as FP64
+template <class C>
+struct CountView {
+    unsigned long long *p;
+    __device__ __forceinline__ C &operator[](int64_t v) const { return *reinterpret_cast<C *>(p + 4 * v); }
 };
 
 __device__ __forceinline__ unsigned long long pack(uint32_t ep, uint32_t lev) {
@@ -93,28 +106,31 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
     return t;
 }
 
+// C = unsigned long long: exact counts (flagged at 2^53, products checked);
+// C = double: FP64 counts, the rerun of a phase whose counts passed 2^53.
+template <class C>
 __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
+    constexpr bool FP = std::is_floating_point<C>::value;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nw = kBiBlock / 32;
     const int64_t n = a.n;
     const size_t slot = blockIdx.x;
     // side 0 = forward from s over out-edges, side 1 = backward from t over in-edges
-    unsigned long long *const vrec = a.vs + slot * (size_t)n * 4;
-    const Strided info0{vrec}, info1{vrec + 1}, sig0{vrec + 2}, sig1{vrec + 3};
-    int32_t *const queue0 = a.queue + (slot * 2) * n, *const queue1 = queue0 + n;
+    unsigned long long *const vslot = a.vs + slot * (size_t)a.nslot * 4;
+    int32_t *const queue0 = a.queue + (slot * 2) * a.nslot, *const queue1 = queue0 + a.nslot;
 
     __shared__ long long s_i;
     __shared__ long long s_lo[2], s_hi[2];
     __shared__ uint32_t s_lev[2];
     __shared__ unsigned long long s_cost[2], s_newcost;
     __shared__ int s_new, s_meet;
-    __shared__ unsigned long long s_red[nw];
     __shared__ int s_nm;
     __shared__ int32_t s_mv[kMeetCap];
-    __shared__ unsigned long long s_mw[kMeetCap];
+    __shared__ C s_mw[kMeetCap];
+    __shared__ C s_redc[nw];
     __shared__ int32_t s_best[nw];
     __shared__ int32_t s_fu[kFlat];
-    __shared__ unsigned long long s_fs[kFlat];
+    __shared__ C s_fs[kFlat];
     __shared__ int32_t s_pre[kFlat + 1];
     __shared__ unsigned long long s_work[4];
     if (threadIdx.x < 4) s_work[threadIdx.x] = 0ull;
@@ -135,12 +151,17 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
         }
         const int32_t s = a.pair_s[i], t = a.pair_t[i];
         const uint32_t ep = a.epoch_base + (uint32_t)i + 1u;
+        // record of vertex v at vrec[4 (v - base)]: the sample's graph starts at base
+        const int64_t base = a.gid ? a.vbase[a.gid[s]] : 0;
+        unsigned long long *const vrec = vslot - 4 * base;
+        const Strided info0{vrec}, info1{vrec + 1};
+        const CountView<C> sig0{vrec + 2}, sig1{vrec + 3};
         if (threadIdx.x == 0) {
             info0[s] = pack(ep, 0);
-            sig0[s] = 1ull;
+            sig0[s] = C(1);
             queue0[0] = s;
             info1[t] = pack(ep, 0);
-            sig1[t] = 1ull;
+            sig1[t] = C(1);
             queue1[0] = t;
             s_cost[0] = (unsigned long long)(a.rp[s + 1] - a.rp[s]);
             s_cost[1] = (unsigned long long)(a.irp[t + 1] - a.irp[t]);
@@ -169,7 +190,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 // every edge into the level in one pass (counts of unreached
                 // vertices are zero: each sample clears the ones it touched)
                 const Strided infx = x ? info1 : info0;
-                const Strided sigx = x ? sig1 : sig0;
+                const CountView<C> sigx = x ? sig1 : sig0;
                 const Strided infy = x ? info0 : info1;
                 int32_t *qx = x ? queue1 : queue0;
                 const int64_t *px = x ? a.irp : a.rp;
@@ -177,7 +198,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 const long long f = hi - lo;
                 // one edge: claim the neighbour if unreached, add the parent's count if
                 // it lies on the new level
-                auto visit = [&](const int32_t v, const unsigned long long su) {
+                auto visit = [&](const int32_t v, const C su) {
                     const unsigned long long old = __ldcg(&infx[v]);
                     bool at = old == want;
                     if ((uint32_t)(old >> 32) != ep) {
@@ -193,8 +214,8 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                     }
                     if (at) {
                         if (a.work) ++n_add;
-                        const unsigned long long o = atomicAdd(&sigx[v], su);
-                        if (o + su >= (1ull << 53)) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                        const C o = atomicAdd(&sigx[v], su);
+                        if ((double)(o + su) >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
                     }
                 };
                 if (f <= kFlat) {
@@ -249,7 +270,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 } else {
                     for (long long q = lo + warp; q < hi; q += nw) {
                         const int32_t u = qx[q];
-                        const unsigned long long su = __ldcg(&sigx[u]);
+                        const C su = __ldcg(&sigx[u]);
                         const int64_t e0 = px[u], e1 = px[u + 1];
                         if (lane == 0) ne += (unsigned long long)(e1 - e0);
                         for (int64_t e = e0 + lane; e < e1; e += 32) visit(ax[e], su);
@@ -287,13 +308,13 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
             // shared memory when they fit
             if (threadIdx.x == 0) s_nm = 0;
             __syncthreads();
-            unsigned long long part = 0ull;
+            C part = C(0);
             for (long long q = mlo + threadIdx.x; q < mhi; q += kBiBlock) {
                 const int32_t v = qx[q];
                 if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) {
-                    const unsigned long long a0 = __ldcg(&sig0[v]), a1 = __ldcg(&sig1[v]);
-                    const unsigned long long p = a0 * a1;
-                    if (__umul64hi(a0, a1) != 0ull || p >= (1ull << 53)) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                    const C a0 = __ldcg(&sig0[v]), a1 = __ldcg(&sig1[v]);
+                    const C p = a0 * a1;
+                    if ((double)a0 * (double)a1 >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
                     part += p;
                     const int slot_m = atomicAdd(&s_nm, 1);
                     if (slot_m < kMeetCap) {
@@ -302,7 +323,8 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                     }
                 }
             }
-            const unsigned long long sst = block_sum(part, s_red);
+            const C sst = block_sum(part, s_redc);
+            if (threadIdx.x == 0 && (double)sst >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
             const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, 0), (double)sst);
             const int nm = s_nm;
             if (a.work && threadIdx.x == 0 && nm > kMeetCap) s_work[3] += 1ull << 32;  // large layers (high word)
@@ -313,7 +335,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 int32_t best = 0x7fffffff;
                 for (int j = threadIdx.x; j < nm; j += kBiBlock) {
                     const int32_t vj = s_mv[j];
-                    unsigned long long pre = 0ull;
+                    C pre = C(0);
                     for (int k2 = 0; k2 < nm; ++k2)
                         if (s_mv[k2] <= vj) pre += s_mw[k2];
                     if ((double)pre >= target) best = min(best, vj);
@@ -331,13 +353,13 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 int32_t blo = 0, bhi = (int32_t)(n - 1);
                 while (blo < bhi) {
                     const int32_t mid = blo + (bhi - blo) / 2;
-                    unsigned long long pm = 0ull;
+                    C pm = C(0);
                     for (long long q = mlo + threadIdx.x; q < mhi; q += kBiBlock) {
                         const int32_t v = qx[q];
                         if (v <= mid && (uint32_t)(__ldcg(&infy[v]) >> 32) == ep)
                             pm += __ldcg(&sig0[v]) * __ldcg(&sig1[v]);
                     }
-                    const unsigned long long sm = block_sum(pm, s_red);
+                    const C sm = block_sum(pm, s_redc);
                     if ((double)sm >= target) bhi = mid;
                     else blo = mid + 1;
                 }
@@ -370,7 +392,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                     const int64_t *bp = z == 0 ? a.irp : a.rp;
                     const int32_t *bc = z == 0 ? a.icol : a.col;
                     const Strided infz = z == 0 ? info0 : info1;
-                    const Strided sigz = z == 0 ? sig0 : sig1;
+                    const CountView<C> sigz = z == 0 ? sig0 : sig1;
                     const int32_t endz = z == 0 ? s : t;
                     int32_t w = vm;
                     while (w != endz) {
@@ -379,27 +401,32 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                         const double tg = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step),
                                                     (double)__ldcg(&sigz[w]));
                         const int64_t e0 = bp[w], e1 = bp[w + 1];
-                        unsigned long long carry = 0ull;
-                        int32_t pick = -1;
+                        C carry = C(0);
+                        int32_t pick = -1, last = -1;
                         for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
                             const int64_t e = base + lane;
                             int32_t pv = -1;
-                            unsigned long long val = 0ull;
+                            C val = C(0);
                             if (e < e1) {
                                 pv = bc[e];
                                 if (__ldcg(&infz[pv]) == prev) val = __ldcg(&sigz[pv]);
                             }
-                            unsigned long long cum = val;
+                            C cum = val;
 #pragma unroll
                             for (int o = 1; o < 32; o <<= 1) {
-                                const unsigned long long t2 = __shfl_up_sync(0xffffffffu, cum, o);
+                                const C t2 = __shfl_up_sync(0xffffffffu, cum, o);
                                 if (lane >= o) cum += t2;
                             }
                             cum += carry;
-                            const unsigned hit = __ballot_sync(0xffffffffu, val > 0ull && (double)cum >= tg);
+                            const unsigned hit = __ballot_sync(0xffffffffu, val > C(0) && (double)cum >= tg);
                             if (hit) pick = __shfl_sync(0xffffffffu, pv, __ffs(hit) - 1);
+                            const unsigned cand = __ballot_sync(0xffffffffu, val > C(0));
+                            if (cand) last = __shfl_sync(0xffffffffu, pv, 31 - __clz(cand));
                             carry = __shfl_sync(0xffffffffu, cum, 31);
                         }
+                        // FP64 counts past 2^53 may round the running sum just below u sigma(w):
+                        // the last candidate then takes the remainder
+                        if (pick < 0 && FP) pick = last;
                         if (pick < 0) {
                             if (lane == 0) atomicOr(a.status, DEV_BAD_PATH);
                             break;
@@ -423,8 +450,8 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
             s_work[2] += (unsigned long long)(s_hi[0] + s_hi[1]);
             s_work[3] += 1ull;
         }
-        for (long long q = threadIdx.x; q < s_hi[0]; q += kBiBlock) sig0[queue0[q]] = 0ull;
-        for (long long q = threadIdx.x; q < s_hi[1]; q += kBiBlock) sig1[queue1[q]] = 0ull;
+        for (long long q = threadIdx.x; q < s_hi[0]; q += kBiBlock) sig0[queue0[q]] = C(0);
+        for (long long q = threadIdx.x; q < s_hi[1]; q += kBiBlock) sig1[queue1[q]] = C(0);
     }
     if (a.work) {
 #pragma unroll
@@ -441,26 +468,32 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
 // targets, |I|, paths and counts, as the batched form leaves them.
 percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count) {
     const int64_t n = ctx->n;
-    const size_t per_slot = (size_t)n * (sizeof(unsigned long long) * 4 + sizeof(int32_t) * 2);
+    const int32_t *gid = nullptr;
+    const int64_t *vbase = nullptr;
+    int64_t nslot = n;
+    if (ctx->multi) multi_graph_view(ctx, &gid, &vbase, &nslot);
+    const size_t per_slot = (size_t)nslot * (sizeof(unsigned long long) * 4 + sizeof(int32_t) * 2);
     static int per_sm = 0;
     if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs, kBiBlock, 0) != cudaSuccess || per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs<unsigned long long>, kBiBlock, 0) !=
+                cudaSuccess ||
+            per_sm < 1)
             per_sm = 1;
     }
     // at most 16 GiB of scratch
     int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, (16ll << 30) / per_slot));
     slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
-    if (ctx->bi_slots < slots || ctx->bi_n != n) {
-        PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 4 * n * slots, "bidirectional records"));
-        PERCIS_TRY(ensure(ctx, ctx->bi_queue, sizeof(int32_t) * 2 * n * slots, "bidirectional queues"));
+    if (ctx->bi_slots < slots || ctx->bi_n != nslot) {
+        PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 4 * nslot * slots, "bidirectional records"));
+        PERCIS_TRY(ensure(ctx, ctx->bi_queue, sizeof(int32_t) * 2 * nslot * slots, "bidirectional queues"));
         // level words of no sample, counts zero (every sample clears the counts it touched)
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * n * slots, ctx->stream));
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * nslot * slots, ctx->stream));
         ctx->bi_slots = slots;
-        ctx->bi_n = n;
+        ctx->bi_n = nslot;
         ctx->bi_epoch = 0;
     }
     if ((uint64_t)ctx->bi_epoch + (uint64_t)count + 2 > 0xffffffffull) {
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * n * ctx->bi_slots,
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * nslot * ctx->bi_slots,
                                          ctx->stream));
         ctx->bi_epoch = 0;
     }
@@ -471,6 +504,9 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(unsigned long long), ctx->stream));
     BiArgs a{};
     a.n = n;
+    a.gid = gid;
+    a.vbase = vbase;
+    a.nslot = nslot;
     a.rp = ctx->rp.as<int64_t>();
     a.col = ctx->col.as<int32_t>();
     a.irp = ctx->directed ? ctx->irp.as<int64_t>() : ctx->rp.as<int64_t>();
@@ -495,7 +531,8 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     a.next = ctx->red.as<unsigned long long>();
     a.status = &ctx->ms_ctl.as<MsCtl>()->status;
     a.work = ctx->opt.instrument ? ctx->counters.as<unsigned long long>() : nullptr;
-    k_bibfs<<<(int)ctx->bi_slots, kBiBlock, 0, ctx->stream>>>(a);
+    if (ctx->sigma_mode == 2) k_bibfs<double><<<(int)ctx->bi_slots, kBiBlock, 0, ctx->stream>>>(a);
+    else k_bibfs<unsigned long long><<<(int)ctx->bi_slots, kBiBlock, 0, ctx->stream>>>(a);
     PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS");
     return PERCIS_OK;
 }

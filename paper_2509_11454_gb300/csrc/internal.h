@@ -212,6 +212,8 @@ struct LaneBatch {
 };
 percis_status multi_plan_batches(percis_ctx *ctx, int64_t n_sources, int W, std::vector<LaneBatch> *out);
 int64_t multi_range(percis_ctx *ctx);  // vertex range of the batch buffers
+// for the bidirectional form: graph of every vertex, first id of every graph, largest graph
+void multi_graph_view(percis_ctx *ctx, const int32_t **gid, const int64_t **vbase, int64_t *largest);
 
 // bounds.cpp
 struct Bounds {

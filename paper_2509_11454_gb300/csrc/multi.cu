@@ -31,6 +31,8 @@ struct MultiGraph {
     std::vector<int32_t> lane_src_host;
     int64_t range = 0;                  // vertex range of the batch buffers
     DevBuf gid;                         // graph of every vertex
+    DevBuf vptr_dev;                    // first vertex id of every graph (device)
+    int64_t largest = 0;
     DevBuf soff_dev, ell_dev, stats, pmax;
     bool paths_scattered = false;
     // recorded per-graph sampling launches of each phase (pair tag 0 / 1), the
@@ -131,7 +133,7 @@ void multi_free(percis_ctx *ctx) {
     drop_graph(m, 0);
     drop_graph(m, 1);
     for (percis_ctx *sub : m->subs) percis_destroy(sub);
-    DevBuf *bufs[] = {&m->gid, &m->soff_dev, &m->ell_dev, &m->stats, &m->pmax, &m->seed_dev};
+    DevBuf *bufs[] = {&m->gid, &m->soff_dev, &m->ell_dev, &m->stats, &m->pmax, &m->seed_dev, &m->vptr_dev};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete m;
@@ -139,6 +141,13 @@ void multi_free(percis_ctx *ctx) {
 }
 
 int64_t multi_range(percis_ctx *ctx) { return ctx->multi ? ctx->multi->range : ctx->n; }
+
+void multi_graph_view(percis_ctx *ctx, const int32_t **gid, const int64_t **vbase, int64_t *largest) {
+    MultiGraph *m = ctx->multi;
+    *gid = m->gid.as<int32_t>();
+    *vbase = m->vptr_dev.as<int64_t>();
+    *largest = m->largest;
+}
 
 void multi_set_options(percis_ctx *ctx) {
     if (!ctx->multi) return;
@@ -366,8 +375,12 @@ extern "C" percis_status percis_load_graphs(percis_ctx *ctx, int32_t num_graphs,
     for (int32_t g = 0; g < num_graphs; ++g)
         std::fill(gid.begin() + graph_vptr[g], gid.begin() + graph_vptr[g + 1], g);
     ctx->multi = m;
+    m->largest = largest;
     PERCIS_TRY(ensure(ctx, m->gid, sizeof(int32_t) * n, "graph ids"));
     PERCIS_CUDA(ctx, cudaMemcpyAsync(m->gid.p, gid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+    PERCIS_TRY(ensure(ctx, m->vptr_dev, sizeof(int64_t) * (num_graphs + 1), "graph offsets"));
+    PERCIS_CUDA(ctx, cudaMemcpyAsync(m->vptr_dev.p, graph_vptr, sizeof(int64_t) * (num_graphs + 1),
+                                     cudaMemcpyHostToDevice, ctx->stream));
     PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->have_graph = true;
     return PERCIS_OK;
@@ -403,8 +416,8 @@ extern "C" percis_status percis_estimate_graphs(percis_ctx *ctx, double eps, dou
     PERCIS_TRY(need_multi(ctx, true));
     if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0) || !pc_out)
         return set_err(ctx, PERCIS_E_INVALID, "eps and delta must lie in (0,1); pc_out must be non-NULL");
-    if (ctx->opt.form != PERCIS_FORM_BATCHED)
-        return set_err(ctx, PERCIS_E_INVALID, "many graphs run in the batched form");
+    if (ctx->opt.form == PERCIS_FORM_PLAIN)
+        return set_err(ctx, PERCIS_E_INVALID, "many graphs run in the batched or bidirectional form");
     MultiGraph *m = ctx->multi;
     const int32_t G = m->G;
     const int64_t launches0 = ctx->launches;
