@@ -46,7 +46,9 @@ WORKLOAD_DESC = {
 NCU_TRAFFIC = {"sha256": "ca2e6806ea9f3f5243f765b02c21eecae307c332c69e267183886b9109460557",
                # DRAM read + write of one phase-2 launch (20 batches) / 20: bytes per batch of lanes
                "bytes_per_launch": (10704329000 + 6086044000) / 20}  # the ncu capture summarised under profiles/
-NCU_TRAFFIC_BIDIR = {"sha256": None, "bytes_per_launch": None}
+NCU_TRAFFIC_BIDIR = {"sha256": "67b8ea28bc7ac86b4641a06b2cd77d8aea5c204f9431f4d8b48c82b960594b67",
+                     # DRAM read + write of one phase-2 launch of k_bibfs (the ncu capture under profiles/)
+                     "bytes_per_launch": 20148118000 + 5032079000}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
 
@@ -301,12 +303,14 @@ def main():
                 inf = step(seed_base + k)
                 work += np.array(inf["work"], dtype=np.float64)
             eng.set_options(instrument=0, form=args.form)
-            return work.sum(axis=0)
+            return work
 
-        w = replay(args.form)
-        wb = w if args.form == "batched" else replay("batched")
+        work = replay(args.form)
+        w = work.sum(axis=0)
+        wb = w if args.form == "batched" else replay("batched").sum(axis=0)
         bfs_ms = sum(sum(i["bfs_ms"]) for i in infos)
         bfs_launches = sum(sum(i["bfs_launches"]) for i in infos)
+        bfs_share = bfs_ms / sum(times)
         if args.form == "batched":
             kernel, src_name, ncu = ("k_msbfs (batched sigma-BFS + backtrack; one persistent launch per phase, "
                                      "figures per batch of W lanes)", "msbfs.cu", NCU_TRAFFIC)
@@ -315,10 +319,14 @@ def main():
                          "union_frontier_edges": w[3], "truncated_bfs_edges": w[4], "bfs_samples": w[6]}
         else:
             kernel, src_name, ncu = ("k_bibfs (bidirectional sigma-BFS + backtrack, one block per sample; "
-                                     "one launch per phase)", "bibfs.cu", NCU_TRAFFIC_BIDIR)
+                                     "figures per phase-2 launch)", "bibfs.cu", NCU_TRAFFIC_BIDIR)
             # per edge scanned: column 4 B + level word 8 B; per count addition 8 B; per vertex reached:
-            # claim 8 B, queue 4 B, count read, write and clear 3 x 8 B
-            algo_bytes = 12.0 * w[0] + 8.0 * w[1] + 36.0 * w[2]
+            # claim 8 B, queue 4 B, count read, write and clear 3 x 8 B.  The unit is the phase-2 launch
+            # (one per step, ~98% of the samples).
+            w2 = work[1]
+            algo_bytes = 12.0 * w2[0] + 8.0 * w2[1] + 36.0 * w2[2]
+            bfs_ms = sum(i["bfs_ms"][1] for i in infos)
+            bfs_launches = sum(i["bfs_launches"][1] for i in infos)
             work_step = {"edges_scanned": w[0], "count_additions": w[1], "vertices_reached": w[2],
                          "bfs_samples": w[3], "one_sided_bfs_edges": wb[4]}
         per_launch_bytes = algo_bytes / max(bfs_launches, 1)
@@ -334,7 +342,7 @@ def main():
                               "avg_launch_ms": per_launch_s * 1000.0, "launches_per_step": bfs_launches / len(infos)}
         extras["gteps"] = wb[4] / t_total / 1e9 if wb[4] else None
         extras["work_per_step"] = {k: v / len(infos) for k, v in work_step.items()}
-        extras["bfs_share_of_step"] = bfs_ms / sum(times)
+        extras["bfs_share_of_step"] = bfs_share
 
         if not args.no_extras:
             # plain form: one BFS launch + one backtrack launch per sampled pair, same seed
