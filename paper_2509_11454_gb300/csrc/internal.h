@@ -68,6 +68,7 @@ struct percis_ctx {
     percis::DevBuf rp, col, irp, icol;  // irp/icol used only when directed
     int64_t vertex_diam = -1;
     percis::DevBuf vorder;  // vertices sorted by (highest-degree neighbour, id): lane order of sources
+    bool vorder_ready = false;
 
     // states and preprocessing
     bool have_states = false;
@@ -157,6 +158,7 @@ int grid_for(percis_ctx *ctx, int64_t work, int block);
 // prep.cu
 percis_status prep_graph(percis_ctx *ctx);  // transpose (directed), validation, VertexDiamUB
 percis_status prep_states(percis_ctx *ctx);  // sort, tables, C_v, lambda, d^
+percis_status prep_vorder(percis_ctx *ctx);  // lane order of the batched form (on first use)
 
 // sampler.cu
 percis_status sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag, int64_t i0, int64_t count, int32_t *s,

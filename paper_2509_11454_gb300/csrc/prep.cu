@@ -362,6 +362,37 @@ static percis_status merge_sort(percis_ctx *ctx, uint64_t *keys, int32_t *vals, 
     return PERCIS_OK;
 }
 
+// Lane order of batched sources: vertices sorted by (highest-degree neighbour,
+// id).  Only the batched form needs it, so it is built on first use.
+percis_status prep_vorder(percis_ctx *ctx) {
+    if (ctx->vorder_ready) return PERCIS_OK;
+    const int64_t n = ctx->n;
+    {
+        PERCIS_TRY(ensure(ctx, ctx->vorder, sizeof(int32_t) * n, "vertex order"));
+        DevBuf k1, k2, v2;
+        cudaError_t e = cudaMalloc(&k1.p, sizeof(uint64_t) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&k2.p, sizeof(uint64_t) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&v2.p, sizeof(int32_t) * n);
+        percis_status rs = PERCIS_OK;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rs = set_err(ctx, PERCIS_E_OOM, "vertex order scratch");
+        } else {
+            k_hub_keys<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                                     n, k1.as<uint64_t>(), ctx->vorder.as<int32_t>());
+            ctx->launches++;
+            rs = merge_sort(ctx, k1.as<uint64_t>(), ctx->vorder.as<int32_t>(), k2.as<uint64_t>(), v2.as<int32_t>(), n);
+        }
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(k1.p);
+        cudaFree(k2.p);
+        cudaFree(v2.p);
+        if (rs != PERCIS_OK) return rs;
+    }
+    ctx->vorder_ready = true;
+    return PERCIS_OK;
+}
+
 percis_status prep_graph(percis_ctx *ctx) {
     const int64_t n = ctx->n, nnz = ctx->nnz;
     PERCIS_TRY(ensure(ctx, ctx->status, 64, "status"));
@@ -416,29 +447,7 @@ percis_status prep_graph(percis_ctx *ctx) {
         if (rs != PERCIS_OK) return rs;
         PERCIS_CUDA(ctx, cudaGetLastError());
     }
-    {
-        // lane order of batched sources: grouped by highest-degree neighbour
-        PERCIS_TRY(ensure(ctx, ctx->vorder, sizeof(int32_t) * n, "vertex order"));
-        DevBuf k1, k2, v2;
-        cudaError_t e = cudaMalloc(&k1.p, sizeof(uint64_t) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&k2.p, sizeof(uint64_t) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&v2.p, sizeof(int32_t) * n);
-        percis_status rs = PERCIS_OK;
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            rs = set_err(ctx, PERCIS_E_OOM, "vertex order scratch");
-        } else {
-            k_hub_keys<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
-                                                                     n, k1.as<uint64_t>(), ctx->vorder.as<int32_t>());
-            ctx->launches++;
-            rs = merge_sort(ctx, k1.as<uint64_t>(), ctx->vorder.as<int32_t>(), k2.as<uint64_t>(), v2.as<int32_t>(), n);
-        }
-        cudaStreamSynchronize(ctx->stream);
-        cudaFree(k1.p);
-        cudaFree(k2.p);
-        cudaFree(v2.p);
-        if (rs != PERCIS_OK) return rs;
-    }
+    ctx->vorder_ready = false;  // built on first use by the batched form
     {
         const int64_t *irp = ctx->directed ? ctx->irp.as<int64_t>() : ctx->rp.as<int64_t>();
         PERCIS_CUDA(ctx, cudaMemsetAsync(st, 0, 64, ctx->stream));

@@ -145,6 +145,7 @@ percis_status group_by_source(percis_ctx *ctx, int64_t count, int64_t *n_sources
     long long *tmp2 = tmp + n + 1;              // n+1 scratch
     if (ctx->opt.lane_order == 1) {
         // sources in lane order: offsets and lane ids are scans over vorder
+        PERCIS_TRY(prep_vorder(ctx));
         const int32_t *perm = ctx->vorder.as<int32_t>();
         k_gather_ll<<<grid_for(ctx, n, block), block, 0, ctx->stream>>>(cnt, perm, n, tmp2);
         PERCIS_CHECK_LAUNCH(ctx, "gather counts");
