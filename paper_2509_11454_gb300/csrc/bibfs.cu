@@ -120,10 +120,10 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
     int32_t *const queue0 = a.queue + (slot * 2) * a.nslot, *const queue1 = queue0 + a.nslot;
 
     __shared__ long long s_i;
-    __shared__ long long s_lo[2], s_hi[2];
-    __shared__ uint32_t s_lev[2];
-    __shared__ unsigned long long s_cost[2], s_newcost;
-    __shared__ int s_new, s_meet;
+    // claims of a level go to counter set it % 3; thread 0 clears set (it + 1) % 3
+    // at the start of level it, two barriers after its last readers
+    __shared__ int s_new[3], s_meet;
+    __shared__ unsigned long long s_newcost[3];
     __shared__ int s_nm;
     __shared__ int32_t s_mv[kMeetCap];
     __shared__ C s_mw[kMeetCap];
@@ -163,27 +163,30 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
             info1[t] = pack(ep, 0);
             sig1[t] = C(1);
             queue1[0] = t;
-            s_cost[0] = (unsigned long long)(a.rp[s + 1] - a.rp[s]);
-            s_cost[1] = (unsigned long long)(a.irp[t + 1] - a.irp[t]);
-            for (int x = 0; x < 2; ++x) {
-                s_lo[x] = 0;
-                s_hi[x] = 1;
-                s_lev[x] = 0;
-            }
-            s_new = 0;
-            s_newcost = 0ull;
+            s_new[0] = 0;
+            s_newcost[0] = 0ull;
             s_meet = 0;
         }
         __syncthreads();
+        // level state of both sides, the same in every thread
+        long long qlo[2] = {0, 0}, qhi[2] = {1, 1};
+        uint32_t lev[2] = {0u, 0u};
+        unsigned long long cost[2] = {(unsigned long long)(a.rp[s + 1] - a.rp[s]),
+                                      (unsigned long long)(a.irp[t + 1] - a.irp[t])};
         int x = 0;
         bool met = s != t;
         if (met) {
             met = false;
-            for (;;) {
-                if (s_hi[0] == s_lo[0] || s_hi[1] == s_lo[1]) break;  // a side ran dry: t unreachable
-                x = s_cost[0] <= s_cost[1] ? 0 : 1;
-                const long long lo = s_lo[x], hi = s_hi[x];
-                const uint32_t nl = s_lev[x] + 1;
+            for (int it = 0;; ++it) {
+                if (qhi[0] == qlo[0] || qhi[1] == qlo[1]) break;  // a side ran dry: t unreachable
+                x = cost[0] <= cost[1] ? 0 : 1;
+                const long long lo = x ? qlo[1] : qlo[0], hi = x ? qhi[1] : qhi[0];
+                const uint32_t nl = (x ? lev[1] : lev[0]) + 1;
+                const int cs = it % 3;
+                if (threadIdx.x == 0) {
+                    s_new[(it + 1) % 3] = 0;
+                    s_newcost[(it + 1) % 3] = 0ull;
+                }
                 const unsigned long long want = pack(ep, nl);
                 unsigned long long ne = 0ull;
                 // level nl: claim unreached neighbours and add the counts over
@@ -205,8 +208,8 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                         const unsigned long long prev = atomicCAS(&infx[v], old, want);
                         if (prev == old) {
                             at = true;
-                            qx[hi + atomicAdd(&s_new, 1)] = v;
-                            atomicAdd(&s_newcost, (unsigned long long)(px[v + 1] - px[v]));
+                            qx[hi + atomicAdd(&s_new[cs], 1)] = v;
+                            atomicAdd(&s_newcost[cs], (unsigned long long)(px[v + 1] - px[v]));
                             if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) s_meet = 1;
                         } else {
                             at = prev == want;  // claimed in this level by another thread
@@ -220,15 +223,9 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 };
                 if (f <= kFlat) {
                     // the level's edges spread evenly over the block (a hub's
-                    // adjacency is not left to one warp): degree prefix sums of the
-                    // frontier in shared memory, each edge finds its vertex by bisection
-                    for (long long k = threadIdx.x; k < f; k += kBiBlock) {
-                        const int32_t u = qx[lo + k];
-                        s_fu[k] = u;
-                        s_fs[k] = __ldcg(&sigx[u]);
-                        s_pre[k] = (int32_t)(px[u + 1] - px[u]);
-                    }
-                    __syncthreads();
+                    // adjacency is not left to one warp): warp 0 loads the frontier and
+                    // writes its degree prefix sums to shared memory, each edge then
+                    // finds its vertex by bisection
                     if (warp == 0) {
                         constexpr int per = kFlat / 32;
                         int32_t loc[per];
@@ -236,8 +233,15 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
 #pragma unroll
                         for (int r = 0; r < per; ++r) {
                             const long long k = (long long)lane * per + r;
+                            int32_t dg = 0;
+                            if (k < f) {
+                                const int32_t u = qx[lo + k];
+                                s_fu[k] = u;
+                                s_fs[k] = __ldcg(&sigx[u]);
+                                dg = (int32_t)(px[u + 1] - px[u]);
+                            }
                             loc[r] = tot;
-                            tot += k < f ? s_pre[k] : 0;
+                            tot += dg;
                         }
                         int32_t incl = tot;
 #pragma unroll
@@ -245,12 +249,11 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             const int32_t t2 = __shfl_up_sync(0xffffffffu, incl, o);
                             if (lane >= o) incl += t2;
                         }
-                        const int32_t base = incl - tot;
-                        __syncwarp();
+                        const int32_t first = incl - tot;
 #pragma unroll
                         for (int r = 0; r < per; ++r) {
                             const long long k = (long long)lane * per + r;
-                            if (k < f) s_pre[k] = base + loc[r];
+                            if (k < f) s_pre[k] = first + loc[r];
                         }
                         if (lane == 31) s_pre[f] = incl;
                     }
@@ -278,15 +281,19 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 }
                 if (a.work && ne) atomicAdd(&s_work[0], ne);
                 __syncthreads();
-                if (threadIdx.x == 0) {
-                    s_lo[x] = hi;
-                    s_hi[x] = hi + s_new;
-                    s_lev[x] = nl;
-                    s_cost[x] = s_newcost;
-                    s_new = 0;
-                    s_newcost = 0ull;
+                const long long nh = hi + s_new[cs];
+                const unsigned long long nc = s_newcost[cs];
+                if (x) {
+                    qlo[1] = hi;
+                    qhi[1] = nh;
+                    lev[1] = nl;
+                    cost[1] = nc;
+                } else {
+                    qlo[0] = hi;
+                    qhi[0] = nh;
+                    lev[0] = nl;
+                    cost[0] = nc;
                 }
-                __syncthreads();
                 if (s_meet) {
                     met = true;
                     break;
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
             // meeting layer: level s_lev[x] of side x reached by the other side
             const Strided infy = x ? info0 : info1;
             const int32_t *qx = x ? queue1 : queue0;
-            const long long mlo = s_lo[x], mhi = s_hi[x];
+            const long long mlo = x ? qlo[1] : qlo[0], mhi = x ? qhi[1] : qhi[0];
             // the layer's members with their weights sigma_s sigma_t, kept in
             // shared memory when they fit
             if (threadIdx.x == 0) s_nm = 0;
@@ -447,11 +454,11 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
         // clear the counts this sample touched (every vertex either side reached)
         __syncthreads();
         if (a.work && threadIdx.x == 0) {
-            s_work[2] += (unsigned long long)(s_hi[0] + s_hi[1]);
+            s_work[2] += (unsigned long long)(qhi[0] + qhi[1]);
             s_work[3] += 1ull;
         }
-        for (long long q = threadIdx.x; q < s_hi[0]; q += kBiBlock) sig0[queue0[q]] = C(0);
-        for (long long q = threadIdx.x; q < s_hi[1]; q += kBiBlock) sig1[queue1[q]] = C(0);
+        for (long long q = threadIdx.x; q < qhi[0]; q += kBiBlock) sig0[queue0[q]] = C(0);
+        for (long long q = threadIdx.x; q < qhi[1]; q += kBiBlock) sig1[queue1[q]] = C(0);
     }
     if (a.work) {
 #pragma unroll
