@@ -369,7 +369,7 @@ void percis_destroy(percis_ctx *ctx) {
                       &ctx->src_fill, &ctx->src_off, &ctx->lane_of_v, &ctx->sorted_samples, &ctx->samp_lane,
                       &ctx->samp_t, &ctx->lane_src, &ctx->lane_off, &ctx->scratch, &ctx->red, &ctx->status,
                       &ctx->pc_tmp, &ctx->grad_tmp, &ctx->host_pinned, &ctx->vorder,
-                      &ctx->fq0, &ctx->fq1, &ctx->qstamp, &ctx->acc_ap,
+                      &ctx->fq0, &ctx->fq1, &ctx->acc_ap,
                       &ctx->ap_tau, &ctx->ap_stamp, &ctx->ap_list, &ctx->plan_dev, &ctx->bi_info,
                       &ctx->bi_queue};
     for (DevBuf *b : bufs)

@@ -85,15 +85,13 @@ struct percis_ctx {
     int32_t lanes_alloc = 0;
     int32_t levels_alloc = 0;
     int sigma_mode = 0;  // batched sigma storage: 0 = 32-bit, 1 = 64-bit integers, 2 = FP64
-    percis::DevBuf fq0, fq1, qstamp;  // frontier queues and per-vertex level stamps
+    percis::DevBuf fq0, fq1;  // frontier queues
     percis::DevBuf acc_ap, ap_tau, ap_stamp, ap_list;  // all-paths estimator
     percis::DevBuf plan_dev;                           // lane batches of a many-graph phase
     percis::DevBuf bi_info, bi_queue;                  // bidirectional form: per-slot scratch
     int64_t bi_slots = 0, bi_n = 0, bi_epoch = 0;
     int64_t ap_warps = 0, ap_n = 0;
     int32_t ap_epoch = 0;
-    int32_t stamp_base = 1;
-    int64_t max_indeg = 0;
 
     // samples of the last phase
     percis::DevBuf pair_s, pair_t, kind, ilen, path_off, arena, cnt, arena_top;

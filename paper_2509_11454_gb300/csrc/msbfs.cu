@@ -83,8 +83,6 @@ struct MsArgs {
     const int32_t *col;
     int32_t *fq0;
     int32_t *fq1;
-    int32_t *qstamp;
-    int32_t stamp_base;
     int32_t policy;                   // 0 = pull every level, 1 = push every level, 2 = by work estimate
     double push_alpha;                // policy 2: push while alpha * push work < pull work
     // instrumentation (INSTR variant only)
@@ -979,14 +977,8 @@ percis_status launch_ms_k(percis_ctx *ctx, int K, MsArgs &a) {
 percis_status ensure_ms(percis_ctx *ctx, int W, int Lcap, int64_t nr) {
     const int64_t n = nr;  // vertices of the largest launch range
     const int K = W / 64;
-    const bool fresh_stamps = ctx->qstamp.bytes < sizeof(int32_t) * (size_t)n;
     PERCIS_TRY(ensure(ctx, ctx->fq0, sizeof(int32_t) * n, "frontier queue"));
     PERCIS_TRY(ensure(ctx, ctx->fq1, sizeof(int32_t) * n, "frontier queue"));
-    PERCIS_TRY(ensure(ctx, ctx->qstamp, sizeof(int32_t) * n, "level stamps"));
-    if (fresh_stamps || ctx->stamp_base > (1 << 30)) {
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->qstamp.p, 0, sizeof(int32_t) * n, ctx->stream));
-        ctx->stamp_base = 1;
-    }
     PERCIS_TRY(ensure(ctx, ctx->vis, sizeof(uint64_t) * n * K, "visited bits"));
     PERCIS_TRY(ensure(ctx, ctx->fhist, sizeof(uint64_t) * n * K * (int64_t)(Lcap + 1), "frontier history"));
     PERCIS_TRY(ensure(ctx, ctx->sigmaW, sizeof(double) * n * W, "lane sigma"));
@@ -1011,15 +1003,8 @@ void fill_common(percis_ctx *ctx, MsArgs &a, int Lcap) {
     a.levdeg = nullptr;
     a.fq0 = ctx->fq0.as<int32_t>();
     a.fq1 = ctx->fq1.as<int32_t>();
-    a.qstamp = ctx->qstamp.as<int32_t>();
     a.policy = ctx->opt.direction;
     a.push_alpha = ctx->opt.push_alpha > 0.0 ? ctx->opt.push_alpha : 0.5;
-}
-
-// Each launch stamps its levels with fresh values, so the stamps never need clearing.
-void next_stamps(percis_ctx *ctx, MsArgs &a) {
-    a.stamp_base = ctx->stamp_base;
-    ctx->stamp_base += a.Lcap + 2;
 }
 
 }  // namespace
@@ -1156,7 +1141,6 @@ percis_status msbfs_full(percis_ctx *ctx, int32_t nsrc, const int32_t *sources, 
         a.nlanes = nsrc;
         a.remaining = ctx->remaining.as<int32_t>();
         a.full = 1;
-        next_stamps(ctx, a);
         PERCIS_TRY(launch_ms_k(ctx, K, a));
         MsCtl hc;
         PERCIS_CUDA(ctx, cudaMemcpyAsync(&hc, ctx->ms_ctl.p, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));

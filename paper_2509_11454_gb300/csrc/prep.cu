@@ -121,11 +121,28 @@ struct TableSlots {
     double x[kRing][kTile], t[kRing][kTile], w[kRing][kTile], c[kRing][kTile], r[kRing][kTile];
 };
 
+// Number of non-zero sorted states (xs is non-increasing and >= 0, so the
+// zeros form a suffix), by bisection, into the int64 word at dscal + 2.
+__global__ void k_nonzero_prefix(const double *xs, int64_t n, double *dscal) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t lo = 0, hi = n;  // first zero in [lo, hi]
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (xs[mid] == 0.0) hi = mid;
+        else lo = mid + 1;
+    }
+    *reinterpret_cast<long long *>(dscal + 2) = (long long)lo;
+}
+
 __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, double *w, double *ci, double *r,
                                                 double *dscal) {
     extern __shared__ __align__(16) unsigned char smem[];
     TableSlots &S = *reinterpret_cast<TableSlots *>(smem);
-    const int64_t T = (n + kTile - 1) / kTile;
+    // positions past the last non-zero state: x_i = 0 and every sum before them
+    // is +0, so w_i = c_i = r_i = 0 exactly; the scans start at the last non-zero one
+    const int64_t nz = *reinterpret_cast<const long long *>(dscal + 2);
+    for (int64_t i = nz + 1 + threadIdx.x; i <= n; i += blockDim.x) w[i] = ci[i] = r[i] = 0.0;
+    const int64_t T = (nz + kTile - 1) / kTile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wtid = threadIdx.x - 64, wcount = blockDim.x - 64;  // warps 2.. form the worker group
     if (threadIdx.x == 0) {
@@ -141,7 +158,7 @@ __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, dou
             const int64_t so = st - 4;  // write out
             if (so >= 0 && so < T) {
                 const int slot = (int)(so % kRing);
-                const int64_t hi = n - so * kTile;
+                const int64_t hi = nz - so * kTile;
                 const int cnt = (int)min((int64_t)kTile, hi);
                 const int64_t lo = hi - cnt + 1;
                 for (int k = wtid; k < cnt; k += wcount) {
@@ -152,7 +169,7 @@ __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, dou
             }
             if (st < T) {  // load tile st
                 const int slot = (int)(st % kRing);
-                const int64_t hi = n - st * kTile;
+                const int64_t hi = nz - st * kTile;
                 const int cnt = (int)min((int64_t)kTile, hi);
                 const int64_t lo = hi - cnt + 1;
                 for (int k = wtid; k < cnt; k += wcount) {
@@ -165,7 +182,7 @@ __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, dou
             const int64_t sc = st - 2;  // c_i of tile st-2
             if (sc >= 0 && sc < T) {
                 const int slot = (int)(sc % kRing);
-                const int cnt = (int)min((int64_t)kTile, n - sc * kTile);
+                const int cnt = (int)min((int64_t)kTile, nz - sc * kTile);
                 for (int k = wtid; k < cnt; k += wcount) {
                     const double cv = __dsub_rn(S.t[slot][k], S.w[slot][k]);
                     S.c[slot][k] = __double_as_longlong(cv) < 0 ? 0.0 : cv;
@@ -175,7 +192,7 @@ __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, dou
             const int64_t sw = st - 1;  // w over tile st-1
             if (sw >= 0 && sw < T) {
                 const int slot = (int)(sw % kRing);
-                const int cnt = (int)min((int64_t)kTile, n - sw * kTile);
+                const int cnt = (int)min((int64_t)kTile, nz - sw * kTile);
                 int k = cnt - 1;
                 // x is non-increasing in i, so a tile whose largest state (k = 0)
                 // is zero holds only zeros; while w is still zero, each sum is
@@ -202,7 +219,7 @@ __global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, dou
             const int64_t sr = st - 3;  // r over tile st-3
             if (sr >= 0 && sr < T) {
                 const int slot = (int)(sr % kRing);
-                const int cnt = (int)min((int64_t)kTile, n - sr * kTile);
+                const int cnt = (int)min((int64_t)kTile, nz - sr * kTile);
                 int k = cnt - 1;
                 // an all-zero tile of states has w = 0 and so c = 0 throughout
                 if (rn == 0.0 && S.x[slot][0] == 0.0) {
@@ -322,19 +339,6 @@ __global__ void k_hub_keys(const int64_t *rp, const int32_t *col, int64_t n, uin
     }
 }
 
-__global__ void k_max_rowlen(const int64_t *rp, int64_t n, unsigned long long *out) {
-    unsigned long long m = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const unsigned long long d = (unsigned long long)(rp[v + 1] - rp[v]);
-        m = m > d ? m : d;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
-        m = m > o ? m : o;
-    }
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
-}
 
 __global__ void k_indeg(const int32_t *col, int64_t nnz, long long *cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -448,16 +452,6 @@ percis_status prep_graph(percis_ctx *ctx) {
         PERCIS_CUDA(ctx, cudaGetLastError());
     }
     ctx->vorder_ready = false;  // built on first use by the batched form
-    {
-        const int64_t *irp = ctx->directed ? ctx->irp.as<int64_t>() : ctx->rp.as<int64_t>();
-        PERCIS_CUDA(ctx, cudaMemsetAsync(st, 0, 64, ctx->stream));
-        k_max_rowlen<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(irp, n, (unsigned long long *)st);
-        PERCIS_CHECK_LAUNCH(ctx, "max in-degree");
-        unsigned long long md = 0;
-        PERCIS_CUDA(ctx, cudaMemcpyAsync(&md, st, sizeof(md), cudaMemcpyDeviceToHost, ctx->stream));
-        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        ctx->max_indeg = (int64_t)md;
-    }
     if (!ctx->skip_diam) {
         int64_t D = 0;
         PERCIS_TRY(vertex_diam_ub(ctx, &D));
@@ -501,6 +495,8 @@ percis_status prep_states(percis_ctx *ctx) {
                                               (int)sizeof(TableSlots)));
         smem_set = true;
     }
+    k_nonzero_prefix<<<1, 32, 0, ctx->stream>>>(ctx->xs.as<double>(), n, ctx->dscal.as<double>());
+    PERCIS_CHECK_LAUNCH(ctx, "non-zero states");
     k_tables<<<1, 256, sizeof(TableSlots), ctx->stream>>>(ctx->xs.as<double>(), n, ctx->w.as<double>(),
                                                          ctx->ci.as<double>(), ctx->r.as<double>(),
                                                          ctx->dscal.as<double>());
