@@ -43,12 +43,12 @@ WORKLOAD_DESC = {
 }
 # DRAM traffic of one batched sigma-BFS launch from an ncu capture, valid only
 # for the kernel source it was taken on (sha256 of csrc/msbfs.cu).
-NCU_TRAFFIC = {"sha256": "ca2e6806ea9f3f5243f765b02c21eecae307c332c69e267183886b9109460557",
+NCU_TRAFFIC = {"sha256": "561848eed978b51f357614804897403671bbedfe50f75d5f87209cd665a35926",
                # DRAM read + write of one phase-2 launch (20 batches) / 20: bytes per batch of lanes
-               "bytes_per_launch": (10704329000 + 6086044000) / 20}  # the ncu capture summarised under profiles/
-NCU_TRAFFIC_BIDIR = {"sha256": "67b8ea28bc7ac86b4641a06b2cd77d8aea5c204f9431f4d8b48c82b960594b67",
+               "bytes_per_launch": (10701870000 + 6086926000) / 20}  # the ncu capture summarised under profiles/
+NCU_TRAFFIC_BIDIR = {"sha256": "8505f79176000f5b5d35e2027983ad77aa7bd041bf45643b4540249359de658b",
                      # DRAM read + write of one phase-2 launch of k_bibfs (the ncu capture under profiles/)
-                     "bytes_per_launch": 20148118000 + 5032079000}
+                     "bytes_per_launch": 19924318000 + 4805433000}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
 
