@@ -97,29 +97,198 @@ __global__ void k_gather_sorted(const double *x, const int32_t *perm, int64_t n,
 }
 
 // ------------------------------------------------------- Algorithm 2 scan
-// The preprocessing recurrence of Algorithm 2 is evaluated sequentially in
-// exactly its order (i = n down to 1) so that w, c_i, r and c are
-// bit-identical to any other sequential evaluation: the sampled pairs depend
-// on them through exact comparisons.
-//
-// On this GPU a warp-wide FP64 add occupies its sub-partition's FP64 pipe for
-// ~64 cycles, so one thread can retire about one FP64 operation per 64 cycles
-// whatever the dependences.  The three sequential parts therefore run on
-// different warps (different sub-partitions) and everything parallel runs on
-// the rest of the block:
-//   warp 0 (one lane):  w_i = w_{i+1} + x_i                 (one add per element)
-//   warps 2..7:         c_i = max(0, (n-i+1) x_i - w_i)     (parallel)
-//   warp 1 (one lane):  r_i = r_{i+1} + c_i                 (one add per element)
-// and c = r_1 (Algorithm 2 accumulates c over the same c_i in the same order
-// as r).  Tiles of 512 elements flow through a four-slot ring, one stage per
-// tile: stage s loads tile s, adds w over tile s-1, computes c_i of tile s-2,
-// adds r over tile s-3 and writes tile s-4 out.
-constexpr int kTile = 512;
-constexpr int kRing = 4;
+// The recurrences of Algorithm 2 (w_i = w_{i+1} + x_i, c_i = max(0, (n-i+1) x_i - w_i),
+// r_i = r_{i+1} + c_i for i = n down to 1, and c = r_1) are chains of FP64 roundings
+// whose results the sampler compares exactly, so w and r must equal the sequential
+// evaluation bit for bit.  A dependent chain of FP64 adds is slow on this GPU (its
+// FP64 pipe is narrow), so the two running sums are evaluated in parallel, exactly:
+//  - every term is >= 0, so a running sum s never decreases and stays in one binade
+//    for long stretches.  Inside a binade the doubles are the integer multiples of
+//    u = ulp(s) (the subnormals and the lowest normal binade share u = 2^-1074), so
+//    fl(s + a) = u * RNE(s/u + a/u) while the result stays below the binade's top:
+//    an integer addition.
+//  - a/u rounds to q or q + 1 from its own bits alone, except at an exact halfway
+//    point, where ties-to-even picks by the parity of s/u before the term.  Each term
+//    is therefore a map (parity in) -> (parity out, integer added); these maps compose
+//    associatively, so one block-wide scan over them gives every running sum of a
+//    chunk of terms at once.
+//  - the first term whose sum reaches the top of the binade is added with one
+//    hardware FP64 add, and the chunk restarts after it in the new binade (a
+//    non-decreasing sum enters each binade once).
+// Both evaluations give the correctly rounded sum of the same operands in the same
+// order (IEEE 754 round to nearest, ties to even) at every step, hence equal results.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;  // terms per thread and chunk
+constexpr int kScanChunk = kScanThreads * kScanPer;
+constexpr unsigned long long kTwo53u = 1ull << 53;
+constexpr int kNoTerm = 0x7fffffff;
 
-struct TableSlots {
-    double x[kRing][kTile], t[kRing][kTile], w[kRing][kTile], c[kRing][kTile], r[kRing][kTile];
+// map of a run of terms: for parity p of s/u before the run, d0 / d1 is the integer
+// added and bit p of par the parity after it
+struct ParityMap {
+    unsigned long long d0, d1;
+    unsigned par;
 };
+
+__device__ __forceinline__ ParityMap pm_identity() { return ParityMap{0ull, 0ull, 2u}; }
+
+// the run f followed by the run g
+__device__ __forceinline__ ParityMap pm_then(const ParityMap &f, const ParityMap &g) {
+    const unsigned f0 = f.par & 1u, f1 = (f.par >> 1) & 1u;
+    ParityMap h;
+    h.d0 = f.d0 + (f0 ? g.d1 : g.d0);
+    h.d1 = f.d1 + (f1 ? g.d1 : g.d0);
+    h.par = ((g.par >> f0) & 1u) | (((g.par >> f1) & 1u) << 1);
+    return h;
+}
+
+__device__ __forceinline__ ParityMap pm_shfl_up(const ParityMap &m, int off) {
+    ParityMap o;
+    o.d0 = __shfl_up_sync(0xffffffffu, m.d0, off);
+    o.d1 = __shfl_up_sync(0xffffffffu, m.d1, off);
+    o.par = __shfl_up_sync(0xffffffffu, m.par, off);
+    return o;
+}
+
+// one term a >= 0 against a running sum whose binade has exponent field e (>= 1):
+// q = a/u rounded down and the rounding kind (0 exact or down, 1 up, 2 halfway,
+// 3 a alone reaches the top of the binade), and the term's map
+__device__ __forceinline__ ParityMap term_map(double a, int e, unsigned long long &q, int &kind) {
+    const unsigned long long ab = (unsigned long long)__double_as_longlong(a);
+    const int ea = (int)((ab >> 52) & 0x7ff);
+    ParityMap m;
+    if (ea > e) {
+        q = kTwo53u;
+        kind = 3;
+        m.d0 = m.d1 = kTwo53u;
+        m.par = 0u;
+        return m;
+    }
+    const unsigned long long ma = (ab & ((1ull << 52) - 1)) | (ea ? (1ull << 52) : 0ull);
+    const int sh = e - max(ea, 1);  // a / u = ma / 2^sh
+    kind = 0;
+    if (sh == 0) {
+        q = ma;
+    } else if (sh > 54) {  // below half a unit
+        q = 0ull;
+    } else {
+        q = ma >> sh;
+        const unsigned long long rem = ma & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        kind = rem > half ? 1 : (rem == half ? 2 : 0);
+    }
+    if (kind == 2) {  // the even neighbour for either parity: parity 0 after
+        m.d0 = q + (q & 1ull);
+        m.d1 = q + 1ull - (q & 1ull);
+        m.par = 0u;
+    } else {
+        const unsigned long long R = q + (unsigned long long)kind;
+        const unsigned b = (unsigned)(R & 1ull);
+        m.d0 = m.d1 = R;
+        m.par = b | ((b ^ 1u) << 1);
+    }
+    return m;
+}
+
+// Running sums s_i = fl(s_{i+1} + a_i) for i = m down to 1 (s_{m+1} = +0), with
+// a_i = src[i + soff] >= 0, written to dst[i]; returns s_1 (+0 when m = 0).  The
+// whole block calls it.
+__device__ double exact_running_sum(const double *src, int64_t soff, double *dst, int64_t m) {
+    __shared__ ParityMap s_wmap[kScanThreads / 32];
+    __shared__ int s_kstar[2];
+    __shared__ double s_sum;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_kstar[0] = s_kstar[1] = kNoTerm;
+    __syncthreads();
+    double s = 0.0;
+    int64_t pos = m;  // positions pos, pos - 1, ..., 1 remain; term k of a chunk sits at pos - k
+    for (int pass = 0; pos > 0; ++pass) {
+        const int cnt = pos < (int64_t)kScanChunk ? (int)pos : kScanChunk;
+        const unsigned long long sb = (unsigned long long)__double_as_longlong(s);
+        const int es = (int)((sb >> 52) & 0x7ff);
+        const int e = max(es, 1);
+        const unsigned long long S0 = (sb & ((1ull << 52) - 1)) | (es ? (1ull << 52) : 0ull);
+        const unsigned long long top = (unsigned long long)(e - 1) << 52;  // bits of u * S are top + S
+        double a[kScanPer];
+        unsigned long long q[kScanPer];
+        int kind[kScanPer];
+        ParityMap mine = pm_identity();
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            const int k = tid * kScanPer + j;
+            a[j] = k < cnt ? src[pos - k + soff] : 0.0;
+            mine = pm_then(mine, term_map(a[j], e, q[j], kind[j]));
+        }
+        // scan of the maps: within the warp, then over the warps
+        ParityMap inc = mine;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const ParityMap o = pm_shfl_up(inc, off);
+            if (lane >= off) inc = pm_then(o, inc);
+        }
+        ParityMap exc = pm_shfl_up(inc, 1);
+        if (lane == 0) exc = pm_identity();
+        if (lane == 31) s_wmap[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            ParityMap wm = lane < kScanThreads / 32 ? s_wmap[lane] : pm_identity();
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const ParityMap o = pm_shfl_up(wm, off);
+                if (lane >= off) wm = pm_then(o, wm);
+            }
+            ParityMap we = pm_shfl_up(wm, 1);
+            if (lane == 0) we = pm_identity();
+            if (lane < kScanThreads / 32) s_wmap[lane] = we;  // runs of the warps before each warp
+        }
+        __syncthreads();
+        const ParityMap pre = pm_then(s_wmap[warp], exc);
+        // this thread's terms under the true parity of S0
+        const unsigned p0 = (unsigned)(S0 & 1ull);
+        unsigned p = (pre.par >> p0) & 1u;
+        unsigned long long acc = p0 ? pre.d1 : pre.d0;  // integer added before this thread's terms
+        unsigned long long before[kScanPer];
+        int first = kNoTerm;
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            const int k = tid * kScanPer + j;
+            before[j] = acc;
+            unsigned long long R;
+            if (kind[j] == 2) {
+                R = q[j] + ((q[j] ^ (unsigned long long)p) & 1ull);
+                p = 0u;
+            } else {
+                R = q[j] + (unsigned long long)(kind[j] & 1);
+                p ^= (unsigned)(R & 1ull);
+            }
+            acc += R;
+            // sums before the first term that leaves the binade stay below 2^54: no wrap
+            if (k < cnt && first == kNoTerm && (kind[j] == 3 || S0 + acc >= kTwo53u)) first = k;
+        }
+        const int slot = pass & 1;
+        if (first != kNoTerm) atomicMin(&s_kstar[slot], first);
+        __syncthreads();
+        const int kstar = min(s_kstar[slot], cnt);  // terms before kstar stay in the binade
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            const int k = tid * kScanPer + j;
+            const unsigned long long after = j + 1 < kScanPer ? before[j + 1] : acc;
+            if (k < kstar) dst[pos - k] = __longlong_as_double((long long)(top + S0 + after));
+            if (k == kstar - 1 && kstar == cnt) s_sum = __longlong_as_double((long long)(top + S0 + after));
+            if (k == kstar && kstar < cnt) {
+                // the term that leaves the binade: one hardware add from the sum before it
+                const double prev = k == 0 ? s : __longlong_as_double((long long)(top + S0 + before[j]));
+                const double nv = __dadd_rn(prev, a[j]);
+                dst[pos - k] = nv;
+                s_sum = nv;
+            }
+        }
+        if (tid == 0) s_kstar[slot ^ 1] = kNoTerm;  // for the next pass
+        __syncthreads();
+        s = s_sum;
+        pos -= kstar < cnt ? kstar + 1 : cnt;
+    }
+    return s;
+}
 
 // Number of non-zero sorted states (xs is non-increasing and >= 0, so the
 // zeros form a suffix), by bisection, into the int64 word at dscal + 2.
@@ -134,116 +303,24 @@ __global__ void k_nonzero_prefix(const double *xs, int64_t n, double *dscal) {
     *reinterpret_cast<long long *>(dscal + 2) = (long long)lo;
 }
 
-__global__ void __launch_bounds__(256) k_tables(const double *xs, int64_t n, double *w, double *ci, double *r,
-                                                double *dscal) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    TableSlots &S = *reinterpret_cast<TableSlots *>(smem);
+__global__ void __launch_bounds__(kScanThreads) k_tables(const double *xs, int64_t n, double *w, double *ci,
+                                                         double *r, double *dscal) {
     // positions past the last non-zero state: x_i = 0 and every sum before them
     // is +0, so w_i = c_i = r_i = 0 exactly; the scans start at the last non-zero one
     const int64_t nz = *reinterpret_cast<const long long *>(dscal + 2);
-    for (int64_t i = nz + 1 + threadIdx.x; i <= n; i += blockDim.x) w[i] = ci[i] = r[i] = 0.0;
-    const int64_t T = (nz + kTile - 1) / kTile;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wtid = threadIdx.x - 64, wcount = blockDim.x - 64;  // warps 2.. form the worker group
-    if (threadIdx.x == 0) {
-        w[n + 1] = 0.0;
-        r[n + 1] = 0.0;
-        ci[n + 1] = 0.0;
-        w[0] = r[0] = ci[0] = 0.0;
+    for (int64_t i = nz + 1 + threadIdx.x; i <= n + 1; i += blockDim.x) w[i] = ci[i] = r[i] = 0.0;
+    if (threadIdx.x == 0) w[0] = r[0] = ci[0] = 0.0;
+    // w_i over x_i = xs[i - 1]
+    exact_running_sum(xs, -1, w, nz);
+    __syncthreads();
+    for (int64_t i = 1 + threadIdx.x; i <= nz; i += blockDim.x) {
+        const double t = __dmul_rn((double)(n - i + 1), xs[i - 1]);
+        const double cv = __dsub_rn(t, w[i]);
+        ci[i] = __double_as_longlong(cv) < 0 ? 0.0 : cv;  // max(0, .), -0 -> +0
     }
-    double wn = 0.0, rn = 0.0;
-    // tile s covers positions i in [hi - cnt + 1, hi], hi = n - s * kTile; local k = i - lo
-    for (int64_t st = 0; st < T + 4; ++st) {
-        if (warp >= 2) {
-            const int64_t so = st - 4;  // write out
-            if (so >= 0 && so < T) {
-                const int slot = (int)(so % kRing);
-                const int64_t hi = nz - so * kTile;
-                const int cnt = (int)min((int64_t)kTile, hi);
-                const int64_t lo = hi - cnt + 1;
-                for (int k = wtid; k < cnt; k += wcount) {
-                    w[lo + k] = S.w[slot][k];
-                    ci[lo + k] = S.c[slot][k];
-                    r[lo + k] = S.r[slot][k];
-                }
-            }
-            if (st < T) {  // load tile st
-                const int slot = (int)(st % kRing);
-                const int64_t hi = nz - st * kTile;
-                const int cnt = (int)min((int64_t)kTile, hi);
-                const int64_t lo = hi - cnt + 1;
-                for (int k = wtid; k < cnt; k += wcount) {
-                    const int64_t i = lo + k;
-                    const double xi = xs[i - 1];
-                    S.x[slot][k] = xi;
-                    S.t[slot][k] = __dmul_rn((double)(n - i + 1), xi);
-                }
-            }
-            const int64_t sc = st - 2;  // c_i of tile st-2
-            if (sc >= 0 && sc < T) {
-                const int slot = (int)(sc % kRing);
-                const int cnt = (int)min((int64_t)kTile, nz - sc * kTile);
-                for (int k = wtid; k < cnt; k += wcount) {
-                    const double cv = __dsub_rn(S.t[slot][k], S.w[slot][k]);
-                    S.c[slot][k] = __double_as_longlong(cv) < 0 ? 0.0 : cv;
-                }
-            }
-        } else if (warp == 0 && lane == 0) {
-            const int64_t sw = st - 1;  // w over tile st-1
-            if (sw >= 0 && sw < T) {
-                const int slot = (int)(sw % kRing);
-                const int cnt = (int)min((int64_t)kTile, nz - sw * kTile);
-                int k = cnt - 1;
-                // x is non-increasing in i, so a tile whose largest state (k = 0)
-                // is zero holds only zeros; while w is still zero, each sum is
-                // exactly +0 and the dependent adds can be skipped
-                if (wn == 0.0 && S.x[slot][0] == 0.0) {
-                    for (; k >= 0; --k) S.w[slot][k] = 0.0;
-                }
-                for (; k >= 7; k -= 8) {  // operands loaded ahead of the dependent adds
-                    double v[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) v[j] = S.x[slot][k - j];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        wn = __dadd_rn(wn, v[j]);
-                        S.w[slot][k - j] = wn;
-                    }
-                }
-                for (; k >= 0; --k) {
-                    wn = __dadd_rn(wn, S.x[slot][k]);
-                    S.w[slot][k] = wn;
-                }
-            }
-        } else if (warp == 1 && lane == 0) {
-            const int64_t sr = st - 3;  // r over tile st-3
-            if (sr >= 0 && sr < T) {
-                const int slot = (int)(sr % kRing);
-                const int cnt = (int)min((int64_t)kTile, nz - sr * kTile);
-                int k = cnt - 1;
-                // an all-zero tile of states has w = 0 and so c = 0 throughout
-                if (rn == 0.0 && S.x[slot][0] == 0.0) {
-                    for (; k >= 0; --k) S.r[slot][k] = 0.0;
-                }
-                for (; k >= 7; k -= 8) {
-                    double v[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) v[j] = S.c[slot][k - j];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        rn = __dadd_rn(rn, v[j]);
-                        S.r[slot][k - j] = rn;
-                    }
-                }
-                for (; k >= 0; --k) {
-                    rn = __dadd_rn(rn, S.c[slot][k]);
-                    S.r[slot][k] = rn;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    if (warp == 1 && lane == 0) dscal[0] = rn;  // c = r_1
+    __syncthreads();
+    const double c = exact_running_sum(ci, 0, r, nz);
+    if (threadIdx.x == 0) dscal[0] = c;  // c = r_1
 }
 
 // C_v = c - A_v with A_i = (w_1 - w_i) - (i-1) x_i + (n-i) x_i - w_{i+1} for
@@ -489,15 +566,9 @@ percis_status prep_states(percis_ctx *ctx) {
     PERCIS_TRY(merge_sort(ctx, k1, perm, k2, v2, n));
     k_gather_sorted<<<g, 256, 0, ctx->stream>>>(ctx->x.as<double>(), perm, n, ctx->xs.as<double>());
     PERCIS_CHECK_LAUNCH(ctx, "gather sorted");
-    static bool smem_set = false;
-    if (!smem_set) {
-        PERCIS_CUDA(ctx, cudaFuncSetAttribute(k_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)sizeof(TableSlots)));
-        smem_set = true;
-    }
     k_nonzero_prefix<<<1, 32, 0, ctx->stream>>>(ctx->xs.as<double>(), n, ctx->dscal.as<double>());
     PERCIS_CHECK_LAUNCH(ctx, "non-zero states");
-    k_tables<<<1, 256, sizeof(TableSlots), ctx->stream>>>(ctx->xs.as<double>(), n, ctx->w.as<double>(),
+    k_tables<<<1, kScanThreads, 0, ctx->stream>>>(ctx->xs.as<double>(), n, ctx->w.as<double>(),
                                                          ctx->ci.as<double>(), ctx->r.as<double>(),
                                                          ctx->dscal.as<double>());
     PERCIS_CHECK_LAUNCH(ctx, "tables");

@@ -86,6 +86,44 @@ def test_prep_bitexact(binding, gcase):
     eng.close()
 
 
+def _adversarial_states(kind, n, seed):
+    """State vectors that stress the exact evaluation of the Algorithm 2 running sums:
+    halfway roundings, subnormal and tiny terms, long runs of zero c_i, many binades."""
+    rng = np.random.default_rng(seed)
+    if kind == "halfway":  # 40-bit significands: once w passes 2^13 every other term is a tie
+        return rng.integers(2 ** 39, 2 ** 40, n).astype(np.float64) * 2.0 ** -40
+    if kind == "dyadic":  # few significant bits: most sums exact, some halfway
+        return rng.integers(1, 4097, n).astype(np.float64) / 4096.0
+    if kind == "subnormal":
+        pool = np.array([0.0, 5e-324, 7e-322, 1e-310, 2.2250738585072014e-308, 1e-300, 1e-20, 0.5, 1.0])
+        return np.where(rng.random(n) < 0.5, pool[rng.integers(0, len(pool), n)], rng.random(n))
+    if kind == "equal":  # 90% equal smallest states: c_i = 0 over them, so r starts with a run of +0
+        return np.where(rng.random(n) < 0.9, 0.375, 0.5 + 0.5 * rng.random(n))
+    if kind == "binades":  # values over ~300 decades: the sums cross many binades
+        return rng.random(n) * 10.0 ** (-rng.random(n) * 300.0)
+    if kind == "large":  # several chunks of terms
+        return rng.random(n)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind,n", [("halfway", 30000), ("dyadic", 20000), ("subnormal", 6000),
+                                    ("equal", 5000), ("binades", 8000), ("large", 300000)])
+def test_tables_bitexact_adversarial(binding, kind, n):
+    """w, c_i, r and c equal the sequential FP64 evaluation of Algorithm 2 bit for bit."""
+    x = _adversarial_states(kind, n, 5)
+    g = synth.barabasi_albert(n, 2, 0)  # the tables do not depend on the graph
+    eng = _engine(binding, g, x)
+    got = eng.prep()
+    prep = oracle.prepare(x, cv_method="sorted")
+    assert np.array_equal(_np(got["xs"]), prep.xs)
+    for k in ("w", "ci", "r"):
+        a, b = _np(got[k]), getattr(prep, k)
+        assert np.array_equal(a.view(np.int64), b.view(np.int64)), (k, int(np.sum(a != b)))
+    assert got["c"] == prep.c
+    assert np.array_equal(_np(got["Cv"]), prep.Cv)
+    eng.close()
+
+
 def test_pairs_bitexact(binding, gcase):
     name, g, og = gcase
     x = _states(name, g.n)
