@@ -208,8 +208,21 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                         const unsigned long long prev = atomicCAS(&infx[v], old, want);
                         if (prev == old) {
                             at = true;
-                            qx[hi + atomicAdd(&s_new[cs], 1)] = v;
-                            atomicAdd(&s_newcost[cs], (unsigned long long)(px[v + 1] - px[v]));
+                            // the lanes that claimed together reserve their queue slots and
+                            // add their degrees with one shared atomic each (a 64-bit shared
+                            // add would be a contended compare-and-swap loop per lane)
+                            const unsigned grp = __activemask();
+                            const int lead = __ffs(grp) - 1;
+                            const uint32_t dg = (uint32_t)(px[v + 1] - px[v]);  // < 2^31
+                            const uint32_t dlo = __reduce_add_sync(grp, dg & 0xffffu);
+                            const uint32_t dhi = __reduce_add_sync(grp, dg >> 16);
+                            int q0 = 0;
+                            if (lane == lead) {
+                                q0 = atomicAdd(&s_new[cs], __popc(grp));
+                                atomicAdd(&s_newcost[cs], ((unsigned long long)dhi << 16) + dlo);
+                            }
+                            q0 = __shfl_sync(grp, q0, lead);
+                            qx[hi + q0 + __popc(grp & ((1u << lane) - 1u))] = v;
                             if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) s_meet = 1;
                         } else {
                             at = prev == want;  // claimed in this level by another thread
