@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                         if ((double)(o + su) >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
                     }
                 };
-                if (f <= kFlat) {
+                // (the flat form keeps the level's edge offsets in 32 bits)
+                if (f <= kFlat && (x ? cost[1] : cost[0]) < (1ull << 31)) {
                     // the level's edges spread evenly over the block (a hub's
                     // adjacency is not left to one warp): warp 0 loads the frontier and
                     // writes its degree prefix sums to shared memory, each edge then
