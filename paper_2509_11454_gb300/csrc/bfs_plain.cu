@@ -33,6 +33,7 @@ struct PlainArgs {
     int64_t idx;
     int32_t s_host, t_host;
     int32_t epoch;
+    int32_t levels_only;  // levels (eccentricity) only: no path counts
     uint64_t budget_ns;
 };
 
@@ -50,6 +51,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_bfs(PlainArgs a) {
         a.qa[0] = s;
         ctl->qsize[0] = 1;
         ctl->qsize[1] = 0;
+        ctl->qsize[2] = 0;
         ctl->level = 0;
         ctl->found = 0;
     }
@@ -60,7 +62,9 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_bfs(PlainArgs a) {
     int32_t *cur = a.qa, *nxt = a.qb;
     int L = 0, ecc = 0;
     for (;;) {
-        const int nq = (int)ld_relaxed_u32((const uint32_t *)&ctl->qsize[L & 1]);
+        const int nq = (int)ld_relaxed_u32((const uint32_t *)&ctl->qsize[L % 3]);
+        // the slot level L + 2 will fill: last read before the previous barrier
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->qsize[(L + 2) % 3] = 0;
         // expand level L: claim undiscovered out-neighbours
         for (int64_t k = gwarp; k < nq; k += nwarps) {
             const int32_t u = __ldcg(&cur[k]);
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_bfs(PlainArgs a) {
                 if (m) {
                     const int leader = __ffs(m) - 1;
                     int base_pos = 0;
-                    if (lane == leader) base_pos = atomicAdd(&ctl->qsize[(L + 1) & 1], __popc(m));
+                    if (lane == leader) base_pos = atomicAdd(&ctl->qsize[(L + 1) % 3], __popc(m));
                     base_pos = __shfl_sync(0xffffffffu, base_pos, leader);
                     if (mine) {
                         const int pos = base_pos + __popc(m & ((1u << lane) - 1u));
@@ -88,10 +92,9 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_bfs(PlainArgs a) {
             }
         }
         if (!grid_sync(bar, status, a.budget_ns)) return;
-        const int nn = (int)ld_relaxed_u32((const uint32_t *)&ctl->qsize[(L + 1) & 1]);
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->qsize[L & 1] = 0;
+        const int nn = (int)ld_relaxed_u32((const uint32_t *)&ctl->qsize[(L + 1) % 3]);
         // sigma of the new level: pull over in-neighbours at level L
-        for (int64_t k = gwarp; k < nn; k += nwarps) {
+        for (int64_t k = gwarp; k < nn && !a.levels_only; k += nwarps) {
             const int32_t wv = __ldcg(&nxt[k]);
             const int64_t e0 = a.irp[wv], e1 = a.irp[wv + 1];
             double acc = 0.0;
@@ -107,7 +110,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_bfs(PlainArgs a) {
                 if (wv == t) atomicExch(&ctl->found, 1);
             }
         }
-        if (!grid_sync(bar, status, a.budget_ns)) return;
+        // (levels only: no target, so the exit test below reads nn alone)
+        if (!a.levels_only && !grid_sync(bar, status, a.budget_ns)) return;
         ++L;
         if (nn > 0) ecc = L;
         if (nn == 0) break;
@@ -124,6 +128,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_bfs(PlainArgs a) {
         ctl->level = ecc;
         ctl->qsize[0] = 0;
         ctl->qsize[1] = 0;
+        ctl->qsize[2] = 0;
     }
 }
 
@@ -252,7 +257,7 @@ static percis_status ensure_plain(percis_ctx *ctx) {
 }
 
 percis_status plain_bfs(percis_ctx *ctx, const int32_t *s_dev, const int32_t *t_dev, int64_t idx, int32_t s_host,
-                        int32_t t_host) {
+                        int32_t t_host, bool levels_only) {
     PERCIS_TRY(ensure_plain(ctx));
     ctx->epoch++;
     PlainArgs a;
@@ -274,6 +279,7 @@ percis_status plain_bfs(percis_ctx *ctx, const int32_t *s_dev, const int32_t *t_
     a.s_host = s_host;
     a.t_host = t_host;
     a.epoch = ctx->epoch;
+    a.levels_only = levels_only ? 1 : 0;
     a.budget_ns = (uint64_t)(ctx->opt.timeout_s * 1e9);
     void *args[] = {&a};
     PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_plain_bfs, dim3(g_plain_grid), dim3(kPlainBlock),
@@ -336,7 +342,7 @@ percis_status vertex_diam_ub(percis_ctx *ctx, int64_t *D) {
         PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         if (key == 0) break;
         const int32_t v = (int32_t)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
-        PERCIS_TRY(plain_bfs(ctx, nullptr, nullptr, 0, v, -1));
+        PERCIS_TRY(plain_bfs(ctx, nullptr, nullptr, 0, v, -1, true));
         PlainCtl hc;
         PERCIS_CUDA(ctx, cudaMemcpyAsync(&hc, ctx->plain_ctl.p, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
         PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

@@ -44,10 +44,9 @@ struct alignas(16) MsCtl {
 struct PlainCtl {
     uint32_t bar_count, bar_gen;
     uint32_t status;
-    int32_t qsize[2];
+    int32_t qsize[3];  // queue sizes, level L in slot L % 3
     int32_t level;
     int32_t found;
-    int32_t pad;
 };
 
 }  // namespace percis
@@ -166,7 +165,7 @@ percis_status group_by_source(percis_ctx *ctx, int64_t count, int64_t *n_sources
 
 // bfs_plain.cu
 percis_status plain_bfs(percis_ctx *ctx, const int32_t *s_dev, const int32_t *t_dev, int64_t idx, int32_t s_host,
-                        int32_t t_host);
+                        int32_t t_host, bool levels_only = false);
 percis_status plain_backtrack(percis_ctx *ctx, uint64_t seed, uint32_t tag, int64_t idx);
 percis_status plain_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count);
 percis_status plain_dist_sigma(percis_ctx *ctx, int32_t *dist, double *sigma);
