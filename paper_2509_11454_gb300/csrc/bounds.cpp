@@ -4,6 +4,7 @@
 // (ln(4 d^ rho^ / (x delta))).
 #include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "internal.h"
 
@@ -28,12 +29,25 @@ double objective(double x, double eps, double delta, double dhat, double rho_h) 
 // sup over (0, x^]: the paper gives no method.  Maximum over the geometric
 // grid x_k = x^ 10^(-12 + 12 k / 4096), k = 0..4096, then 100 golden-section
 // steps on [x_{k*-1}, x_{k*+1}] around the best grid point.
+constexpr int kGrid = 4096;
+
+// the grid factors 10^(-12 + 12 k / 4096), computed once (the same values each call)
+const double *grid_factors() {
+    static const std::vector<double> f = [] {
+        std::vector<double> v(kGrid + 1);
+        for (int k = 0; k <= kGrid; ++k) v[k] = std::pow(10.0, -12.0 + 12.0 * k / kGrid);
+        return v;
+    }();
+    return f.data();
+}
+
 double sup_objective(double eps, double delta, double dhat, double rho_h, double xh) {
-    const int K = 4096;
+    const int K = kGrid;
+    const double *gf = grid_factors();
     double best = -INFINITY;
     int best_k = 0;
     for (int k = 0; k <= K; ++k) {
-        const double xk = xh * std::pow(10.0, -12.0 + 12.0 * k / K);
+        const double xk = xh * gf[k];
         const double fv = objective(xk, eps, delta, dhat, rho_h);
         if (fv > best) {
             best = fv;
@@ -42,8 +56,8 @@ double sup_objective(double eps, double delta, double dhat, double rho_h, double
     }
     const int klo = best_k - 1 < 0 ? 0 : best_k - 1;
     const int khi = best_k + 1 > K ? K : best_k + 1;
-    double a = xh * std::pow(10.0, -12.0 + 12.0 * klo / K);
-    double b = xh * std::pow(10.0, -12.0 + 12.0 * khi / K);
+    double a = xh * gf[klo];
+    double b = xh * gf[khi];
     const double gr = (std::sqrt(5.0) - 1.0) / 2.0;
     double c1 = b - gr * (b - a);
     double c2 = a + gr * (b - a);
