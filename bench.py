@@ -28,6 +28,7 @@ import subprocess
 import sys
 import tempfile
 import time
+import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -68,7 +69,7 @@ def _sha(path):
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -76,16 +77,26 @@ class Clocks:
         self.index = index
         self.proc = None
         self.path = None
+        self.window = None
 
     def start(self):
+        """Starts sampling every 25 ms and returns once the first sample is in."""
         fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
+
+    def mark(self, t0: float, t1: float):
+        """The timed region in host wall-clock seconds: samples outside it are dropped."""
+        self.window = (t0, t1)
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -95,22 +106,33 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
+                if len(parts) < 10:
                     continue
                 try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                except (ValueError, IndexError):
+                    ts = None
+                try:
+                    rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
                 except ValueError:
                     continue
-                for nm, val in zip(names, parts[5:9]):
-                    if val.lower().startswith("active"):
-                        reasons.add(nm)
         os.unlink(self.path)
+        inside = rows
+        if self.window and all(r[0] is not None for r in rows):
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 - 0.03 <= r[0] <= t1 + 0.03]
+            if not inside:  # a region shorter than the interval: the first sample after it began
+                later = [r for r in rows if r[0] >= t0 - 0.03]
+                inside = later[:1]
+        sm = [r[1] for r in inside]
+        smax = [r[2] for r in inside]
+        reasons = {nm for r in inside for nm, val in zip(names, r[3]) if val.lower().startswith("active")}
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
 
@@ -269,11 +291,12 @@ def main():
 
     clocks = Clocks(local)
     infos, times = [], []
+    clocks.start()
     launches0 = binding.percis_launch_count(eng.ctx)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    t_wall0 = time.time()
     for k in range(args.steps):
         flush.zero_()  # a write larger than L2 between timed steps
         e0 = torch.cuda.Event(enable_timing=True)
@@ -284,6 +307,7 @@ def main():
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    clocks.mark(t_wall0, time.time())
     clk = clocks.stop()
     launches = binding.percis_launch_count(eng.ctx) - launches0
     t_total = sum(times) / 1000.0
