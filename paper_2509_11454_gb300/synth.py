@@ -217,6 +217,57 @@ def states_random_seeds(n: int, k: int, seed: int) -> np.ndarray:
     return x
 
 
+def states_seeds_spread(g: Graph, seed: int, k: int | None = None) -> np.ndarray:
+    """Random Seeds Spread (Section V-A): k = ceil(ln n) random seeds, and every vertex
+    gets x_v = max over seeds s of 4^(-d(s, v)) (0 where no seed reaches v; distances
+    along out-edges).  The paper writes "log n" seeds; the natural log is taken here."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import breadth_first_order
+
+    rng = np.random.default_rng([seed, 19])
+    n = g.n
+    if k is None:
+        k = max(1, int(math.ceil(math.log(n)))) if n > 1 else 1
+    seeds = rng.choice(n, size=min(k, n), replace=False)
+    a = csr_matrix((np.ones(g.nnz, dtype=np.int8), g.col, g.row_ptr), shape=(n, n))
+    x = np.zeros(n)
+    for s in seeds:
+        order, pred = breadth_first_order(a, int(s), directed=True, return_predecessors=True)
+        d = np.zeros(n, dtype=np.int64)
+        for v in order[1:]:  # BFS order: a predecessor's distance is set before its children
+            d[v] = d[pred[v]] + 1
+        x[order] = np.maximum(x[order], 4.0 ** (-d[order].astype(np.float64)))
+    return x
+
+
+def isolated_component(g: Graph, seed: int, length: int = 50) -> tuple[Graph, np.ndarray]:
+    """Isolated Component (Section V-A): a path P of `length` new vertices is added, both
+    directions of each path edge (so P is strongly connected).  Undirected: P is its own
+    component.  Directed: one edge from a random vertex of the largest strongly connected
+    component of g to the first vertex of P.  Half of P's vertices (a seeded random half)
+    get state 1, every other vertex 0."""
+    rng = np.random.default_rng([seed, 23])
+    n0, n = g.n, g.n + length
+    rows = np.repeat(np.arange(n0, dtype=np.int64), np.diff(g.row_ptr))
+    src = [rows, np.arange(n0, n - 1), np.arange(n0 + 1, n)]
+    dst = [g.col.astype(np.int64), np.arange(n0 + 1, n), np.arange(n0, n - 1)]
+    if g.directed:
+        from scipy.sparse import csr_matrix
+        from scipy.sparse.csgraph import connected_components
+
+        a = csr_matrix((np.ones(g.nnz, dtype=np.int8), g.col, g.row_ptr), shape=(n0, n0))
+        _, lab = connected_components(a, directed=True, connection="strong")
+        big = np.flatnonzero(lab == np.bincount(lab).argmax())
+        src.append(np.array([rng.choice(big)]))
+        dst.append(np.array([n0]))
+    else:  # undirected: csr_from_edges adds the reverse of every edge, the path's included
+        src, dst = src[:2], dst[:2]
+    h = csr_from_edges(n, np.concatenate(src), np.concatenate(dst), g.directed, name=f"{g.name}+ic{length}")
+    x = np.zeros(n)
+    x[n0 + rng.choice(length, size=length // 2, replace=False)] = 1.0
+    return h, x
+
+
 # ---------------------------------------------------------------- named workloads
 
 def workload(name: str, seed: int = 0):

@@ -426,6 +426,60 @@ def test_epsilon_guarantee_gpu(binding):
     eng.close()
 
 
+def _state_setting(setting):
+    """The four state settings of Section V-A on small synthetic graphs."""
+    if setting == "rs":
+        g = synth.barabasi_albert(3000, 3, 1)
+        return g, synth.states_random_seeds(g.n, 50, 0)
+    if setting == "rss":
+        g = synth.barabasi_albert(3000, 3, 1)
+        return g, synth.states_seeds_spread(g, 0)
+    if setting == "ic":
+        return synth.isolated_component(synth.barabasi_albert(3000, 3, 1), 0)
+    if setting == "ic_directed":
+        return synth.isolated_component(synth.rmat(12, 8, 0.57, 0.19, 0.19, 2), 0)
+    if setting == "un":
+        g = synth.barabasi_albert(3000, 3, 1)
+        return g, synth.states_uniform(g.n, 0)
+    raise ValueError(setting)
+
+
+@pytest.mark.parametrize("form", ["batched", "bidir"])
+@pytest.mark.parametrize("setting", ["rs", "rss", "ic", "ic_directed", "un"])
+def test_state_settings_match_oracle(binding, setting, form):
+    """Algorithm 1 on the paper's four state settings (random seeds, seeds spread,
+    isolated component, uniform): l and the estimate as the oracle computes them."""
+    g, x = _state_setting(setting)
+    og = oracle.from_synth(g)
+    eng = _engine(binding, g, x, form=form)
+    pc, info = eng.estimate(0.02, 0.1, seed=3)
+    res = oracle.percis(og, x, 0.02, 0.1, 3, keep_paths=False, bidir=form == "bidir")
+    assert info["ell1"] == res.ell1 and info["vertex_diam"] == res.D
+    assert info["rho_tilde"] == res.rho_tilde
+    assert abs(info["ell"] - res.ell) <= 1
+    if info["ell"] != res.ell:
+        res = oracle.percis(og, x, 0.02, 0.1, 3, ell=info["ell"], keep_paths=False, bidir=form == "bidir")
+    assert np.max(np.abs(_np(pc) - res.pc)) <= 1e-9
+    eng.close()
+
+
+def test_epsilon_guarantee_isolated_component(binding):
+    """Section V-A's isolated-component setting (the shape of Proposition 7's
+    instance): max |p~ - p| <= eps in at least 18 of 20 runs."""
+    g, x = synth.isolated_component(synth.erdos_renyi(1000, 8.0, 0), 0)
+    og = oracle.from_synth(g)
+    exact = oracle.exact_pc(og, x, oracle.prepare(x).Cv)
+    assert exact[:1000].max() == 0.0 and exact[1000:].max() > 0.0  # all of it on the path
+    eng = _engine(binding, g, x, form="bidir")
+    eps = 0.002  # well below max p (0.0122), so an all-zero estimate fails
+    ok = 0
+    for seed in range(20):
+        pc, _ = eng.estimate(eps, 0.1, seed=seed)
+        ok += int(np.max(np.abs(_np(pc) - exact)) <= eps)
+    assert ok >= 18
+    eng.close()
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("name", ["ba100k_outbreak", "ba200k_uniform"])
 def test_epsilon_guarantee_full_size_gpu_exact(binding, name):

@@ -208,3 +208,25 @@ def test_percis_di_guarantee_and_larger_sample():
             dd = oracle.percis(og, x, eps, delta, seed, prep=prep, D=D, keep_paths=False)
             assert res.ell >= dd.ell
     assert ok >= 18
+
+
+def test_state_settings_inputs():
+    """The Section V-A state settings as generated: seeds-spread states are
+    max_s 4^-d(s, v) over the seeds (x = 1), with d from the oracle's BFS; the
+    isolated component is a separate 50-vertex path with 25 states at 1."""
+    g = synth.barabasi_albert(2000, 3, 4)
+    x = synth.states_seeds_spread(g, 1)
+    og = oracle.from_synth(g)
+    seeds = np.flatnonzero(x == 1.0)
+    assert len(seeds) == int(np.ceil(np.log(g.n)))
+    ref = np.zeros(g.n)
+    for s in seeds:
+        _, dist, _, _, _, _ = oracle.bfs(og, int(s))  # dist -1: unreached
+        ref = np.maximum(ref, np.where(dist >= 0, 4.0 ** (-dist.astype(np.float64)), 0.0))
+    assert np.array_equal(x, ref)
+    h, xi = synth.isolated_component(g, 2)
+    assert h.n == g.n + 50 and xi[: g.n].max() == 0.0 and xi[g.n:].sum() == 25.0
+    oh = oracle.from_synth(h)
+    _, dist, _, _, _, _ = oracle.bfs(oh, g.n)
+    assert np.all(dist[: g.n] == -1)  # a component of its own
+    assert np.array_equal(dist[g.n:], np.arange(50))  # a path from its first vertex
