@@ -17,9 +17,10 @@
 // never wait on one another.  Each block owns a slot of scratch arrays
 // (level + epoch word, count and queue per vertex and side); a vertex belongs
 // to the current sample only while its word carries the sample's epoch, so
-// the level words are never cleared, and each sample zeroes the counts of the
-// vertices it reached (its queues list them), so a level's claims and count
-// additions go in one pass over its edges.
+// nothing is ever cleared: a claim swaps a side's {level word, count} pair in
+// one 16-byte compare-and-swap, setting the count to the claiming parent's,
+// and the other parents of the level add theirs, all in one pass over the
+// level's edges.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,9 +61,9 @@ struct BiArgs {
     uint64_t seed;
     uint32_t tag;
     uint32_t epoch_base;
-    unsigned long long *vs;     // [slots][n][4]: per vertex the level words of the two sides
-                                // (epoch << 32 | level), then their path counts: one 32-byte
-                                // sector holds everything a visit touches
+    unsigned long long *vs;     // [slots][n][4]: per vertex and side {level word (epoch << 32 |
+                                // level), path count}, side 0 first: one 32-byte sector holds
+                                // everything a visit touches
     int32_t *queue;             // [slots][2][n]: visited vertices of each side in level order
     int32_t slots;
     unsigned long long *next;   // next sample to take
@@ -91,6 +92,37 @@ struct CountView {
 
 __device__ __forceinline__ unsigned long long pack(uint32_t ep, uint32_t lev) {
     return ((unsigned long long)ep << 32) | lev;
+}
+
+template <class C>
+__device__ __forceinline__ unsigned long long count_bits(C c) {
+    if constexpr (std::is_floating_point<C>::value) return (unsigned long long)__double_as_longlong(c);
+    else return c;
+}
+template <class C>
+__device__ __forceinline__ C count_of(unsigned long long b) {
+    if constexpr (std::is_floating_point<C>::value) return __longlong_as_double((long long)b);
+    else return b;
+}
+
+// one side's {level word, count} of a vertex: 16 aligned bytes, read in one request
+__device__ __forceinline__ void ld_pair(const unsigned long long *p, unsigned long long &w, unsigned long long &c) {
+    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(w), "=l"(c) : "l"(p) : "memory");
+}
+
+// 16-byte compare-and-swap of {level word, count}: the previous pair
+__device__ __forceinline__ void cas_pair(unsigned long long *p, unsigned long long cw, unsigned long long cc,
+                                         unsigned long long nw, unsigned long long nc, unsigned long long &ow,
+                                         unsigned long long &oc) {
+    asm volatile(
+        "{\n\t.reg .b128 d, c, s;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 s, {%4, %5};\n\t"
+        "atom.global.cas.b128 d, [%6], c, s;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(ow), "=l"(oc)
+        : "l"(cw), "l"(cc), "l"(nw), "l"(nc), "l"(p)
+        : "memory");
 }
 
 template <class T>
@@ -154,8 +186,9 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
         // record of vertex v at vrec[4 (v - base)]: the sample's graph starts at base
         const int64_t base = a.gid ? a.vbase[a.gid[s]] : 0;
         unsigned long long *const vrec = vslot - 4 * base;
-        const Strided info0{vrec}, info1{vrec + 1};
-        const CountView<C> sig0{vrec + 2}, sig1{vrec + 3};
+        // record: {level word, count} of side 0, then of side 1
+        const Strided info0{vrec}, info1{vrec + 2};
+        const CountView<C> sig0{vrec + 1}, sig1{vrec + 3};
         if (threadIdx.x == 0) {
             info0[s] = pack(ep, 0);
             sig0[s] = C(1);
@@ -200,14 +233,20 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 const int32_t *ax = x ? a.icol : a.col;
                 const long long f = hi - lo;
                 // one edge: claim the neighbour if unreached, add the parent's count if
-                // it lies on the new level
+                // it lies on the new level.  A claim swaps the whole {level word,
+                // count} pair, so it also sets the count to the claiming parent's and
+                // counts never need clearing: a count is read only where its level
+                // word carries the sample's epoch.
                 auto visit = [&](const int32_t v, const C su) {
-                    const unsigned long long old = __ldcg(&infx[v]);
-                    bool at = old == want;
-                    if ((uint32_t)(old >> 32) != ep) {
-                        const unsigned long long prev = atomicCAS(&infx[v], old, want);
-                        if (prev == old) {
-                            at = true;
+                    unsigned long long *const pr = &infx[v];
+                    unsigned long long ow, oc;
+                    ld_pair(pr, ow, oc);
+                    bool at = ow == want, won = false;
+                    if ((uint32_t)(ow >> 32) != ep) {
+                        unsigned long long pw, pc;
+                        cas_pair(pr, ow, oc, want, count_bits(su), pw, pc);
+                        if (pw == ow && pc == oc) {
+                            won = true;
                             // the lanes that claimed together reserve their queue slots and
                             // add their degrees with one shared atomic each (a 64-bit shared
                             // add would be a contended compare-and-swap loop per lane)
@@ -225,11 +264,11 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             qx[hi + q0 + __popc(grp & ((1u << lane) - 1u))] = v;
                             if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) s_meet = 1;
                         } else {
-                            at = prev == want;  // claimed in this level by another thread
+                            at = pw == want;  // claimed in this level by another thread
                         }
                     }
+                    if (a.work && (at || won)) ++n_add;
                     if (at) {
-                        if (a.work) ++n_add;
                         const C o = atomicAdd(&sigx[v], su);
                         if ((double)(o + su) >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
                     }
@@ -430,7 +469,9 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             C val = C(0);
                             if (e < e1) {
                                 pv = bc[e];
-                                if (__ldcg(&infz[pv]) == prev) val = __ldcg(&sigz[pv]);
+                                unsigned long long lw2, lc2;
+                                ld_pair(&infz[pv], lw2, lc2);
+                                if (lw2 == prev) val = count_of<C>(lc2);
                             }
                             C cum = val;
 #pragma unroll
@@ -465,14 +506,11 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 }
             }
         }
-        // clear the counts this sample touched (every vertex either side reached)
         __syncthreads();
         if (a.work && threadIdx.x == 0) {
             s_work[2] += (unsigned long long)(qhi[0] + qhi[1]);
             s_work[3] += 1ull;
         }
-        for (long long q = threadIdx.x; q < qhi[0]; q += kBiBlock) sig0[queue0[q]] = C(0);
-        for (long long q = threadIdx.x; q < qhi[1]; q += kBiBlock) sig1[queue1[q]] = C(0);
     }
     if (a.work) {
 #pragma unroll
@@ -507,7 +545,7 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     if (ctx->bi_slots < slots || ctx->bi_n != nslot) {
         PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 4 * nslot * slots, "bidirectional records"));
         PERCIS_TRY(ensure(ctx, ctx->bi_queue, sizeof(int32_t) * 2 * nslot * slots, "bidirectional queues"));
-        // level words of no sample, counts zero (every sample clears the counts it touched)
+        // level words of no sample (epoch 0)
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * nslot * slots, ctx->stream));
         ctx->bi_slots = slots;
         ctx->bi_n = nslot;
