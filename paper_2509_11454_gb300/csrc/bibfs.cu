@@ -34,7 +34,7 @@ namespace percis {
 namespace {
 
 #ifndef PERCIS_BI_BLOCK
-#define PERCIS_BI_BLOCK 128
+#define PERCIS_BI_BLOCK 256
 #endif
 constexpr int kBiBlock = PERCIS_BI_BLOCK;
 #ifndef PERCIS_MEET_CAP
@@ -43,7 +43,7 @@ constexpr int kBiBlock = PERCIS_BI_BLOCK;
 constexpr int kMeetCap = PERCIS_MEET_CAP;  // meeting-layer members kept in shared memory
 constexpr int kFlat = 512;  // frontiers up to this size have their edges spread over the block
 #ifndef PERCIS_BI_MINB
-#define PERCIS_BI_MINB 12
+#define PERCIS_BI_MINB 7
 #endif
 
 struct BiArgs {
