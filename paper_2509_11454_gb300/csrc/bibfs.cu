@@ -43,7 +43,7 @@ constexpr int kBiBlock = PERCIS_BI_BLOCK;
 constexpr int kMeetCap = PERCIS_MEET_CAP;  // meeting-layer members kept in shared memory
 constexpr int kFlat = 512;  // frontiers up to this size have their edges spread over the block
 #ifndef PERCIS_BI_MINB
-#define PERCIS_BI_MINB 7
+#define PERCIS_BI_MINB 6
 #endif
 
 struct BiArgs {
@@ -239,6 +239,10 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 // word carries the sample's epoch.
                 auto visit = [&](const int32_t v, const C su) {
                     unsigned long long *const pr = &infx[v];
+                    // what a claim needs (degree, the other side's level word) is read
+                    // alongside the pair, off the claim's dependent chain
+                    const uint32_t dg = (uint32_t)(px[v + 1] - px[v]);  // < 2^31
+                    const unsigned long long oy = __ldcg(&infy[v]);
                     unsigned long long ow, oc;
                     ld_pair(pr, ow, oc);
                     bool at = ow == want, won = false;
@@ -252,7 +256,6 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             // add would be a contended compare-and-swap loop per lane)
                             const unsigned grp = __activemask();
                             const int lead = __ffs(grp) - 1;
-                            const uint32_t dg = (uint32_t)(px[v + 1] - px[v]);  // < 2^31
                             const uint32_t dlo = __reduce_add_sync(grp, dg & 0xffffu);
                             const uint32_t dhi = __reduce_add_sync(grp, dg >> 16);
                             int q0 = 0;
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             }
                             q0 = __shfl_sync(grp, q0, lead);
                             qx[hi + q0 + __popc(grp & ((1u << lane) - 1u))] = v;
-                            if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) s_meet = 1;
+                            if ((uint32_t)(oy >> 32) == ep) s_meet = 1;
                         } else {
                             at = pw == want;  // claimed in this level by another thread
                         }
