@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
     __shared__ C s_mw[kMeetCap];
     __shared__ C s_redc[nw];
     __shared__ int32_t s_best[nw];
-    __shared__ int32_t s_fu[kFlat];
+    __shared__ int64_t s_fe[kFlat];  // first edge of each frontier vertex
     __shared__ C s_fs[kFlat];
     __shared__ int32_t s_pre[kFlat + 1];
     __shared__ unsigned long long s_work[4];
@@ -292,9 +292,10 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             int32_t dg = 0;
                             if (k < f) {
                                 const int32_t u = qx[lo + k];
-                                s_fu[k] = u;
+                                const int64_t e0 = px[u];
+                                s_fe[k] = e0;
                                 s_fs[k] = __ldcg(&sigx[u]);
-                                dg = (int32_t)(px[u + 1] - px[u]);
+                                dg = (int32_t)(px[u + 1] - e0);
                             }
                             loc[r] = tot;
                             tot += dg;
@@ -323,8 +324,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             if (s_pre[mid] <= j) klo = mid;
                             else khi = mid - 1;
                         }
-                        const int32_t u = s_fu[klo];
-                        visit(ax[px[u] + (j - s_pre[klo])], s_fs[klo]);
+                        visit(ax[s_fe[klo] + (j - s_pre[klo])], s_fs[klo]);
                     }
                 } else {
                     for (long long q = lo + warp; q < hi; q += nw) {
