@@ -47,7 +47,7 @@ WORKLOAD_DESC = {
 NCU_TRAFFIC = {"sha256": "561848eed978b51f357614804897403671bbedfe50f75d5f87209cd665a35926",
                # DRAM read + write of one phase-2 launch (20 batches) / 20: bytes per batch of lanes
                "bytes_per_launch": (10701870000 + 6086926000) / 20}  # the ncu capture summarised under profiles/
-NCU_TRAFFIC_BIDIR = {"sha256": "3a79e1148ec2dec005da377d01ed76c7289a716dcfdd404869283675a41aed37",
+NCU_TRAFFIC_BIDIR = {"sha256": "fc707be831092024a85af111c98bdb7879e84aa8865e1df393ea1f8e190be1ab",
                      # DRAM read + write of one phase-2 launch of k_bibfs (the ncu capture under profiles/)
                      "bytes_per_launch": 13255927000 + 2781047000}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}

@@ -223,8 +223,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 const unsigned long long want = pack(ep, nl);
                 unsigned long long ne = 0ull;
                 // level nl: claim unreached neighbours and add the counts over
-                // every edge into the level in one pass (counts of unreached
-                // vertices are zero: each sample clears the ones it touched)
+                // every edge into the level in one pass
                 const Strided infx = x ? info1 : info0;
                 const CountView<C> sigx = x ? sig1 : sig0;
                 const Strided infy = x ? info0 : info1;
