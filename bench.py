@@ -344,11 +344,11 @@ def main():
         else:
             kernel, src_name, ncu = ("k_bibfs (bidirectional sigma-BFS + backtrack, one block per sample; "
                                      "figures per phase-2 launch)", "bibfs.cu", NCU_TRAFFIC_BIDIR)
-            # per edge scanned: column 4 B + level word 8 B; per count addition 8 B; per vertex reached:
-            # claim 8 B, queue 4 B, count read, write and clear 3 x 8 B.  The unit is the phase-2 launch
-            # (one per step, ~98% of the samples).
+            # per edge scanned: column 4 B + level word 8 B; per count addition (the claim's included)
+            # 8 B; per vertex reached: level word written 8 B, queue 4 B, count read and written 2 x 8 B.
+            # The unit is the phase-2 launch (one per step, ~98% of the samples).
             w2 = work[1]
-            algo_bytes = 12.0 * w2[0] + 8.0 * w2[1] + 36.0 * w2[2]
+            algo_bytes = 12.0 * w2[0] + 8.0 * w2[1] + 28.0 * w2[2]
             bfs_ms = sum(i["bfs_ms"][1] for i in infos)
             bfs_launches = sum(i["bfs_launches"][1] for i in infos)
             work_step = {"edges_scanned": w[0], "count_additions": w[1], "vertices_reached": w[2],
