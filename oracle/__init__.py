@@ -447,18 +447,33 @@ def Lambda_literal(ilen) -> float:
     return tot / (L * (L - 1))
 
 
+def Lambda_sums(ilen) -> float:
+    """Proposition 2's Lambda(S) from two exact integer sums: the pairwise sum
+    sum_{i<j} (a_i - a_j)^2 equals l sum a_i^2 - (sum a_i)^2, so the integer
+    numerator is the same as Lambda_literal's and one division gives the same
+    double."""
+    a = [int(v) for v in ilen]
+    L = len(a)
+    S = sum(a)
+    Q = sum(v * v for v in a)
+    return (L * Q - S * S) / (L * (L - 1))
+
+
 def rho_hat(ilen, D: int, delta: float) -> tuple[float, float, float]:
-    """Algorithm 1: rho^ = rho~ + sqrt(2 Lambda log(8/delta)/l1) + 7 D log(8/delta)/(3(l1-1))."""
+    """Algorithm 1: rho^ = rho~ + sqrt(2 Lambda log(8/delta)/l1) + 7 D log(8/delta)/(3(l1-1)),
+    i.e. Proposition 2 (an empirical Bernstein bound on the mean of |I| in
+    [0, D]) at confidence delta/4, as the proof of Proposition 4 applies it."""
     l1 = len(ilen)
     rt = float(np.sum(np.asarray(ilen, dtype=np.int64))) / l1
-    Lam = Lambda_literal(ilen)
+    Lam = Lambda_sums(ilen)
     lg = math.log(8.0 / delta)
     return rt + math.sqrt(2.0 * Lam * lg / l1) + 7.0 * D * lg / (3.0 * (l1 - 1)), rt, Lam
 
 
 def v_hat(p1_max: float, dhat: float, l1: int, delta: float) -> float:
-    """Algorithm 1: v^ = d^2 max_v {p~ + sqrt(2 p~ log(4/delta)/l1) + log(4/delta)/(3 l1)}.
-    The braced expression increases with p~, so the max is at max_v p~(v)."""
+    """Algorithm 1: v^ = d^2 max_v {p~ + sqrt(2 p~ log(4/delta)/l1) + log(4/delta)/(3 l1)},
+    i.e. Proposition 3 at confidence delta/4.  The braced expression increases
+    with p~, so the max is at max_v p~(v)."""
     lg = math.log(4.0 / delta)
     return dhat * dhat * (p1_max + math.sqrt(2.0 * p1_max * lg / l1) + lg / (3.0 * l1))
 
