@@ -2,14 +2,24 @@
 """Throughput of the PercIS estimator on GB300 (one JSON line on stdout).
 
 A step is one complete estimate through the library's C ABI -- load the
-CSR (validation, VertexDiamUB), set the states (sort, Algorithm 2 tables,
-C_v, lambda), phase 1 (l1 samples), the Theorem 1 bound, phase 2 (l samples)
-and the final estimate -- on Barabasi-Albert n=100,000, m=5 with a seeded
-10% outbreak (x = 0 for 90% of the vertices, U[0.5, 1] for the rest),
-eps = 0.005, delta = 0.1.  The metric is sampled pairs per second
-(l1 + l per step over the device time of the step).
+CSR (validation, in-adjacency, VertexDiamUB), set the states (sort,
+Algorithm 2 tables, C_v, lambda), phase 1 (l1 samples), the Theorem 1
+bound, phase 2 (l samples) and the final estimate.  The metric is sampled
+pairs per second (l1 + l per step over the device time of the step) with
+the inputs resident in HBM.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Default workload: directed R-MAT scale 22 (4,194,304 vertices, edge factor
+16, a=0.57 b=0.19 c=0.19, self-loops and duplicates removed, ids permuted),
+x ~ Beta(0.5, 2), eps = 0.01, delta = 0.1, timed in the bidirectional form
+(Section III-B).  Reported beside it: the plain and batched forms on the
+same graph, the differentiated step, the end-to-end figure through host
+buffers, GTEPS, the roofline of the dominant kernel, the CPU oracle (same
+bidirectional algorithm) on a bounded sample, and three more workloads:
+Barabasi-Albert n=100,000 with a 10% outbreak (eps = 0.005), Barabasi-Albert
+n=200,000 forward + backward (eps = 0.01), and 512 uneven graphs forward +
+backward (eps = 0.01 per graph).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
 N > 1 runs under torchrun, one rank per GPU, each rank an independent
 estimate (its own seeds; weak scaling, no collective on the data path).
@@ -21,36 +31,38 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
 import time
-import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "ba100k_outbreak"
-WORKLOAD_DESC = {
-    "workload": "ba100k_m5_outbreak10",
-    "graph": "Barabasi-Albert n=100000, m=5, undirected, int64 row offsets / int32 columns",
-    "states": "x=0 on 90% of vertices, U[0.5,1] on a seeded random 10%",
-    "eps": 0.005,
-    "delta": 0.1,
+WORKLOADS = {
+    "rmat22_beta": {
+        "workload": "rmat22_beta",
+        "graph": "R-MAT scale 22 (n=4194304), edge factor 16, a=0.57 b=0.19 c=0.19, directed, self-loops and "
+                 "duplicates removed, ids permuted; int64 row offsets / int32 columns",
+        "states": "x ~ Beta(0.5, 2)", "eps": 0.01, "delta": 0.1},
+    "ba100k_outbreak": {
+        "workload": "ba100k_m5_outbreak10",
+        "graph": "Barabasi-Albert n=100000, m=5, undirected, int64 row offsets / int32 columns",
+        "states": "x=0 on 90% of vertices, U[0.5,1] on a seeded random 10%", "eps": 0.005, "delta": 0.1},
+    "ba200k_uniform": {
+        "workload": "ba200k_m4_uniform",
+        "graph": "Barabasi-Albert n=200000, m=4, undirected", "states": "x ~ U[0,1]", "eps": 0.01,
+        "delta": 0.1},
 }
-# DRAM traffic of one batched sigma-BFS launch from an ncu capture, valid only
-# for the kernel source it was taken on (sha256 of csrc/msbfs.cu).
-NCU_TRAFFIC = {"sha256": "561848eed978b51f357614804897403671bbedfe50f75d5f87209cd665a35926",
-               # DRAM read + write of one phase-2 launch (20 batches) / 20: bytes per batch of lanes
-               "bytes_per_launch": (10701870000 + 6086926000) / 20}  # the ncu capture summarised under profiles/
-NCU_TRAFFIC_BIDIR = {"sha256": "fc707be831092024a85af111c98bdb7879e84aa8865e1df393ea1f8e190be1ab",
-                     # DRAM read + write of one phase-2 launch of k_bibfs (the ncu capture under profiles/)
-                     "bytes_per_launch": 13255927000 + 2781047000}
+DEFAULT_WORKLOAD = "rmat22_beta"
+# DRAM traffic per launch of the dominant kernel from an ncu capture, valid only
+# for the kernel source it was taken on (sha256 of the .cu file) and the workload.
+NCU_TRAFFIC = {}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+L2_FLUSH_BYTES = 256 << 20
 
 
 def _peaks():
@@ -137,41 +149,75 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def _oracle_worker(args):
-    """One host process: the oracle on samples i0, i0 + stride, ... for budget_s."""
-    i0, stride, budget_s = args
-    sys.path.insert(0, ROOT)
+# ------------------------------------------------------------ CPU oracle arms
+
+def _save_workload(name: str, d: str):
+    """The workload's CSR and states as .npy files, so host worker processes
+    map them instead of regenerating the graph."""
+    import numpy as np
+
+    from paper_2509_11454_gb300 import synth
+
+    g, x, eps, delta = synth.workload(name, 0)
+    np.save(os.path.join(d, "rp.npy"), g.row_ptr)
+    np.save(os.path.join(d, "col.npy"), g.col)
+    np.save(os.path.join(d, "x.npy"), x)
+    with open(os.path.join(d, "meta.json"), "w") as f:
+        json.dump({"n": g.n, "directed": bool(g.directed)}, f)
+
+
+def _load_oracle_workload(d: str):
+    import numpy as np
+
     import oracle
     from paper_2509_11454_gb300 import synth
 
-    g, x, eps, delta = synth.workload(WORKLOAD, 0)
-    og = oracle.from_synth(g)
-    prep = oracle.prepare(x)
+    with open(os.path.join(d, "meta.json")) as f:
+        meta = json.load(f)
+    g = synth.Graph(n=meta["n"], row_ptr=np.load(os.path.join(d, "rp.npy")),
+                    col=np.load(os.path.join(d, "col.npy")), directed=meta["directed"])
+    x = np.load(os.path.join(d, "x.npy"))
+    return oracle.from_synth(g), oracle.prepare(x)
+
+
+def _oracle_worker(args):
+    """One host process: the oracle on phase-2 samples i0, i0 + stride, ... (in
+    chunks) for budget_s seconds; bidir picks the bidirectional RandomSP."""
+    d, i0, stride, budget_s, bidir, chunk = args
+    sys.path.insert(0, ROOT)
+    import oracle
+
+    og, prep = _load_oracle_workload(d)
     done, t_used, k = 0, 0.0, 0
-    chunk = 100
     while t_used < budget_s:
         t0 = time.perf_counter()
-        oracle.run_samples(og, prep, 0, 1, 3, (i0 + k * stride) * chunk, chunk, keep_paths=False)
+        oracle.run_samples(og, prep, 0, 1, 3, (i0 + k * stride) * chunk, chunk, keep_paths=False, bidir=bidir)
         t_used += time.perf_counter() - t0
         done += chunk
         k += 1
     return done, t_used
 
 
-def cpu_baseline(budget_s: float = 12.0) -> dict:
-    """The CPU oracle as it stands (sampler + RandomSP + estimator) on a bounded
-    sample of phase-2 pairs of the same workload: one host thread, then one
-    process per host core (spawned, each with its own copy of the graph)."""
+def cpu_baseline(name: str, bidir: bool, budget_s: float = 10.0) -> dict:
+    """The CPU oracle as it stands (Algorithm 2 sampler + RandomSP + estimator)
+    on a bounded sample of phase-2 pairs of the same workload and the same
+    RandomSP algorithm as the timed GPU form: one host thread, then one
+    process per host core (spawned, each mapping the saved graph)."""
     import multiprocessing as mp
 
-    done1, t1 = _oracle_worker((0, 1, budget_s))
+    algo = "bidirectional BFS" if bidir else "one-sided truncated sigma-BFS"
     cores = os.cpu_count() or 1
-    with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_oracle_worker, [(c, cores, budget_s / 2) for c in range(cores)])
+    with tempfile.TemporaryDirectory(prefix="percis_bench_") as d:
+        _save_workload(name, d)
+        chunk = 20
+        done1, t1 = _oracle_worker((d, 0, 1, budget_s, bidir, chunk))
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [(d, c, cores, budget_s / 2, bidir, chunk) for c in range(cores)])
     done_all = sum(r[0] for r in res)
     t_all = max(r[1] for r in res)
     return {"value": done_all / t_all, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done_all} phase-2 pairs of the same workload (Algorithm 2 sampler, sigma-BFS RandomSP, "
+            "algorithm": f"RandomSP by {algo}",
+            "sample": f"{done_all} phase-2 pairs of the same workload (Algorithm 2 sampler, RandomSP by {algo}, "
                       f"estimator) split over {cores} processes, {t_all:.1f} s each",
             "single_thread": {"value": done1 / t1, "cores": 1,
                               "sample": f"{done1} pairs, {t1:.1f} s on one host thread"}}
@@ -197,33 +243,123 @@ def job_totals(t_local: float, pairs_local: int, dist, device: str):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (bidirectional RandomSP, as the timed
+    GPU form) on a bounded sample of the workload per step, one host thread."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
-    from paper_2509_11454_gb300 import synth
 
-    g, x, eps, delta = synth.workload(WORKLOAD, 0)
-    og = oracle.from_synth(g)
-    prep = oracle.prepare(x)
+    bidir = args.form == "bidir"
+    with tempfile.TemporaryDirectory(prefix="percis_ref_") as d:
+        _save_workload(args.workload, d)
+        og, prep = _load_oracle_workload(d)
     per_step = args.ref_pairs
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.run_samples(og, prep, 1000 + k, 1, 3, 0, per_step, keep_paths=False)
+        oracle.run_samples(og, prep, 1000 + k, 1, 3, 0, per_step, keep_paths=False, bidir=bidir)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
     tot = sum(times)
     value = per_step * len(times) / tot
+    algo = "bidirectional BFS" if bidir else "one-sided truncated sigma-BFS"
     line = {"impl": "reference", "metric": "sampled pairs/s", "value": value, "unit": "pairs/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * tot / len(times), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD_DESC),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOADS[args.workload]),
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} phase-2 pairs per step on one host thread"},
+                             "sample": f"{per_step} phase-2 pairs per step (RandomSP by {algo}) on one host thread"},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU helpers
+
+def _timed(torch, stream, flush, fn):
+    """Device time (s) of fn() on `stream`, L2 flushed before it."""
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1000.0, out
+
+
+def extra_workload(binding, synth, torch, stream, flush, name: str, steps: int, warmup: int, backward: bool,
+                   seed_base: int) -> dict:
+    """pairs/s of another single-graph workload (bidirectional form), forward
+    or forward + backward per step, inputs resident in HBM."""
+    g, x, eps, delta = synth.workload(name, 0)
+    eng = binding.PercIS(torch.cuda.current_device())
+    eng.set_options(form="bidir")
+    rp_d = torch.as_tensor(g.row_ptr, dtype=torch.int64, device="cuda")
+    col_d = torch.as_tensor(g.col, dtype=torch.int32, device="cuda")
+    x_d = torch.as_tensor(x, dtype=torch.float64, device="cuda")
+    pc_d = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    gvec = torch.randn(g.n, dtype=torch.float64, device="cuda")
+    gx = torch.empty(g.n, dtype=torch.float64, device="cuda")
+
+    def step(seed):
+        binding.percis_load_csr(eng.ctx, g.n, g.nnz, rp_d, col_d, g.directed, 1)
+        binding.percis_set_states(eng.ctx, x_d, 1)
+        inf = binding.percis_estimate(eng.ctx, eps, delta, seed, pc_d, 1)
+        if backward:
+            binding.percis_backward(eng.ctx, gvec, gx, 1)
+        return inf
+
+    for k in range(warmup):
+        step(seed_base + 50_000 + k)
+    ts, pairs = [], 0
+    for k in range(steps):
+        dt, inf = _timed(torch, stream, flush, lambda: step(seed_base + k))
+        ts.append(dt)
+        pairs += inf["ell1"] + inf["ell"]
+    eng.close()
+    return {"workload": WORKLOADS[name]["workload"], "value": pairs / sum(ts), "unit": "pairs/s",
+            "ms_per_step": 1000.0 * sum(ts) / len(ts), "steps": steps, "eps": eps,
+            "form": "bidirectional" + (" forward + backward (dPC/dx)" if backward else ""),
+            "pairs_per_step": pairs / steps}
+
+
+def extra_uneven(binding, synth, torch, stream, flush, steps: int, seed_base: int) -> dict:
+    """512 independent graphs (Watts-Strogatz k=10 p=0.05, Barabasi-Albert m=3,
+    grids with 5% of edges deleted; n log-uniform in [1e3, 2e5]), x ~ U[0,1],
+    eps = 0.01 per graph, bidirectional form with recorded sampling launches;
+    forward + backward per step."""
+    sizes = synth.uneven_batch_sizes(512, 1000, 200_000, 0)
+    graphs = synth.graph_batch(sizes, 0)
+    vptr, rp, col = synth.union_csr(graphs)
+    n = int(vptr[-1])
+    x = synth.states_uniform(n, 0)
+    eng = binding.PercIS(torch.cuda.current_device())
+    eng.set_options(form="bidir", cuda_graphs=1)
+    eng.load_graphs(vptr, rp, col)
+    eng.set_states(x)
+    pc = torch.empty(n, dtype=torch.float64, device="cuda")
+    gvec = torch.randn(n, dtype=torch.float64, device="cuda")
+    gx = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def step(seed):
+        infos = binding.percis_estimate_graphs(eng.ctx, 0.01, 0.1, seed, pc, 1)
+        binding.percis_backward(eng.ctx, gvec, gx, 1)
+        return infos
+
+    step(seed_base + 70_000)  # warm-up (records the sampling graphs)
+    ts, pairs = [], 0
+    for k in range(steps):
+        dt, infos = _timed(torch, stream, flush, lambda: step(seed_base + k))
+        ts.append(dt)
+        pairs += sum(f["ell1"] + f["ell"] for f in infos)
+    eng.close()
+    return {"workload": "uneven512_ws_ba_grid", "value": pairs / sum(ts), "unit": "pairs/s",
+            "ms_per_step": 1000.0 * sum(ts) / len(ts), "steps": steps, "graphs": 512, "n": n,
+            "nnz": int(col.shape[0]), "eps": 0.01,
+            "form": "bidirectional, sampling launches in CUDA graphs, forward + backward (dPC/dx)",
+            "pairs_per_step": pairs / steps}
 
 
 def main():
@@ -232,8 +368,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-pairs", type=int, default=300)
-    ap.add_argument("--no-extras", action="store_true", help="skip plain/differentiated/e2e/cpu legs")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-pairs", type=int, default=100)
+    ap.add_argument("--no-extras", action="store_true", help="only the headline and its roofline")
+    ap.add_argument("--no-other-workloads", action="store_true", help="skip the extra workloads")
     ap.add_argument("--form", default="bidir", choices=["bidir", "batched"],
                     help="form of the timed step: bidirectional BFS per sample, or the batched multi-source BFS")
     ap.add_argument("--lanes", type=int, default=0, help="batched lane width (0 = library default)")
@@ -260,7 +398,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     binding.load_library()
 
-    g, x, eps, delta = synth.workload(WORKLOAD, 0)
+    wl = WORKLOADS[args.workload]
+    g, x, eps, delta = synth.workload(args.workload, 0)
     stream = torch.cuda.Stream(device=local)
     torch.cuda.set_stream(stream)
     eng = binding.PercIS(local)
@@ -277,11 +416,11 @@ def main():
     col_d = torch.as_tensor(g.col, dtype=torch.int32, device="cuda")
     x_d = torch.as_tensor(x, dtype=torch.float64, device="cuda")
     pc_d = torch.empty(g.n, dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     seed_base = replica_seed_base(rank)
 
     def step(seed):
-        binding.percis_load_csr(eng.ctx, g.n, g.nnz, rp_d, col_d, False, 1)
+        binding.percis_load_csr(eng.ctx, g.n, g.nnz, rp_d, col_d, g.directed, 1)
         binding.percis_set_states(eng.ctx, x_d, 1)
         return binding.percis_estimate(eng.ctx, eps, delta, seed, pc_d, 1)
 
@@ -298,19 +437,14 @@ def main():
     torch.cuda.synchronize()
     t_wall0 = time.time()
     for k in range(args.steps):
-        flush.zero_()  # a write larger than L2 between timed steps
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        infos.append(step(seed_base + k))
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+        dt, inf = _timed(torch, stream, flush, lambda: step(seed_base + k))  # L2 flushed before every step
+        times.append(dt)
+        infos.append(inf)
     torch.cuda.synchronize()
     clocks.mark(t_wall0, time.time())
     clk = clocks.stop()
     launches = binding.percis_launch_count(eng.ctx) - launches0
-    t_total = sum(times) / 1000.0
+    t_total = sum(times)
     pairs = sum(i["ell1"] + i["ell"] for i in infos)
     t_job, pairs_job = job_totals(t_total, pairs, dist, "cuda")
     value = pairs_job / t_job
@@ -318,12 +452,13 @@ def main():
     extras = {}
     if rank == 0:
         peaks, peak_kind = _peaks()
+        replay_steps = min(args.steps, 3)
+
         # algorithmic work of the same estimates, counted in an untimed instrumented replay
-        # (the batched replay also gives the one-sided BFS edges of the same pairs, for GTEPS)
         def replay(form):
             eng.set_options(instrument=1, form=form)
             work = np.zeros((2, 8))
-            for k in range(args.steps):
+            for k in range(replay_steps):
                 inf = step(seed_base + k)
                 work += np.array(inf["work"], dtype=np.float64)
             eng.set_options(instrument=0, form=args.form)
@@ -332,74 +467,74 @@ def main():
         work = replay(args.form)
         w = work.sum(axis=0)
         wb = w if args.form == "batched" else replay("batched").sum(axis=0)
-        bfs_ms = sum(sum(i["bfs_ms"]) for i in infos)
-        bfs_launches = sum(sum(i["bfs_launches"]) for i in infos)
-        bfs_share = bfs_ms / sum(times)
+        step_s_replayed = sum(times[:replay_steps])
+        bfs_share = sum(sum(i["bfs_ms"]) for i in infos) / 1000.0 / t_total
         if args.form == "batched":
-            kernel, src_name, ncu = ("k_msbfs (batched sigma-BFS + backtrack; one persistent launch per phase, "
-                                     "figures per batch of W lanes)", "msbfs.cu", NCU_TRAFFIC)
+            kernel, src_name = ("k_msbfs (batched sigma-BFS + backtrack; one persistent launch per phase, "
+                                "figures per batch of W lanes)", "msbfs.cu")
             algo_bytes = 8.0 * w[0] + 8.0 * w[1] + 8.0 * w[2] + 4.0 * w[3]
+            bfs_ms = sum(sum(i["bfs_ms"]) for i in infos[:replay_steps])
+            bfs_launches = sum(sum(i["bfs_launches"]) for i in infos[:replay_steps])
             work_step = {"sigma_dag_reads": w[0], "sigma_writes": w[1], "union_frontier_rows": w[2],
                          "union_frontier_edges": w[3], "truncated_bfs_edges": w[4], "bfs_samples": w[6]}
+            scanned = w[3]
         else:
-            kernel, src_name, ncu = ("k_bibfs (bidirectional sigma-BFS + backtrack, one block per sample; "
-                                     "figures per phase-2 launch)", "bibfs.cu", NCU_TRAFFIC_BIDIR)
+            kernel, src_name = ("k_bibfs (bidirectional sigma-BFS + backtrack, one block per sample; "
+                                "figures per phase-2 launch)", "bibfs.cu")
             # per edge scanned: column 4 B + level word 8 B; per count addition (the claim's included)
             # 8 B; per vertex reached: level word written 8 B, queue 4 B, count read and written 2 x 8 B.
-            # The unit is the phase-2 launch (one per step, ~98% of the samples).
+            # The unit is the phase-2 launch (one per step, most of the samples).
             w2 = work[1]
             algo_bytes = 12.0 * w2[0] + 8.0 * w2[1] + 28.0 * w2[2]
-            bfs_ms = sum(i["bfs_ms"][1] for i in infos)
-            bfs_launches = sum(i["bfs_launches"][1] for i in infos)
+            bfs_ms = sum(i["bfs_ms"][1] for i in infos[:replay_steps])
+            bfs_launches = sum(i["bfs_launches"][1] for i in infos[:replay_steps])
             work_step = {"edges_scanned": w[0], "count_additions": w[1], "vertices_reached": w[2],
                          "bfs_samples": w[3], "one_sided_bfs_edges": wb[4]}
+            scanned = w[0]
         per_launch_bytes = algo_bytes / max(bfs_launches, 1)
         per_launch_s = bfs_ms / 1000.0 / max(bfs_launches, 1)
         achieved = per_launch_bytes / per_launch_s / 1e9
         traffic = None
-        if ncu["sha256"] == _sha(os.path.join(ROOT, "paper_2509_11454_gb300", "csrc", src_name)):
+        ncu = NCU_TRAFFIC.get((args.workload, src_name))
+        if ncu and ncu["sha256"] == _sha(os.path.join(ROOT, "paper_2509_11454_gb300", "csrc", src_name)):
             traffic = ncu["bytes_per_launch"]
         extras["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
                               "peak_source": f"{peak_kind} HBM copy bandwidth",
                               "algorithmic_bytes_per_launch": per_launch_bytes,
-                              "avg_launch_ms": per_launch_s * 1000.0, "launches_per_step": bfs_launches / len(infos)}
-        extras["gteps"] = wb[4] / t_total / 1e9 if wb[4] else None
-        extras["work_per_step"] = {k: v / len(infos) for k, v in work_step.items()}
+                              "avg_launch_ms": per_launch_s * 1000.0,
+                              "launches_per_step": bfs_launches / replay_steps}
+        # GTEPS two ways: the edges a one-sided truncated BFS from s_i scans to settle t_i
+        # (the paper-independent work measure), and the edges the timed kernel scanned
+        extras["gteps"] = wb[4] / step_s_replayed / 1e9 if wb[4] else None
+        extras["gteps_scanned"] = scanned / step_s_replayed / 1e9 if scanned else None
+        extras["gteps_note"] = ("gteps: one-sided truncated-BFS edges of the same pairs per second (counted in an "
+                                "instrumented replay); gteps_scanned: edges the timed kernel actually scanned")
+        extras["work_per_step"] = {k: v / replay_steps for k, v in work_step.items()}
         extras["bfs_share_of_step"] = bfs_share
 
         if not args.no_extras:
-            # plain form: one BFS launch + one backtrack launch per sampled pair, same seed
-            eng.set_options(form="plain")
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            flush.zero_()
-            e0.record(stream)
-            inf_p = step(seed_base)
-            e1.record(stream)
-            e1.synchronize()
-            t_p = e0.elapsed_time(e1) / 1000.0
-            eng.set_options(form="batched")
+            # plain form: one BFS launch + one backtrack launch per sampled pair, on a bounded
+            # sample size (l1 = l = 1000; pairs/s does not depend on l)
+            eng.set_options(form="plain", ell1=1000, ell=1000)
+            t_p, inf_p = _timed(torch, stream, flush, lambda: step(seed_base))
+            eng.set_options(form=args.form, ell1=0, ell=0)
             extras["plain"] = {"value": (inf_p["ell1"] + inf_p["ell"]) / t_p, "unit": "pairs/s",
-                               "ms_per_step": t_p * 1000.0, "steps": 1}
+                               "ms_per_step": t_p * 1000.0, "steps": 1,
+                               "sample": "l1 = l = 1000 (the plain form takes one launch per pair)"}
 
             # the other sampling form on the same seeds
             other = "batched" if args.form == "bidir" else "bidir"
             eng.set_options(form=other)
             to, po = [], 0
-            for k in range(args.steps):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                inf = step(seed_base + k)
-                e1.record(stream)
-                e1.synchronize()
-                to.append(e0.elapsed_time(e1) / 1000.0)
+            for k in range(replay_steps):
+                dt, inf = _timed(torch, stream, flush, lambda: step(seed_base + k))
+                to.append(dt)
                 po += inf["ell1"] + inf["ell"]
             eng.set_options(form=args.form)
             extras["batched" if other == "batched" else "bidirectional"] = {
-                "value": po / sum(to), "unit": "pairs/s", "ms_per_step": 1000.0 * sum(to) / len(to)}
+                "value": po / sum(to), "unit": "pairs/s", "ms_per_step": 1000.0 * sum(to) / len(to),
+                "steps": replay_steps}
             b_val = value / world if args.form == "batched" else extras["batched"]["value"]
             extras["batched_over_plain"] = b_val / extras["plain"]["value"]
             extras["headline_over_plain"] = value / world / extras["plain"]["value"]
@@ -407,21 +542,19 @@ def main():
             # differentiated form: forward + backward (dPC/dx) per step
             gvec = torch.randn(g.n, dtype=torch.float64, device="cuda")
             gx = torch.empty(g.n, dtype=torch.float64, device="cuda")
-            tds = []
-            ninfo = []
-            for k in range(args.steps):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                inf = step(seed_base + k)
+            tds, npairs = [], 0
+
+            def fwd_bwd(seed):
+                inf = step(seed)
                 binding.percis_backward(eng.ctx, gvec, gx, 1)
-                e1.record(stream)
-                e1.synchronize()
-                tds.append(e0.elapsed_time(e1) / 1000.0)
-                ninfo.append(inf)
-            extras["differentiated"] = {"value": sum(i["ell1"] + i["ell"] for i in ninfo) / sum(tds),
-                                        "unit": "pairs/s", "ms_per_step": 1000.0 * sum(tds) / len(tds)}
+                return inf
+
+            for k in range(args.steps):
+                dt, inf = _timed(torch, stream, flush, lambda: fwd_bwd(seed_base + k))
+                tds.append(dt)
+                npairs += inf["ell1"] + inf["ell"]
+            extras["differentiated"] = {"value": npairs / sum(tds), "unit": "pairs/s",
+                                        "ms_per_step": 1000.0 * sum(tds) / len(tds)}
 
             # end to end through the public API with host buffers (pinned), copies inside the timed region
             rp_h = torch.as_tensor(g.row_ptr, dtype=torch.int64).pin_memory()
@@ -433,7 +566,7 @@ def main():
                 flush.zero_()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                binding.percis_load_csr(eng.ctx, g.n, g.nnz, rp_h, col_h, False, 0)
+                binding.percis_load_csr(eng.ctx, g.n, g.nnz, rp_h, col_h, g.directed, 0)
                 binding.percis_set_states(eng.ctx, x_h, 0)
                 inf = binding.percis_estimate(eng.ctx, eps, delta, seed_base + k, pc_h, 0)
                 te.append(time.perf_counter() - t0)
@@ -441,41 +574,53 @@ def main():
             h2d = rp_h.numel() * 8 + col_h.numel() * 4 + x_h.numel() * 8
             extras["e2e"] = {"value": pe / sum(te), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                              "d2h_bytes_per_step": pc_h.numel() * 8}
-            # Graph500-style full traversals: 512 sources, every edge of the (connected) graph each
+            del rp_h, col_h, x_h, pc_h
+
+            # Graph500-style full traversals: 512 sources, every reachable edge each
             src = torch.as_tensor(np.random.default_rng(7).choice(g.n, 512, replace=False).astype(np.int32),
                                   device="cuda")
             binding.percis_msbfs(eng.ctx, 512, src, None, None)
             tf = []
             for k in range(3):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                binding.percis_msbfs(eng.ctx, 512, src, None, None)
-                e1.record(stream)
-                e1.synchronize()
-                tf.append(e0.elapsed_time(e1) / 1000.0)
-            extras["full_bfs_teps"] = {"gteps": 512 * (g.nnz // 2) / min(tf) / 1e9, "sources": 512,
+                dt, _ = _timed(torch, stream, flush, lambda: binding.percis_msbfs(eng.ctx, 512, src, None, None))
+                tf.append(dt)
+            und = 1 if g.directed else 2
+            extras["full_bfs_teps"] = {"gteps": 512 * (g.nnz // und) / min(tf) / 1e9, "sources": 512,
                                        "ms": 1000.0 * min(tf),
                                        "note": "sigma-counting BFS from 512 sources to exhaustion in one "
-                                               "batched launch; undirected edges counted once"}
+                                               "batched launch; every edge of the graph counted once per source "
+                                               "(undirected edges once)"}
+            eng.close()
+            eng = None
+            torch.cuda.empty_cache()
+
+            if not args.no_other_workloads and world == 1:
+                others = []
+                for nm, bw in (("ba100k_outbreak", False), ("ba200k_uniform", True)):
+                    if nm != args.workload:
+                        others.append(extra_workload(binding, synth, torch, stream, flush, nm, 5, 3, bw,
+                                                     seed_base))
+                        torch.cuda.empty_cache()
+                others.append(extra_uneven(binding, synth, torch, stream, flush, 2, seed_base))
+                torch.cuda.empty_cache()
+                extras["other_workloads"] = others
             if world == 1:
-                extras["cpu_baseline"] = cpu_baseline()
+                extras["cpu_baseline"] = cpu_baseline(args.workload, bidir=args.form == "bidir")
+                extras["cpu_baseline_one_sided"] = cpu_baseline(args.workload, bidir=False, budget_s=4.0)
 
     if rank == 0:
         i0 = infos[0]
-        cfg = dict(WORKLOAD_DESC)
+        cfg = dict(wl)
         cfg.update({"n": g.n, "nnz": g.nnz,
                     "form": {"bidir": "bidirectional BFS per sample", "batched": "batched multi-source BFS"}[args.form],
-                    "lanes": i0["lanes"],
-                    "lane_order": ["vertex id", "hub neighbour"][eng.options.lane_order],
-                    "direction": ["pull", "push", "per level by work estimate"][eng.options.direction],
-                    "push_alpha": eng.options.push_alpha or 0.5,
                     "ell1": i0["ell1"],
                     "ell_mean": statistics.mean(i["ell"] for i in infos),
-                    "distinct_sources_phase2_mean": statistics.mean(i["sources"][1] for i in infos),
                     "vertex_diam": i0["vertex_diam"], "dhat": i0["dhat"],
-                    "l2": "256 MiB buffer written before every timed step", "parallelism": f"replicas x{world}"})
+                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written before every timed step",
+                    "parallelism": f"replicas x{world}"})
+        if args.form == "batched":
+            cfg.update({"lanes": i0["lanes"],
+                        "distinct_sources_phase2_mean": statistics.mean(i["sources"][1] for i in infos)})
         line = {"metric": "sampled pairs/s", "value": value, "unit": "pairs/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_job / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -485,7 +630,8 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
-    eng.close()
+    if eng is not None:
+        eng.close()
 
 
 if __name__ == "__main__":

@@ -62,8 +62,12 @@ typedef enum {
  *           backtracked from it.  Same pairs and the same path distribution,
  *           other paths than BATCHED (each path uniform over the shortest
  *           paths); paths list the meeting vertex, then the s side, then the
- *           t side.  No all-paths estimator.  Scratch per block: 40 bytes per
- *           vertex of the graph (of the largest graph in a many-graph context). */
+ *           t side.  No all-paths estimator.  Scratch per block: a hashed
+ *           table of the vertices the sample reaches (32 bytes per entry, at
+ *           most half full; 2,048 entries to start, up to 131,072), plus, for
+ *           samples that outgrow it, a second pass with 48 bytes per vertex of
+ *           the graph (of the largest graph in a many-graph context) and
+ *           block. */
 enum { PERCIS_FORM_BATCHED = 0, PERCIS_FORM_PLAIN = 1, PERCIS_FORM_BIDIR = 2 };
 
 typedef struct {
@@ -75,8 +79,9 @@ typedef struct {
     int32_t keep_paths;       /* 1 (default): keep phase-2 paths for percis_backward */
     int32_t data_independent; /* 1: PercIS-DI (rho^ = D, v^ = d^2/4, no phase 1; Section IV-B) */
     double timeout_s;         /* budget of every device-side wait (default 10 s) */
-    int32_t instrument;       /* 1: batched launches also count their work into percis_info.work
-                                 (slower; for measurement runs only) */
+    int32_t instrument;       /* 1: sampling launches also count their work into percis_info.work;
+                                 2: the bidirectional form also records a per-sample trace
+                                 (percis_sample_trace).  Slower; for measurement runs only. */
     int32_t lane_order;       /* batched lane assignment: 0 = sources by vertex id, 1 (default) =
                                  sources grouped by their highest-degree neighbour, so that lanes
                                  with similar BFS levels share 64-bit words and sigma sectors */
@@ -94,7 +99,18 @@ typedef struct {
                                  launches of a phase once in a CUDA graph and replays it while
                                  the per-graph sample counts repeat (phase 1 always does);
                                  the seed is read from device memory, results are unchanged */
-    int32_t reserved;
+    int32_t bi_table_log;     /* bidirectional form: 0 (default) = a sample starts in a hashed
+                                 table of 2^11 entries per block and moves to tables 4x larger
+                                 as it grows; k in [10, 17] = start at 2^k; < 0 = every sample
+                                 in the direct store (an entry per vertex of the graph and
+                                 block).  Results do not depend on it. */
+    int32_t bi_table_max_log; /* largest hashed table: 0 (default) = the smallest size 4^j
+                                 times the first that holds every vertex of the (largest)
+                                 graph at most half full, at most 2^17 entries; k = at most
+                                 2^k.  Samples that would fill more than 3/4 of it, or pass
+                                 4,095 levels on a side, run in the direct store. */
+    int32_t bi_scratch_gib;   /* direct store: device memory its blocks may use, GiB (0 = 16);
+                                 it holds 56 bytes per vertex and block, so it caps the blocks */
 } percis_options;
 
 typedef struct {
@@ -128,8 +144,10 @@ typedef struct {
      * work[p][7] reserved
      * Bidirectional form instead: [0] edges scanned by both sides, [1] count
      * additions (edges into a new level), [2] vertices reached by both
-     * sides, [3] samples traversed; the rest 0.  bfs_launches is then the
-     * number of bidirectional launches (one per phase). */
+     * sides, [3] samples traversed (plus 2^32 per meeting layer above 256
+     * members), [4] samples the hashed tables handed to the direct store,
+     * [5] moves to a larger table; the rest 0.  bfs_launches is then the
+     * number of bidirectional passes (one per phase). */
     int64_t work[2][8];
 } percis_info;
 
@@ -218,11 +236,15 @@ percis_status percis_get_prep(percis_ctx *ctx, int32_t *perm, double *xs, double
 percis_status percis_sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag, int64_t i0, int64_t count, int32_t *s,
                                   int32_t *t);
 
-/* Single-source sigma-counting BFS with the plain kernel.  target < 0: full
- * traversal; else truncated once target's level is discovered.  Device
- * outputs dist int32[n] (-1 = not reached), sigma double[n] (0 = not
- * reached); either may be NULL. */
-percis_status percis_bfs(percis_ctx *ctx, int32_t source, int32_t target, int32_t *dist, double *sigma);
+/* Single-source sigma-counting BFS with the plain kernel (Section III-B:
+ * the BFS from s that RandomSP backtracks).  target < 0: full traversal;
+ * target == source: level 0 only; else truncated once target's level is
+ * discovered (that level's counts complete).  Device outputs dist int32[n]
+ * (-1 = not reached), sigma double[n] (0 = not reached); either may be NULL.
+ * sigma_overflow (host, optional): set to 1 when some path count reached 2^53
+ * (its FP64 value is then rounded), else 0. */
+percis_status percis_bfs(percis_ctx *ctx, int32_t source, int32_t target, int32_t *dist, double *sigma,
+                         int32_t *sigma_overflow);
 
 /* Multi-source sigma-counting BFS with the batched kernel, full traversal
  * from nsrc distinct sources (nsrc <= 512).  Device outputs, source-major:
@@ -295,6 +317,15 @@ percis_status percis_autotune(percis_ctx *ctx, int64_t probe_samples, uint64_t s
  * Returns the number of levels. */
 int64_t percis_last_levels(percis_ctx *ctx, int64_t *out, int64_t cap);
 
+/* Per-sample trace of the last bidirectional phase (measurement aid), recorded
+ * when options.instrument = 2: for sample i, out[6i..6i+5] = device time (ns)
+ * when a block took it and when it finished, edges its levels scanned,
+ * levels | store << 32 | block << 33 (store 0 = hashed tables, 1 = direct;
+ * a sample handed over shows its direct-store run), and the times the levels
+ * ended and the meeting vertex was chosen.  Returns the number of samples
+ * written (at most cap). */
+int64_t percis_sample_trace(percis_ctx *ctx, int64_t *out, int64_t cap);
+
 /* Internal nodes of the paths of the last sampling phase, t-side first.
  * Device outputs: path_ptr int64[count+1], path_nodes int32[path_ptr[count]]
  * (pass path_nodes = NULL to size it first; *total receives the total). */
@@ -321,20 +352,31 @@ percis_status percis_get_paths(percis_ctx *ctx, int64_t *path_ptr, int32_t *path
  * row_ptr int64[n+1] / col int32[nnz] the CSR (valid as percis_load_csr
  * requires; column indices outside [0, n) make the call return INVALID);
  * in_row_ptr / in_col the in-adjacency of a directed graph, or both NULL for
- * an undirected graph (in-lists = CSR rows).  target < 0: full traversal;
- * else the traversal stops once target's level is discovered.  Outputs
- * dist int32[n] (-1 = not reached) and sigma double[n] (0 = not reached),
- * written in full.  Results equal percis_bfs's.
+ * an undirected graph (in-lists = CSR rows).  The row offsets are NOT
+ * validated (there is no context that could have checked them): they must
+ * start at 0, never decrease and stay within the column array, or the kernel
+ * reads outside the caller's buffers.  target < 0: full traversal;
+ * target == source: level 0 only; else the traversal stops once target's
+ * level is discovered.  Outputs dist int32[n] (-1 = not reached) and sigma
+ * double[n] (0 = not reached), written in full.  Results equal percis_bfs's.
+ * timeout_s: budget of each device-side wait (<= 0: 10 s); a wait that runs
+ * out makes the call return TIMEOUT and leaves the scratch usable by the next
+ * call.  sigma_overflow (host, optional): set to 1 when some path count
+ * reached 2^53 (its FP64 value is then rounded), else 0.
  *
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) and the launch size; make that first call before any
- * stream capture.  Every call uses the same scratch array and clears what
- * must start at zero; calls that overlap on the GPU race on it, so serialise
- * them.  Errors: INVALID (n outside [1, PERCIS_NOALLOC_MAX_N], NULL pointer,
- * vertex out of range), TIMEOUT, CUDA. */
+ * (cudaGetSymbolAddress) and the launch size.  Every call enqueues a
+ * memset, a cooperative launch and a copy, then synchronises the stream, so
+ * it must never be called on a stream that is being captured: such a call
+ * returns INVALID without issuing any work.  Every call uses the same
+ * scratch array and clears what must start at zero; calls that overlap on
+ * the GPU race on it, so serialise them.  Errors: INVALID (n outside [1,
+ * PERCIS_NOALLOC_MAX_N], NULL pointer, vertex out of range, a column index
+ * outside [0, n) -- that entry is skipped and the outputs hold the traversal
+ * without it --, a capturing stream), TIMEOUT, CUDA. */
 percis_status percis_bfs_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col, const int64_t *in_row_ptr,
                                  const int32_t *in_col, int32_t source, int32_t target, int32_t *dist, double *sigma,
-                                 void *stream);
+                                 void *stream, double timeout_s, int32_t *sigma_overflow);
 
 #ifdef __cplusplus
 }

@@ -40,7 +40,8 @@ class percis_options(ctypes.Structure):
                 ("data_independent", ctypes.c_int32), ("timeout_s", ctypes.c_double),
                 ("instrument", ctypes.c_int32), ("lane_order", ctypes.c_int32),
                 ("direction", ctypes.c_int32), ("estimator", ctypes.c_int32), ("push_alpha", ctypes.c_double),
-                ("cuda_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cuda_graphs", ctypes.c_int32), ("bi_table_log", ctypes.c_int32),
+                ("bi_table_max_log", ctypes.c_int32), ("bi_scratch_gib", ctypes.c_int32)]
 
 
 class percis_info(ctypes.Structure):
@@ -86,16 +87,17 @@ SIGNATURES = {
     "percis_backward": (_ST, [_P, _P, _P, ctypes.c_int]),
     "percis_get_prep": (_ST, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "percis_sample_pairs": (_ST, [_P, _U64, _U32, _I64, _I64, _P, _P]),
-    "percis_bfs": (_ST, [_P, _I32, _I32, _P, _P]),
+    "percis_bfs": (_ST, [_P, _I32, _I32, _P, _P, _P]),
     "percis_msbfs": (_ST, [_P, _I32, _P, _P, _P]),
     "percis_run_phase": (_ST, [_P, _U64, ctypes.c_int, _I64, _P, _P, _P, _P, _P]),
     "percis_get_paths": (_ST, [_P, _P, _P, _P]),
     "percis_last_levels": (_I64, [_P, _P, _I64]),
+    "percis_sample_trace": (_I64, [_P, _P, _I64]),
     "percis_autotune": (_ST, [_P, _I64, _U64, ctypes.POINTER(percis_options)]),
     "percis_load_graphs": (_ST, [_P, _I32, _P, _I64, _I64, _P, _P, ctypes.c_int]),
     "percis_num_graphs": (_I32, [_P]),
     "percis_estimate_graphs": (_ST, [_P, _F64, _F64, _U64, _P, ctypes.c_int, _P]),
-    "percis_bfs_noalloc": (_ST, [_I64, _P, _P, _P, _P, _I32, _I32, _P, _P, _P]),
+    "percis_bfs_noalloc": (_ST, [_I64, _P, _P, _P, _P, _I32, _I32, _P, _P, _P, _F64, _P]),
 }
 
 _lib = None
@@ -214,8 +216,12 @@ def percis_sample_pairs(ctx, seed: int, tag: int, i0: int, count: int, s, t):
     _check(ctx, load_library().percis_sample_pairs(ctx, seed, tag, i0, count, _ptr(s), _ptr(t)))
 
 
-def percis_bfs(ctx, source: int, target: int, dist, sigma):
-    _check(ctx, load_library().percis_bfs(ctx, source, target, _ptr(dist), _ptr(sigma)))
+def percis_bfs(ctx, source: int, target: int, dist, sigma) -> bool:
+    """Single-source sigma BFS into device tensors; returns True when a path
+    count reached 2^53 (sigma rounded there)."""
+    ovf = ctypes.c_int32(0)
+    _check(ctx, load_library().percis_bfs(ctx, source, target, _ptr(dist), _ptr(sigma), ctypes.byref(ovf)))
+    return bool(ovf.value)
 
 
 def percis_msbfs(ctx, nsrc: int, sources, dist, sigma):
@@ -234,10 +240,17 @@ def percis_get_paths(ctx, path_ptr=None, path_nodes=None) -> int:
 
 
 def percis_bfs_noalloc(n: int, row_ptr, col, in_row_ptr, in_col, source: int, target: int, dist, sigma,
-                       stream: int | None = None) -> int:
-    """Allocation-free single-source sigma BFS (device tensors); returns the status code."""
-    return int(load_library().percis_bfs_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(in_row_ptr), _ptr(in_col),
-                                                 source, target, _ptr(dist), _ptr(sigma), stream))
+                       stream: int | None = None, timeout_s: float = 0.0, overflow: list | None = None) -> int:
+    """Allocation-free single-source sigma BFS (device tensors); returns the
+    status code.  If `overflow` is a list, the sigma-overflow flag (0/1) is
+    appended to it."""
+    ovf = ctypes.c_int32(0)
+    st = int(load_library().percis_bfs_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(in_row_ptr), _ptr(in_col),
+                                               source, target, _ptr(dist), _ptr(sigma), stream, float(timeout_s),
+                                               ctypes.byref(ovf)))
+    if overflow is not None:
+        overflow.append(int(ovf.value))
+    return st
 
 
 def percis_load_graphs(ctx, graph_vptr, row_ptr, col, directed: bool = False):
@@ -266,6 +279,15 @@ def percis_autotune(ctx, probe_samples: int, seed: int) -> percis_options:
     o = percis_options()
     _check(ctx, load_library().percis_autotune(ctx, probe_samples, seed, ctypes.byref(o)))
     return o
+
+
+def percis_sample_trace(ctx, cap: int) -> np.ndarray:
+    """Per-sample trace of the last bidirectional phase (instrument = 2):
+    rows {start ns, end ns, edges, levels | store << 32 | block << 33, levels end ns,
+    meeting choice end ns}."""
+    out = np.zeros((max(cap, 1), 6), dtype=np.int64)
+    k = int(load_library().percis_sample_trace(ctx, out.ctypes.data, cap))
+    return out[:k]
 
 
 def percis_last_levels(ctx, cap: int = 32) -> list[tuple[int, ...]]:

@@ -43,18 +43,23 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, defines=(),
+          lib_path: str | None = None) -> str:
+    """Compiles the library; `defines` (NAME=VALUE strings) and `lib_path` build a
+    variant of the tuning constants into another file (always rebuilt)."""
+    lib = lib_path or LIB
+    out = OUT if not defines and lib_path is None else lib + ".objs"
+    if not force and not defines and lib_path is None and up_to_date():
         return LIB
-    os.makedirs(OUT, exist_ok=True)
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", ARCH, "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-              "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
+              "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")] + ["-D" + d for d in defines]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
 
     def one(src: str) -> str:
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
+        obj = os.path.join(out, os.path.basename(src) + ".o")
         cmd = [nvcc] + common + ["-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, "-x", "cu"] + common + ["-c", src, "-o", obj]
@@ -67,13 +72,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", ARCH, "-cudart", "static", "-o", tmp] + objs + ["-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

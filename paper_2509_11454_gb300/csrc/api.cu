@@ -371,7 +371,9 @@ void percis_destroy(percis_ctx *ctx) {
                       &ctx->pc_tmp, &ctx->grad_tmp, &ctx->host_pinned, &ctx->vorder,
                       &ctx->fq0, &ctx->fq1, &ctx->acc_ap,
                       &ctx->ap_tau, &ctx->ap_stamp, &ctx->ap_list, &ctx->plan_dev, &ctx->bi_info,
-                      &ctx->bi_queue};
+                      &ctx->bi_queue, &ctx->radix_counts, &ctx->sort_a, &ctx->sort_b,
+                      &ctx->table_ctl, &ctx->bi_hent, &ctx->bi_hq, &ctx->bi_hep, &ctx->bi_defer,
+                      &ctx->bi_trace};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->counters.p) cudaFree(ctx->counters.p);
@@ -620,7 +622,9 @@ percis_status percis_sample_pairs(percis_ctx *ctx, uint64_t seed, uint32_t tag, 
     return PERCIS_OK;
 }
 
-percis_status percis_bfs(percis_ctx *ctx, int32_t source, int32_t target, int32_t *dist, double *sigma) {
+percis_status percis_bfs(percis_ctx *ctx, int32_t source, int32_t target, int32_t *dist, double *sigma,
+                         int32_t *sigma_overflow) {
+    if (sigma_overflow) *sigma_overflow = 0;
     PERCIS_TRY(need_graph(ctx));
     if (source < 0 || source >= ctx->n || target >= ctx->n) return set_err(ctx, PERCIS_E_INVALID, "bad vertex");
     DeviceGuard g(ctx->device);
@@ -630,6 +634,7 @@ percis_status percis_bfs(percis_ctx *ctx, int32_t source, int32_t target, int32_
     const uint32_t st = read_status(ctx);
     if (st & DEV_TIMEOUT) return set_err(ctx, PERCIS_E_TIMEOUT, "device wait exceeded its budget");
     PERCIS_CUDA(ctx, cudaGetLastError());
+    if (sigma_overflow) *sigma_overflow = (st & DEV_SIGMA_OVERFLOW) ? 1 : 0;
     return PERCIS_OK;
 }
 
@@ -772,6 +777,19 @@ int64_t percis_last_levels(percis_ctx *ctx, int64_t *out, int64_t cap) {
     for (int64_t L = 0; L < lv; ++L)
         for (int k = 0; k < 6; ++k) out[6 * L + k] = (int64_t)hc.lvl_rec[L][k];
     return lv;
+}
+
+int64_t percis_sample_trace(percis_ctx *ctx, int64_t *out, int64_t cap) {
+    if (!ctx || !ctx->bi_trace.p || !out || cap < 0) return 0;
+    DeviceGuard g(ctx->device);
+    const int64_t k = std::min<int64_t>(ctx->bi_trace_n, cap);
+    if (k > 0 && (cudaMemcpyAsync(out, ctx->bi_trace.p, sizeof(int64_t) * 6 * k, cudaMemcpyDeviceToHost,
+                                  ctx->stream) != cudaSuccess ||
+                  cudaStreamSynchronize(ctx->stream) != cudaSuccess)) {
+        cudaGetLastError();
+        return 0;
+    }
+    return k;
 }
 
 percis_status percis_get_paths(percis_ctx *ctx, int64_t *path_ptr, int32_t *path_nodes, int64_t *total) {

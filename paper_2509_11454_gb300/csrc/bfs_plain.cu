@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_bfs(PlainArgs a) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t *cur = a.qa, *nxt = a.qb;
     int L = 0, ecc = 0;
-    for (;;) {
+    // a target equal to the source is settled at level 0: nothing to expand
+    for (; t < 0 || t != s;) {
         const int nq = (int)ld_relaxed_u32((const uint32_t *)&ctl->qsize[L % 3]);
         // the slot level L + 2 will fill: last read before the previous barrier
         if (blockIdx.x == 0 && threadIdx.x == 0) ctl->qsize[(L + 2) % 3] = 0;
@@ -230,8 +231,6 @@ __global__ void k_argmax_degree(const int64_t *rp, const int32_t *ep, const int3
     if ((threadIdx.x & 31) == 0 && m) atomicMax(best, m);
 }
 
-int g_plain_grid = 0;
-
 }  // namespace
 
 static percis_status ensure_plain(percis_ctx *ctx) {
@@ -248,10 +247,10 @@ static percis_status ensure_plain(percis_ctx *ctx) {
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->plain_ctl.p, 0, 256, ctx->stream));
         ctx->epoch = 0;
     }
-    if (g_plain_grid == 0) {
+    if (ctx->plain_grid == 0) {  // co-resident blocks on this context's device
         int per_sm = 0;
         PERCIS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plain_bfs, kPlainBlock, 0));
-        g_plain_grid = std::max(1, per_sm) * ctx->num_sms;
+        ctx->plain_grid = std::max(1, per_sm) * ctx->num_sms;
     }
     return PERCIS_OK;
 }
@@ -282,7 +281,7 @@ percis_status plain_bfs(percis_ctx *ctx, const int32_t *s_dev, const int32_t *t_
     a.levels_only = levels_only ? 1 : 0;
     a.budget_ns = (uint64_t)(ctx->opt.timeout_s * 1e9);
     void *args[] = {&a};
-    PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_plain_bfs, dim3(g_plain_grid), dim3(kPlainBlock),
+    PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_plain_bfs, dim3(ctx->plain_grid), dim3(kPlainBlock),
                                                  args, 0, ctx->stream));
     ctx->launches++;
     return PERCIS_OK;

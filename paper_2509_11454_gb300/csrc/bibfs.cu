@@ -14,13 +14,27 @@
 //     from it (towards s over in-edges, towards t over out-edges), each step
 //     taking the first candidate whose running count reaches u sigma(w).
 // Samples are independent, so blocks take them from a shared counter and
-// never wait on one another.  Each block owns a slot of scratch arrays
-// (level + epoch word, count and queue per vertex and side); a vertex belongs
-// to the current sample only while its word carries the sample's epoch, so
-// nothing is ever cleared: a claim swaps a side's {level word, count} pair in
-// one 16-byte compare-and-swap, setting the count to the claiming parent's,
-// and the other parents of the level add theirs, all in one pass over the
-// level's edges.
+// never wait on one another.
+//
+// Scratch.  Each block owns a slot; a sample's state is one 32-byte entry per
+// vertex it reached: per side a word {level, sample epoch} and a path count.
+// A vertex belongs to the current sample only while a word carries the
+// sample's epoch, so nothing is ever cleared: a claim swaps a side's {word,
+// count} pair in one 16-byte compare-and-swap, setting the count to the
+// claiming parent's, and the other parents of the level add theirs, all in
+// one pass over the level's edges.  Two stores of the entries:
+//   * hashed (every sample first): an open-addressing table per slot keyed by
+//     vertex id (the words carry the vertex too), linear probing.  A sample
+//     starts in a small table that stays in L2 across the samples of the slot
+//     (2,048 entries = 64 KB by default) and, between levels, moves to a table
+//     four times larger whenever the coming level could fill more than half of
+//     it (the entries are re-inserted by walking both sides' queues).  Work and
+//     memory follow the vertices a sample touches, not n.
+//   * direct (samples that would overfill the largest table or pass 4,095
+//     levels): entry v for vertex v, O(n) per slot, so few slots.  The hashed
+//     pass hands such samples over untouched (it writes nothing outside its
+//     slot before the sides meet).
+// A sample's pairs, paths and counts do not depend on which store ran it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,16 +55,29 @@ constexpr int kBiBlock = PERCIS_BI_BLOCK;
 #define PERCIS_MEET_CAP 256
 #endif
 constexpr int kMeetCap = PERCIS_MEET_CAP;  // meeting-layer members kept in shared memory
-constexpr int kFlat = 512;  // frontiers up to this size have their edges spread over the block
+constexpr int kMeetBuckets = 1024;          // id buckets per round of the large-layer search
+constexpr int kBackWarp = 256;              // candidate lists up to this length: one warp per backtrack step
+constexpr int kLvCap = 64;                  // levels per side whose queue ranges are kept (reverse backtrack)
+constexpr int kFlat = 512;  // frontier vertices per chunk whose edges are spread over the block
+#ifndef PERCIS_EDGE_BATCH
+#define PERCIS_EDGE_BATCH 2
+#endif
+constexpr int kEdgeBatch = PERCIS_EDGE_BATCH;  // edges a thread has in flight (their loads issued together)
 #ifndef PERCIS_BI_MINB
 #define PERCIS_BI_MINB 6
 #endif
+constexpr uint32_t kHashLevels = 4095;            // levels a hashed word holds (12 bits)
+constexpr uint32_t kHashEpochs = (1u << 20) - 1;  // epochs a hashed word holds (20 bits)
+constexpr int kDefaultH0Log = 11;                 // first table: 2,048 entries
+constexpr int kMaxHLog = 20;                      // largest table: at most 2^20 entries
+constexpr int kMinHLog = 10;                      // smallest table (new entries stop at 3/4 minus a block)
 
 struct BiArgs {
     int64_t n;
     const int64_t *rp, *irp;
     const int32_t *col, *icol;
-    int64_t count;
+    int64_t count;               // samples of the phase, or of the list
+    const int32_t *list;         // sample indices to run (null: 0 .. count-1)
     const int32_t *pair_s, *pair_t;
     int32_t *kind, *ilen;
     long long *path_off;
@@ -60,38 +87,62 @@ struct BiArgs {
     unsigned long long *cnt;
     uint64_t seed;
     uint32_t tag;
-    uint32_t epoch_base;
-    unsigned long long *vs;     // [slots][n][4]: per vertex and side {level word (epoch << 32 |
-                                // level), path count}, side 0 first: one 32-byte sector holds
-                                // everything a visit touches
-    int32_t *queue;             // [slots][2][n]: visited vertices of each side in level order
-    int32_t slots;
-    unsigned long long *next;   // next sample to take
+    unsigned long long *ent;     // entries: [slots][region][4] {word 0, count 0, word 1, count 1}
+    int2 *queue;                 // [slots][3][qcap]: {vertex, entry} of each side in level order, then
+                                 // the meeting layer's members (claims of vertices the other side holds)
+    int64_t region;              // entries per slot
+    int64_t qcap;                // queue entries per side and slot
+    unsigned long long *next;    // next sample to take
     uint32_t *status;
-    // many graphs: records are indexed within the sample's graph (vertex - its
-    // first id), so a slot holds nslot records (the largest graph)
-    const int32_t *gid;         // graph of every vertex, or null for one graph
-    const int64_t *vbase;       // first vertex id of every graph
-    int64_t nslot;
-    unsigned long long *work;   // optional work counters: [0] edges scanned, [1] count additions,
-                                // [2] vertices reached (both sides), [3] samples traversed
+    unsigned long long *work;    // optional work counters: [0] edges scanned, [1] count additions,
+                                 // [2] vertices reached (both sides), [3] samples traversed (+ 2^32 per
+                                 // meeting layer above the shared capacity), [4] samples handed to the
+                                 // direct store, [5] table moves
+    // direct store
+    uint32_t epoch_base;         // epoch of sample i: epoch_base + i + 1 (32 bits)
+    const int32_t *gid;          // many graphs: graph of every vertex (entries indexed within the
+    const int64_t *vbase;        //   sample's graph: vertex - first id), or null for one graph
+    // hashed store
+    int32_t h0_log, hmax_log;    // first and largest table: 2^h0_log, 2^hmax_log entries (step x4)
+    uint32_t *slot_epoch;        // per slot: last epoch used (20 bits; persists across launches)
+    int32_t *deferred;           // samples handed to the direct store
+    unsigned int *n_deferred;
+    int32_t sorted;              // every adjacency list strictly increasing (reverse backtrack allowed)
+    unsigned long long *trace;   // optional, per sample: {start ns, end ns, edges scanned,
+                                 // levels | store << 32 | slot << 33, end of the levels ns,
+                                 // end of the meeting vertex's choice ns}
 };
 
-// one field of the per-vertex records, indexed by vertex
-struct Strided {
-    unsigned long long *p;
-    __device__ __forceinline__ unsigned long long &operator[](int64_t v) const { return p[4 * v]; }
+// ------------------------------------------------------------------ words
+// direct:  word = epoch (32) << 32 | level (32)
+// hashed:  word = vertex (32) << 32 | epoch (20) << 12 | level (12)
+template <bool HASH>
+struct Word;
+template <>
+struct Word<false> {
+    static __device__ __forceinline__ unsigned long long make(int32_t, uint32_t ep, uint32_t lev) {
+        return ((unsigned long long)ep << 32) | lev;
+    }
+    static __device__ __forceinline__ bool current(unsigned long long w, uint32_t ep) {
+        return (uint32_t)(w >> 32) == ep;
+    }
+    static __device__ __forceinline__ uint32_t level(unsigned long long w) { return (uint32_t)w; }
+};
+template <>
+struct Word<true> {
+    static __device__ __forceinline__ unsigned long long make(int32_t v, uint32_t ep, uint32_t lev) {
+        return ((unsigned long long)(uint32_t)v << 32) | ((unsigned long long)ep << 12) | lev;
+    }
+    static __device__ __forceinline__ bool current(unsigned long long w, uint32_t ep) {
+        return (uint32_t)((w >> 12) & 0xfffffu) == ep;
+    }
+    static __device__ __forceinline__ uint32_t level(unsigned long long w) { return (uint32_t)(w & 0xfffu); }
+    static __device__ __forceinline__ int32_t vertex(unsigned long long w) { return (int32_t)(w >> 32); }
 };
 
-// the path-count fields, as exact integers or (past 2^53) as FP64
-template <class C>
-struct CountView {
-    unsigned long long *p;
-    __device__ __forceinline__ C &operator[](int64_t v) const { return *reinterpret_cast<C *>(p + 4 * v); }
-};
-
-__device__ __forceinline__ unsigned long long pack(uint32_t ep, uint32_t lev) {
-    return ((unsigned long long)ep << 32) | lev;
+// home entry of vertex v in a table of 2^lg entries (Fibonacci hashing)
+__device__ __forceinline__ uint32_t hash_home(int32_t v, int lg) {
+    return ((uint32_t)v * 0x9E3779B1u) >> (32 - lg);
 }
 
 template <class C>
@@ -105,12 +156,16 @@ __device__ __forceinline__ C count_of(unsigned long long b) {
     else return b;
 }
 
-// one side's {level word, count} of a vertex: 16 aligned bytes, read in one request
+// one side's {word, count} of an entry: 16 aligned bytes, read in one request
 __device__ __forceinline__ void ld_pair(const unsigned long long *p, unsigned long long &w, unsigned long long &c) {
     asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(w), "=l"(c) : "l"(p) : "memory");
 }
 
-// 16-byte compare-and-swap of {level word, count}: the previous pair
+__device__ __forceinline__ void st_pair(unsigned long long *p, unsigned long long w, unsigned long long c) {
+    asm volatile("st.global.cg.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(w), "l"(c) : "memory");
+}
+
+// 16-byte compare-and-swap of {word, count}: the previous pair
 __device__ __forceinline__ void cas_pair(unsigned long long *p, unsigned long long cw, unsigned long long cc,
                                          unsigned long long nw, unsigned long long nc, unsigned long long &ow,
                                          unsigned long long &oc) {
@@ -138,42 +193,79 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
     return t;
 }
 
+// Entry of vertex v in a hashed table (tab, 2^lg entries), or -1 when no word
+// of the current sample carries v.  An entry holds one vertex: its words of
+// the current epoch (one or both sides) all name it.
+__device__ __forceinline__ int64_t hash_find(const unsigned long long *tab, int lg, int32_t v, uint32_t ep) {
+    using W = Word<true>;
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t p = hash_home(v, lg);
+    for (uint32_t k = 0; k <= mask; ++k, p = (p + 1) & mask) {
+        const unsigned long long w0 = __ldcg(&tab[4ull * p]), w1 = __ldcg(&tab[4ull * p + 2]);
+        const bool c0 = W::current(w0, ep), c1 = W::current(w1, ep);
+        if (!c0 && !c1) return -1;
+        if (W::vertex(c0 ? w0 : w1) == v) return p;
+    }
+    return -1;
+}
+
 // C = unsigned long long: exact counts (flagged at 2^53, products checked);
 // C = double: FP64 counts, the rerun of a phase whose counts passed 2^53.
-template <class C>
+template <class C, bool HASH>
 __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
+    using W = Word<HASH>;
     constexpr bool FP = std::is_floating_point<C>::value;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nw = kBiBlock / 32;
     const int64_t n = a.n;
     const size_t slot = blockIdx.x;
-    // side 0 = forward from s over out-edges, side 1 = backward from t over in-edges
-    unsigned long long *const vslot = a.vs + slot * (size_t)a.nslot * 4;
-    int32_t *const queue0 = a.queue + (slot * 2) * a.nslot, *const queue1 = queue0 + a.nslot;
+    unsigned long long *const sent = a.ent + slot * (size_t)a.region * 4;
+    int2 *const queue0 = a.queue + (slot * 3) * (size_t)a.qcap, *const queue1 = queue0 + a.qcap;
+    int2 *const memb = queue1 + a.qcap;
 
     __shared__ long long s_i;
     // claims of a level go to counter set it % 3; thread 0 clears set (it + 1) % 3
     // at the start of level it, two barriers after its last readers
-    __shared__ int s_new[3], s_meet;
+    __shared__ int s_new[3], s_meet, s_full;
+    __shared__ C s_bkt[kMeetBuckets];
+    __shared__ int s_sel;
+    __shared__ C s_base;
+    __shared__ unsigned long long s_off;  // the sample's path slot in the arena
+    __shared__ int32_t s_pick;            // a backtrack step's choice
+    __shared__ long long s_pickp;
+    __shared__ int s_tstar, s_tlast;      // segment of a long candidate list holding the choice
+    __shared__ C s_tpre;
+    __shared__ int32_t s_lv[2][kLvCap + 2];  // queue range of level L of a side: [s_lv[L], s_lv[L+1])
+    __shared__ int32_t s_mj[kMeetCap];       // a reverse backtrack candidate's place in the list
+    __shared__ int s_nc;
     __shared__ unsigned long long s_newcost[3];
-    __shared__ int s_nm;
     __shared__ int32_t s_mv[kMeetCap];
+    __shared__ int32_t s_mp[kMeetCap];
     __shared__ C s_mw[kMeetCap];
     __shared__ C s_redc[nw];
-    __shared__ int32_t s_best[nw];
-    __shared__ int64_t s_fe[kFlat];  // first edge of each frontier vertex
-    __shared__ C s_fs[kFlat];
-    __shared__ int32_t s_pre[kFlat + 1];
-    __shared__ unsigned long long s_work[4];
-    if (threadIdx.x < 4) s_work[threadIdx.x] = 0ull;
+    __shared__ unsigned long long s_best[nw];
+    __shared__ int64_t s_fe[kFlat];  // first edge of each frontier vertex of a chunk
+    __shared__ C s_fs[kFlat];        // its path count
+    __shared__ int64_t s_pre[kFlat + 1];  // prefix sums of the chunk's degrees
+    __shared__ unsigned long long s_work[6];
+    if (threadIdx.x < 6) s_work[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) s_tlast = -1;
     unsigned long long n_add = 0ull;
+    uint32_t ep_slot = HASH ? a.slot_epoch[slot] : 0u;
 
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_i = (long long)atomicAdd(a.next, 1ull);
+        if (threadIdx.x == 0) {
+            const long long k = (long long)atomicAdd(a.next, 1ull);
+            s_i = k < a.count ? (a.list ? (long long)a.list[k] : k) : -1ll;
+        }
         __syncthreads();
         const long long i = s_i;
-        if (i >= a.count) break;
+        if (i < 0) break;
+        const unsigned long long t_start = a.trace && threadIdx.x == 0 ? globaltimer_ns() : 0ull;
+        unsigned long long t_levels = 0ull, t_meet = 0ull;
+        unsigned long long smp_edges = 0ull;  // (thread 0)
+        int smp_levels = 0;
         if (a.kind[i] != 0) {  // zero weight: no path (block-uniform)
             if (threadIdx.x == 0) {
                 a.ilen[i] = 0;
@@ -182,23 +274,53 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
             continue;
         }
         const int32_t s = a.pair_s[i], t = a.pair_t[i];
-        const uint32_t ep = a.epoch_base + (uint32_t)i + 1u;
-        // record of vertex v at vrec[4 (v - base)]: the sample's graph starts at base
-        const int64_t base = a.gid ? a.vbase[a.gid[s]] : 0;
-        unsigned long long *const vrec = vslot - 4 * base;
-        // record: {level word, count} of side 0, then of side 1
-        const Strided info0{vrec}, info1{vrec + 2};
-        const CountView<C> sig0{vrec + 1}, sig1{vrec + 3};
+        uint32_t ep;
+        if constexpr (HASH) {
+            if (ep_slot >= kHashEpochs) {
+                // the slot's epochs are used up: clear every word of its tables (once per
+                // 2^20 - 1 samples of the slot), then start again at 1
+                for (int64_t e = threadIdx.x; e < a.region; e += kBiBlock) {
+                    sent[4 * e] = 0ull;
+                    sent[4 * e + 2] = 0ull;
+                }
+                __threadfence();
+                __syncthreads();
+                ep_slot = 0u;
+            }
+            ep = ++ep_slot;
+        } else {
+            ep = a.epoch_base + (uint32_t)i + 1u;
+        }
+        // the table in use: hashed, 2^lg entries at tab (offset toff in the slot);
+        // direct, entry v - base of the sample's graph at tab + 4 v
+        int lg = a.h0_log;
+        int64_t toff = 0;
+        unsigned long long *tab = sent;
+        if constexpr (!HASH) {
+            if (a.gid) tab = sent - 4 * a.vbase[a.gid[s]];
+        }
+        int64_t ps, pt;
+        if constexpr (HASH) {
+            // s and t are the sample's first entries: s at its home, t at its own
+            // (the next entry, as linear probing gives, when the homes collide)
+            ps = hash_home(s, lg);
+            pt = hash_home(t, lg);
+            if (pt == ps) pt = (pt + 1) & ((1 << lg) - 1);
+        } else {
+            ps = s;
+            pt = t;
+        }
         if (threadIdx.x == 0) {
-            info0[s] = pack(ep, 0);
-            sig0[s] = C(1);
-            queue0[0] = s;
-            info1[t] = pack(ep, 0);
-            sig1[t] = C(1);
-            queue1[0] = t;
+            st_pair(&tab[4 * ps], W::make(s, ep, 0), count_bits(C(1)));
+            st_pair(&tab[4 * pt + 2], W::make(t, ep, 0), count_bits(C(1)));
+            queue0[0] = make_int2(s, (int)ps);
+            queue1[0] = make_int2(t, (int)pt);
             s_new[0] = 0;
             s_newcost[0] = 0ull;
             s_meet = 0;
+            s_full = 0;
+            s_lv[0][0] = s_lv[1][0] = 0;
+            s_lv[0][1] = s_lv[1][1] = 1;
         }
         __syncthreads();
         // level state of both sides, the same in every thread
@@ -207,7 +329,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
         unsigned long long cost[2] = {(unsigned long long)(a.rp[s + 1] - a.rp[s]),
                                       (unsigned long long)(a.irp[t + 1] - a.irp[t])};
         int x = 0;
-        bool met = s != t;
+        bool met = s != t, handed = false;
         if (met) {
             met = false;
             for (int it = 0;; ++it) {
@@ -215,129 +337,271 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 x = cost[0] <= cost[1] ? 0 : 1;
                 const long long lo = x ? qlo[1] : qlo[0], hi = x ? qhi[1] : qhi[0];
                 const uint32_t nl = (x ? lev[1] : lev[0]) + 1;
+                if constexpr (HASH) {
+                    if (nl > kHashLevels) {  // past the words' 12 bits: the direct store takes it
+                        handed = true;
+                        break;
+                    }
+                    // the coming level adds at most cost[x] entries: keep the table at most
+                    // half full (the largest table is the limit; claims past 3/4 of it hand
+                    // the sample over)
+                    const unsigned long long need =
+                        2ull * ((unsigned long long)(qhi[0] + qhi[1]) + (x ? cost[1] : cost[0])) + 2ull * kBiBlock;
+                    int nlg = lg;
+                    int64_t noff = toff;
+                    while (nlg + 2 <= a.hmax_log && (1ull << nlg) < need) {
+                        noff += 1ll << nlg;
+                        nlg += 2;
+                    }
+                    if (nlg != lg) {
+                        // move to the table of 2^nlg entries: re-insert every entry by
+                        // walking the queues.  Side 0's queue first, claiming side-0 pairs
+                        // only (and copying a side-1 pair of the same vertex with it); then,
+                        // after a barrier, side 1's queue, whose vertices are either found
+                        // (reached by side 0 too) or claim side-1 pairs.  Within each walk
+                        // every claim is on the same pair of words, so two vertices never
+                        // share an entry.
+                        unsigned long long *ntab = sent + 4 * noff;
+                        const uint32_t nmask = (1u << nlg) - 1u;
+                        for (int z = 0; z < 2; ++z) {
+                            int2 *qz = z ? queue1 : queue0;
+                            const long long qn = z ? qhi[1] : qhi[0];
+                            const int zs = z ? 2 : 0;
+                            for (long long k = threadIdx.x; k < qn; k += kBiBlock) {
+                                const int2 qe = qz[k];
+                                unsigned long long o0, oc0, o1, oc1;
+                                ld_pair(&tab[4ull * qe.y], o0, oc0);
+                                ld_pair(&tab[4ull * qe.y + 2], o1, oc1);
+                                const bool cur0 = W::current(o0, ep), cur1 = W::current(o1, ep);
+                                uint32_t p = hash_home(qe.x, nlg);
+                                for (uint32_t probes = 0; probes <= nmask;) {
+                                    unsigned long long w0, c0, w1, c1;
+                                    ld_pair(&ntab[4ull * p], w0, c0);
+                                    ld_pair(&ntab[4ull * p + 2], w1, c1);
+                                    const bool n0 = W::current(w0, ep), n1 = W::current(w1, ep);
+                                    if (n0 || n1) {
+                                        if (Word<true>::vertex(n0 ? w0 : w1) == qe.x) break;  // inserted
+                                        p = (p + 1) & nmask;  // another vertex's entry
+                                        ++probes;
+                                        continue;
+                                    }
+                                    // an empty entry: claim it with this walk's pair (side 1 walk:
+                                    // only vertices side 0 never reached get here)
+                                    unsigned long long pw, pc;
+                                    const unsigned long long ew = z ? w1 : w0, ec = z ? c1 : c0;
+                                    cas_pair(&ntab[4ull * p + zs], ew, ec, z ? o1 : o0, z ? oc1 : oc0, pw, pc);
+                                    if (pw == ew && pc == ec) {
+                                        if (z == 0 && cur1) st_pair(&ntab[4ull * p + 2], o1, oc1);
+                                        break;
+                                    }
+                                    // claimed meanwhile: look at the same entry again
+                                }
+                                (void)cur0;
+                                qz[k].y = (int)p;
+                            }
+                            __syncthreads();
+                        }
+                        if (a.work && threadIdx.x == 0) s_work[5] += 1ull;
+                        __syncthreads();
+                        lg = nlg;
+                        toff = noff;
+                        tab = ntab;
+                    }
+                }
                 const int cs = it % 3;
                 if (threadIdx.x == 0) {
                     s_new[(it + 1) % 3] = 0;
                     s_newcost[(it + 1) % 3] = 0ull;
                 }
-                const unsigned long long want = pack(ep, nl);
+                const int64_t hmask = HASH ? (1ll << lg) - 1 : 0;
+                // new entries stop short of 3/4 of the table (each thread has at most one
+                // claim in flight past the check)
+                const long long cap_new = HASH ? ((3ll << lg) >> 2) - kBiBlock : 0ll;
+                const long long known = qhi[0] + qhi[1];
                 unsigned long long ne = 0ull;
                 // level nl: claim unreached neighbours and add the counts over
                 // every edge into the level in one pass
-                const Strided infx = x ? info1 : info0;
-                const CountView<C> sigx = x ? sig1 : sig0;
-                const Strided infy = x ? info0 : info1;
-                int32_t *qx = x ? queue1 : queue0;
+                const int xs = x ? 2 : 0, ys = x ? 0 : 2;  // word offsets of the two sides in an entry
+                int2 *qx = x ? queue1 : queue0;
                 const int64_t *px = x ? a.irp : a.rp;
                 const int32_t *ax = x ? a.icol : a.col;
-                const long long f = hi - lo;
                 // one edge: claim the neighbour if unreached, add the parent's count if
-                // it lies on the new level.  A claim swaps the whole {level word,
-                // count} pair, so it also sets the count to the claiming parent's and
-                // counts never need clearing: a count is read only where its level
-                // word carries the sample's epoch.
-                auto visit = [&](const int32_t v, const C su) {
-                    unsigned long long *const pr = &infx[v];
-                    // what a claim needs (degree, the other side's level word) is read
-                    // alongside the pair, off the claim's dependent chain
-                    const uint32_t dg = (uint32_t)(px[v + 1] - px[v]);  // < 2^31
-                    const unsigned long long oy = __ldcg(&infy[v]);
-                    unsigned long long ow, oc;
-                    ld_pair(pr, ow, oc);
-                    bool at = ow == want, won = false;
-                    if ((uint32_t)(ow >> 32) != ep) {
-                        unsigned long long pw, pc;
-                        cas_pair(pr, ow, oc, want, count_bits(su), pw, pc);
-                        if (pw == ow && pc == oc) {
-                            won = true;
-                            // the lanes that claimed together reserve their queue slots and
-                            // add their degrees with one shared atomic each (a 64-bit shared
-                            // add would be a contended compare-and-swap loop per lane)
-                            const unsigned grp = __activemask();
-                            const int lead = __ffs(grp) - 1;
-                            const uint32_t dlo = __reduce_add_sync(grp, dg & 0xffffu);
-                            const uint32_t dhi = __reduce_add_sync(grp, dg >> 16);
-                            int q0 = 0;
-                            if (lane == lead) {
-                                q0 = atomicAdd(&s_new[cs], __popc(grp));
-                                atomicAdd(&s_newcost[cs], ((unsigned long long)dhi << 16) + dlo);
+                // it lies on the new level.  A claim swaps the whole {word, count} pair,
+                // so it also sets the count to the claiming parent's and counts never
+                // need clearing: a count is read only where its word carries the epoch.
+                // one edge into v: what the claim or the count addition needs is loaded
+                // first (prefetch), for several edges at once, then resolved
+                struct Pre {
+                    int32_t v;
+                    uint32_t dg;
+                    int64_t p;
+                    unsigned long long ow, oc, oy;
+                };
+                auto prefetch = [&](const int32_t v) -> Pre {
+                    Pre r;
+                    r.v = v;
+                    r.dg = (uint32_t)(px[v + 1] - px[v]);  // < 2^31
+                    r.p = HASH ? (int64_t)hash_home(v, lg) : (int64_t)v;
+                    ld_pair(&tab[4 * r.p + xs], r.ow, r.oc);
+                    r.oy = __ldcg(&tab[4 * r.p + ys]);
+                    return r;
+                };
+                // claim v if unreached, add the parent's count if it lies on the new
+                // level.  A claim swaps the whole {word, count} pair, so it also sets the
+                // count to the claiming parent's and counts never need clearing: a count
+                // is read only where its word carries the sample's epoch.
+                auto resolve = [&](Pre &r, const C su) {
+                    if (HASH && s_full) return;  // the sample goes to the direct store
+                    const int32_t v = r.v;
+                    const unsigned long long want = W::make(v, ep, nl);
+                    int64_t p = r.p;
+                    unsigned long long ow = r.ow, oc = r.oc, oy = r.oy;
+                    bool at = false, won = false, meet = false;
+                    for (int64_t probes = 0;;) {
+                        const bool yc = W::current(oy, ep);
+                        bool again = false;
+                        if constexpr (HASH) {
+                            const bool xc = W::current(ow, ep);
+                            if ((xc || yc) && Word<true>::vertex(xc ? ow : oy) != v) {
+                                p = (p + 1) & hmask;  // another vertex's entry
+                                if (++probes > hmask) {
+                                    s_full = 1;
+                                    break;
+                                }
+                                again = true;
+                            } else if (!xc && !yc && known + s_new[cs] >= cap_new) {  // would overfill
+                                s_full = 1;
+                                break;
                             }
-                            q0 = __shfl_sync(grp, q0, lead);
-                            qx[hi + q0 + __popc(grp & ((1u << lane) - 1u))] = v;
-                            if ((uint32_t)(oy >> 32) == ep) s_meet = 1;
-                        } else {
-                            at = pw == want;  // claimed in this level by another thread
+                        }
+                        if (!again) {
+                            if (W::current(ow, ep)) {
+                                at = ow == want;
+                                break;
+                            }
+                            unsigned long long pw, pc;
+                            cas_pair(&tab[4 * p + xs], ow, oc, want, count_bits(su), pw, pc);
+                            if (pw == ow && pc == oc) {
+                                won = true;
+                                meet = yc;
+                                break;
+                            }
+                        }
+                        // another entry, or this one claimed meanwhile: (re)read it
+                        ld_pair(&tab[4 * p + xs], ow, oc);
+                        oy = __ldcg(&tab[4 * p + ys]);
+                    }
+                    if (won) {
+                        // the lanes that claimed together reserve their queue slots and
+                        // add their degrees with one shared atomic each (a 64-bit shared
+                        // add would be a contended compare-and-swap loop per lane)
+                        const unsigned grp = __activemask();
+                        const int lead = __ffs(grp) - 1;
+                        const uint32_t dlo = __reduce_add_sync(grp, r.dg & 0xffffu);
+                        const uint32_t dhi = __reduce_add_sync(grp, r.dg >> 16);
+                        int q0 = 0;
+                        if (lane == lead) {
+                            q0 = atomicAdd(&s_new[cs], __popc(grp));
+                            atomicAdd(&s_newcost[cs], ((unsigned long long)dhi << 16) + dlo);
+                        }
+                        q0 = __shfl_sync(grp, q0, lead);
+                        qx[hi + q0 + __popc(grp & ((1u << lane) - 1u))] = make_int2(v, (int)p);
+                        if (meet) {  // a member of the meeting layer: listed for the meeting step
+                            const unsigned mg = __activemask();
+                            const int ml = __ffs(mg) - 1;
+                            int m0 = 0;
+                            if (lane == ml) m0 = atomicAdd(&s_meet, __popc(mg));
+                            m0 = __shfl_sync(mg, m0, ml);
+                            memb[m0 + __popc(mg & ((1u << lane) - 1u))] = make_int2(v, (int)p);
                         }
                     }
                     if (a.work && (at || won)) ++n_add;
                     if (at) {
-                        const C o = atomicAdd(&sigx[v], su);
+                        C *cp = reinterpret_cast<C *>(&tab[4 * p + xs + 1]);
+                        const C o = atomicAdd(cp, su);
                         if ((double)(o + su) >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
                     }
                 };
-                // (the flat form keeps the level's edge offsets in 32 bits)
-                if (f <= kFlat && (x ? cost[1] : cost[0]) < (1ull << 31)) {
-                    // the level's edges spread evenly over the block (a hub's
-                    // adjacency is not left to one warp): warp 0 loads the frontier and
-                    // writes its degree prefix sums to shared memory, each edge then
-                    // finds its vertex by bisection
+                // the level's edges spread evenly over the block, kFlat frontier vertices
+                // at a time (a hub's adjacency is not left to one warp): warp 0 loads the
+                // chunk and writes its degree prefix sums to shared memory, each edge then
+                // finds its vertex by bisection
+                for (long long c0 = lo; c0 < hi; c0 += kFlat) {
+                    const int fc = (int)(hi - c0 < kFlat ? hi - c0 : kFlat);
                     if (warp == 0) {
                         constexpr int per = kFlat / 32;
-                        int32_t loc[per];
-                        int32_t tot = 0;
+                        int64_t loc[per];
+                        int64_t tot = 0;
 #pragma unroll
                         for (int r = 0; r < per; ++r) {
-                            const long long k = (long long)lane * per + r;
-                            int32_t dg = 0;
-                            if (k < f) {
-                                const int32_t u = qx[lo + k];
-                                const int64_t e0 = px[u];
+                            const int k = lane * per + r;
+                            int64_t dg = 0;
+                            if (k < fc) {
+                                const int2 qe = qx[c0 + k];
+                                const int64_t e0 = px[qe.x];
                                 s_fe[k] = e0;
-                                s_fs[k] = __ldcg(&sigx[u]);
-                                dg = (int32_t)(px[u + 1] - e0);
+                                s_fs[k] = count_of<C>(__ldcg(&tab[4ll * qe.y + xs + 1]));
+                                dg = px[qe.x + 1] - e0;
                             }
                             loc[r] = tot;
                             tot += dg;
                         }
-                        int32_t incl = tot;
+                        int64_t incl = tot;
 #pragma unroll
                         for (int o = 1; o < 32; o <<= 1) {
-                            const int32_t t2 = __shfl_up_sync(0xffffffffu, incl, o);
+                            const int64_t t2 = __shfl_up_sync(0xffffffffu, incl, o);
                             if (lane >= o) incl += t2;
                         }
-                        const int32_t first = incl - tot;
+                        const int64_t first = incl - tot;
 #pragma unroll
                         for (int r = 0; r < per; ++r) {
-                            const long long k = (long long)lane * per + r;
-                            if (k < f) s_pre[k] = first + loc[r];
+                            const int k = lane * per + r;
+                            if (k < fc) s_pre[k] = first + loc[r];
                         }
-                        if (lane == 31) s_pre[f] = incl;
+                        if (lane == 31) s_pre[fc] = incl;
                     }
                     __syncthreads();
-                    const int32_t E = s_pre[f];
-                    ne = threadIdx.x == 0 ? (unsigned long long)E : 0ull;
-                    for (int32_t j = threadIdx.x; j < E; j += kBiBlock) {
-                        int32_t klo = 0, khi = (int32_t)f - 1;  // last k with s_pre[k] <= j
+                    const int64_t E = s_pre[fc];
+                    if (threadIdx.x == 0) ne += (unsigned long long)E;
+                    auto vertex_of = [&](int64_t j) -> int {  // last k with s_pre[k] <= j
+                        int klo = 0, khi = fc - 1;
                         while (klo < khi) {
-                            const int32_t mid = (klo + khi + 1) >> 1;
+                            const int mid = (klo + khi + 1) >> 1;
                             if (s_pre[mid] <= j) klo = mid;
                             else khi = mid - 1;
                         }
-                        visit(ax[s_fe[klo] + (j - s_pre[klo])], s_fs[klo]);
+                        return klo;
+                    };
+                    for (int64_t j = threadIdx.x; j < E; j += (int64_t)kEdgeBatch * kBiBlock) {
+                        Pre pr[kEdgeBatch];
+                        int kk[kEdgeBatch];
+                        int32_t vv[kEdgeBatch];
+#pragma unroll
+                        for (int b = 0; b < kEdgeBatch; ++b) {
+                            const int64_t jb = j + (int64_t)b * kBiBlock;
+                            kk[b] = jb < E ? vertex_of(jb) : 0;
+                            vv[b] = jb < E ? ax[s_fe[kk[b]] + (jb - s_pre[kk[b]])] : -1;
+                        }
+#pragma unroll
+                        for (int b = 0; b < kEdgeBatch; ++b)
+                            if (vv[b] >= 0) pr[b] = prefetch(vv[b]);
+#pragma unroll
+                        for (int b = 0; b < kEdgeBatch; ++b)
+                            if (vv[b] >= 0) resolve(pr[b], s_fs[kk[b]]);
                     }
-                } else {
-                    for (long long q = lo + warp; q < hi; q += nw) {
-                        const int32_t u = qx[q];
-                        const C su = __ldcg(&sigx[u]);
-                        const int64_t e0 = px[u], e1 = px[u + 1];
-                        if (lane == 0) ne += (unsigned long long)(e1 - e0);
-                        for (int64_t e = e0 + lane; e < e1; e += 32) visit(ax[e], su);
-                    }
+                    if (c0 + kFlat < hi) __syncthreads();  // the chunk's shared arrays are reused
                 }
                 if (a.work && ne) atomicAdd(&s_work[0], ne);
+                smp_edges += ne;
+                ++smp_levels;
                 __syncthreads();
+                if (HASH && s_full) {  // (the same in every thread after the barrier)
+                    handed = true;
+                    break;
+                }
                 const long long nh = hi + s_new[cs];
                 const unsigned long long nc = s_newcost[cs];
+                if (threadIdx.x == 0 && nl + 1 <= (uint32_t)kLvCap) s_lv[x][nl + 1] = (int32_t)nh;
                 if (x) {
                     qlo[1] = hi;
                     qhi[1] = nh;
@@ -355,6 +619,15 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 }
             }
         }
+        if (a.trace && threadIdx.x == 0) t_levels = globaltimer_ns();
+        if (handed) {
+            // nothing of the sample was written outside the slot: the direct store runs it
+            if (threadIdx.x == 0) {
+                a.deferred[atomicAdd(a.n_deferred, 1u)] = (int32_t)i;
+                if (a.work) s_work[4] += 1ull;
+            }
+            continue;
+        }
         if (!met) {
             if (threadIdx.x == 0) {
                 a.kind[i] = 2;
@@ -362,149 +635,347 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 a.path_off[i] = 0;
             }
         } else {
-            // meeting layer: level s_lev[x] of side x reached by the other side
-            const Strided infy = x ? info0 : info1;
-            const int32_t *qx = x ? queue1 : queue0;
-            const long long mlo = x ? qlo[1] : qlo[0], mhi = x ? qhi[1] : qhi[0];
-            // the layer's members with their weights sigma_s sigma_t, kept in
-            // shared memory when they fit
-            if (threadIdx.x == 0) s_nm = 0;
-            __syncthreads();
+            // meeting layer: the members of the last level of side x (vertices the
+            // other side holds), listed as they were claimed; weights sigma_s sigma_t,
+            // kept in shared memory when they fit
+            const int nm = s_meet;
+            auto weight = [&](const int2 qe) -> C {
+                return count_of<C>(__ldcg(&tab[4ll * qe.y + 1])) * count_of<C>(__ldcg(&tab[4ll * qe.y + 3]));
+            };
             C part = C(0);
-            for (long long q = mlo + threadIdx.x; q < mhi; q += kBiBlock) {
-                const int32_t v = qx[q];
-                if ((uint32_t)(__ldcg(&infy[v]) >> 32) == ep) {
-                    const C a0 = __ldcg(&sig0[v]), a1 = __ldcg(&sig1[v]);
-                    const C p = a0 * a1;
-                    if ((double)a0 * (double)a1 >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
-                    part += p;
-                    const int slot_m = atomicAdd(&s_nm, 1);
-                    if (slot_m < kMeetCap) {
-                        s_mv[slot_m] = v;
-                        s_mw[slot_m] = p;
-                    }
+            for (int m = threadIdx.x; m < nm; m += kBiBlock) {
+                const int2 qe = memb[m];
+                const C a0 = count_of<C>(__ldcg(&tab[4ll * qe.y + 1]));
+                const C a1 = count_of<C>(__ldcg(&tab[4ll * qe.y + 3]));
+                const C p = a0 * a1;
+                if ((double)a0 * (double)a1 >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                part += p;
+                if (m < kMeetCap) {
+                    s_mv[m] = qe.x;
+                    s_mp[m] = qe.y;
+                    s_mw[m] = p;
                 }
             }
             const C sst = block_sum(part, s_redc);
             if (threadIdx.x == 0 && (double)sst >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
             const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, 0), (double)sst);
-            const int nm = s_nm;
             if (a.work && threadIdx.x == 0 && nm > kMeetCap) s_work[3] += 1ull << 32;  // large layers (high word)
             int32_t vm;
+            int64_t pm;
             if (nm <= kMeetCap) {
                 // member j qualifies when the weights of the members with ids <= its
                 // own reach the target; the meeting vertex is the smallest such id
-                int32_t best = 0x7fffffff;
+                unsigned long long best = ~0ull;  // vertex << 32 | entry
                 for (int j = threadIdx.x; j < nm; j += kBiBlock) {
                     const int32_t vj = s_mv[j];
                     C pre = C(0);
                     for (int k2 = 0; k2 < nm; ++k2)
                         if (s_mv[k2] <= vj) pre += s_mw[k2];
-                    if ((double)pre >= target) best = min(best, vj);
+                    if ((double)pre >= target)
+                        best = min(best, ((unsigned long long)(uint32_t)vj << 32) | (uint32_t)s_mp[j]);
                 }
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
                 __syncthreads();
                 if (lane == 0) s_best[warp] = best;
                 __syncthreads();
-                vm = s_best[0];
-                for (int q = 1; q < nw; ++q) vm = min(vm, s_best[q]);
+                unsigned long long bk = s_best[0];
+                for (int q = 1; q < nw; ++q) bk = min(bk, s_best[q]);
+                vm = (int32_t)(bk >> 32);
+                pm = (int64_t)(uint32_t)bk;
             } else {
-                // a large layer: the first vertex id T whose layer prefix sum
-                // reaches the target, by bisection over the ids
-                int32_t blo = 0, bhi = (int32_t)(n - 1);
-                while (blo < bhi) {
-                    const int32_t mid = blo + (bhi - blo) / 2;
-                    C pm = C(0);
-                    for (long long q = mlo + threadIdx.x; q < mhi; q += kBiBlock) {
-                        const int32_t v = qx[q];
-                        if (v <= mid && (uint32_t)(__ldcg(&infy[v]) >> 32) == ep)
-                            pm += __ldcg(&sig0[v]) * __ldcg(&sig1[v]);
+                // a large layer: the first id whose prefix sum (members in id order)
+                // reaches the target, narrowed in rounds of kMeetBuckets id buckets: the
+                // members' weights are summed per bucket in shared memory, the first
+                // bucket whose running total reaches the target holds the answer, and
+                // the next round splits that bucket (exact integer sums, so the same id
+                // as a sequential scan; three rounds for 2^30 ids)
+                int64_t lo_id = 0, span = n;
+                C base = C(0);  // weight of the members below lo_id
+                while (span > 1) {
+                    const int64_t wb = (span + kMeetBuckets - 1) / kMeetBuckets;
+                    for (int b = threadIdx.x; b < kMeetBuckets; b += kBiBlock) s_bkt[b] = C(0);
+                    __syncthreads();
+                    for (int m = threadIdx.x; m < nm; m += kBiBlock) {
+                        const int2 qe = memb[m];
+                        if (qe.x >= lo_id && qe.x < lo_id + span) atomicAdd(&s_bkt[(qe.x - lo_id) / wb], weight(qe));
                     }
-                    const C sm = block_sum(pm, s_redc);
-                    if ((double)sm >= target) bhi = mid;
-                    else blo = mid + 1;
+                    __syncthreads();
+                    if (warp == 0) {
+                        constexpr int per = kMeetBuckets / 32;
+                        C lsum = C(0);
+                        for (int j = 0; j < per; ++j) lsum += s_bkt[lane * per + j];
+                        C incl = lsum;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const C t2 = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += t2;
+                        }
+                        const unsigned hit = __ballot_sync(0xffffffffu, (double)(base + incl) >= target);
+                        const unsigned nz = __ballot_sync(0xffffffffu, lsum > C(0));
+                        // FP64 counts past 2^53 may leave every total just below the target:
+                        // the last bucket with weight then takes the remainder
+                        const int L0 = hit ? __ffs(hit) - 1 : 31 - __clz(nz);
+                        if (lane == L0) {  // the bucket within this lane's range, and the total below it
+                            C run = base + (incl - lsum), below = run;
+                            int bsel = 0;
+                            for (int j = 0; j < per; ++j) {
+                                const C bw = s_bkt[L0 * per + j];
+                                if (bw == C(0)) continue;
+                                bsel = j;
+                                below = run;
+                                run += bw;
+                                if (hit && (double)run >= target) break;
+                            }
+                            s_sel = L0 * per + bsel;
+                            s_base = below;
+                        }
+                    }
+                    __syncthreads();
+                    const int64_t nlo = lo_id + (int64_t)s_sel * wb;
+                    span = min(wb, lo_id + span - nlo);
+                    lo_id = nlo;
+                    base = s_base;
+                    __syncthreads();
                 }
-                vm = blo;
+                vm = (int32_t)lo_id;
+                if constexpr (HASH) pm = hash_find(tab, lg, vm, ep);
+                else pm = vm;
             }
-            if (warp == 0) {
-                const uint32_t la = (uint32_t)(__ldcg(&info0[vm]) & 0xffffffffu);
-                const uint32_t lb = (uint32_t)(__ldcg(&info1[vm]) & 0xffffffffu);
+            if (a.trace && threadIdx.x == 0) t_meet = globaltimer_ns();
+            // the path: the meeting vertex, then the s side backtracked from it, then
+            // the t side.  A backtrack step scans the candidates (in-neighbours towards
+            // s, out-neighbours towards t) in adjacency order for the first one one level
+            // closer whose running count reaches u sigma(w): one warp for short lists; the
+            // whole block for long ones (hubs), in two passes -- every thread sums a
+            // contiguous segment, a block scan of the sums finds the segment where the
+            // running count reaches the target, one warp scans that segment.
+            {
+                const uint32_t la = W::level(__ldcg(&tab[4 * pm]));
+                const uint32_t lb = W::level(__ldcg(&tab[4 * pm + 2]));
                 const int32_t len = (int32_t)(la + lb) - 1;
-                unsigned long long off = 0ull;
-                if (lane == 0) {
-                    off = atomicAdd(a.arena_top, (unsigned long long)len);
-                    if ((int64_t)(off + len) > a.arena_cap) atomicOr(a.status, DEV_ARENA_OVERFLOW);
+                if (threadIdx.x == 0) {
+                    const unsigned long long o = atomicAdd(a.arena_top, (unsigned long long)len);
+                    if ((int64_t)(o + len) > a.arena_cap) atomicOr(a.status, DEV_ARENA_OVERFLOW);
                     a.ilen[i] = len;
-                    a.path_off[i] = (long long)off;
-                }
-                off = __shfl_sync(0xffffffffu, off, 0);
-                const bool store = (int64_t)(off + len) <= a.arena_cap;
-                int32_t k = 0;
-                if (vm != s && vm != t) {
-                    if (lane == 0) {
-                        if (store) a.arena[off] = vm;
+                    a.path_off[i] = (long long)o;
+                    s_off = o;
+                    if (vm != s && vm != t) {
+                        if ((int64_t)(o + len) <= a.arena_cap) a.arena[o] = vm;
                         atomicAdd(&a.cnt[vm], 1ull);
                     }
-                    k = 1;
                 }
+                __syncthreads();
+                const unsigned long long off = s_off;
+                const bool store = (int64_t)(off + len) <= a.arena_cap;
+                int32_t k = (vm != s && vm != t) ? 1 : 0;
                 uint32_t step = 1;
                 for (int z = 0; z < 2; ++z) {
                     // towards s: predecessors over in-edges; towards t: successors over out-edges
                     const int64_t *bp = z == 0 ? a.irp : a.rp;
                     const int32_t *bc = z == 0 ? a.icol : a.col;
-                    const Strided infz = z == 0 ? info0 : info1;
-                    const CountView<C> sigz = z == 0 ? sig0 : sig1;
+                    const int zs = z ? 2 : 0;
                     const int32_t endz = z == 0 ? s : t;
                     int32_t w = vm;
-                    while (w != endz) {
-                        const uint32_t lw = (uint32_t)(__ldcg(&infz[w]) & 0xffffffffu);
-                        const unsigned long long prev = pack(ep, lw - 1);
+                    int64_t pw = pm;
+                    bool bad = false;
+                    while (w != endz) {  // (the same in every thread)
+                        const uint32_t lw = W::level(__ldcg(&tab[4 * pw + zs]));
                         const double tg = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, step),
-                                                    (double)__ldcg(&sigz[w]));
+                                                    (double)count_of<C>(__ldcg(&tab[4 * pw + zs + 1])));
                         const int64_t e0 = bp[w], e1 = bp[w + 1];
-                        C carry = C(0);
-                        int32_t pick = -1, last = -1;
-                        for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
-                            const int64_t e = base + lane;
-                            int32_t pv = -1;
-                            C val = C(0);
-                            if (e < e1) {
-                                pv = bc[e];
-                                unsigned long long lw2, lc2;
-                                ld_pair(&infz[pv], lw2, lc2);
-                                if (lw2 == prev) val = count_of<C>(lc2);
+                        // the count of candidate e if it lies one level closer, else 0
+                        auto cand = [&](int64_t e, int32_t &pv, int64_t &pp) -> C {
+                            pv = bc[e];
+                            if constexpr (HASH) pp = hash_find(tab, lg, pv, ep);
+                            else pp = pv;
+                            if (pp < 0) return C(0);
+                            unsigned long long lw2, lc2;
+                            ld_pair(&tab[4 * pp + zs], lw2, lc2);
+                            return (W::current(lw2, ep) && W::level(lw2) + 1 == lw) ? count_of<C>(lc2) : C(0);
+                        };
+                        // one warp scans [b0, b1) from running count c0: first lane whose running
+                        // count reaches tg, else (FP64 counts) the last candidate
+                        auto warp_scan = [&](int64_t b0, int64_t b1, C c0) {
+                            C carry = c0;
+                            int32_t pick = -1, last = -1;
+                            int64_t pickp = -1, lastp = -1;
+                            for (int64_t eb = b0; eb < b1 && pick < 0; eb += 32) {
+                                const int64_t e = eb + lane;
+                                int32_t pv = -1;
+                                int64_t pp = -1;
+                                const C val = e < b1 ? cand(e, pv, pp) : C(0);
+                                C cum = val;
+#pragma unroll
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    const C t2 = __shfl_up_sync(0xffffffffu, cum, o);
+                                    if (lane >= o) cum += t2;
+                                }
+                                cum += carry;
+                                const unsigned hit = __ballot_sync(0xffffffffu, val > C(0) && (double)cum >= tg);
+                                if (hit) {
+                                    pick = __shfl_sync(0xffffffffu, pv, __ffs(hit) - 1);
+                                    pickp = __shfl_sync(0xffffffffu, pp, __ffs(hit) - 1);
+                                }
+                                const unsigned cm = __ballot_sync(0xffffffffu, val > C(0));
+                                if (cm) {
+                                    last = __shfl_sync(0xffffffffu, pv, 31 - __clz(cm));
+                                    lastp = __shfl_sync(0xffffffffu, pp, 31 - __clz(cm));
+                                }
+                                carry = __shfl_sync(0xffffffffu, cum, 31);
                             }
-                            C cum = val;
+                            // FP64 counts past 2^53 may round the running sum just below u sigma(w):
+                            // the last candidate then takes the remainder
+                            if (pick < 0 && FP) {
+                                pick = last;
+                                pickp = lastp;
+                            }
+                            if (lane == 0) {
+                                s_pick = pick;
+                                s_pickp = pickp;
+                            }
+                        };
+                        // the previous level of side z, when its queue range is kept
+                        const uint32_t Lp = lw - 1;
+                        const long long lq0 = Lp + 1 <= (uint32_t)kLvCap ? s_lv[z][Lp] : 0;
+                        const long long lq1 = Lp + 1 <= (uint32_t)kLvCap ? s_lv[z][Lp + 1] : 0;
+                        if (e1 - e0 <= kBackWarp) {
+                            if (warp == 0) warp_scan(e0, e1, C(0));
+                        } else if (a.sorted && Lp + 1 <= (uint32_t)kLvCap && lq1 - lq0 <= kMeetCap) {
+                            // a long list and a small previous level: the candidates are that
+                            // level's vertices found in w's (sorted) list by bisection, their
+                            // places in it give the scan order; the choice is the first, in
+                            // that order, whose running count reaches the target
+                            const int2 *qz = z ? queue1 : queue0;
+                            if (threadIdx.x == 0) s_nc = 0;
+                            __syncthreads();
+                            for (long long q = lq0 + threadIdx.x; q < lq1; q += kBiBlock) {
+                                const int2 qe = qz[q];
+                                int64_t blo = e0, bhi = e1;
+                                while (blo < bhi) {
+                                    const int64_t mid = blo + ((bhi - blo) >> 1);
+                                    if (bc[mid] < qe.x) blo = mid + 1;
+                                    else bhi = mid;
+                                }
+                                if (blo < e1 && bc[blo] == qe.x) {
+                                    const int c = atomicAdd(&s_nc, 1);
+                                    s_mv[c] = qe.x;
+                                    s_mp[c] = qe.y;
+                                    s_mw[c] = count_of<C>(__ldcg(&tab[4ll * qe.y + zs + 1]));
+                                    s_mj[c] = (int32_t)(blo - e0);
+                                }
+                            }
+                            __syncthreads();
+                            const int nc = s_nc;
+                            unsigned long long best = ~0ull, lastc = 0ull;  // place << 32 | candidate
+                            for (int c = threadIdx.x; c < nc; c += kBiBlock) {
+                                const int32_t jc = s_mj[c];
+                                C pre = C(0);
+                                for (int c2 = 0; c2 < nc; ++c2)
+                                    if (s_mj[c2] <= jc) pre += s_mw[c2];
+                                const unsigned long long key = ((unsigned long long)(uint32_t)jc << 32) | (uint32_t)c;
+                                if (s_mw[c] > C(0)) {
+                                    if ((double)pre >= tg) best = min(best, key);
+                                    lastc = max(lastc, key + 1ull);
+                                }
+                            }
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) {
+                                best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+                                lastc = max(lastc, __shfl_xor_sync(0xffffffffu, lastc, o));
+                            }
+                            if (lane == 0) {
+                                s_best[warp] = best;
+                                s_redc[warp] = C(0);
+                            }
+                            __syncthreads();
+                            unsigned long long bk = s_best[0];
+                            for (int q = 1; q < nw; ++q) bk = min(bk, s_best[q]);
+                            __syncthreads();
+                            if (lane == 0) s_best[warp] = lastc;
+                            __syncthreads();
+                            if (threadIdx.x == 0) {
+                                // FP64 counts past 2^53 may round the running sum just below u
+                                // sigma(w): the last candidate then takes the remainder
+                                if (bk == ~0ull && FP) {
+                                    unsigned long long lk = 0ull;
+                                    for (int q = 0; q < nw; ++q) lk = max(lk, s_best[q]);
+                                    bk = lk ? lk - 1ull : ~0ull;
+                                }
+                                const int c = bk == ~0ull ? -1 : (int)(uint32_t)bk;
+                                s_pick = c < 0 ? -1 : s_mv[c];
+                                s_pickp = c < 0 ? -1 : s_mp[c];
+                            }
+                        } else {
+                            const int64_t seg = (e1 - e0 + kBiBlock - 1) / kBiBlock;
+                            const int64_t sb = min(e1, e0 + (int64_t)threadIdx.x * seg), se = min(e1, sb + seg);
+                            C my = C(0);
+                            int64_t e = sb;
+                            for (; e + 4 <= se; e += 4) {  // four candidates in flight
+                                int32_t pv[4];
+                                int64_t pp[4];
+                                C v[4];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) v[u] = cand(e + u, pv[u], pp[u]);
+                                my += (v[0] + v[1]) + (v[2] + v[3]);
+                            }
+                            for (; e < se; ++e) {
+                                int32_t pv;
+                                int64_t pp;
+                                my += cand(e, pv, pp);
+                            }
+                            // exclusive block scan of the segment sums
+                            C inc = my;
 #pragma unroll
                             for (int o = 1; o < 32; o <<= 1) {
-                                const C t2 = __shfl_up_sync(0xffffffffu, cum, o);
-                                if (lane >= o) cum += t2;
+                                const C t2 = __shfl_up_sync(0xffffffffu, inc, o);
+                                if (lane >= o) inc += t2;
                             }
-                            cum += carry;
-                            const unsigned hit = __ballot_sync(0xffffffffu, val > C(0) && (double)cum >= tg);
-                            if (hit) pick = __shfl_sync(0xffffffffu, pv, __ffs(hit) - 1);
-                            const unsigned cand = __ballot_sync(0xffffffffu, val > C(0));
-                            if (cand) last = __shfl_sync(0xffffffffu, pv, 31 - __clz(cand));
-                            carry = __shfl_sync(0xffffffffu, cum, 31);
+                            if (threadIdx.x == 0) s_tstar = 0x7fffffff;
+                            if (lane == 31) s_redc[warp] = inc;
+                            __syncthreads();
+                            C pre = inc - my;
+                            for (int q = 0; q < warp; ++q) pre += s_redc[q];
+                            const bool reach = my > C(0) && (double)(pre + my) >= tg;
+                            const unsigned rb = __ballot_sync(0xffffffffu, reach);
+                            if (rb && lane == __ffs(rb) - 1) atomicMin(&s_tstar, (int)threadIdx.x);
+                            __syncthreads();
+                            int ts = s_tstar;
+                            if (ts == 0x7fffffff) {  // FP64 counts: the last segment with a candidate
+                                const unsigned nzb = __ballot_sync(0xffffffffu, my > C(0));
+                                if (nzb && lane == 31 - __clz(nzb)) atomicMax(&s_tlast, (int)threadIdx.x);
+                                __syncthreads();
+                                ts = s_tlast;
+                            }
+                            if ((int)threadIdx.x == ts) s_tpre = pre;
+                            __syncthreads();
+                            if (warp == 0) {
+                                const int64_t tb = min(e1, e0 + (int64_t)ts * seg);
+                                warp_scan(tb, min(e1, tb + seg), s_tpre);
+                            }
+                            if (threadIdx.x == 0) s_tlast = -1;
                         }
-                        // FP64 counts past 2^53 may round the running sum just below u sigma(w):
-                        // the last candidate then takes the remainder
-                        if (pick < 0 && FP) pick = last;
+                        __syncthreads();
+                        const int32_t pick = s_pick;
+                        const int64_t pickp = s_pickp;
+                        __syncthreads();  // s_pick is written again by the next step
                         if (pick < 0) {
-                            if (lane == 0) atomicOr(a.status, DEV_BAD_PATH);
+                            if (threadIdx.x == 0) atomicOr(a.status, DEV_BAD_PATH);
+                            bad = true;
                             break;
                         }
                         if (pick != endz) {
-                            if (lane == 0) {
+                            if (threadIdx.x == 0) {
                                 if (store && k < len) a.arena[off + k] = pick;
                                 atomicAdd(&a.cnt[pick], 1ull);
                             }
                             ++k;
                         }
                         w = pick;
+                        pw = pickp;
                         ++step;
                     }
+                    if (bad) break;
                 }
             }
         }
@@ -513,66 +984,49 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
             s_work[2] += (unsigned long long)(qhi[0] + qhi[1]);
             s_work[3] += 1ull;
         }
+        if (a.trace && threadIdx.x == 0) {
+            unsigned long long *tr = a.trace + 6 * i;
+            tr[0] = t_start;
+            tr[1] = globaltimer_ns();
+            tr[2] = smp_edges;
+            tr[3] = (unsigned long long)smp_levels | ((unsigned long long)(HASH ? 0 : 1) << 32) |
+                    ((unsigned long long)slot << 33);
+            tr[4] = t_levels;
+            tr[5] = t_meet ? t_meet : t_levels;
+        }
     }
+    if (HASH && threadIdx.x == 0) a.slot_epoch[slot] = ep_slot;
     if (a.work) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) n_add += __shfl_xor_sync(0xffffffffu, n_add, off);
         if (lane == 0 && n_add) atomicAdd(&s_work[1], n_add);
     }
     __syncthreads();
-    if (a.work && threadIdx.x < 4 && s_work[threadIdx.x]) atomicAdd(&a.work[threadIdx.x], s_work[threadIdx.x]);
+    if (a.work && threadIdx.x < 6 && s_work[threadIdx.x]) atomicAdd(&a.work[threadIdx.x], s_work[threadIdx.x]);
 }
 
-}  // namespace
-
-// All samples of a phase (pairs, kinds already drawn): kinds of unreachable
-// targets, |I|, paths and counts, as the batched form leaves them.
-percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count) {
-    const int64_t n = ctx->n;
-    const int32_t *gid = nullptr;
-    const int64_t *vbase = nullptr;
-    int64_t nslot = n;
-    if (ctx->multi) multi_graph_view(ctx, &gid, &vbase, &nslot);
-    const size_t per_slot = (size_t)nslot * (sizeof(unsigned long long) * 4 + sizeof(int32_t) * 2);
-    static int per_sm = 0;
-    if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs<unsigned long long>, kBiBlock, 0) !=
+template <bool HASH>
+int blocks_per_sm(percis_ctx *ctx, int *cache) {
+    if (!*cache) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs<unsigned long long, HASH>, kBiBlock, 0) !=
                 cudaSuccess ||
-            per_sm < 1)
+            per_sm < 1) {
+            cudaGetLastError();
             per_sm = 1;
+        }
+        *cache = per_sm;
     }
-    // at most 16 GiB of scratch
-    int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, (16ll << 30) / per_slot));
-    slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
-    if (ctx->bi_slots < slots || ctx->bi_n != nslot) {
-        PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 4 * nslot * slots, "bidirectional records"));
-        PERCIS_TRY(ensure(ctx, ctx->bi_queue, sizeof(int32_t) * 2 * nslot * slots, "bidirectional queues"));
-        // level words of no sample (epoch 0)
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * nslot * slots, ctx->stream));
-        ctx->bi_slots = slots;
-        ctx->bi_n = nslot;
-        ctx->bi_epoch = 0;
-    }
-    if ((uint64_t)ctx->bi_epoch + (uint64_t)count + 2 > 0xffffffffull) {
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * nslot * ctx->bi_slots,
-                                         ctx->stream));
-        ctx->bi_epoch = 0;
-    }
-    PERCIS_TRY(ensure(ctx, ctx->ms_ctl, sizeof(MsCtl), "ms ctl"));
-    // the status word may be freshly allocated: it must start at zero
-    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ms_ctl.p, 0, sizeof(MsCtl), ctx->stream));
-    PERCIS_TRY(ensure(ctx, ctx->red, 64, "sample counter"));
-    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(unsigned long long), ctx->stream));
+    return *cache;
+}
+
+BiArgs common_args(percis_ctx *ctx, uint64_t seed, uint32_t tag_path) {
     BiArgs a{};
-    a.n = n;
-    a.gid = gid;
-    a.vbase = vbase;
-    a.nslot = nslot;
+    a.n = ctx->n;
     a.rp = ctx->rp.as<int64_t>();
     a.col = ctx->col.as<int32_t>();
     a.irp = ctx->directed ? ctx->irp.as<int64_t>() : ctx->rp.as<int64_t>();
     a.icol = ctx->directed ? ctx->icol.as<int32_t>() : ctx->col.as<int32_t>();
-    a.count = count;
     a.pair_s = ctx->pair_s.as<int32_t>();
     a.pair_t = ctx->pair_t.as<int32_t>();
     a.kind = ctx->kind.as<int32_t>();
@@ -584,17 +1038,136 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     a.cnt = ctx->cnt.as<unsigned long long>();
     a.seed = seed;
     a.tag = tag_path;
-    a.epoch_base = (uint32_t)ctx->bi_epoch;
-    ctx->bi_epoch += count + 1;
-    a.vs = ctx->bi_info.as<unsigned long long>();
-    a.queue = ctx->bi_queue.as<int32_t>();
-    a.slots = (int32_t)ctx->bi_slots;
-    a.next = ctx->red.as<unsigned long long>();
     a.status = &ctx->ms_ctl.as<MsCtl>()->status;
     a.work = ctx->opt.instrument ? ctx->counters.as<unsigned long long>() : nullptr;
-    if (ctx->sigma_mode == 2) k_bibfs<double><<<(int)ctx->bi_slots, kBiBlock, 0, ctx->stream>>>(a);
-    else k_bibfs<unsigned long long><<<(int)ctx->bi_slots, kBiBlock, 0, ctx->stream>>>(a);
-    PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS");
+    a.trace = ctx->opt.instrument >= 2 ? ctx->bi_trace.as<unsigned long long>() : nullptr;
+    a.sorted = ctx->rows_sorted ? 1 : 0;
+    return a;
+}
+
+// The direct store over `count` samples (all of the phase, or the list).
+percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count, const int32_t *list) {
+    const int32_t *gid = nullptr;
+    const int64_t *vbase = nullptr;
+    int64_t nslot = ctx->n;
+    if (ctx->multi) multi_graph_view(ctx, &gid, &vbase, &nslot);
+    const size_t per_slot = (size_t)nslot * (sizeof(unsigned long long) * 4 + sizeof(int2) * 3);
+    const int per_sm = blocks_per_sm<false>(ctx, &ctx->bi_per_sm);
+    const int64_t budget = (int64_t)(ctx->opt.bi_scratch_gib > 0 ? ctx->opt.bi_scratch_gib : 16) << 30;
+    int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, budget / (int64_t)per_slot));
+    slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
+    if (ctx->bi_slots < slots || ctx->bi_n != nslot) {
+        PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 4 * nslot * slots, "bidirectional records"));
+        PERCIS_TRY(ensure(ctx, ctx->bi_queue, sizeof(int2) * 3 * nslot * slots, "bidirectional queues"));
+        // level words of no sample (epoch 0)
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * nslot * slots, ctx->stream));
+        ctx->bi_slots = slots;
+        ctx->bi_n = nslot;
+        ctx->bi_epoch = 0;
+    }
+    const int64_t span = ctx->phase_span;  // epochs are indexed by sample number
+    if ((uint64_t)ctx->bi_epoch + (uint64_t)span + 2 > 0xffffffffull) {
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_info.p, 0, sizeof(unsigned long long) * 4 * nslot * ctx->bi_slots,
+                                         ctx->stream));
+        ctx->bi_epoch = 0;
+    }
+    PERCIS_TRY(ensure(ctx, ctx->red, 64, "sample counter"));
+    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(unsigned long long), ctx->stream));
+    BiArgs a = common_args(ctx, seed, tag_path);
+    a.count = count;
+    a.list = list;
+    a.gid = gid;
+    a.vbase = vbase;
+    a.epoch_base = (uint32_t)ctx->bi_epoch;
+    ctx->bi_epoch += span + 1;
+    a.ent = ctx->bi_info.as<unsigned long long>();
+    a.queue = ctx->bi_queue.as<int2>();
+    a.region = nslot;
+    a.qcap = nslot;
+    a.next = ctx->red.as<unsigned long long>();
+    const int grid = (int)std::min<int64_t>(ctx->bi_slots, std::max<int64_t>(count, 1));
+    if (ctx->sigma_mode == 2) k_bibfs<double, false><<<grid, kBiBlock, 0, ctx->stream>>>(a);
+    else k_bibfs<unsigned long long, false><<<grid, kBiBlock, 0, ctx->stream>>>(a);
+    PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS (direct)");
+    return PERCIS_OK;
+}
+
+}  // namespace
+
+// All samples of a phase (pairs, kinds already drawn): kinds of unreachable
+// targets, |I|, paths and counts, as the batched form leaves them.  Every
+// sample runs in the hashed store first; the ones it hands over run in the
+// direct store after it.
+percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count) {
+    PERCIS_TRY(ensure(ctx, ctx->ms_ctl, sizeof(MsCtl), "ms ctl"));
+    // the status word may be freshly allocated: it must start at zero
+    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ms_ctl.p, 0, sizeof(MsCtl), ctx->stream));
+    ctx->phase_span = count;
+    if (ctx->opt.instrument >= 2) {
+        PERCIS_TRY(ensure(ctx, ctx->bi_trace, sizeof(unsigned long long) * 6 * std::max<int64_t>(count, 1),
+                          "sample trace"));
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_trace.p, 0, sizeof(unsigned long long) * 6 * count, ctx->stream));
+        ctx->bi_trace_n = count;
+    }
+    if (ctx->opt.bi_table_log < 0) return direct_pass(ctx, seed, tag_path, count, nullptr);
+    int64_t nslot = ctx->n;
+    if (ctx->multi) {
+        const int32_t *gid;
+        const int64_t *vbase;
+        multi_graph_view(ctx, &gid, &vbase, &nslot);
+    }
+    // tables of 2^h0 .. 2^hmax entries in steps of 4x; the largest holds every
+    // vertex of the (largest) graph at most half full, up to 2^17 entries
+    const int h0 = ctx->opt.bi_table_log > 0 ? std::min(std::max(ctx->opt.bi_table_log, kMinHLog), kMaxHLog)
+                                             : kDefaultH0Log;
+    const int cap = ctx->opt.bi_table_max_log > 0 ? std::min(ctx->opt.bi_table_max_log, kMaxHLog) : kMaxHLog;
+    int hmax = h0;
+    while (hmax + 2 <= cap && (1ll << hmax) < 2 * nslot + 4 * kBiBlock) hmax += 2;
+    int64_t region = 0;
+    for (int l = h0; l <= hmax; l += 2) region += 1ll << l;
+    const int64_t qcap = 1ll << hmax;
+    const int per_sm = blocks_per_sm<true>(ctx, &ctx->bi_hash_per_sm);
+    const int64_t slots = (int64_t)per_sm * ctx->num_sms;
+    const size_t ent_bytes = sizeof(unsigned long long) * 4 * (size_t)region * slots;
+    const size_t q_bytes = sizeof(int2) * 3 * (size_t)qcap * slots;
+    if (ctx->bi_hregion != region || ctx->bi_hslots != slots || ctx->bi_h0 != h0) {
+        PERCIS_TRY(ensure(ctx, ctx->bi_hent, ent_bytes, "hashed entries"));
+        PERCIS_TRY(ensure(ctx, ctx->bi_hq, q_bytes, "hashed queues"));
+        PERCIS_TRY(ensure(ctx, ctx->bi_hep, sizeof(uint32_t) * slots, "slot epochs"));
+        // words of no sample (epoch 0) and epochs from 1
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_hent.p, 0, ent_bytes, ctx->stream));
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_hep.p, 0, sizeof(uint32_t) * slots, ctx->stream));
+        ctx->bi_hregion = region;
+        ctx->bi_hslots = slots;
+        ctx->bi_h0 = h0;
+    }
+    PERCIS_TRY(ensure(ctx, ctx->bi_defer, sizeof(int32_t) * std::max<int64_t>(count, 1) + 64, "handed-over samples"));
+    unsigned int *n_def = reinterpret_cast<unsigned int *>(ctx->bi_defer.as<int32_t>() + std::max<int64_t>(count, 1));
+    PERCIS_TRY(ensure(ctx, ctx->red, 64, "sample counter"));
+    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(unsigned long long), ctx->stream));
+    PERCIS_CUDA(ctx, cudaMemsetAsync(n_def, 0, sizeof(unsigned int), ctx->stream));
+    BiArgs a = common_args(ctx, seed, tag_path);
+    a.count = count;
+    a.list = nullptr;
+    a.ent = ctx->bi_hent.as<unsigned long long>();
+    a.queue = ctx->bi_hq.as<int2>();
+    a.region = region;
+    a.qcap = qcap;
+    a.next = ctx->red.as<unsigned long long>();
+    a.h0_log = h0;
+    a.hmax_log = hmax;
+    a.slot_epoch = ctx->bi_hep.as<uint32_t>();
+    a.deferred = ctx->bi_defer.as<int32_t>();
+    a.n_deferred = n_def;
+    const int grid = (int)std::min<int64_t>(slots, std::max<int64_t>(count, 1));
+    if (ctx->sigma_mode == 2) k_bibfs<double, true><<<grid, kBiBlock, 0, ctx->stream>>>(a);
+    else k_bibfs<unsigned long long, true><<<grid, kBiBlock, 0, ctx->stream>>>(a);
+    PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS (hashed)");
+    unsigned int nd = 0;
+    PERCIS_CUDA(ctx, cudaMemcpyAsync(&nd, n_def, sizeof(nd), cudaMemcpyDeviceToHost, ctx->stream));
+    PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->bi_handed = nd;
+    if (nd > 0) PERCIS_TRY(direct_pass(ctx, seed, tag_path, (int64_t)nd, ctx->bi_defer.as<int32_t>()));
     return PERCIS_OK;
 }
 

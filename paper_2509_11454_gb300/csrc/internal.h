@@ -66,6 +66,7 @@ struct percis_ctx {
     int directed = 0;
     percis::DevBuf rp, col, irp, icol;  // irp/icol used only when directed
     int64_t vertex_diam = -1;
+    bool rows_sorted = false;  // every CSR row strictly increasing (no duplicate edges)
     percis::DevBuf vorder;  // vertices sorted by (highest-degree neighbour, id): lane order of sources
     bool vorder_ready = false;
 
@@ -78,6 +79,8 @@ struct percis_ctx {
     // plain BFS state
     percis::DevBuf ep, lvl, sigma1, qa, qb, plain_ctl;
     int32_t epoch = 0;
+    int plain_grid = 0;  // cooperative grid of the plain BFS on this device (0 = not yet queried)
+    int bi_per_sm = 0;   // resident blocks per SM of the bidirectional kernel (0 = not yet queried)
 
     // batched BFS state
     percis::DevBuf vis, fhist, sigmaW, ms_ctl, remaining, found;
@@ -87,8 +90,16 @@ struct percis_ctx {
     percis::DevBuf fq0, fq1;  // frontier queues
     percis::DevBuf acc_ap, ap_tau, ap_stamp, ap_list;  // all-paths estimator
     percis::DevBuf plan_dev;                           // lane batches of a many-graph phase
-    percis::DevBuf bi_info, bi_queue;                  // bidirectional form: per-slot scratch
+    percis::DevBuf bi_info, bi_queue;                  // bidirectional form, direct store: per-slot scratch
     int64_t bi_slots = 0, bi_n = 0, bi_epoch = 0;
+    percis::DevBuf bi_hent, bi_hq, bi_hep, bi_defer;   // bidirectional form, hashed store: tables, queues,
+                                                       // slot epochs, samples handed to the direct store
+    int64_t bi_hregion = 0, bi_hslots = 0;
+    int bi_h0 = 0, bi_hash_per_sm = 0;
+    int64_t bi_handed = 0;   // samples the last hashed pass handed to the direct store
+    int64_t phase_span = 0;  // samples of the running phase (direct-store epochs are indexed by sample)
+    percis::DevBuf bi_trace;  // per-sample trace of the last bidirectional phase (instrument = 2)
+    int64_t bi_trace_n = 0;
     int64_t ap_warps = 0, ap_n = 0;
     int32_t ap_epoch = 0;
 
@@ -109,6 +120,9 @@ struct percis_ctx {
 
     // scratch for reductions/scans
     percis::DevBuf scratch, red, status;
+    percis::DevBuf radix_counts, sort_a, sort_b;  // radix sort: per-tile digit counts, transpose scratch
+    percis::DevBuf table_ctl;                      // cooperative table scan: barrier, window state, block runs
+    int table_grid = 0;                            // co-resident blocks of the table scan (0 = not yet queried)
     percis::DevBuf pc_tmp, grad_tmp, host_pinned;
 
     // many graphs: one sub-context per graph for everything but the batched BFS
@@ -151,6 +165,13 @@ double events_elapsed_ms(percis_ctx *ctx);
 percis_status scan_exclusive_i64(percis_ctx *ctx, const int64_t *in, int64_t *out, int64_t n);
 percis_status scan_exclusive_f64(percis_ctx *ctx, const double *in, double *out, int64_t n);
 int grid_for(percis_ctx *ctx, int64_t work, int block);
+
+// radix.cu: stable LSD radix sort of (key, value) pairs by key bits [lo_bit, lo_bit + bits),
+// 8 bits per pass, in place (tk/tv: scratch of n keys and n values); the in-adjacency
+// (irp, icol) of the loaded directed CSR, every in-list ordered by source
+percis_status radix_sort_u64(percis_ctx *ctx, uint64_t *keys, int32_t *vals, uint64_t *tk, int32_t *tv, int64_t n,
+                             int lo_bit, int bits);
+percis_status build_transpose(percis_ctx *ctx);
 
 // prep.cu
 percis_status prep_graph(percis_ctx *ctx);  // transpose (directed), validation, VertexDiamUB

@@ -30,7 +30,7 @@ constexpr int64_t kNoAllocMaxN = PERCIS_NOALLOC_MAX_N;
 constexpr size_t kCtlBytes = 256;
 constexpr size_t kScratchBytes = kCtlBytes + 2 * sizeof(int32_t) * (size_t)kNoAllocMaxN;
 constexpr int kBlock = 256;
-constexpr uint64_t kBudgetNs = 10ull * 1000000000ull;
+constexpr double kDefaultBudgetS = 10.0;
 
 struct NoAllocCtl {
     uint32_t bar_count, bar_gen;  // GridBarrier
@@ -46,7 +46,7 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 __global__ void __launch_bounds__(kBlock) k_bfs_noalloc(int64_t n, const int64_t *rp, const int32_t *col,
                                                         const int64_t *irp, const int32_t *icol, int32_t s,
                                                         int32_t t, int32_t *dist, double *sigma,
-                                                        unsigned char *scratch) {
+                                                        unsigned char *scratch, uint64_t budget_ns) {
     NoAllocCtl *ctl = reinterpret_cast<NoAllocCtl *>(scratch);
     int32_t *qa = reinterpret_cast<int32_t *>(scratch + kCtlBytes);
     int32_t *qb = qa + kNoAllocMaxN;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kBlock) k_bfs_noalloc(int64_t n, const int64_t
         dist[v] = -1;
         sigma[v] = 0.0;
     }
-    if (!grid_sync(bar, status, kBudgetNs)) return;
+    if (!grid_sync(bar, status, budget_ns)) return;
     if (tid == 0) {
         dist[s] = 0;
         sigma[s] = 1.0;
@@ -67,11 +67,12 @@ __global__ void __launch_bounds__(kBlock) k_bfs_noalloc(int64_t n, const int64_t
         ctl->qsize[1] = 0;
         ctl->found = 0;
     }
-    if (!grid_sync(bar, status, kBudgetNs)) return;
+    if (!grid_sync(bar, status, budget_ns)) return;
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = tid >> 5, nwarps = nthreads >> 5;
     int32_t *cur = qa, *nxt = qb;
-    for (int L = 0;; ++L) {
+    // a target equal to the source is settled at level 0: nothing to expand
+    for (int L = 0; t < 0 || t != s; ++L) {
         const int nq = (int)ld_relaxed_u32((const uint32_t *)&ctl->qsize[L & 1]);
         // expand level L: claim unreached out-neighbours for level L+1
         for (int64_t k = gwarp; k < nq; k += nwarps) {
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) k_bfs_noalloc(int64_t n, const int64_t
                 }
             }
         }
-        if (!grid_sync(bar, status, kBudgetNs)) return;
+        if (!grid_sync(bar, status, budget_ns)) return;
         const int nn = (int)ld_relaxed_u32((const uint32_t *)&ctl->qsize[(L + 1) & 1]);
         if (tid == 0) ctl->qsize[L & 1] = 0;
         // sigma of the new level: sum over in-neighbours at level L
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(kBlock) k_bfs_noalloc(int64_t n, const int64_t
                 if (w == t) atomicExch(&ctl->found, 1);
             }
         }
-        if (!grid_sync(bar, status, kBudgetNs)) return;
+        if (!grid_sync(bar, status, budget_ns)) return;
         if (nn == 0) break;
         // only values fixed until every block passes the next barrier decide the exit
         if (t >= 0 && ld_relaxed_u32((const uint32_t *)&ctl->found)) break;
@@ -168,10 +169,23 @@ using namespace percis;
 
 extern "C" percis_status percis_bfs_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col,
                                             const int64_t *in_row_ptr, const int32_t *in_col, int32_t source,
-                                            int32_t target, int32_t *dist, double *sigma, void *stream) {
+                                            int32_t target, int32_t *dist, double *sigma, void *stream,
+                                            double timeout_s, int32_t *sigma_overflow) {
+    if (sigma_overflow) *sigma_overflow = 0;
     if (n < 1 || n > kNoAllocMaxN || !row_ptr || !col || !dist || !sigma) return PERCIS_E_INVALID;
     if (source < 0 || source >= n || target >= n) return PERCIS_E_INVALID;
     if ((in_row_ptr == nullptr) != (in_col == nullptr)) return PERCIS_E_INVALID;
+    if (!(timeout_s > 0.0)) timeout_s = kDefaultBudgetS;
+    uint64_t budget_ns = timeout_s < 1e9 ? (uint64_t)(timeout_s * 1e9) : ~0ull;
+    if (budget_ns == 0) budget_ns = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the memset, launch, copy and synchronisation below cannot be captured
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return PERCIS_E_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return PERCIS_E_INVALID;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -180,7 +194,6 @@ extern "C" percis_status percis_bfs_noalloc(int64_t n, const int64_t *row_ptr, c
     DeviceSlot *sl = nullptr;
     const percis_status st = device_slot(dev, &sl);
     if (st != PERCIS_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t *irp = in_row_ptr ? in_row_ptr : row_ptr;
     const int32_t *icol = in_col ? in_col : col;
     int32_t tgt = target < 0 ? -1 : target;
@@ -190,7 +203,7 @@ extern "C" percis_status percis_bfs_noalloc(int64_t n, const int64_t *row_ptr, c
         cudaGetLastError();
         return PERCIS_E_CUDA;
     }
-    void *args[] = {&n, &row_ptr, &col, &irp, &icol, &source, &tgt, &dist, &sigma, &scratch};
+    void *args[] = {&n, &row_ptr, &col, &irp, &icol, &source, &tgt, &dist, &sigma, &scratch, &budget_ns};
     if (cudaLaunchCooperativeKernel((const void *)k_bfs_noalloc, dim3(sl->grid), dim3(kBlock), args, 0, s) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -203,6 +216,7 @@ extern "C" percis_status percis_bfs_noalloc(int64_t n, const int64_t *row_ptr, c
         cudaGetLastError();
         return PERCIS_E_CUDA;
     }
+    if (sigma_overflow) *sigma_overflow = (status & DEV_SIGMA_OVERFLOW) ? 1 : 0;
     if (status & DEV_TIMEOUT) return PERCIS_E_TIMEOUT;
     if (status & DEV_BAD_INPUT) return PERCIS_E_INVALID;
     return PERCIS_OK;

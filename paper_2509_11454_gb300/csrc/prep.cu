@@ -12,15 +12,22 @@ namespace {
 
 // ------------------------------------------------------------- validation
 
-__global__ void k_check_csr(const int64_t *rp, const int32_t *col, int64_t n, int64_t nnz, uint32_t *status) {
+// Validation, and whether every row is strictly increasing: desc[0] counts the
+// positions e >= 1 with col[e] <= col[e-1], desc[1] those among them that start
+// a row; the rows are strictly sorted when the counts agree.
+__global__ void k_check_csr(const int64_t *rp, const int32_t *col, int64_t n, int64_t nnz, uint32_t *status,
+                            unsigned long long *desc) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        if (rp[v] > rp[v + 1] || rp[v] < 0 || rp[v + 1] > nnz) atomicOr(status, 1u);
+        const int64_t r0 = rp[v], r1 = rp[v + 1];
+        if (r0 > r1 || r0 < 0 || r1 > nnz) atomicOr(status, 1u);
+        else if (r0 > 0 && r0 < r1 && col[r0] <= col[r0 - 1]) atomicAdd(&desc[1], 1ull);
         if (v == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, 1u);
     }
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
         const int32_t c = col[e];
         if (c < 0 || (int64_t)c >= n) atomicOr(status, 1u);
+        if (e > 0 && c <= col[e - 1]) atomicAdd(&desc[0], 1ull);
     }
 }
 
@@ -29,53 +36,6 @@ __global__ void k_check_states(const double *x, int64_t n, uint32_t *status) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const double a = x[v];
         if (!(a >= 0.0 && a <= 1.0)) atomicOr(status, DEV_BAD_STATE);
-    }
-}
-
-// ----------------------------------------------------------- merge sort
-// Stable bottom-up merge sort of (key, val) pairs: in a pass of width w an
-// element of the left run lands at (its rank in its run) + (number of
-// right-run keys < key); an element of the right run at (its rank) +
-// (number of left-run keys <= key).  Equal keys keep their input order.
-
-__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *a, int64_t lo, int64_t hi, uint64_t key) {
-    while (lo < hi) {
-        const int64_t mid = lo + ((hi - lo) >> 1);
-        if (a[mid] < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int64_t upper_bound_u64(const uint64_t *a, int64_t lo, int64_t hi, uint64_t key) {
-    while (lo < hi) {
-        const int64_t mid = lo + ((hi - lo) >> 1);
-        if (a[mid] <= key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-__global__ void k_merge_pass(const uint64_t *kin, const int32_t *vin, uint64_t *kout, int32_t *vout, int64_t n,
-                             int64_t w) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int64_t run = i / w;
-        const uint64_t key = kin[i];
-        int64_t out;
-        if ((run & 1) == 0) {
-            const int64_t a0 = run * w;
-            const int64_t b0 = a0 + w;
-            const int64_t b1 = min(b0 + w, n);
-            const int64_t rank = b0 < n ? lower_bound_u64(kin, b0, b1, key) - b0 : 0;
-            out = a0 + (i - a0) + rank;
-        } else {
-            const int64_t b0 = run * w;
-            const int64_t a0 = b0 - w;
-            out = a0 + (i - b0) + (upper_bound_u64(kin, a0, b0, key) - a0);
-        }
-        kout[out] = key;
-        vout[out] = vin[i];
     }
 }
 
@@ -110,18 +70,20 @@ __global__ void k_gather_sorted(const double *x, const int32_t *perm, int64_t n,
 //  - a/u rounds to q or q + 1 from its own bits alone, except at an exact halfway
 //    point, where ties-to-even picks by the parity of s/u before the term.  Each term
 //    is therefore a map (parity in) -> (parity out, integer added); these maps compose
-//    associatively, so one block-wide scan over them gives every running sum of a
-//    chunk of terms at once.
-//  - the first term whose sum reaches the top of the binade is added with one
-//    hardware FP64 add, and the chunk restarts after it in the new binade (a
-//    non-decreasing sum enters each binade once).
+//    associatively, so one scan over them gives every running sum of a window of
+//    terms at once: each block scans its chunk of 4,096 terms, the blocks' runs are
+//    composed after a grid barrier, so a window spans every block of the launch.
+//  - the first term whose sum reaches the top of the binade (a grid-wide minimum)
+//    is added with one hardware FP64 add, and the next window starts after it in
+//    the new binade (a non-decreasing sum enters each binade once).
 // Both evaluations give the correctly rounded sum of the same operands in the same
 // order (IEEE 754 round to nearest, ties to even) at every step, hence equal results.
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;  // terms per thread and chunk
 constexpr int kScanChunk = kScanThreads * kScanPer;
+constexpr int kMaxTableBlocks = 1024;
 constexpr unsigned long long kTwo53u = 1ull << 53;
-constexpr int kNoTerm = 0x7fffffff;
+constexpr long long kNoTerm = 0x7fffffffffffffffll;
 
 // map of a run of terms: for parity p of s/u before the run, d0 / d1 is the integer
 // added and bit p of par the parity after it
@@ -189,20 +151,55 @@ __device__ __forceinline__ ParityMap term_map(double a, int e, unsigned long lon
     return m;
 }
 
+// map of a run of terms, as stored between the phases of a window
+struct alignas(16) RunMap {
+    unsigned long long d0, d1;
+    unsigned long long par;
+};
+
+// Control block of the cooperative table launch.
+struct TableCtl {
+    GridBarrier bar;
+    uint32_t status;
+    uint32_t pad;
+    long long kstar[2];  // first term of the window that leaves the binade (one slot per window parity)
+    long long pos;       // positions pos, pos - 1, ..., 1 remain
+    double s;            // running sum before them
+    RunMap agg[kMaxTableBlocks];
+};
+
+__device__ __forceinline__ ParityMap run_load(const RunMap *p) {
+    ParityMap m;
+    m.d0 = __ldcg(&p->d0);
+    m.d1 = __ldcg(&p->d1);
+    m.par = (unsigned)__ldcg(&p->par);
+    return m;
+}
+
 // Running sums s_i = fl(s_{i+1} + a_i) for i = m down to 1 (s_{m+1} = +0), with
-// a_i = src[i + soff] >= 0, written to dst[i]; returns s_1 (+0 when m = 0).  The
-// whole block calls it.
-__device__ double exact_running_sum(const double *src, int64_t soff, double *dst, int64_t m) {
+// a_i = src[i + soff] >= 0, written to dst[i]; *sum = s_1 (+0 when m = 0).  Every
+// block of the cooperative launch calls it; false when a grid barrier timed out.
+__device__ bool grid_running_sum(const double *src, int64_t soff, double *dst, int64_t m, TableCtl *ctl,
+                                 uint64_t budget_ns, double *sum) {
     __shared__ ParityMap s_wmap[kScanThreads / 32];
-    __shared__ int s_kstar[2];
-    __shared__ double s_sum;
+    __shared__ ParityMap s_bpre;
+    __shared__ unsigned s_first;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_kstar[0] = s_kstar[1] = kNoTerm;
-    __syncthreads();
-    double s = 0.0;
-    int64_t pos = m;  // positions pos, pos - 1, ..., 1 remain; term k of a chunk sits at pos - k
-    for (int pass = 0; pos > 0; ++pass) {
-        const int cnt = pos < (int64_t)kScanChunk ? (int)pos : kScanChunk;
+    const int G = gridDim.x;
+    static_assert((long long)kMaxTableBlocks * kScanChunk < 0xffffffffll, "window indexes fit 32 bits");
+    if (tid == 0) s_first = 0xffffffffu;
+    if (blockIdx.x == 0 && tid == 0) {
+        ctl->pos = m;
+        ctl->s = 0.0;
+        ctl->kstar[0] = ctl->kstar[1] = kNoTerm;
+    }
+    if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return false;
+    for (int pass = 0;; ++pass) {
+        const long long pos = __ldcg(&ctl->pos);
+        const double s = __ldcg(&ctl->s);
+        if (pos <= 0) break;  // the same in every block
+        const long long window = pos < (long long)G * kScanChunk ? pos : (long long)G * kScanChunk;
+        const long long kb = (long long)blockIdx.x * kScanChunk;  // window index of the block's first term
         const unsigned long long sb = (unsigned long long)__double_as_longlong(s);
         const int es = (int)((sb >> 52) & 0x7ff);
         const int e = max(es, 1);
@@ -214,11 +211,11 @@ __device__ double exact_running_sum(const double *src, int64_t soff, double *dst
         ParityMap mine = pm_identity();
 #pragma unroll
         for (int j = 0; j < kScanPer; ++j) {
-            const int k = tid * kScanPer + j;
-            a[j] = k < cnt ? src[pos - k + soff] : 0.0;
+            const long long k = kb + tid * kScanPer + j;
+            a[j] = k < window ? __ldcg(&src[pos - k + soff]) : 0.0;  // written by other blocks (c_i)
             mine = pm_then(mine, term_map(a[j], e, q[j], kind[j]));
         }
-        // scan of the maps: within the warp, then over the warps
+        // scan of the maps: within the warp, then over the warps, then over the blocks
         ParityMap inc = mine;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -239,18 +236,42 @@ __device__ double exact_running_sum(const double *src, int64_t soff, double *dst
             ParityMap we = pm_shfl_up(wm, 1);
             if (lane == 0) we = pm_identity();
             if (lane < kScanThreads / 32) s_wmap[lane] = we;  // runs of the warps before each warp
+            if (lane == 31) {  // the block's whole run
+                RunMap *g = &ctl->agg[blockIdx.x];
+                g->d0 = wm.d0;
+                g->d1 = wm.d1;
+                g->par = wm.par;
+            }
+        }
+        if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return false;
+        if (warp == 0) {  // the run of the blocks before this one
+            ParityMap bp = pm_identity();
+            for (int b0 = 0; b0 < (int)blockIdx.x; b0 += 32) {
+                ParityMap bm = b0 + lane < (int)blockIdx.x ? run_load(&ctl->agg[b0 + lane]) : pm_identity();
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const ParityMap o = pm_shfl_up(bm, off);
+                    if (lane >= off) bm = pm_then(o, bm);
+                }
+                ParityMap last;
+                last.d0 = __shfl_sync(0xffffffffu, bm.d0, 31);
+                last.d1 = __shfl_sync(0xffffffffu, bm.d1, 31);
+                last.par = __shfl_sync(0xffffffffu, bm.par, 31);
+                bp = pm_then(bp, last);
+            }
+            if (lane == 0) s_bpre = bp;
         }
         __syncthreads();
-        const ParityMap pre = pm_then(s_wmap[warp], exc);
+        const ParityMap pre = pm_then(s_bpre, pm_then(s_wmap[warp], exc));
         // this thread's terms under the true parity of S0
         const unsigned p0 = (unsigned)(S0 & 1ull);
         unsigned p = (pre.par >> p0) & 1u;
         unsigned long long acc = p0 ? pre.d1 : pre.d0;  // integer added before this thread's terms
         unsigned long long before[kScanPer];
-        int first = kNoTerm;
+        long long first = kNoTerm;
 #pragma unroll
         for (int j = 0; j < kScanPer; ++j) {
-            const int k = tid * kScanPer + j;
+            const long long k = kb + tid * kScanPer + j;
             before[j] = acc;
             unsigned long long R;
             if (kind[j] == 2) {
@@ -262,32 +283,41 @@ __device__ double exact_running_sum(const double *src, int64_t soff, double *dst
             }
             acc += R;
             // sums before the first term that leaves the binade stay below 2^54: no wrap
-            if (k < cnt && first == kNoTerm && (kind[j] == 3 || S0 + acc >= kTwo53u)) first = k;
+            if (k < window && first == kNoTerm && (kind[j] == 3 || S0 + acc >= kTwo53u)) first = k;
         }
+        // the window's first crossing: minimum over the warp, the block, then one
+        // global atomic per block (window indexes fit 32 bits)
         const int slot = pass & 1;
-        if (first != kNoTerm) atomicMin(&s_kstar[slot], first);
+        unsigned fm = __reduce_min_sync(0xffffffffu, first == kNoTerm ? 0xffffffffu : (unsigned)first);
+        if (lane == 0 && fm != 0xffffffffu) atomicMin(&s_first, fm);
         __syncthreads();
-        const int kstar = min(s_kstar[slot], cnt);  // terms before kstar stay in the binade
+        if (tid == 0 && s_first != 0xffffffffu) atomicMin(&ctl->kstar[slot], (long long)s_first);
+        if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return false;
+        if (tid == 0) s_first = 0xffffffffu;  // read by thread 0 alone, before the barrier above
+        const long long ks = __ldcg(&ctl->kstar[slot]);
+        const long long kstar = ks < window ? ks : window;  // terms before kstar stay in the binade
 #pragma unroll
         for (int j = 0; j < kScanPer; ++j) {
-            const int k = tid * kScanPer + j;
+            const long long k = kb + tid * kScanPer + j;
             const unsigned long long after = j + 1 < kScanPer ? before[j + 1] : acc;
             if (k < kstar) dst[pos - k] = __longlong_as_double((long long)(top + S0 + after));
-            if (k == kstar - 1 && kstar == cnt) s_sum = __longlong_as_double((long long)(top + S0 + after));
-            if (k == kstar && kstar < cnt) {
+            if (k == kstar - 1 && kstar == window) ctl->s = __longlong_as_double((long long)(top + S0 + after));
+            if (k == kstar && kstar < window) {
                 // the term that leaves the binade: one hardware add from the sum before it
                 const double prev = k == 0 ? s : __longlong_as_double((long long)(top + S0 + before[j]));
                 const double nv = __dadd_rn(prev, a[j]);
                 dst[pos - k] = nv;
-                s_sum = nv;
+                ctl->s = nv;
             }
         }
-        if (tid == 0) s_kstar[slot ^ 1] = kNoTerm;  // for the next pass
-        __syncthreads();
-        s = s_sum;
-        pos -= kstar < cnt ? kstar + 1 : cnt;
+        if (blockIdx.x == 0 && tid == 0) {
+            ctl->kstar[slot ^ 1] = kNoTerm;  // for the next window
+            ctl->pos = pos - (kstar < window ? kstar + 1 : window);
+        }
+        if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return false;
     }
-    return s;
+    *sum = __ldcg(&ctl->s);
+    return true;
 }
 
 // Number of non-zero sorted states (xs is non-increasing and >= 0, so the
@@ -303,24 +333,28 @@ __global__ void k_nonzero_prefix(const double *xs, int64_t n, double *dscal) {
     *reinterpret_cast<long long *>(dscal + 2) = (long long)lo;
 }
 
+// Cooperative launch of G blocks (all co-resident): w, then c_i, then r.
 __global__ void __launch_bounds__(kScanThreads) k_tables(const double *xs, int64_t n, double *w, double *ci,
-                                                         double *r, double *dscal) {
+                                                         double *r, double *dscal, TableCtl *ctl,
+                                                         uint64_t budget_ns) {
     // positions past the last non-zero state: x_i = 0 and every sum before them
     // is +0, so w_i = c_i = r_i = 0 exactly; the scans start at the last non-zero one
     const int64_t nz = *reinterpret_cast<const long long *>(dscal + 2);
-    for (int64_t i = nz + 1 + threadIdx.x; i <= n + 1; i += blockDim.x) w[i] = ci[i] = r[i] = 0.0;
-    if (threadIdx.x == 0) w[0] = r[0] = ci[0] = 0.0;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = nz + 1 + gt; i <= n + 1; i += gs) w[i] = ci[i] = r[i] = 0.0;
+    if (gt == 0) w[0] = r[0] = ci[0] = 0.0;
     // w_i over x_i = xs[i - 1]
-    exact_running_sum(xs, -1, w, nz);
-    __syncthreads();
-    for (int64_t i = 1 + threadIdx.x; i <= nz; i += blockDim.x) {
+    double wsum;
+    if (!grid_running_sum(xs, -1, w, nz, ctl, budget_ns, &wsum)) return;
+    for (int64_t i = 1 + gt; i <= nz; i += gs) {
         const double t = __dmul_rn((double)(n - i + 1), xs[i - 1]);
-        const double cv = __dsub_rn(t, w[i]);
+        const double cv = __dsub_rn(t, __ldcg(&w[i]));
         ci[i] = __double_as_longlong(cv) < 0 ? 0.0 : cv;  // max(0, .), -0 -> +0
     }
-    __syncthreads();
-    const double c = exact_running_sum(ci, 0, r, nz);
-    if (threadIdx.x == 0) dscal[0] = c;  // c = r_1
+    if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return;
+    double c;
+    if (!grid_running_sum(ci, 0, r, nz, ctl, budget_ns, &c)) return;
+    if (gt == 0) dscal[0] = c;  // c = r_1
 }
 
 // C_v = c - A_v with A_i = (w_1 - w_i) - (i-1) x_i + (n-i) x_i - w_{i+1} for
@@ -386,16 +420,6 @@ __global__ void k_groups(const double *xs, int64_t n, int32_t *glo, int32_t *ghi
 
 // ------------------------------------------------------------- transpose
 
-__global__ void k_edge_keys(const int64_t *rp, const int32_t *col, int64_t n, uint64_t *keys, int32_t *vals) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
-        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
-            keys[e] = ((uint64_t)(uint32_t)col[e] << 32) | (uint32_t)u;
-            vals[e] = (int32_t)u;
-        }
-    }
-}
-
 // key(v) = (highest-degree out-neighbour of v, ties to the smallest id) << 32 | v;
 // vertices without neighbours use themselves.
 __global__ void k_hub_keys(const int64_t *rp, const int32_t *col, int64_t n, uint64_t *keys, int32_t *vals) {
@@ -417,31 +441,7 @@ __global__ void k_hub_keys(const int64_t *rp, const int32_t *col, int64_t n, uin
 }
 
 
-__global__ void k_indeg(const int32_t *col, int64_t nnz, long long *cnt) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
-        atomicAdd((unsigned long long *)&cnt[col[e]], 1ULL);
-}
-
 }  // namespace
-
-// Stable sort of (keys, vals) in place using the given scratch (same sizes).
-static percis_status merge_sort(percis_ctx *ctx, uint64_t *keys, int32_t *vals, uint64_t *k2, int32_t *v2, int64_t n) {
-    uint64_t *ka = keys, *kb = k2;
-    int32_t *va = vals, *vb = v2;
-    const int grid = grid_for(ctx, n, 256);
-    for (int64_t w = 1; w < n; w <<= 1) {
-        k_merge_pass<<<grid, 256, 0, ctx->stream>>>(ka, va, kb, vb, n, w);
-        PERCIS_CHECK_LAUNCH(ctx, "merge pass");
-        std::swap(ka, kb);
-        std::swap(va, vb);
-    }
-    if (ka != keys) {
-        PERCIS_CUDA(ctx, cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-        PERCIS_CUDA(ctx, cudaMemcpyAsync(vals, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    }
-    return PERCIS_OK;
-}
 
 // Lane order of batched sources: vertices sorted by (highest-degree neighbour,
 // id).  Only the batched form needs it, so it is built on first use.
@@ -462,7 +462,9 @@ percis_status prep_vorder(percis_ctx *ctx) {
             k_hub_keys<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
                                                                      n, k1.as<uint64_t>(), ctx->vorder.as<int32_t>());
             ctx->launches++;
-            rs = merge_sort(ctx, k1.as<uint64_t>(), ctx->vorder.as<int32_t>(), k2.as<uint64_t>(), v2.as<int32_t>(), n);
+            // (the low word is the vertex id, already in order: a stable sort by the high word suffices)
+            rs = radix_sort_u64(ctx, k1.as<uint64_t>(), ctx->vorder.as<int32_t>(), k2.as<uint64_t>(),
+                                v2.as<int32_t>(), n, 32, 32);
         }
         cudaStreamSynchronize(ctx->stream);
         cudaFree(k1.p);
@@ -479,53 +481,19 @@ percis_status prep_graph(percis_ctx *ctx) {
     PERCIS_TRY(ensure(ctx, ctx->status, 64, "status"));
     uint32_t *st = ctx->status.as<uint32_t>();
     PERCIS_CUDA(ctx, cudaMemsetAsync(st, 0, 64, ctx->stream));
+    unsigned long long *desc = reinterpret_cast<unsigned long long *>(ctx->status.as<char>() + 8);
     k_check_csr<<<grid_for(ctx, std::max(n, nnz), 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(),
-                                                                             ctx->col.as<int32_t>(), n, nnz, st);
+                                                                             ctx->col.as<int32_t>(), n, nnz, st, desc);
     PERCIS_CHECK_LAUNCH(ctx, "check csr");
-    uint32_t hst = 0;
-    PERCIS_CUDA(ctx, cudaMemcpyAsync(&hst, st, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned long long hst[3] = {0ull, 0ull, 0ull};
+    PERCIS_CUDA(ctx, cudaMemcpyAsync(hst, st, sizeof(hst), cudaMemcpyDeviceToHost, ctx->stream));
     PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (hst) return set_err(ctx, PERCIS_E_INVALID, "malformed CSR (row_ptr not monotone or column out of range)");
+    if ((uint32_t)hst[0])
+        return set_err(ctx, PERCIS_E_INVALID, "malformed CSR (row_ptr not monotone or column out of range)");
+    ctx->rows_sorted = hst[1] == hst[2];  // (the in-lists of a stable transpose are then sorted too)
 
     if (ctx->directed) {
-        PERCIS_TRY(ensure(ctx, ctx->irp, sizeof(int64_t) * (n + 1), "in-CSR offsets"));
-        PERCIS_TRY(ensure(ctx, ctx->icol, sizeof(int32_t) * std::max<int64_t>(nnz, 1), "in-CSR columns"));
-        DevBuf k1, k2, v2;
-        size_t kb = sizeof(uint64_t) * std::max<int64_t>(nnz, 1);
-        cudaError_t e = cudaMalloc(&k1.p, kb);
-        if (e == cudaSuccess) e = cudaMalloc(&k2.p, kb);
-        if (e == cudaSuccess) e = cudaMalloc(&v2.p, sizeof(int32_t) * std::max<int64_t>(nnz, 1));
-        percis_status rs = PERCIS_OK;
-        if (e != cudaSuccess) {
-            rs = set_err(ctx, PERCIS_E_OOM, "transpose scratch");
-        } else {
-            int32_t *icol = ctx->icol.as<int32_t>();
-            k_edge_keys<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(),
-                                                                      n, k1.as<uint64_t>(), icol);
-            ctx->launches++;
-            rs = merge_sort(ctx, k1.as<uint64_t>(), icol, k2.as<uint64_t>(), v2.as<int32_t>(), nnz);
-            if (rs == PERCIS_OK) {
-                long long *cnt = (long long *)ctx->irp.as<int64_t>();
-                // in-degree counts into a temporary, then exclusive scan into irp
-                DevBuf tmp;
-                e = cudaMalloc(&tmp.p, sizeof(long long) * (n + 1));
-                if (e != cudaSuccess) rs = set_err(ctx, PERCIS_E_OOM, "in-degree scratch");
-                else {
-                    cudaMemsetAsync(tmp.p, 0, sizeof(long long) * (n + 1), ctx->stream);
-                    k_indeg<<<grid_for(ctx, nnz, 256), 256, 0, ctx->stream>>>(ctx->col.as<int32_t>(), nnz,
-                                                                            tmp.as<long long>());
-                    ctx->launches++;
-                    rs = scan_exclusive_i64(ctx, tmp.as<int64_t>(), (int64_t *)cnt, n);
-                    cudaStreamSynchronize(ctx->stream);
-                    cudaFree(tmp.p);
-                }
-            }
-        }
-        cudaStreamSynchronize(ctx->stream);
-        cudaFree(k1.p);
-        cudaFree(k2.p);
-        cudaFree(v2.p);
-        if (rs != PERCIS_OK) return rs;
+        PERCIS_TRY(build_transpose(ctx));
         PERCIS_CUDA(ctx, cudaGetLastError());
     }
     ctx->vorder_ready = false;  // built on first use by the batched form
@@ -563,15 +531,41 @@ percis_status prep_states(percis_ctx *ctx) {
     const int g = grid_for(ctx, n, 256);
     k_state_keys<<<g, 256, 0, ctx->stream>>>(ctx->x.as<double>(), n, k1, perm);
     PERCIS_CHECK_LAUNCH(ctx, "state keys");
-    PERCIS_TRY(merge_sort(ctx, k1, perm, k2, v2, n));
+    PERCIS_TRY(radix_sort_u64(ctx, k1, perm, k2, v2, n, 0, 64));
     k_gather_sorted<<<g, 256, 0, ctx->stream>>>(ctx->x.as<double>(), perm, n, ctx->xs.as<double>());
     PERCIS_CHECK_LAUNCH(ctx, "gather sorted");
     k_nonzero_prefix<<<1, 32, 0, ctx->stream>>>(ctx->xs.as<double>(), n, ctx->dscal.as<double>());
     PERCIS_CHECK_LAUNCH(ctx, "non-zero states");
-    k_tables<<<1, kScanThreads, 0, ctx->stream>>>(ctx->xs.as<double>(), n, ctx->w.as<double>(),
-                                                         ctx->ci.as<double>(), ctx->r.as<double>(),
-                                                         ctx->dscal.as<double>());
-    PERCIS_CHECK_LAUNCH(ctx, "tables");
+    {
+        // as many co-resident blocks as the non-zero states fill (read back: the launch
+        // size is set on the host)
+        long long nz = 0;
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(&nz, ctx->dscal.as<double>() + 2, sizeof(nz), cudaMemcpyDeviceToHost,
+                                         ctx->stream));
+        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->table_grid == 0) {
+            int per_sm = 0;
+            PERCIS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tables, kScanThreads, 0));
+            ctx->table_grid = std::min(kMaxTableBlocks, std::max(1, per_sm) * ctx->num_sms);
+        }
+        const int G = (int)std::max<long long>(1, std::min<long long>(ctx->table_grid, (nz + kScanChunk - 1) / kScanChunk));
+        PERCIS_TRY(ensure(ctx, ctx->table_ctl, sizeof(TableCtl), "table control"));
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->table_ctl.p, 0, sizeof(TableCtl), ctx->stream));
+        const double *xs = ctx->xs.as<double>();
+        double *w = ctx->w.as<double>(), *ci = ctx->ci.as<double>(), *r = ctx->r.as<double>();
+        double *dscal = ctx->dscal.as<double>();
+        TableCtl *tctl = ctx->table_ctl.as<TableCtl>();
+        uint64_t budget = (uint64_t)(ctx->opt.timeout_s * 1e9);
+        int64_t nn = n;
+        void *args[] = {&xs, &nn, &w, &ci, &r, &dscal, &tctl, &budget};
+        PERCIS_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_tables, dim3(G), dim3(kScanThreads), args, 0,
+                                                     ctx->stream));
+        ctx->launches++;
+        uint32_t tst = 0;
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(&tst, &tctl->status, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (tst & DEV_TIMEOUT) return set_err(ctx, PERCIS_E_TIMEOUT, "table scan wait exceeded its budget");
+    }
     PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->dscal.as<double>() + 1, 0, sizeof(double), ctx->stream));
     k_cv_lambda<<<g, 256, 0, ctx->stream>>>(ctx->xs.as<double>(), perm, ctx->w.as<double>(), ctx->dscal.as<double>(),
                                             n, ctx->Cv.as<double>(), ctx->lam.as<double>(), st);

@@ -1,0 +1,276 @@
+// Stable sorts of (key, int32 value) pairs -- an LSD radix sort, and a merge
+// sort for small arrays -- and the directed graph's in-adjacency built with them.
+//
+// Each pass orders the pairs by one 8-bit digit of the key, stably, in three
+// launches: per-tile digit counts (tiles of 4096 pairs), one exclusive scan of
+// the counts laid out digit-major (so the scan gives every (digit, tile) its
+// first output slot), and a scatter in which every tile ranks its pairs among
+// equal digits in index order (warp ballots, then per-warp counts in shared
+// memory).  Passes run from the lowest digit up, so the result is ordered by
+// the key's sorted bits and, among equal keys, by input position.
+//
+// The in-adjacency of a directed CSR is the stable sort of its edges by
+// target: the edges arrive ordered by source, so every in-list comes out
+// ordered by source (the order the backtrack scans predecessors in).
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace percis {
+
+namespace {
+
+constexpr int kRadixBlock = 256;
+constexpr int kRadixRounds = 16;
+constexpr int kRadixTile = kRadixBlock * kRadixRounds;
+constexpr int kRadixBins = 256;
+constexpr int kRadixWarps = kRadixBlock / 32;
+
+template <class K>
+__device__ __forceinline__ int digit_of(K key, int shift) {
+    return (int)((key >> shift) & (K)(kRadixBins - 1));
+}
+
+// counts[d * ntiles + tile] = pairs of the tile whose digit is d
+template <class K>
+__global__ void __launch_bounds__(kRadixBlock) k_radix_count(const K *keys, int64_t n, int shift, int64_t ntiles,
+                                                             long long *counts) {
+    __shared__ int s_hist[kRadixBins];
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int d = threadIdx.x; d < kRadixBins; d += kRadixBlock) s_hist[d] = 0;
+        __syncthreads();
+        const int64_t base = tile * kRadixTile;
+#pragma unroll 4
+        for (int r = 0; r < kRadixRounds; ++r) {
+            const int64_t i = base + (int64_t)r * kRadixBlock + threadIdx.x;
+            if (i < n) atomicAdd(&s_hist[digit_of(keys[i], shift)], 1);
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < kRadixBins; d += kRadixBlock)
+            counts[(int64_t)d * ntiles + tile] = s_hist[d];
+        __syncthreads();
+    }
+}
+
+// pairs of each tile to offs[d * ntiles + tile] + (rank among the tile's earlier pairs of digit d)
+template <class K>
+__global__ void __launch_bounds__(kRadixBlock) k_radix_scatter(const K *kin, const int32_t *vin, K *kout,
+                                                               int32_t *vout, int64_t n, int shift, int64_t ntiles,
+                                                               const long long *offs) {
+    __shared__ int s_cnt[kRadixWarps][kRadixBins];
+    __shared__ int s_tot[kRadixBins];
+    __shared__ long long s_base[kRadixBins];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int d = threadIdx.x; d < kRadixBins; d += kRadixBlock) s_base[d] = offs[(int64_t)d * ntiles + tile];
+        const int64_t base = tile * kRadixTile;
+        for (int r = 0; r < kRadixRounds; ++r) {
+            for (int j = threadIdx.x; j < kRadixWarps * kRadixBins; j += kRadixBlock) (&s_cnt[0][0])[j] = 0;
+            __syncthreads();
+            // pairs r*256 .. r*256+255 of the tile: index order = (warp, lane) order
+            const int64_t i = base + (int64_t)r * kRadixBlock + threadIdx.x;
+            const bool valid = i < n;
+            K key = K(0);
+            int32_t val = 0;
+            int d = kRadixBins;  // invalid lanes form a group of their own
+            if (valid) {
+                key = kin[i];
+                val = vin[i];
+                d = digit_of(key, shift);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int rank = __popc(peers & lt);
+            if (valid && rank == 0) s_cnt[warp][d] = __popc(peers);
+            __syncthreads();
+            for (int dd = threadIdx.x; dd < kRadixBins; dd += kRadixBlock) {
+                int acc = 0;
+#pragma unroll
+                for (int w = 0; w < kRadixWarps; ++w) {
+                    const int c = s_cnt[w][dd];
+                    s_cnt[w][dd] = acc;
+                    acc += c;
+                }
+                s_tot[dd] = acc;
+            }
+            __syncthreads();
+            if (valid) {
+                const long long pos = s_base[d] + s_cnt[warp][d] + rank;
+                kout[pos] = key;
+                vout[pos] = val;
+            }
+            __syncthreads();
+            for (int dd = threadIdx.x; dd < kRadixBins; dd += kRadixBlock) s_base[dd] += s_tot[dd];
+        }
+        __syncthreads();
+    }
+}
+
+// src[e] = the row of edge e (one warp per row, so long rows are spread over lanes)
+__global__ void k_edge_rows(const int64_t *rp, int64_t n, int32_t *src) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int64_t e1 = rp[u + 1];
+        for (int64_t e = rp[u] + lane; e < e1; e += 32) src[e] = (int32_t)u;
+    }
+}
+
+__global__ void k_copy_u32(const int32_t *in, int64_t n, uint32_t *out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (uint32_t)in[i];
+}
+
+// irp[v] = first position of target v in the sorted targets (= nnz past the last):
+// position e writes irp[v] for every v in (tgt[e-1], tgt[e]], and e = nnz the tail
+__global__ void k_offsets_from_sorted(const uint32_t *tgt, int64_t nnz, int64_t n, int64_t *irp) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= nnz; e += stride) {
+        const int64_t lo = e == 0 ? 0 : (int64_t)tgt[e - 1] + 1;
+        const int64_t hi = e == nnz ? n : (int64_t)tgt[e];
+        for (int64_t v = lo; v <= hi; ++v) irp[v] = e;
+    }
+}
+
+// Small arrays: a bottom-up merge sort of whole 64-bit keys (log2 n passes of
+// one launch each) beats eight radix passes of five launches.  In a pass of
+// width w every element finds its output slot by a binary search in the
+// neighbouring run (ties: the left run first, so the sort is stable).
+__device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long *a, int64_t lo, int64_t hi,
+                                                   unsigned long long key) {
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t upper_bound_u64(const unsigned long long *a, int64_t lo, int64_t hi,
+                                                   unsigned long long key) {
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] <= key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_merge_pass(const unsigned long long *kin, const int32_t *vin, unsigned long long *kout,
+                             int32_t *vout, int64_t n, int64_t w) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t run = i / w;
+        const unsigned long long key = kin[i];
+        int64_t out;
+        if ((run & 1) == 0) {  // left run: after the right run's keys that are smaller
+            const int64_t a0 = run * w, b0 = a0 + w, b1 = min(b0 + w, n);
+            out = i + (b0 < n ? lower_bound_u64(kin, b0, b1, key) - b0 : 0);
+        } else {  // right run: after the left run's keys that are not larger
+            const int64_t b0 = run * w, a0 = b0 - w;
+            out = a0 + (i - b0) + (upper_bound_u64(kin, a0, b0, key) - a0);
+        }
+        kout[out] = key;
+        vout[out] = vin[i];
+    }
+}
+
+constexpr int64_t kMergeMaxN = 1 << 18;
+
+int radix_grid(percis_ctx *ctx, int64_t ntiles) {
+    const int64_t cap = (int64_t)ctx->num_sms * 8;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, cap));
+}
+
+template <class K>
+percis_status radix_sort_impl(percis_ctx *ctx, K *keys, int32_t *vals, K *tk, int32_t *tv, int64_t n, int lo_bit,
+                              int bits, K **out_keys, int32_t **out_vals) {
+    *out_keys = keys;
+    *out_vals = vals;
+    if (n <= 1 || bits <= 0) return PERCIS_OK;
+    const int64_t ntiles = (n + kRadixTile - 1) / kRadixTile;
+    const int64_t nc = ntiles * kRadixBins;
+    PERCIS_TRY(ensure(ctx, ctx->radix_counts, sizeof(long long) * (size_t)(nc + 1), "radix counts"));
+    long long *counts = ctx->radix_counts.as<long long>();
+    const int grid = radix_grid(ctx, ntiles);
+    K *ka = keys, *kb = tk;
+    int32_t *va = vals, *vb = tv;
+    for (int shift = lo_bit; shift < lo_bit + bits; shift += 8) {
+        k_radix_count<K><<<grid, kRadixBlock, 0, ctx->stream>>>(ka, n, shift, ntiles, counts);
+        PERCIS_CHECK_LAUNCH(ctx, "radix count");
+        PERCIS_TRY(scan_exclusive_i64(ctx, (const int64_t *)counts, (int64_t *)counts, nc));
+        k_radix_scatter<K><<<grid, kRadixBlock, 0, ctx->stream>>>(ka, va, kb, vb, n, shift, ntiles, counts);
+        PERCIS_CHECK_LAUNCH(ctx, "radix scatter");
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    *out_keys = ka;
+    *out_vals = va;
+    return PERCIS_OK;
+}
+
+}  // namespace
+
+percis_status radix_sort_u64(percis_ctx *ctx, uint64_t *keys, int32_t *vals, uint64_t *tk, int32_t *tv, int64_t n,
+                             int lo_bit, int bits) {
+    uint64_t *ok = keys;
+    int32_t *ov = vals;
+    if (n <= kMergeMaxN && lo_bit == 0 && bits == 64) {
+        unsigned long long *ka = (unsigned long long *)keys, *kb = (unsigned long long *)tk;
+        int32_t *va = vals, *vb = tv;
+        const int grid = grid_for(ctx, n, 256);
+        for (int64_t w = 1; w < n; w <<= 1) {
+            k_merge_pass<<<grid, 256, 0, ctx->stream>>>(ka, va, kb, vb, n, w);
+            PERCIS_CHECK_LAUNCH(ctx, "merge pass");
+            std::swap(ka, kb);
+            std::swap(va, vb);
+        }
+        ok = (uint64_t *)ka;
+        ov = va;
+    } else {
+        PERCIS_TRY(radix_sort_impl<unsigned long long>(ctx, (unsigned long long *)keys, vals,
+                                                       (unsigned long long *)tk, tv, n, lo_bit, bits,
+                                                       (unsigned long long **)&ok, &ov));
+    }
+    if (ok != keys) {
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(keys, ok, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(vals, ov, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return PERCIS_OK;
+}
+
+// In-adjacency of the loaded directed CSR: irp (int64[n+1]) and icol (int32[nnz],
+// every in-list ordered by source).
+percis_status build_transpose(percis_ctx *ctx) {
+    const int64_t n = ctx->n, nnz = ctx->nnz;
+    PERCIS_TRY(ensure(ctx, ctx->irp, sizeof(int64_t) * (n + 1), "in-CSR offsets"));
+    PERCIS_TRY(ensure(ctx, ctx->icol, sizeof(int32_t) * std::max<int64_t>(nnz, 1), "in-CSR columns"));
+    if (nnz == 0) {
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->irp.p, 0, sizeof(int64_t) * (n + 1), ctx->stream));
+        return PERCIS_OK;
+    }
+    // scratch (grow-only, kept in the context): two key arrays and one value array
+    const size_t kb = sizeof(uint32_t) * (size_t)nnz;
+    PERCIS_TRY(ensure(ctx, ctx->sort_a, 2 * kb, "transpose keys"));
+    PERCIS_TRY(ensure(ctx, ctx->sort_b, kb, "transpose values"));
+    uint32_t *k1 = ctx->sort_a.as<uint32_t>(), *k2 = k1 + nnz;
+    int32_t *v1 = ctx->icol.as<int32_t>(), *v2 = ctx->sort_b.as<int32_t>();
+    const int g = grid_for(ctx, nnz, 256);
+    k_copy_u32<<<g, 256, 0, ctx->stream>>>(ctx->col.as<int32_t>(), nnz, k1);
+    PERCIS_CHECK_LAUNCH(ctx, "transpose keys");
+    k_edge_rows<<<grid_for(ctx, n * 32, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, v1);
+    PERCIS_CHECK_LAUNCH(ctx, "edge rows");
+    int bits = 1;
+    while (bits < 32 && (1ll << bits) < n) ++bits;
+    uint32_t *ok;
+    int32_t *ov;
+    PERCIS_TRY(radix_sort_impl<unsigned int>(ctx, k1, v1, k2, v2, nnz, 0, bits, &ok, &ov));
+    if (ov != v1)
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(v1, ov, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, ctx->stream));
+    k_offsets_from_sorted<<<grid_for(ctx, nnz + 1, 256), 256, 0, ctx->stream>>>(ok, nnz, n, ctx->irp.as<int64_t>());
+    PERCIS_CHECK_LAUNCH(ctx, "in-CSR offsets");
+    return PERCIS_OK;
+}
+
+}  // namespace percis

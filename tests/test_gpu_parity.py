@@ -142,10 +142,10 @@ def test_plain_bfs_bitexact(binding, gcase):
     eng = _engine(binding, g)
     rng = np.random.default_rng(0)
     for src in rng.integers(0, g.n, 4):
-        for tgt in (-1, int(rng.integers(0, g.n))):
+        for tgt in (-1, int(rng.integers(0, g.n)), int(src)):
             dist, sig = eng.bfs(int(src), tgt)
             ret, rd, rsig, _, _, _ = oracle.bfs(og, int(src), tgt)
-            if tgt < 0:
+            if tgt < 0 or tgt == src:  # full traversal, or level 0 alone
                 assert np.array_equal(_np(dist), rd)
                 assert _sigma_equal(_np(sig), rsig)
             else:
@@ -173,13 +173,22 @@ def test_msbfs_bitexact(binding, gcase, nsrc, direction):
     eng.close()
 
 
+# bidirectional stores: hashed tables (default), every sample in the direct
+# store, and small first tables that must move to larger ones
+BIDIR_STORES = {"bidir": {}, "bidir_direct": {"bi_table_log": -1},
+                "bidir_grow": {"bi_table_log": 10, "bi_table_max_log": 14}}
+
+
 @pytest.mark.parametrize("form,direction", [("batched", 0), ("batched", 1), ("batched", 2), ("plain", 2),
-                                            ("bidir", 2)])
+                                            ("bidir", 2), ("bidir_direct", 2), ("bidir_grow", 2)])
 def test_phase_bitexact(binding, gcase, form, direction):
     name, g, og = gcase
     x = _states(name, g.n)
     count = 600 if form == "plain" else 3000
-    eng = _engine(binding, g, x, form=form, direction=direction)
+    store = BIDIR_STORES.get(form)
+    if store is not None:
+        form = "bidir"
+    eng = _engine(binding, g, x, form=form, direction=direction, **(store or {}))
     prep = oracle.prepare(x)
     got = eng.run_phase(seed=11, phase=1, count=count)
     ph = oracle.run_samples(og, prep, 11, 1, 3, 0, count, keep_paths=True, bidir=form == "bidir")
@@ -276,6 +285,95 @@ def test_bidir_estimate_matches_oracle(binding, name):
     F = prep.lam * res.phase2.cnt / info["ell"]
     ref = oracle.vjp_fixed(prep, info["ell"], res.phase2, F, gvec)
     assert np.linalg.norm(gx - ref) <= 1e-10 * np.linalg.norm(ref)
+    eng.close()
+
+
+def test_bidir_hand_over_to_direct_store(binding):
+    """Samples the hashed tables cannot hold -- more vertices than 3/4 of
+    the largest table minus a block's claims in flight (a 60x60 grid with the
+    tables capped at 2^10 entries), or more than 4,095 levels on a side (a
+    path of 12,000 vertices with states falling along it, so that far pairs
+    weigh most) -- are handed to the direct store and give the oracle's paths
+    and counts bit for bit."""
+    cases = [(synth.grid_2d(60, 0.05, 7), None, {"bi_table_log": 10, "bi_table_max_log": 10}),
+             (synth.path_graph(12000), "falling", {})]
+    for g, xs, opts in cases:
+        og = oracle.from_synth(g)
+        x = 1.0 - np.arange(g.n) / g.n if xs == "falling" else synth.states_uniform(g.n, 3)
+        eng = _engine(binding, g, x, form="bidir", instrument=1, ell1=200, ell=600, **opts)
+        pc, info = eng.estimate(0.05, 0.1, seed=4)
+        assert info["work"][1][4] > 0 and info["work"][0][4] >= 0  # some samples handed over
+        prep = oracle.prepare(x)
+        ph = oracle.run_samples(og, prep, 4, 1, 3, 0, 600, keep_paths=True, bidir=True)
+        assert np.array_equal(_np(pc), prep.lam * ph.cnt / 600) or \
+            np.max(np.abs(_np(pc) - prep.lam * ph.cnt / 600)) <= 1e-12
+        ptr, nodes = eng.get_paths(600)
+        assert np.array_equal(_np(ptr), ph.path_ptr)
+        assert np.array_equal(_np(nodes), ph.path_nodes)
+        eng.close()
+
+
+@pytest.mark.parametrize("shuffle", [False, True])
+@pytest.mark.parametrize("name", ["rmat14", "ba20000"])
+def test_bidir_hub_backtracks_bitexact(binding, name, shuffle):
+    """Backtrack steps through hubs (candidate lists longer than a warp's
+    share): with strictly sorted rows the kernel may find a small previous
+    level's vertices in w's list by bisection; with every row shuffled it must
+    scan the list in its stored order, as the oracle does.  Paths and counts
+    equal the oracle's either way."""
+    g = synth.rmat(14, 16, 0.57, 0.19, 0.19, 5) if name == "rmat14" else synth.barabasi_albert(20000, 3, 5)
+    if shuffle:
+        rng = np.random.default_rng(9)
+        col = g.col.copy()
+        for u in range(g.n):
+            a, b = g.row_ptr[u], g.row_ptr[u + 1]
+            col[a:b] = rng.permutation(col[a:b])
+        g = synth.Graph(n=g.n, row_ptr=g.row_ptr, col=col, directed=g.directed)
+    og = oracle.from_synth(g)
+    x = synth.states_uniform(g.n, 2)
+    eng = _engine(binding, g, x, form="bidir")
+    got = eng.run_phase(seed=13, phase=1, count=3000)
+    prep = oracle.prepare(x)
+    ph = oracle.run_samples(og, prep, 13, 1, 3, 0, 3000, keep_paths=True, bidir=True)
+    assert np.array_equal(_np(got["kind"]), ph.kind)
+    assert np.array_equal(_np(got["cnt"]), ph.cnt)
+    ptr, nodes = eng.get_paths(3000)
+    assert np.array_equal(_np(ptr), ph.path_ptr)
+    assert np.array_equal(_np(nodes), ph.path_nodes)
+    eng.close()
+
+
+@pytest.mark.slow
+def test_bidir_full_size_rmat22_sampled(binding):
+    """Directed R-MAT scale 22, Beta(0.5, 2) states, eps=0.01 in the
+    bidirectional form (hashed tables, the heavy samples in the direct store):
+    every phase-2 pair bit-exact, 40 sampled paths (reachable, unreachable and
+    long ones) against the oracle's bidirectional replica one by one, and the
+    estimate equal to lambda_v cnt_v / l over the returned paths."""
+    g, x, eps, delta = synth.workload("rmat22_beta")
+    og = oracle.from_synth(g)
+    eng = _engine(binding, g, x, form="bidir", instrument=1)
+    pc, info = eng.estimate(eps, delta, seed=0)
+    ell = info["ell"]
+    assert info["ell1"] == 1000 and info["vertex_diam"] == g.n - 2
+    prep = oracle.prepare(x)
+    s, t = eng.sample_pairs(0, 1, 0, ell)
+    rs, rt, _, _ = oracle.sample_pairs(prep, 0, 1, 0, ell)
+    assert np.array_equal(_np(s), rs) and np.array_equal(_np(t), rt)
+    ptr, nodes = eng.get_paths(ell)
+    ptr, nodes = _np(ptr), _np(nodes)
+    cnt = np.bincount(nodes, minlength=g.n)
+    assert np.max(np.abs(_np(pc) - prep.lam * cnt / ell)) <= 1e-12
+    assert info["sum_internal"][1] == int(ptr[-1])
+    rng = np.random.default_rng(0)
+    long_ = np.flatnonzero(np.diff(ptr) >= 2)
+    picks = np.concatenate([rng.choice(ell, 30, replace=False), rng.choice(long_, 10, replace=False)])
+    kinds = set()
+    for i in picks:
+        ph = oracle.run_samples(og, prep, 0, 1, 3, int(i), 1, keep_paths=True, bidir=True)
+        kinds.add(int(ph.kind[0]))
+        assert np.array_equal(nodes[ptr[i]:ptr[i + 1]], ph.path_nodes), i
+    assert {0, 2} <= kinds
     eng.close()
 
 
