@@ -48,6 +48,11 @@ WORKLOADS = {
         "graph": "R-MAT scale 22 (n=4194304), edge factor 16, a=0.57 b=0.19 c=0.19, directed, self-loops and "
                  "duplicates removed, ids permuted; int64 row offsets / int32 columns",
         "states": "x ~ Beta(0.5, 2)", "eps": 0.01, "delta": 0.1},
+    "rmat20_beta": {
+        "workload": "rmat20_beta",
+        "graph": "R-MAT scale 20 (n=1048576), edge factor 16, a=0.57 b=0.19 c=0.19, directed, self-loops and "
+                 "duplicates removed, ids permuted; the scale-22 workload's generator at a quarter of its size",
+        "states": "x ~ Beta(0.5, 2)", "eps": 0.01, "delta": 0.1},
     "ba100k_outbreak": {
         "workload": "ba100k_m5_outbreak10",
         "graph": "Barabasi-Albert n=100000, m=5, undirected, int64 row offsets / int32 columns",
@@ -378,6 +383,9 @@ def main():
     ap.add_argument("--lane-order", type=int, default=-1, help="0 = by vertex id, 1 = by hub neighbour")
     ap.add_argument("--direction", type=int, default=-1, help="0 = pull, 1 = push, 2 = by work estimate")
     ap.add_argument("--push-alpha", type=float, default=0.0)
+    ap.add_argument("--bi-table-log", type=int, default=0, help="bidirectional store (0 = library default)")
+    ap.add_argument("--bi-table-max-log", type=int, default=0)
+    ap.add_argument("--bi-heavy-edges", type=int, default=0, help="heavy-level threshold (0 = default, <0 = off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -412,6 +420,8 @@ def main():
         eng.set_options(direction=args.direction)
     if args.push_alpha > 0:
         eng.set_options(push_alpha=args.push_alpha)
+    eng.set_options(bi_table_log=args.bi_table_log, bi_table_max_log=args.bi_table_max_log,
+                    bi_heavy_edges=args.bi_heavy_edges)
     rp_d = torch.as_tensor(g.row_ptr, dtype=torch.int64, device="cuda")
     col_d = torch.as_tensor(g.col, dtype=torch.int32, device="cuda")
     x_d = torch.as_tensor(x, dtype=torch.float64, device="cuda")
@@ -481,15 +491,22 @@ def main():
         else:
             kernel, src_name = ("k_bibfs (bidirectional sigma-BFS + backtrack, one block per sample; "
                                 "figures per phase-2 launch)", "bibfs.cu")
-            # per edge scanned: column 4 B + level word 8 B; per count addition (the claim's included)
-            # 8 B; per vertex reached: level word written 8 B, queue 4 B, count read and written 2 x 8 B.
-            # The unit is the phase-2 launch (one per step, most of the samples).
+            # Byte model of the per-pair work: per edge scanned the column (4 B); per
+            # vertex reached its row offsets (8 B) and its level and count written
+            # (12 B); per count addition (an edge into the next level) the count read
+            # (8 B).  The store's own model, reported beside it, adds what the kernel
+            # must also move: per edge the level word read at the far end (8 B), per
+            # vertex the queue entry (4 B) and the count read back by the meeting and
+            # the backtrack (8 B).  The unit is the phase-2 launch (one per step, most
+            # of the samples); the heavy pass, when it runs, is a second launch.
             w2 = work[1]
-            algo_bytes = 12.0 * w2[0] + 8.0 * w2[1] + 28.0 * w2[2]
+            algo_bytes = 4.0 * w2[0] + 20.0 * w2[2] + 8.0 * w2[1]
+            store_bytes = 12.0 * w2[0] + 8.0 * w2[1] + 28.0 * w2[2]
             bfs_ms = sum(i["bfs_ms"][1] for i in infos[:replay_steps])
             bfs_launches = sum(i["bfs_launches"][1] for i in infos[:replay_steps])
             work_step = {"edges_scanned": w[0], "count_additions": w[1], "vertices_reached": w[2],
-                         "bfs_samples": w[3], "one_sided_bfs_edges": wb[4]}
+                         "bfs_samples": w[3] % (1 << 32), "meeting_layers_above_256": w[3] // (1 << 32),
+                         "handed_over_samples": w[4], "one_sided_bfs_edges": wb[4]}
             scanned = w[0]
         per_launch_bytes = algo_bytes / max(bfs_launches, 1)
         per_launch_s = bfs_ms / 1000.0 / max(bfs_launches, 1)
@@ -504,6 +521,13 @@ def main():
                               "algorithmic_bytes_per_launch": per_launch_bytes,
                               "avg_launch_ms": per_launch_s * 1000.0,
                               "launches_per_step": bfs_launches / replay_steps}
+        if args.form != "batched":
+            sb = store_bytes / max(bfs_launches, 1)
+            extras["roofline"]["store_model"] = {
+                "bytes_per_launch": sb, "achieved": sb / per_launch_s / 1e9,
+                "frac": sb / per_launch_s / 1e9 / peaks["hbm_gbs"],
+                "note": "adds per edge the level word read (8 B), per vertex the queue entry (4 B) and the "
+                        "count read back (8 B)"}
         # GTEPS two ways: the edges a one-sided truncated BFS from s_i scans to settle t_i
         # (the paper-independent work measure), and the edges the timed kernel scanned
         extras["gteps"] = wb[4] / step_s_replayed / 1e9 if wb[4] else None

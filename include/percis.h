@@ -99,18 +99,25 @@ typedef struct {
                                  launches of a phase once in a CUDA graph and replays it while
                                  the per-graph sample counts repeat (phase 1 always does);
                                  the seed is read from device memory, results are unchanged */
-    int32_t bi_table_log;     /* bidirectional form: 0 (default) = a sample starts in a hashed
-                                 table of 2^11 entries per block and moves to tables 4x larger
-                                 as it grows; k in [10, 17] = start at 2^k; < 0 = every sample
-                                 in the direct store (an entry per vertex of the graph and
-                                 block).  Results do not depend on it. */
-    int32_t bi_table_max_log; /* largest hashed table: 0 (default) = the smallest size 4^j
-                                 times the first that holds every vertex of the (largest)
-                                 graph at most half full, at most 2^17 entries; k = at most
-                                 2^k.  Samples that would fill more than 3/4 of it, or pass
-                                 4,095 levels on a side, run in the direct store. */
+    int32_t bi_table_log;     /* bidirectional form, store of the first pass: 0 (default) = the
+                                 direct store (an entry per vertex of the graph and block) when
+                                 it fits bi_scratch_gib with every resident block, else one
+                                 hashed table per block of the smallest 2^k >= 2n + 1024
+                                 entries, k <= 18; k in [10, 20] = hashed, starting at 2^k and
+                                 moving to tables 4x larger as a sample grows; < 0 = the
+                                 direct store.  Results do not depend on it. */
+    int32_t bi_table_max_log; /* largest hashed table when bi_table_log > 0: 0 = the smallest
+                                 size 4^j times the first that holds every vertex of the
+                                 (largest) graph at most half full, at most 2^20 entries; k =
+                                 at most 2^k.  Samples that would fill more than 3/4 of it, or
+                                 pass 4,095 levels on a side, are handed to the heavy pass. */
     int32_t bi_scratch_gib;   /* direct store: device memory its blocks may use, GiB (0 = 16);
                                  it holds 56 bytes per vertex and block, so it caps the blocks */
+    int64_t bi_heavy_edges;   /* a sample whose next level would scan more than this many edges
+                                 stops untouched and runs again after the first pass, alone in
+                                 a block of 1,024 threads in the direct store (the heavy pass);
+                                 0 = default (16,384), < 0 = never */
+    int64_t reserved;         /* must be 0 */
 } percis_options;
 
 typedef struct {
@@ -145,9 +152,10 @@ typedef struct {
      * Bidirectional form instead: [0] edges scanned by both sides, [1] count
      * additions (edges into a new level), [2] vertices reached by both
      * sides, [3] samples traversed (plus 2^32 per meeting layer above 256
-     * members), [4] samples the hashed tables handed to the direct store,
-     * [5] moves to a larger table; the rest 0.  bfs_launches is then the
-     * number of bidirectional passes (one per phase). */
+     * members), [4] samples handed over to the heavy pass (a level above
+     * bi_heavy_edges, a full table or a side past 4,095 levels), [5] moves to
+     * a larger table; the rest 0.  bfs_launches is then the number of
+     * bidirectional passes (one per phase, two when the heavy pass ran). */
     int64_t work[2][8];
 } percis_info;
 
@@ -318,12 +326,14 @@ percis_status percis_autotune(percis_ctx *ctx, int64_t probe_samples, uint64_t s
 int64_t percis_last_levels(percis_ctx *ctx, int64_t *out, int64_t cap);
 
 /* Per-sample trace of the last bidirectional phase (measurement aid), recorded
- * when options.instrument = 2: for sample i, out[6i..6i+5] = device time (ns)
- * when a block took it and when it finished, edges its levels scanned,
- * levels | store << 32 | block << 33 (store 0 = hashed tables, 1 = direct;
- * a sample handed over shows its direct-store run), and the times the levels
- * ended and the meeting vertex was chosen.  Returns the number of samples
- * written (at most cap). */
+ * when options.instrument = 2: for sample i, out[8i..8i+7] = device time (ns)
+ * when a block took it and when it finished; edges its levels scanned;
+ * levels | store << 32 | block << 33 | heavy << 63 (store 0 = hashed tables,
+ * 1 = direct; heavy = 1 for the 1,024-thread pass, whose run a handed-over
+ * sample shows); the times the levels ended and the meeting vertex was
+ * chosen; and two words that are 0 unless the path walk failed (a
+ * BAD_PATH status): the step, side and list length, and the vertex and level
+ * it stopped at.  Returns the number of samples written (at most cap). */
 int64_t percis_sample_trace(percis_ctx *ctx, int64_t *out, int64_t cap);
 
 /* Internal nodes of the paths of the last sampling phase, t-side first.

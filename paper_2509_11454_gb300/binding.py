@@ -41,7 +41,8 @@ class percis_options(ctypes.Structure):
                 ("instrument", ctypes.c_int32), ("lane_order", ctypes.c_int32),
                 ("direction", ctypes.c_int32), ("estimator", ctypes.c_int32), ("push_alpha", ctypes.c_double),
                 ("cuda_graphs", ctypes.c_int32), ("bi_table_log", ctypes.c_int32),
-                ("bi_table_max_log", ctypes.c_int32), ("bi_scratch_gib", ctypes.c_int32)]
+                ("bi_table_max_log", ctypes.c_int32), ("bi_scratch_gib", ctypes.c_int32),
+                ("bi_heavy_edges", ctypes.c_int64), ("reserved", ctypes.c_int64)]
 
 
 class percis_info(ctypes.Structure):
@@ -283,9 +284,9 @@ def percis_autotune(ctx, probe_samples: int, seed: int) -> percis_options:
 
 def percis_sample_trace(ctx, cap: int) -> np.ndarray:
     """Per-sample trace of the last bidirectional phase (instrument = 2):
-    rows {start ns, end ns, edges, levels | store << 32 | block << 33, levels end ns,
-    meeting choice end ns}."""
-    out = np.zeros((max(cap, 1), 6), dtype=np.int64)
+    rows {start ns, end ns, edges, levels | store << 32 | block << 33 | heavy << 63,
+    levels end ns, meeting choice end ns, failed walk step, failed walk vertex}."""
+    out = np.zeros((max(cap, 1), 8), dtype=np.int64)
     k = int(load_library().percis_sample_trace(ctx, out.ctypes.data, cap))
     return out[:k]
 

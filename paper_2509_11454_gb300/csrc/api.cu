@@ -233,7 +233,7 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
             if (e0) cudaEventRecord(e0, ctx->stream);
             PERCIS_TRY(bidir_phase(ctx, seed, (uint32_t)(2 + phase), count));
             if (e1) cudaEventRecord(e1, ctx->stream);
-            *batches = 1;
+            *batches = ctx->bi_handed > 0 ? 2 : 1;
         } else {
             int64_t U = 0, valid = 0;
             PERCIS_TRY(group_by_source(ctx, count, &U, &valid));
@@ -783,7 +783,7 @@ int64_t percis_sample_trace(percis_ctx *ctx, int64_t *out, int64_t cap) {
     if (!ctx || !ctx->bi_trace.p || !out || cap < 0) return 0;
     DeviceGuard g(ctx->device);
     const int64_t k = std::min<int64_t>(ctx->bi_trace_n, cap);
-    if (k > 0 && (cudaMemcpyAsync(out, ctx->bi_trace.p, sizeof(int64_t) * 6 * k, cudaMemcpyDeviceToHost,
+    if (k > 0 && (cudaMemcpyAsync(out, ctx->bi_trace.p, sizeof(int64_t) * 8 * k, cudaMemcpyDeviceToHost,
                                   ctx->stream) != cudaSuccess ||
                   cudaStreamSynchronize(ctx->stream) != cudaSuccess)) {
         cudaGetLastError();

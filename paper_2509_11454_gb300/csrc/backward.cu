@@ -82,6 +82,7 @@ percis_status backward_fixed(percis_ctx *ctx, const double *g, double *grad) {
                                                                   ctx->Cv.as<double>(), (double)ctx->last_ell, gs);
     PERCIS_CHECK_LAUNCH(ctx, "backward gamma");
     PERCIS_TRY(scan_exclusive_f64(ctx, gs, G, n));
+    PERCIS_TRY(prep_groups(ctx));
     k_bw_final<<<grid_for(ctx, n, block), block, 0, ctx->stream>>>(n, ctx->perm.as<int32_t>(),
                                                                   ctx->grp_lo.as<int32_t>(),
                                                                   ctx->grp_hi.as<int32_t>(), gs, G, grad);

@@ -68,9 +68,9 @@ constexpr int kEdgeBatch = PERCIS_EDGE_BATCH;  // edges a thread has in flight (
 #endif
 constexpr uint32_t kHashLevels = 4095;            // levels a hashed word holds (12 bits)
 constexpr uint32_t kHashEpochs = (1u << 20) - 1;  // epochs a hashed word holds (20 bits)
-constexpr int kDefaultH0Log = 11;                 // first table: 2,048 entries
 constexpr int kMaxHLog = 20;                      // largest table: at most 2^20 entries
 constexpr int kMinHLog = 10;                      // smallest table (new entries stop at 3/4 minus a block)
+constexpr int kDefaultHLog = 18;                  // default: one table of at most 262,144 entries per block
 
 struct BiArgs {
     int64_t n;
@@ -108,9 +108,12 @@ struct BiArgs {
     int32_t *deferred;           // samples handed to the direct store
     unsigned int *n_deferred;
     int32_t sorted;              // every adjacency list strictly increasing (reverse backtrack allowed)
+    unsigned long long heavy_edges;  // a level scanning more edges than this hands the sample over (0: never)
     unsigned long long *trace;   // optional, per sample: {start ns, end ns, edges scanned,
-                                 // levels | store << 32 | slot << 33, end of the levels ns,
-                                 // end of the meeting vertex's choice ns}
+                                 // levels | store << 32 | slot << 33 | heavy pass << 63, end of the
+                                 // levels ns, end of the meeting vertex's choice ns, and where a
+                                 // backtrack found no candidate: kind | side << 4 | step << 8 |
+                                 // list length << 32, vertex << 32 | its level}
 };
 
 // ------------------------------------------------------------------ words
@@ -180,7 +183,7 @@ __device__ __forceinline__ void cas_pair(unsigned long long *p, unsigned long lo
         : "memory");
 }
 
-template <class T>
+template <int BT, class T>
 __device__ __forceinline__ T block_sum(T v, T *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -189,7 +192,7 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
     if (lane == 0) red[warp] = v;
     __syncthreads();
     T t = T(0);
-    for (int q = 0; q < kBiBlock / 32; ++q) t += red[q];
+    for (int q = 0; q < BT / 32; ++q) t += red[q];
     return t;
 }
 
@@ -211,12 +214,12 @@ __device__ __forceinline__ int64_t hash_find(const unsigned long long *tab, int 
 
 // C = unsigned long long: exact counts (flagged at 2^53, products checked);
 // C = double: FP64 counts, the rerun of a phase whose counts passed 2^53.
-template <class C, bool HASH>
-__global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
+template <class C, bool HASH, int BT>
+__global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bibfs(BiArgs a) {
     using W = Word<HASH>;
     constexpr bool FP = std::is_floating_point<C>::value;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int nw = kBiBlock / 32;
+    constexpr int nw = BT / 32;
     const int64_t n = a.n;
     const size_t slot = blockIdx.x;
     unsigned long long *const sent = a.ent + slot * (size_t)a.region * 4;
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
             if (ep_slot >= kHashEpochs) {
                 // the slot's epochs are used up: clear every word of its tables (once per
                 // 2^20 - 1 samples of the slot), then start again at 1
-                for (int64_t e = threadIdx.x; e < a.region; e += kBiBlock) {
+                for (int64_t e = threadIdx.x; e < a.region; e += BT) {
                     sent[4 * e] = 0ull;
                     sent[4 * e + 2] = 0ull;
                 }
@@ -337,6 +340,10 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 x = cost[0] <= cost[1] ? 0 : 1;
                 const long long lo = x ? qlo[1] : qlo[0], hi = x ? qhi[1] : qhi[0];
                 const uint32_t nl = (x ? lev[1] : lev[0]) + 1;
+                if (a.heavy_edges && (x ? cost[1] : cost[0]) > a.heavy_edges) {
+                    handed = true;  // a heavy level: the pass with larger blocks takes the sample
+                    break;
+                }
                 if constexpr (HASH) {
                     if (nl > kHashLevels) {  // past the words' 12 bits: the direct store takes it
                         handed = true;
@@ -346,7 +353,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                     // half full (the largest table is the limit; claims past 3/4 of it hand
                     // the sample over)
                     const unsigned long long need =
-                        2ull * ((unsigned long long)(qhi[0] + qhi[1]) + (x ? cost[1] : cost[0])) + 2ull * kBiBlock;
+                        2ull * ((unsigned long long)(qhi[0] + qhi[1]) + (x ? cost[1] : cost[0])) + 2ull * BT;
                     int nlg = lg;
                     int64_t noff = toff;
                     while (nlg + 2 <= a.hmax_log && (1ull << nlg) < need) {
@@ -367,7 +374,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             int2 *qz = z ? queue1 : queue0;
                             const long long qn = z ? qhi[1] : qhi[0];
                             const int zs = z ? 2 : 0;
-                            for (long long k = threadIdx.x; k < qn; k += kBiBlock) {
+                            for (long long k = threadIdx.x; k < qn; k += BT) {
                                 const int2 qe = qz[k];
                                 unsigned long long o0, oc0, o1, oc1;
                                 ld_pair(&tab[4ull * qe.y], o0, oc0);
@@ -416,7 +423,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 const int64_t hmask = HASH ? (1ll << lg) - 1 : 0;
                 // new entries stop short of 3/4 of the table (each thread has at most one
                 // claim in flight past the check)
-                const long long cap_new = HASH ? ((3ll << lg) >> 2) - kBiBlock : 0ll;
+                const long long cap_new = HASH ? ((3ll << lg) >> 2) - BT : 0ll;
                 const long long known = qhi[0] + qhi[1];
                 unsigned long long ne = 0ull;
                 // level nl: claim unreached neighbours and add the counts over
@@ -572,13 +579,13 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                         }
                         return klo;
                     };
-                    for (int64_t j = threadIdx.x; j < E; j += (int64_t)kEdgeBatch * kBiBlock) {
+                    for (int64_t j = threadIdx.x; j < E; j += (int64_t)kEdgeBatch * BT) {
                         Pre pr[kEdgeBatch];
                         int kk[kEdgeBatch];
                         int32_t vv[kEdgeBatch];
 #pragma unroll
                         for (int b = 0; b < kEdgeBatch; ++b) {
-                            const int64_t jb = j + (int64_t)b * kBiBlock;
+                            const int64_t jb = j + (int64_t)b * BT;
                             kk[b] = jb < E ? vertex_of(jb) : 0;
                             vv[b] = jb < E ? ax[s_fe[kk[b]] + (jb - s_pre[kk[b]])] : -1;
                         }
@@ -621,7 +628,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
         }
         if (a.trace && threadIdx.x == 0) t_levels = globaltimer_ns();
         if (handed) {
-            // nothing of the sample was written outside the slot: the direct store runs it
+            // nothing of the sample was written outside the slot: the heavy pass runs it
             if (threadIdx.x == 0) {
                 a.deferred[atomicAdd(a.n_deferred, 1u)] = (int32_t)i;
                 if (a.work) s_work[4] += 1ull;
@@ -643,7 +650,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 return count_of<C>(__ldcg(&tab[4ll * qe.y + 1])) * count_of<C>(__ldcg(&tab[4ll * qe.y + 3]));
             };
             C part = C(0);
-            for (int m = threadIdx.x; m < nm; m += kBiBlock) {
+            for (int m = threadIdx.x; m < nm; m += BT) {
                 const int2 qe = memb[m];
                 const C a0 = count_of<C>(__ldcg(&tab[4ll * qe.y + 1]));
                 const C a1 = count_of<C>(__ldcg(&tab[4ll * qe.y + 3]));
@@ -656,7 +663,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                     s_mw[m] = p;
                 }
             }
-            const C sst = block_sum(part, s_redc);
+            const C sst = block_sum<BT>(part, s_redc);
             if (threadIdx.x == 0 && (double)sst >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
             const double target = __dmul_rn(uniform_at(a.seed, (uint64_t)i, a.tag, 0), (double)sst);
             if (a.work && threadIdx.x == 0 && nm > kMeetCap) s_work[3] += 1ull << 32;  // large layers (high word)
@@ -666,7 +673,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 // member j qualifies when the weights of the members with ids <= its
                 // own reach the target; the meeting vertex is the smallest such id
                 unsigned long long best = ~0ull;  // vertex << 32 | entry
-                for (int j = threadIdx.x; j < nm; j += kBiBlock) {
+                for (int j = threadIdx.x; j < nm; j += BT) {
                     const int32_t vj = s_mv[j];
                     C pre = C(0);
                     for (int k2 = 0; k2 < nm; ++k2)
@@ -681,6 +688,12 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 __syncthreads();
                 unsigned long long bk = s_best[0];
                 for (int q = 1; q < nw; ++q) bk = min(bk, s_best[q]);
+                if (bk == ~0ull) {  // (FP64 counts) no member reaches the target: the last one takes it
+                    unsigned long long lk = 0ull;
+                    for (int j = 0; j < nm; ++j)
+                        lk = max(lk, ((unsigned long long)(uint32_t)s_mv[j] << 32) | (uint32_t)s_mp[j]);
+                    bk = lk;
+                }
                 vm = (int32_t)(bk >> 32);
                 pm = (int64_t)(uint32_t)bk;
             } else {
@@ -694,9 +707,9 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                 C base = C(0);  // weight of the members below lo_id
                 while (span > 1) {
                     const int64_t wb = (span + kMeetBuckets - 1) / kMeetBuckets;
-                    for (int b = threadIdx.x; b < kMeetBuckets; b += kBiBlock) s_bkt[b] = C(0);
+                    for (int b = threadIdx.x; b < kMeetBuckets; b += BT) s_bkt[b] = C(0);
                     __syncthreads();
-                    for (int m = threadIdx.x; m < nm; m += kBiBlock) {
+                    for (int m = threadIdx.x; m < nm; m += BT) {
                         const int2 qe = memb[m];
                         if (qe.x >= lo_id && qe.x < lo_id + span) atomicAdd(&s_bkt[(qe.x - lo_id) / wb], weight(qe));
                     }
@@ -715,7 +728,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                         const unsigned nz = __ballot_sync(0xffffffffu, lsum > C(0));
                         // FP64 counts past 2^53 may leave every total just below the target:
                         // the last bucket with weight then takes the remainder
-                        const int L0 = hit ? __ffs(hit) - 1 : 31 - __clz(nz);
+                        const int L0 = hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : 0);
                         if (lane == L0) {  // the bucket within this lane's range, and the total below it
                             C run = base + (incl - lsum), below = run;
                             int bsel = 0;
@@ -849,7 +862,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             const int2 *qz = z ? queue1 : queue0;
                             if (threadIdx.x == 0) s_nc = 0;
                             __syncthreads();
-                            for (long long q = lq0 + threadIdx.x; q < lq1; q += kBiBlock) {
+                            for (long long q = lq0 + threadIdx.x; q < lq1; q += BT) {
                                 const int2 qe = qz[q];
                                 int64_t blo = e0, bhi = e1;
                                 while (blo < bhi) {
@@ -868,7 +881,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             __syncthreads();
                             const int nc = s_nc;
                             unsigned long long best = ~0ull, lastc = 0ull;  // place << 32 | candidate
-                            for (int c = threadIdx.x; c < nc; c += kBiBlock) {
+                            for (int c = threadIdx.x; c < nc; c += BT) {
                                 const int32_t jc = s_mj[c];
                                 C pre = C(0);
                                 for (int c2 = 0; c2 < nc; ++c2)
@@ -907,7 +920,7 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                                 s_pickp = c < 0 ? -1 : s_mp[c];
                             }
                         } else {
-                            const int64_t seg = (e1 - e0 + kBiBlock - 1) / kBiBlock;
+                            const int64_t seg = (e1 - e0 + BT - 1) / BT;
                             const int64_t sb = min(e1, e0 + (int64_t)threadIdx.x * seg), se = min(e1, sb + seg);
                             C my = C(0);
                             int64_t e = sb;
@@ -950,8 +963,13 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                             if ((int)threadIdx.x == ts) s_tpre = pre;
                             __syncthreads();
                             if (warp == 0) {
-                                const int64_t tb = min(e1, e0 + (int64_t)ts * seg);
-                                warp_scan(tb, min(e1, tb + seg), s_tpre);
+                                if (ts >= 0 && ts < BT) {  // (no segment with a candidate: no choice)
+                                    const int64_t tb = min(e1, e0 + (int64_t)ts * seg);
+                                    warp_scan(tb, min(e1, tb + seg), s_tpre);
+                                } else if (lane == 0) {
+                                    s_pick = -1;
+                                    s_pickp = -1;
+                                }
                             }
                             if (threadIdx.x == 0) s_tlast = -1;
                         }
@@ -960,7 +978,15 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
                         const int64_t pickp = s_pickp;
                         __syncthreads();  // s_pick is written again by the next step
                         if (pick < 0) {
-                            if (threadIdx.x == 0) atomicOr(a.status, DEV_BAD_PATH);
+                            if (threadIdx.x == 0) {
+                                atomicOr(a.status, DEV_BAD_PATH);
+                                if (a.trace) {  // where the path ended without a candidate
+                                    a.trace[8 * i + 6] = (e1 - e0 <= BT ? 1ull : 2ull) | ((unsigned long long)z << 4) |
+                                                         ((unsigned long long)step << 8) |
+                                                         ((unsigned long long)(e1 - e0) << 32);
+                                    a.trace[8 * i + 7] = ((unsigned long long)(uint32_t)w << 32) | lw;
+                                }
+                            }
                             bad = true;
                             break;
                         }
@@ -985,12 +1011,12 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
             s_work[3] += 1ull;
         }
         if (a.trace && threadIdx.x == 0) {
-            unsigned long long *tr = a.trace + 6 * i;
+            unsigned long long *tr = a.trace + 8 * i;
             tr[0] = t_start;
             tr[1] = globaltimer_ns();
             tr[2] = smp_edges;
             tr[3] = (unsigned long long)smp_levels | ((unsigned long long)(HASH ? 0 : 1) << 32) |
-                    ((unsigned long long)slot << 33);
+                    ((unsigned long long)slot << 33) | ((unsigned long long)(BT != kBiBlock) << 63);
             tr[4] = t_levels;
             tr[5] = t_meet ? t_meet : t_levels;
         }
@@ -1005,11 +1031,14 @@ __global__ void __launch_bounds__(kBiBlock, PERCIS_BI_MINB) k_bibfs(BiArgs a) {
     if (a.work && threadIdx.x < 6 && s_work[threadIdx.x]) atomicAdd(&a.work[threadIdx.x], s_work[threadIdx.x]);
 }
 
-template <bool HASH>
-int blocks_per_sm(percis_ctx *ctx, int *cache) {
+constexpr int kHeavyBlock = 1024;                        // threads per sample in the heavy pass
+constexpr unsigned long long kDefaultHeavyEdges = 16384;  // a level scanning more edges is heavy
+
+template <bool HASH, int BT>
+int blocks_per_sm(int *cache) {
     if (!*cache) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs<unsigned long long, HASH>, kBiBlock, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs<unsigned long long, HASH, BT>, BT, 0) !=
                 cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
@@ -1018,6 +1047,12 @@ int blocks_per_sm(percis_ctx *ctx, int *cache) {
         *cache = per_sm;
     }
     return *cache;
+}
+
+template <bool HASH, int BT>
+void launch(percis_ctx *ctx, int grid, const BiArgs &a) {
+    if (ctx->sigma_mode == 2) k_bibfs<double, HASH, BT><<<grid, BT, 0, ctx->stream>>>(a);
+    else k_bibfs<unsigned long long, HASH, BT><<<grid, BT, 0, ctx->stream>>>(a);
 }
 
 BiArgs common_args(percis_ctx *ctx, uint64_t seed, uint32_t tag_path) {
@@ -1045,14 +1080,18 @@ BiArgs common_args(percis_ctx *ctx, uint64_t seed, uint32_t tag_path) {
     return a;
 }
 
-// The direct store over `count` samples (all of the phase, or the list).
-percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count, const int32_t *list) {
+// The direct store over `count` samples (all of the phase, or the list), BT
+// threads per sample; samples with a level above heavy_edges are listed in
+// defer (heavy_edges = 0: none).
+template <int BT>
+percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count, const int32_t *list,
+                          unsigned long long heavy_edges, int32_t *defer, unsigned int *n_def) {
     const int32_t *gid = nullptr;
     const int64_t *vbase = nullptr;
     int64_t nslot = ctx->n;
     if (ctx->multi) multi_graph_view(ctx, &gid, &vbase, &nslot);
     const size_t per_slot = (size_t)nslot * (sizeof(unsigned long long) * 4 + sizeof(int2) * 3);
-    const int per_sm = blocks_per_sm<false>(ctx, &ctx->bi_per_sm);
+    const int per_sm = blocks_per_sm<false, BT>(BT == kBiBlock ? &ctx->bi_per_sm : &ctx->bi_heavy_per_sm);
     const int64_t budget = (int64_t)(ctx->opt.bi_scratch_gib > 0 ? ctx->opt.bi_scratch_gib : 16) << 30;
     int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, budget / (int64_t)per_slot));
     slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
@@ -1085,10 +1124,11 @@ percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     a.region = nslot;
     a.qcap = nslot;
     a.next = ctx->red.as<unsigned long long>();
-    const int grid = (int)std::min<int64_t>(ctx->bi_slots, std::max<int64_t>(count, 1));
-    if (ctx->sigma_mode == 2) k_bibfs<double, false><<<grid, kBiBlock, 0, ctx->stream>>>(a);
-    else k_bibfs<unsigned long long, false><<<grid, kBiBlock, 0, ctx->stream>>>(a);
-    PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS (direct)");
+    a.heavy_edges = heavy_edges;
+    a.deferred = defer;
+    a.n_deferred = n_def;
+    launch<false, BT>(ctx, (int)slots, a);
+    PERCIS_CHECK_LAUNCH(ctx, BT == kBiBlock ? "bidirectional sigma-BFS (direct)" : "bidirectional sigma-BFS (heavy)");
     return PERCIS_OK;
 }
 
@@ -1096,78 +1136,101 @@ percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
 
 // All samples of a phase (pairs, kinds already drawn): kinds of unreachable
 // targets, |I|, paths and counts, as the batched form leaves them.  Every
-// sample runs in the hashed store first; the ones it hands over run in the
-// direct store after it.
+// sample runs first with 256 threads (the direct store, or hashed tables);
+// samples with a heavy level, or that outgrow their table, are handed over
+// untouched and run afterwards with 1,024 threads in the direct store.
 percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count) {
     PERCIS_TRY(ensure(ctx, ctx->ms_ctl, sizeof(MsCtl), "ms ctl"));
     // the status word may be freshly allocated: it must start at zero
     PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->ms_ctl.p, 0, sizeof(MsCtl), ctx->stream));
     ctx->phase_span = count;
     if (ctx->opt.instrument >= 2) {
-        PERCIS_TRY(ensure(ctx, ctx->bi_trace, sizeof(unsigned long long) * 6 * std::max<int64_t>(count, 1),
+        PERCIS_TRY(ensure(ctx, ctx->bi_trace, sizeof(unsigned long long) * 8 * std::max<int64_t>(count, 1),
                           "sample trace"));
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_trace.p, 0, sizeof(unsigned long long) * 6 * count, ctx->stream));
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_trace.p, 0, sizeof(unsigned long long) * 8 * count, ctx->stream));
         ctx->bi_trace_n = count;
     }
-    if (ctx->opt.bi_table_log < 0) return direct_pass(ctx, seed, tag_path, count, nullptr);
+    const unsigned long long heavy =
+        ctx->opt.bi_heavy_edges == 0 ? kDefaultHeavyEdges
+                                     : (ctx->opt.bi_heavy_edges < 0 ? 0ull : (unsigned long long)ctx->opt.bi_heavy_edges);
+    PERCIS_TRY(ensure(ctx, ctx->bi_defer, sizeof(int32_t) * std::max<int64_t>(count, 1) + 64, "handed-over samples"));
+    int32_t *defer = ctx->bi_defer.as<int32_t>();
+    unsigned int *n_def = reinterpret_cast<unsigned int *>(defer + std::max<int64_t>(count, 1));
+    PERCIS_CUDA(ctx, cudaMemsetAsync(n_def, 0, sizeof(unsigned int), ctx->stream));
     int64_t nslot = ctx->n;
     if (ctx->multi) {
         const int32_t *gid;
         const int64_t *vbase;
         multi_graph_view(ctx, &gid, &vbase, &nslot);
     }
-    // tables of 2^h0 .. 2^hmax entries in steps of 4x; the largest holds every
-    // vertex of the (largest) graph at most half full, up to 2^17 entries
-    const int h0 = ctx->opt.bi_table_log > 0 ? std::min(std::max(ctx->opt.bi_table_log, kMinHLog), kMaxHLog)
-                                             : kDefaultH0Log;
-    const int cap = ctx->opt.bi_table_max_log > 0 ? std::min(ctx->opt.bi_table_max_log, kMaxHLog) : kMaxHLog;
-    int hmax = h0;
-    while (hmax + 2 <= cap && (1ll << hmax) < 2 * nslot + 4 * kBiBlock) hmax += 2;
-    int64_t region = 0;
-    for (int l = h0; l <= hmax; l += 2) region += 1ll << l;
-    const int64_t qcap = 1ll << hmax;
-    const int per_sm = blocks_per_sm<true>(ctx, &ctx->bi_hash_per_sm);
-    const int64_t slots = (int64_t)per_sm * ctx->num_sms;
-    const size_t ent_bytes = sizeof(unsigned long long) * 4 * (size_t)region * slots;
-    const size_t q_bytes = sizeof(int2) * 3 * (size_t)qcap * slots;
-    if (ctx->bi_hregion != region || ctx->bi_hslots != slots || ctx->bi_h0 != h0) {
-        PERCIS_TRY(ensure(ctx, ctx->bi_hent, ent_bytes, "hashed entries"));
-        PERCIS_TRY(ensure(ctx, ctx->bi_hq, q_bytes, "hashed queues"));
-        PERCIS_TRY(ensure(ctx, ctx->bi_hep, sizeof(uint32_t) * slots, "slot epochs"));
-        // words of no sample (epoch 0) and epochs from 1
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_hent.p, 0, ent_bytes, ctx->stream));
-        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_hep.p, 0, sizeof(uint32_t) * slots, ctx->stream));
-        ctx->bi_hregion = region;
-        ctx->bi_hslots = slots;
-        ctx->bi_h0 = h0;
+    // default: the direct store when its entries for every resident block fit the
+    // scratch budget (it is the faster store per sample), else hashed tables, whose
+    // memory follows the vertices a sample reaches rather than n
+    bool direct = ctx->opt.bi_table_log < 0;
+    if (ctx->opt.bi_table_log == 0) {
+        const int64_t per_slot = nslot * (int64_t)(sizeof(unsigned long long) * 4 + sizeof(int2) * 3);
+        const int64_t budget = (int64_t)(ctx->opt.bi_scratch_gib > 0 ? ctx->opt.bi_scratch_gib : 16) << 30;
+        const int64_t full = (int64_t)blocks_per_sm<false, kBiBlock>(&ctx->bi_per_sm) * ctx->num_sms;
+        direct = full * per_slot <= budget;
     }
-    PERCIS_TRY(ensure(ctx, ctx->bi_defer, sizeof(int32_t) * std::max<int64_t>(count, 1) + 64, "handed-over samples"));
-    unsigned int *n_def = reinterpret_cast<unsigned int *>(ctx->bi_defer.as<int32_t>() + std::max<int64_t>(count, 1));
-    PERCIS_TRY(ensure(ctx, ctx->red, 64, "sample counter"));
-    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(unsigned long long), ctx->stream));
-    PERCIS_CUDA(ctx, cudaMemsetAsync(n_def, 0, sizeof(unsigned int), ctx->stream));
-    BiArgs a = common_args(ctx, seed, tag_path);
-    a.count = count;
-    a.list = nullptr;
-    a.ent = ctx->bi_hent.as<unsigned long long>();
-    a.queue = ctx->bi_hq.as<int2>();
-    a.region = region;
-    a.qcap = qcap;
-    a.next = ctx->red.as<unsigned long long>();
-    a.h0_log = h0;
-    a.hmax_log = hmax;
-    a.slot_epoch = ctx->bi_hep.as<uint32_t>();
-    a.deferred = ctx->bi_defer.as<int32_t>();
-    a.n_deferred = n_def;
-    const int grid = (int)std::min<int64_t>(slots, std::max<int64_t>(count, 1));
-    if (ctx->sigma_mode == 2) k_bibfs<double, true><<<grid, kBiBlock, 0, ctx->stream>>>(a);
-    else k_bibfs<unsigned long long, true><<<grid, kBiBlock, 0, ctx->stream>>>(a);
-    PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS (hashed)");
+    if (direct) {
+        PERCIS_TRY(direct_pass<kBiBlock>(ctx, seed, tag_path, count, nullptr, heavy, defer, n_def));
+    } else {
+        // default: one table per block that holds the (largest) graph's vertices half
+        // full, at most 2^18 entries; else 2^h0 growing 4x up to 2^hmax
+        int h0, cap;
+        if (ctx->opt.bi_table_log == 0) {
+            h0 = kMinHLog;
+            while (h0 < kDefaultHLog && (1ll << h0) < 2 * nslot + 4 * kBiBlock) ++h0;
+            cap = h0;
+        } else {
+            h0 = std::min(std::max(ctx->opt.bi_table_log, kMinHLog), kMaxHLog);
+            cap = ctx->opt.bi_table_max_log > 0 ? std::min(ctx->opt.bi_table_max_log, kMaxHLog) : kMaxHLog;
+        }
+        int hmax = h0;
+        while (hmax + 2 <= cap && (1ll << hmax) < 2 * nslot + 4 * kBiBlock) hmax += 2;
+        int64_t region = 0;
+        for (int l = h0; l <= hmax; l += 2) region += 1ll << l;
+        const int64_t qcap = 1ll << hmax;
+        const int per_sm = blocks_per_sm<true, kBiBlock>(&ctx->bi_hash_per_sm);
+        const int64_t slots = (int64_t)per_sm * ctx->num_sms;
+        const size_t ent_bytes = sizeof(unsigned long long) * 4 * (size_t)region * slots;
+        const size_t q_bytes = sizeof(int2) * 3 * (size_t)qcap * slots;
+        if (ctx->bi_hregion != region || ctx->bi_hslots != slots || ctx->bi_h0 != h0) {
+            PERCIS_TRY(ensure(ctx, ctx->bi_hent, ent_bytes, "hashed entries"));
+            PERCIS_TRY(ensure(ctx, ctx->bi_hq, q_bytes, "hashed queues"));
+            PERCIS_TRY(ensure(ctx, ctx->bi_hep, sizeof(uint32_t) * slots, "slot epochs"));
+            // words of no sample (epoch 0) and epochs from 1
+            PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_hent.p, 0, ent_bytes, ctx->stream));
+            PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_hep.p, 0, sizeof(uint32_t) * slots, ctx->stream));
+            ctx->bi_hregion = region;
+            ctx->bi_hslots = slots;
+            ctx->bi_h0 = h0;
+        }
+        PERCIS_TRY(ensure(ctx, ctx->red, 64, "sample counter"));
+        PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(unsigned long long), ctx->stream));
+        BiArgs a = common_args(ctx, seed, tag_path);
+        a.count = count;
+        a.list = nullptr;
+        a.ent = ctx->bi_hent.as<unsigned long long>();
+        a.queue = ctx->bi_hq.as<int2>();
+        a.region = region;
+        a.qcap = qcap;
+        a.next = ctx->red.as<unsigned long long>();
+        a.h0_log = h0;
+        a.hmax_log = hmax;
+        a.slot_epoch = ctx->bi_hep.as<uint32_t>();
+        a.deferred = defer;
+        a.n_deferred = n_def;
+        a.heavy_edges = heavy;
+        launch<true, kBiBlock>(ctx, (int)std::min<int64_t>(slots, std::max<int64_t>(count, 1)), a);
+        PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS (hashed)");
+    }
     unsigned int nd = 0;
     PERCIS_CUDA(ctx, cudaMemcpyAsync(&nd, n_def, sizeof(nd), cudaMemcpyDeviceToHost, ctx->stream));
     PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->bi_handed = nd;
-    if (nd > 0) PERCIS_TRY(direct_pass(ctx, seed, tag_path, (int64_t)nd, ctx->bi_defer.as<int32_t>()));
+    if (nd > 0) PERCIS_TRY(direct_pass<kHeavyBlock>(ctx, seed, tag_path, (int64_t)nd, defer, 0ull, nullptr, nullptr));
     return PERCIS_OK;
 }
 

@@ -95,8 +95,9 @@ struct percis_ctx {
     percis::DevBuf bi_hent, bi_hq, bi_hep, bi_defer;   // bidirectional form, hashed store: tables, queues,
                                                        // slot epochs, samples handed to the direct store
     int64_t bi_hregion = 0, bi_hslots = 0;
-    int bi_h0 = 0, bi_hash_per_sm = 0;
-    int64_t bi_handed = 0;   // samples the last hashed pass handed to the direct store
+    int bi_h0 = 0, bi_hash_per_sm = 0, bi_heavy_per_sm = 0;
+    bool groups_ready = false;  // grp_lo / grp_hi hold the current states' tie groups
+    int64_t bi_handed = 0;   // samples the last first pass handed to the heavy pass
     int64_t phase_span = 0;  // samples of the running phase (direct-store epochs are indexed by sample)
     percis::DevBuf bi_trace;  // per-sample trace of the last bidirectional phase (instrument = 2)
     int64_t bi_trace_n = 0;
@@ -176,6 +177,7 @@ percis_status build_transpose(percis_ctx *ctx);
 // prep.cu
 percis_status prep_graph(percis_ctx *ctx);  // transpose (directed), validation, VertexDiamUB
 percis_status prep_states(percis_ctx *ctx);  // sort, tables, C_v, lambda, d^
+percis_status prep_groups(percis_ctx *ctx);  // tie groups of the sorted states (backward, on first use)
 percis_status prep_vorder(percis_ctx *ctx);  // lane order of the batched form (on first use)
 
 // sampler.cu

@@ -17,17 +17,30 @@ namespace {
 // a row; the rows are strictly sorted when the counts agree.
 __global__ void k_check_csr(const int64_t *rp, const int32_t *col, int64_t n, int64_t nnz, uint32_t *status,
                             unsigned long long *desc) {
+    // counts are summed per warp: one atomic per warp and loop instead of per
+    // position (most rows of a sorted CSR start below the previous row's end)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    unsigned long long d0 = 0, d1 = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const int64_t r0 = rp[v], r1 = rp[v + 1];
         if (r0 > r1 || r0 < 0 || r1 > nnz) atomicOr(status, 1u);
-        else if (r0 > 0 && r0 < r1 && col[r0] <= col[r0 - 1]) atomicAdd(&desc[1], 1ull);
+        else if (r0 > 0 && r0 < r1 && col[r0] <= col[r0 - 1]) ++d1;
         if (v == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, 1u);
     }
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
         const int32_t c = col[e];
         if (c < 0 || (int64_t)c >= n) atomicOr(status, 1u);
-        if (e > 0 && c <= col[e - 1]) atomicAdd(&desc[0], 1ull);
+        if (e > 0 && c <= col[e - 1]) ++d0;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        d0 += __shfl_xor_sync(0xffffffffu, d0, off);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, off);
+    }
+    if (lane == 0) {
+        if (d0) atomicAdd(&desc[0], d0);
+        if (d1) atomicAdd(&desc[1], d1);
     }
 }
 
@@ -519,8 +532,6 @@ percis_status prep_states(percis_ctx *ctx) {
     PERCIS_TRY(ensure(ctx, ctx->r, sizeof(double) * (n + 2), "r"));
     PERCIS_TRY(ensure(ctx, ctx->Cv, sizeof(double) * n, "Cv"));
     PERCIS_TRY(ensure(ctx, ctx->lam, sizeof(double) * n, "lambda"));
-    PERCIS_TRY(ensure(ctx, ctx->grp_lo, sizeof(int32_t) * n, "groups"));
-    PERCIS_TRY(ensure(ctx, ctx->grp_hi, sizeof(int32_t) * n, "groups"));
     PERCIS_TRY(ensure(ctx, ctx->dscal, 64, "scalars"));
     // sort scratch: keys, keys2, vals2 (reuse the sigma buffer space if large)
     PERCIS_TRY(ensure(ctx, ctx->pc_tmp, (sizeof(uint64_t) * 2 + sizeof(int32_t)) * n + 64, "sort scratch"));
@@ -572,9 +583,7 @@ percis_status prep_states(percis_ctx *ctx) {
     PERCIS_CHECK_LAUNCH(ctx, "cv lambda");
     k_max_lambda<<<g, 256, 0, ctx->stream>>>(ctx->lam.as<double>(), n, ctx->dscal.as<double>());
     PERCIS_CHECK_LAUNCH(ctx, "max lambda");
-    k_groups<<<g, 256, 0, ctx->stream>>>(ctx->xs.as<double>(), n, ctx->grp_lo.as<int32_t>(),
-                                         ctx->grp_hi.as<int32_t>());
-    PERCIS_CHECK_LAUNCH(ctx, "tie groups");
+    ctx->groups_ready = false;  // built by the first backward pass that needs them
     double sc[2];
     uint32_t hst = 0;
     PERCIS_CUDA(ctx, cudaMemcpyAsync(sc, ctx->dscal.p, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream));
@@ -585,6 +594,20 @@ percis_status prep_states(percis_ctx *ctx) {
     ctx->dhat_host = sc[1];
     if (hst & DEV_DEGENERATE)
         return set_err(ctx, PERCIS_E_DEGENERATE, "some C_v <= 0: percolation centrality undefined (all other states equal)");
+    return PERCIS_OK;
+}
+
+// Tie groups of the sorted states (the backward pass's sums over C_u run over
+// strictly smaller and strictly larger states), once per set of states.
+percis_status prep_groups(percis_ctx *ctx) {
+    if (ctx->groups_ready) return PERCIS_OK;
+    const int64_t n = ctx->n;
+    PERCIS_TRY(ensure(ctx, ctx->grp_lo, sizeof(int32_t) * n, "groups"));
+    PERCIS_TRY(ensure(ctx, ctx->grp_hi, sizeof(int32_t) * n, "groups"));
+    k_groups<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->xs.as<double>(), n, ctx->grp_lo.as<int32_t>(),
+                                                             ctx->grp_hi.as<int32_t>());
+    PERCIS_CHECK_LAUNCH(ctx, "tie groups");
+    ctx->groups_ready = true;
     return PERCIS_OK;
 }
 

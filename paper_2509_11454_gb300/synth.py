@@ -281,6 +281,9 @@ def workload(name: str, seed: int = 0):
     if name == "rmat22_beta":
         g = rmat(22, 16, 0.57, 0.19, 0.19, seed)
         return g, states_beta(g.n, 0.5, 2.0, seed), 0.01, 0.1
+    if name == "rmat20_beta":
+        g = rmat(20, 16, 0.57, 0.19, 0.19, seed)
+        return g, states_beta(g.n, 0.5, 2.0, seed), 0.01, 0.1
     if name == "ba200k_uniform":
         g = barabasi_albert(200_000, 4, seed)
         return g, states_uniform(g.n, seed), 0.01, 0.1
