@@ -386,6 +386,7 @@ def main():
     ap.add_argument("--bi-table-log", type=int, default=0, help="bidirectional store (0 = library default)")
     ap.add_argument("--bi-table-max-log", type=int, default=0)
     ap.add_argument("--bi-heavy-edges", type=int, default=0, help="heavy-level threshold (0 = default, <0 = off)")
+    ap.add_argument("--bi-scratch-gib", type=int, default=0, help="direct-store budget, GiB (0 = default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -421,7 +422,7 @@ def main():
     if args.push_alpha > 0:
         eng.set_options(push_alpha=args.push_alpha)
     eng.set_options(bi_table_log=args.bi_table_log, bi_table_max_log=args.bi_table_max_log,
-                    bi_heavy_edges=args.bi_heavy_edges)
+                    bi_heavy_edges=args.bi_heavy_edges, bi_scratch_gib=args.bi_scratch_gib)
     rp_d = torch.as_tensor(g.row_ptr, dtype=torch.int64, device="cuda")
     col_d = torch.as_tensor(g.col, dtype=torch.int32, device="cuda")
     x_d = torch.as_tensor(x, dtype=torch.float64, device="cuda")

@@ -111,12 +111,13 @@ typedef struct {
                                  (largest) graph at most half full, at most 2^20 entries; k =
                                  at most 2^k.  Samples that would fill more than 3/4 of it, or
                                  pass 4,095 levels on a side, are handed to the heavy pass. */
-    int32_t bi_scratch_gib;   /* direct store: device memory its blocks may use, GiB (0 = 16);
-                                 it holds 56 bytes per vertex and block, so it caps the blocks */
+    int32_t bi_scratch_gib;   /* direct store: device memory its blocks may use, GiB (0 = 48);
+                                 it holds 56 bytes per vertex and block, so it caps the blocks
+                                 (the heavy pass wants one block per SM: 152 x 56 x n bytes) */
     int64_t bi_heavy_edges;   /* a sample whose next level would scan more than this many edges
                                  stops untouched and runs again after the first pass, alone in
                                  a block of 1,024 threads in the direct store (the heavy pass);
-                                 0 = default (16,384), < 0 = never */
+                                 0 = default (4,096), < 0 = never */
     int64_t reserved;         /* must be 0 */
 } percis_options;
 

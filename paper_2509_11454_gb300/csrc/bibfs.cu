@@ -64,7 +64,7 @@ constexpr int kFlat = 512;  // frontier vertices per chunk whose edges are sprea
 #endif
 constexpr int kEdgeBatch = PERCIS_EDGE_BATCH;  // edges a thread has in flight (their loads issued together)
 #ifndef PERCIS_BI_MINB
-#define PERCIS_BI_MINB 6
+#define PERCIS_BI_MINB 4
 #endif
 constexpr uint32_t kHashLevels = 4095;            // levels a hashed word holds (12 bits)
 constexpr uint32_t kHashEpochs = (1u << 20) - 1;  // epochs a hashed word holds (20 bits)
@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
     __shared__ C s_fs[kFlat];        // its path count
     __shared__ int64_t s_pre[kFlat + 1];  // prefix sums of the chunk's degrees
     __shared__ unsigned long long s_work[6];
+    __shared__ long long s_wsum[nw];    // per-warp degree sums of a chunk
     if (threadIdx.x < 6) s_work[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) s_tlast = -1;
     unsigned long long n_add = 0ull;
@@ -530,18 +531,19 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                     }
                 };
                 // the level's edges spread evenly over the block, kFlat frontier vertices
-                // at a time (a hub's adjacency is not left to one warp): warp 0 loads the
-                // chunk and writes its degree prefix sums to shared memory, each edge then
-                // finds its vertex by bisection
+                // at a time (a hub's adjacency is not left to one warp): the block loads
+                // the chunk, a few vertices per thread with their loads in flight
+                // together, and writes its degree prefix sums to shared memory; each
+                // edge then finds its vertex by bisection
                 for (long long c0 = lo; c0 < hi; c0 += kFlat) {
                     const int fc = (int)(hi - c0 < kFlat ? hi - c0 : kFlat);
-                    if (warp == 0) {
-                        constexpr int per = kFlat / 32;
+                    {
+                        constexpr int per = kFlat >= BT ? kFlat / BT : 1;
                         int64_t loc[per];
                         int64_t tot = 0;
 #pragma unroll
                         for (int r = 0; r < per; ++r) {
-                            const int k = lane * per + r;
+                            const int k = (int)threadIdx.x * per + r;
                             int64_t dg = 0;
                             if (k < fc) {
                                 const int2 qe = qx[c0 + k];
@@ -559,13 +561,16 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                             const int64_t t2 = __shfl_up_sync(0xffffffffu, incl, o);
                             if (lane >= o) incl += t2;
                         }
-                        const int64_t first = incl - tot;
+                        if (lane == 31) s_wsum[warp] = incl;
+                        __syncthreads();
+                        int64_t first = incl - tot;
+                        for (int q = 0; q < warp; ++q) first += s_wsum[q];
 #pragma unroll
                         for (int r = 0; r < per; ++r) {
-                            const int k = lane * per + r;
+                            const int k = (int)threadIdx.x * per + r;
                             if (k < fc) s_pre[k] = first + loc[r];
                         }
-                        if (lane == 31) s_pre[fc] = incl;
+                        if (threadIdx.x == BT - 1) s_pre[fc] = first + tot;  // (vertices past fc add 0)
                     }
                     __syncthreads();
                     const int64_t E = s_pre[fc];
@@ -1032,7 +1037,8 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
 }
 
 constexpr int kHeavyBlock = 1024;                        // threads per sample in the heavy pass
-constexpr unsigned long long kDefaultHeavyEdges = 16384;  // a level scanning more edges is heavy
+constexpr unsigned long long kDefaultHeavyEdges = 4096;   // a level scanning more edges is heavy
+constexpr int64_t kDefaultScratchGiB = 48;  // direct store: one heavy-pass block per SM up to n = 6M
 
 template <bool HASH, int BT>
 int blocks_per_sm(int *cache) {
@@ -1092,7 +1098,7 @@ percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     if (ctx->multi) multi_graph_view(ctx, &gid, &vbase, &nslot);
     const size_t per_slot = (size_t)nslot * (sizeof(unsigned long long) * 4 + sizeof(int2) * 3);
     const int per_sm = blocks_per_sm<false, BT>(BT == kBiBlock ? &ctx->bi_per_sm : &ctx->bi_heavy_per_sm);
-    const int64_t budget = (int64_t)(ctx->opt.bi_scratch_gib > 0 ? ctx->opt.bi_scratch_gib : 16) << 30;
+    const int64_t budget = (int64_t)(ctx->opt.bi_scratch_gib > 0 ? ctx->opt.bi_scratch_gib : kDefaultScratchGiB) << 30;
     int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, budget / (int64_t)per_slot));
     slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
     if (ctx->bi_slots < slots || ctx->bi_n != nslot) {
@@ -1169,7 +1175,7 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     bool direct = ctx->opt.bi_table_log < 0;
     if (ctx->opt.bi_table_log == 0) {
         const int64_t per_slot = nslot * (int64_t)(sizeof(unsigned long long) * 4 + sizeof(int2) * 3);
-        const int64_t budget = (int64_t)(ctx->opt.bi_scratch_gib > 0 ? ctx->opt.bi_scratch_gib : 16) << 30;
+        const int64_t budget = (int64_t)(ctx->opt.bi_scratch_gib > 0 ? ctx->opt.bi_scratch_gib : kDefaultScratchGiB) << 30;
         const int64_t full = (int64_t)blocks_per_sm<false, kBiBlock>(&ctx->bi_per_sm) * ctx->num_sms;
         direct = full * per_slot <= budget;
     }

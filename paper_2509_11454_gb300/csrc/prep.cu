@@ -170,15 +170,38 @@ struct alignas(16) RunMap {
     unsigned long long par;
 };
 
+constexpr int kKeys = 2048;    // binade keys max(exponent field, 1)
+constexpr int kMaxSegs = 256;  // binades the resolution of a predicted pass holds
+
+// A binade of the running sum in the predicted pass: its first term (the one
+// whose sum enters it, added in plain FP64) and, once resolved, the sum there.
+struct SegSlot {
+    unsigned int gen;         // the pass that claimed the slot
+    int prev;                 // key of the binade before (-1: the first term)
+    long long b;              // the first term
+    double a;                 // its value
+    RunMap mprev;             // map of the terms of the binade before, after its first
+    unsigned long long s0;    // resolved: sum after term b in units of the binade's ulp
+    double scross;            // resolved: sum after term b
+};
+
 // Control block of the cooperative table launch.
 struct TableCtl {
     GridBarrier bar;
     uint32_t status;
-    uint32_t pad;
+    uint32_t conflict;   // the predicted pass found its binades inconsistent
     long long kstar[2];  // first term of the window that leaves the binade (one slot per window parity)
     long long pos;       // positions pos, pos - 1, ..., 1 remain
     double s;            // running sum before them
+    long long fail_b;    // predicted pass: terms before this one are resolved
+    int klast;           // predicted pass: key of the last term
+    int pad2;
+    RunMap mlast;        // predicted pass: map of the last binade's terms after its first
     RunMap agg[kMaxTableBlocks];
+    RunMap sagg[kMaxTableBlocks];  // predicted pass: segmented run of each block (flag in par bit 2)
+    double bsum[kMaxTableBlocks];  // predicted pass: FP64 sum of each block's terms
+    int blast[kMaxTableBlocks];    // predicted pass: key after each block's last term
+    SegSlot seg[kKeys];
 };
 
 __device__ __forceinline__ ParityMap run_load(const RunMap *p) {
@@ -189,11 +212,310 @@ __device__ __forceinline__ ParityMap run_load(const RunMap *p) {
     return m;
 }
 
+__device__ __forceinline__ int sum_key(double v) {
+    const int ef = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff);
+    return ef > 1 ? ef : 1;
+}
+
+// segmented runs: f = the run holds the first term of a binade (the map then
+// covers the terms after the last such term)
+struct SegRun {
+    ParityMap m;
+    unsigned f;
+};
+
+__device__ __forceinline__ SegRun sr_identity() { return SegRun{pm_identity(), 0u}; }
+
+__device__ __forceinline__ SegRun sr_then(const SegRun &x, const SegRun &y) {
+    SegRun r;
+    r.f = x.f | y.f;
+    r.m = y.f ? y.m : pm_then(x.m, y.m);
+    return r;
+}
+
+__device__ __forceinline__ SegRun sr_shfl_up(const SegRun &v, int off) {
+    SegRun o;
+    o.m = pm_shfl_up(v.m, off);
+    o.f = __shfl_up_sync(0xffffffffu, v.f, off);
+    return o;
+}
+
+__device__ __forceinline__ RunMap sr_store(const SegRun &v) {
+    RunMap r;
+    r.d0 = v.m.d0;
+    r.d1 = v.m.d1;
+    r.par = (unsigned long long)(v.m.par | (v.f << 2));
+    return r;
+}
+
+__device__ __forceinline__ SegRun sr_load(const RunMap *p) {
+    SegRun v;
+    v.m.d0 = __ldcg(&p->d0);
+    v.m.d1 = __ldcg(&p->d1);
+    const unsigned par = (unsigned)__ldcg(&p->par);
+    v.m.par = par & 3u;
+    v.f = (par >> 2) & 1u;
+    return v;
+}
+
+// Predicted pass over the same running sums, in a few grid barriers: a plain
+// FP64 prefix sum of the terms (any order) predicts the binade every term's
+// sum falls in; every binade's run of terms after its first is then one
+// segment of a segmented scan of the per-term maps, all binades at once; one
+// thread walks the binades in order, adds each first term in plain FP64 from
+// the sum before it and checks that it lands in the predicted binade and that
+// the binade's run stays below its top; every term before the first failed
+// check gets its exact sum.  The prediction only chooses the segments: each
+// binade's result is checked against the sequential definition, and the terms
+// from the first failure on (a sum within rounding of a binade's edge, more
+// than kMaxSegs binades) are left to the windowed scan, which starts from
+// ctl->pos and ctl->s.
+__device__ bool running_sum_predicted(const double *src, int64_t soff, double *dst, int64_t m, TableCtl *ctl,
+                                      uint64_t budget_ns, unsigned gen) {
+    constexpr int nw = kScanThreads / 32;
+    __shared__ double s_wd[nw];
+    __shared__ SegRun s_wr[nw];
+    __shared__ int s_lastkey[kScanThreads];
+    __shared__ double s_bc;
+    __shared__ SegRun s_bsr;
+    __shared__ int s_key[kMaxSegs];
+    __shared__ int s_pc[nw];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long nth = (long long)gridDim.x * kScanThreads;
+    const long long T = (m + nth - 1) / nth;
+    const long long g = (long long)blockIdx.x * kScanThreads + tid;
+    const long long k0 = min((long long)m, g * T), k1 = min((long long)m, k0 + T);
+    // term k of the scan (k = 0 is position m)
+    auto term = [&](long long k) { return __ldcg(&src[m - k + soff]); };
+
+    // 1. the prediction: exclusive FP64 prefix of the threads' sums
+    if (blockIdx.x == 0 && tid == 0) ctl->conflict = 0u;  // (set only after the barrier below)
+    double ts = 0.0;
+    for (long long k = k0; k < k1; ++k) ts = __dadd_rn(ts, term(k));
+    double inc = warp_inclusive_scan(ts);
+    double exc = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) exc = 0.0;
+    if (lane == 31) s_wd[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const double v = lane < nw ? s_wd[lane] : 0.0;
+        const double vi = warp_inclusive_scan(v);
+        double ve = __shfl_up_sync(0xffffffffu, vi, 1);
+        if (lane == 0) ve = 0.0;
+        if (lane < nw) s_wd[lane] = ve;
+        if (lane == 31) ctl->bsum[blockIdx.x] = vi;
+    }
+    if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return false;
+    if (warp == 0) {
+        double c = 0.0;
+        for (int b0 = 0; b0 < (int)blockIdx.x; b0 += 32)
+            c = __dadd_rn(c, __shfl_sync(0xffffffffu,
+                                         warp_inclusive_scan(b0 + lane < (int)blockIdx.x ? __ldcg(&ctl->bsum[b0 + lane])
+                                                                                         : 0.0),
+                                         31));
+        if (lane == 0) s_bc = c;
+    }
+    __syncthreads();
+    const double pin = __dadd_rn(__dadd_rn(s_bc, s_wd[warp]), exc);
+
+    // 2. binades: a term whose predicted sum has another key than the one before
+    // starts a binade (term 0 always); the segmented run of every thread
+    const int key_in = k0 == 0 ? -1 : sum_key(pin);
+    int before = key_in;
+    double P = pin;
+    SegRun agg = sr_identity();
+    ParityMap lfirst = pm_identity();  // the thread's terms before its first binade start
+    int efirst = -1;
+    for (long long k = k0; k < k1; ++k) {
+        const double a = term(k);
+        P = __dadd_rn(P, a);
+        const int E = sum_key(P);
+        if (E != before) {
+            SegSlot *sg = &ctl->seg[E];
+            if (atomicExch(&sg->gen, gen) == gen) atomicOr(&ctl->conflict, 1u);  // a binade entered twice
+            sg->b = k;
+            sg->a = a;
+            sg->prev = before;
+            if (efirst >= 0) sg->mprev = RunMap{agg.m.d0, agg.m.d1, (unsigned long long)agg.m.par};
+            else {
+                efirst = E;
+                lfirst = agg.m;
+            }
+            agg.m = pm_identity();
+            agg.f = 1u;
+            before = E;
+        } else {
+            unsigned long long q;
+            int kind;
+            agg.m = pm_then(agg.m, term_map(a, E, q, kind));
+        }
+    }
+    s_lastkey[tid] = before;
+    // segmented scan of the runs: the warp, the block, then the blocks before
+    SegRun sinc = agg;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const SegRun o = sr_shfl_up(sinc, off);
+        if (lane >= off) sinc = sr_then(o, sinc);
+    }
+    SegRun sexc = sr_shfl_up(sinc, 1);
+    if (lane == 0) sexc = sr_identity();
+    if (lane == 31) s_wr[warp] = sinc;
+    __syncthreads();
+    // the key the thread's first term starts from must be the one the thread
+    // before ended on (both predicted, in different summation orders)
+    if (tid > 0 && k0 < k1 && key_in != s_lastkey[tid - 1]) atomicOr(&ctl->conflict, 1u);
+    if (warp == 0) {
+        SegRun v = lane < nw ? s_wr[lane] : sr_identity();
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const SegRun o = sr_shfl_up(v, off);
+            if (lane >= off) v = sr_then(o, v);
+        }
+        SegRun ve = sr_shfl_up(v, 1);
+        if (lane == 0) ve = sr_identity();
+        if (lane < nw) s_wr[lane] = ve;
+        if (lane == 31) ctl->sagg[blockIdx.x] = sr_store(v);
+        if (lane == 0) ctl->blast[blockIdx.x] = s_lastkey[kScanThreads - 1];
+    }
+    if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return false;
+    if (warp == 0) {
+        SegRun bp = sr_identity();
+        for (int b0 = 0; b0 < (int)blockIdx.x; b0 += 32) {
+            SegRun v = b0 + lane < (int)blockIdx.x ? sr_load(&ctl->sagg[b0 + lane]) : sr_identity();
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const SegRun o = sr_shfl_up(v, off);
+                if (lane >= off) v = sr_then(o, v);
+            }
+            SegRun last;
+            last.m.d0 = __shfl_sync(0xffffffffu, v.m.d0, 31);
+            last.m.d1 = __shfl_sync(0xffffffffu, v.m.d1, 31);
+            last.m.par = __shfl_sync(0xffffffffu, v.m.par, 31);
+            last.f = __shfl_sync(0xffffffffu, v.f, 31);
+            bp = sr_then(bp, last);
+        }
+        if (lane == 0) {
+            s_bsr = bp;
+            if (blockIdx.x > 0 && k0 < k1 && key_in != __ldcg(&ctl->blast[blockIdx.x - 1]))
+                atomicOr(&ctl->conflict, 1u);
+        }
+    }
+    __syncthreads();
+    const SegRun cin = sr_then(s_bsr, sr_then(s_wr[warp], sexc));  // the run since the binade start before k0
+    if (efirst >= 0) {
+        const ParityMap mp = pm_then(cin.m, lfirst);
+        ctl->seg[efirst].mprev = RunMap{mp.d0, mp.d1, (unsigned long long)mp.par};
+    }
+    if (k1 == m && k0 < k1) {
+        const ParityMap ml = efirst >= 0 ? agg.m : pm_then(cin.m, agg.m);
+        ctl->mlast = RunMap{ml.d0, ml.d1, (unsigned long long)ml.par};
+        ctl->klast = before;
+    }
+    if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return false;
+
+    // 3. resolution, in block 0: the binades present, in key order, then one
+    // thread walks them from s = +0
+    if (blockIdx.x == 0) {
+        const int E0 = 2 * tid, E1 = E0 + 1;
+        const int p0 = __ldcg(&ctl->seg[E0].gen) == gen, p1 = __ldcg(&ctl->seg[E1].gen) == gen;
+        const int c = p0 + p1;
+        int ci = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, ci, off);
+            if (lane >= off) ci += o;
+        }
+        if (lane == 31) s_pc[warp] = ci;
+        __syncthreads();
+        int base = 0, total = 0;
+        for (int q = 0; q < nw; ++q) {
+            if (q < warp) base += s_pc[q];
+            total += s_pc[q];
+        }
+        const int at = base + ci - c;
+        if (total <= kMaxSegs) {
+            if (p0) s_key[at] = E0;
+            if (p1) s_key[at + p0] = E1;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long fail = m;
+            double S = 0.0;
+            if (__ldcg(&ctl->conflict) || total > kMaxSegs || total < 1 || __ldcg(&ctl->klast) != s_key[total - 1])
+                fail = 0;
+            for (int i = 0; fail == m && i < total; ++i) {
+                const int E = s_key[i];
+                SegSlot *sg = &ctl->seg[E];
+                const long long b = __ldcg(&sg->b);
+                if ((i == 0) != (b == 0) || __ldcg(&sg->prev) != (i == 0 ? -1 : s_key[i - 1])) {
+                    fail = i == 0 ? 0 : b;
+                    break;
+                }
+                const double sc = __dadd_rn(S, __ldcg(&sg->a));
+                if (sum_key(sc) != E) {  // the first term did not land in the predicted binade
+                    fail = b;
+                    break;
+                }
+                const unsigned long long sb = (unsigned long long)__double_as_longlong(sc);
+                const int es = (int)((sb >> 52) & 0x7ff);
+                const unsigned long long S0 = (sb & ((1ull << 52) - 1)) | (es ? (1ull << 52) : 0ull);
+                const RunMap *mr = i + 1 < total ? &ctl->seg[s_key[i + 1]].mprev : &ctl->mlast;
+                const unsigned long long d = (S0 & 1ull) ? __ldcg(&mr->d1) : __ldcg(&mr->d0);
+                if (S0 + d >= kTwo53u) {  // the run leaves the binade before the next predicted start
+                    fail = b;
+                    break;
+                }
+                sg->s0 = S0;
+                sg->scross = sc;
+                S = __longlong_as_double((long long)(((unsigned long long)(E - 1) << 52) + S0 + d));
+            }
+            ctl->fail_b = fail;
+            ctl->pos = m - fail;
+            ctl->s = S;  // the sum before term `fail` (every binade before it resolved)
+        }
+    }
+    if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return false;
+
+    // 4. every term before the first failure: its binade's sum after the first
+    // term plus the integer its run added, under that sum's parity
+    const long long fail = __ldcg(&ctl->fail_b);
+    if (k0 < fail) {
+        const long long kend = min(k1, fail);
+        int cur = key_in;
+        unsigned long long S0 = 0ull, top = 0ull;
+        if (cur >= 1) {
+            S0 = __ldcg(&ctl->seg[cur].s0);
+            top = (unsigned long long)(cur - 1) << 52;
+        }
+        ParityMap pre = cin.m;
+        P = pin;
+        for (long long k = k0; k < kend; ++k) {
+            const double a = term(k);
+            P = __dadd_rn(P, a);
+            const int E = sum_key(P);
+            if (E != cur) {
+                cur = E;
+                S0 = __ldcg(&ctl->seg[E].s0);
+                top = (unsigned long long)(E - 1) << 52;
+                pre = pm_identity();
+                dst[m - k] = __ldcg(&ctl->seg[E].scross);
+            } else {
+                unsigned long long q;
+                int kind;
+                pre = pm_then(pre, term_map(a, E, q, kind));
+                dst[m - k] = __longlong_as_double((long long)(top + S0 + ((S0 & 1ull) ? pre.d1 : pre.d0)));
+            }
+        }
+    }
+    return grid_sync(&ctl->bar, &ctl->status, budget_ns);
+}
+
 // Running sums s_i = fl(s_{i+1} + a_i) for i = m down to 1 (s_{m+1} = +0), with
 // a_i = src[i + soff] >= 0, written to dst[i]; *sum = s_1 (+0 when m = 0).  Every
 // block of the cooperative launch calls it; false when a grid barrier timed out.
 __device__ bool grid_running_sum(const double *src, int64_t soff, double *dst, int64_t m, TableCtl *ctl,
-                                 uint64_t budget_ns, double *sum) {
+                                 uint64_t budget_ns, unsigned gen, double *sum) {
     __shared__ ParityMap s_wmap[kScanThreads / 32];
     __shared__ ParityMap s_bpre;
     __shared__ unsigned s_first;
@@ -207,6 +529,8 @@ __device__ bool grid_running_sum(const double *src, int64_t soff, double *dst, i
         ctl->kstar[0] = ctl->kstar[1] = kNoTerm;
     }
     if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return false;
+    // the predicted pass resolves what it can; windows of the terms left
+    if (m > 0 && !running_sum_predicted(src, soff, dst, m, ctl, budget_ns, gen)) return false;
     for (int pass = 0;; ++pass) {
         const long long pos = __ldcg(&ctl->pos);
         const double s = __ldcg(&ctl->s);
@@ -358,7 +682,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tables(const double *xs, int64
     if (gt == 0) w[0] = r[0] = ci[0] = 0.0;
     // w_i over x_i = xs[i - 1]
     double wsum;
-    if (!grid_running_sum(xs, -1, w, nz, ctl, budget_ns, &wsum)) return;
+    if (!grid_running_sum(xs, -1, w, nz, ctl, budget_ns, 1u, &wsum)) return;
     for (int64_t i = 1 + gt; i <= nz; i += gs) {
         const double t = __dmul_rn((double)(n - i + 1), xs[i - 1]);
         const double cv = __dsub_rn(t, __ldcg(&w[i]));
@@ -366,7 +690,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tables(const double *xs, int64
     }
     if (!grid_sync(&ctl->bar, &ctl->status, budget_ns)) return;
     double c;
-    if (!grid_running_sum(ci, 0, r, nz, ctl, budget_ns, &c)) return;
+    if (!grid_running_sum(ci, 0, r, nz, ctl, budget_ns, 2u, &c)) return;
     if (gt == 0) dscal[0] = c;  // c = r_1
 }
 

@@ -5,9 +5,10 @@
 // launches: per-tile digit counts (tiles of 4096 pairs), one exclusive scan of
 // the counts laid out digit-major (so the scan gives every (digit, tile) its
 // first output slot), and a scatter in which every tile ranks its pairs among
-// equal digits in index order (warp ballots, then per-warp counts in shared
-// memory).  Passes run from the lowest digit up, so the result is ordered by
-// the key's sorted bits and, among equal keys, by input position.
+// equal digits in index order (per-warp match groups and counters), regroups
+// them by digit in shared memory and writes each digit's run contiguously.
+// Passes run from the lowest digit up, so the result is ordered by the key's
+// sorted bits and, among equal keys, by input position.
 //
 // The in-adjacency of a directed CSR is the stable sort of its edges by
 // target: the edges arrive ordered by source, so every in-list comes out
@@ -53,57 +54,108 @@ __global__ void __launch_bounds__(kRadixBlock) k_radix_count(const K *keys, int6
     }
 }
 
-// pairs of each tile to offs[d * ntiles + tile] + (rank among the tile's earlier pairs of digit d)
+// Pairs of each tile to offs[d * ntiles + tile] + (rank among the tile's earlier
+// pairs of digit d).  Warp w ranks the tile's pairs [512 w, 512 w + 512) among
+// equal digits with warp-private counters (no block barrier), the per-digit
+// counts of the warps then give every pair its place in the tile ordered by
+// digit, stably; the pairs are regrouped so in shared memory and written out
+// in that order, so the writes of one digit's run are contiguous.
 template <class K>
-__global__ void __launch_bounds__(kRadixBlock) k_radix_scatter(const K *kin, const int32_t *vin, K *kout,
-                                                               int32_t *vout, int64_t n, int shift, int64_t ntiles,
-                                                               const long long *offs) {
-    __shared__ int s_cnt[kRadixWarps][kRadixBins];
-    __shared__ int s_tot[kRadixBins];
-    __shared__ long long s_base[kRadixBins];
+constexpr size_t scatter_smem() {
+    return (sizeof(K) + sizeof(int32_t)) * kRadixTile + sizeof(int) * kRadixWarps * kRadixBins +
+           sizeof(long long) * kRadixBins + sizeof(int) * kRadixBins + sizeof(int) * kRadixWarps;
+}
+
+template <class K>
+__global__ void __launch_bounds__(kRadixBlock, 3) k_radix_scatter(const K *kin, const int32_t *vin, K *kout,
+                                                                  int32_t *vout, int64_t n, int shift,
+                                                                  int64_t ntiles, const long long *offs) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    K *sk = reinterpret_cast<K *>(s_raw);
+    int32_t *sv = reinterpret_cast<int32_t *>(sk + kRadixTile);
+    int *s_wc = reinterpret_cast<int *>(sv + kRadixTile);  // [warp][digit]
+    long long *s_base = reinterpret_cast<long long *>(s_wc + kRadixWarps * kRadixBins);
+    int *s_lpre = reinterpret_cast<int *>(s_base + kRadixBins);
+    int *s_wtot = s_lpre + kRadixBins;
+    constexpr int kPerWarp = kRadixTile / kRadixWarps;
+    constexpr int kRounds = kPerWarp / 32;
+    static_assert(kRadixBins == kRadixBlock, "one digit per thread in the count scan");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    int *wc = s_wc + warp * kRadixBins;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        for (int d = threadIdx.x; d < kRadixBins; d += kRadixBlock) s_base[d] = offs[(int64_t)d * ntiles + tile];
         const int64_t base = tile * kRadixTile;
-        for (int r = 0; r < kRadixRounds; ++r) {
-            for (int j = threadIdx.x; j < kRadixWarps * kRadixBins; j += kRadixBlock) (&s_cnt[0][0])[j] = 0;
-            __syncthreads();
-            // pairs r*256 .. r*256+255 of the tile: index order = (warp, lane) order
-            const int64_t i = base + (int64_t)r * kRadixBlock + threadIdx.x;
-            const bool valid = i < n;
-            K key = K(0);
-            int32_t val = 0;
-            int d = kRadixBins;  // invalid lanes form a group of their own
-            if (valid) {
-                key = kin[i];
-                val = vin[i];
-                d = digit_of(key, shift);
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const int rank = __popc(peers & lt);
-            if (valid && rank == 0) s_cnt[warp][d] = __popc(peers);
-            __syncthreads();
-            for (int dd = threadIdx.x; dd < kRadixBins; dd += kRadixBlock) {
-                int acc = 0;
+        const int64_t wbase = base + (int64_t)warp * kPerWarp;
+        for (int d = lane; d < kRadixBins; d += 32) wc[d] = 0;
+        K key[kRounds];
+        int32_t val[kRounds];
 #pragma unroll
-                for (int w = 0; w < kRadixWarps; ++w) {
-                    const int c = s_cnt[w][dd];
-                    s_cnt[w][dd] = acc;
-                    acc += c;
-                }
-                s_tot[dd] = acc;
-            }
-            __syncthreads();
-            if (valid) {
-                const long long pos = s_base[d] + s_cnt[warp][d] + rank;
-                kout[pos] = key;
-                vout[pos] = val;
-            }
-            __syncthreads();
-            for (int dd = threadIdx.x; dd < kRadixBins; dd += kRadixBlock) s_base[dd] += s_tot[dd];
+        for (int r = 0; r < kRounds; ++r) {
+            const int64_t i = wbase + r * 32 + lane;
+            key[r] = i < n ? kin[i] : K(0);
+            val[r] = i < n ? vin[i] : 0;
+        }
+        __syncwarp();
+        int rk[kRounds];
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const bool valid = wbase + r * 32 + lane < n;
+            const int d = valid ? digit_of(key[r], shift) : kRadixBins;  // invalid lanes: a group of their own
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int lead = __ffs(peers) - 1;
+            int run = (valid && lane == lead) ? wc[d] : 0;
+            run = __shfl_sync(0xffffffffu, run, lead);
+            rk[r] = run + __popc(peers & lt);
+            __syncwarp();
+            if (valid && lane == lead) wc[d] = run + __popc(peers);
+            __syncwarp();
         }
         __syncthreads();
+        {
+            // digit d = this thread: its count in the tile, its first place in the tile
+            // (exclusive scan over the digits), and each warp's first place among it
+            const int d = threadIdx.x;
+            int wpre[kRadixWarps];
+            int c = 0;
+#pragma unroll
+            for (int w = 0; w < kRadixWarps; ++w) {
+                wpre[w] = c;
+                c += s_wc[w * kRadixBins + d];
+            }
+            int inc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t2 = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t2;
+            }
+            if (lane == 31) s_wtot[warp] = inc;
+            s_base[d] = offs[(int64_t)d * ntiles + tile];
+            __syncthreads();
+            int lp = inc - c;
+            for (int q = 0; q < warp; ++q) lp += s_wtot[q];
+            s_lpre[d] = lp;
+#pragma unroll
+            for (int w = 0; w < kRadixWarps; ++w) s_wc[w * kRadixBins + d] = lp + wpre[w];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            if (wbase + r * 32 + lane < n) {
+                const int pos = wc[digit_of(key[r], shift)] + rk[r];
+                sk[pos] = key[r];
+                sv[pos] = val[r];
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)(n - base < (int64_t)kRadixTile ? n - base : (int64_t)kRadixTile);
+        for (int p = threadIdx.x; p < cnt; p += kRadixBlock) {
+            const K k = sk[p];
+            const int d = digit_of(k, shift);
+            const long long g = s_base[d] + (p - s_lpre[d]);
+            kout[g] = k;
+            vout[g] = sv[p];
+        }
+        __syncthreads();  // the tile's shared arrays are reused by the next
     }
 }
 
@@ -194,13 +246,17 @@ percis_status radix_sort_impl(percis_ctx *ctx, K *keys, int32_t *vals, K *tk, in
     PERCIS_TRY(ensure(ctx, ctx->radix_counts, sizeof(long long) * (size_t)(nc + 1), "radix counts"));
     long long *counts = ctx->radix_counts.as<long long>();
     const int grid = radix_grid(ctx, ntiles);
+    if (scatter_smem<K>() > 48 * 1024)
+        PERCIS_CUDA(ctx, cudaFuncSetAttribute(k_radix_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)scatter_smem<K>()));
     K *ka = keys, *kb = tk;
     int32_t *va = vals, *vb = tv;
     for (int shift = lo_bit; shift < lo_bit + bits; shift += 8) {
         k_radix_count<K><<<grid, kRadixBlock, 0, ctx->stream>>>(ka, n, shift, ntiles, counts);
         PERCIS_CHECK_LAUNCH(ctx, "radix count");
         PERCIS_TRY(scan_exclusive_i64(ctx, (const int64_t *)counts, (int64_t *)counts, nc));
-        k_radix_scatter<K><<<grid, kRadixBlock, 0, ctx->stream>>>(ka, va, kb, vb, n, shift, ntiles, counts);
+        k_radix_scatter<K><<<grid, kRadixBlock, scatter_smem<K>(), ctx->stream>>>(ka, va, kb, vb, n, shift, ntiles,
+                                                                                   counts);
         PERCIS_CHECK_LAUNCH(ctx, "radix scatter");
         std::swap(ka, kb);
         std::swap(va, vb);

@@ -118,3 +118,135 @@ def test_halfway_cases_are_exercised():
             ties += _term(a, e)[1] == 2
         s += a
     assert ties > 1000
+
+
+# ---------------------------------------------------------------- predicted pass
+
+def _key(v: float) -> int:
+    return max((_bits(v) >> 52) & 0x7FF, 1)
+
+
+def _map(a: float, e: int):
+    """(d0, d1, par) of one term against binade key e: the integer added for
+    parity 0 / 1 of the sum before it, bit p of par the parity after it."""
+    q, kind = _term(a, e)
+    if kind == 2:
+        return q + (q & 1), q + 1 - (q & 1), 0
+    r = q + (kind & 1)
+    b = r & 1
+    return r, r, b | ((b ^ 1) << 1)
+
+
+def _then(f, g):
+    f0, f1 = f[2] & 1, (f[2] >> 1) & 1
+    return (f[0] + (g[1] if f0 else g[0]), f[1] + (g[1] if f1 else g[0]),
+            ((g[2] >> f0) & 1) | (((g[2] >> f1) & 1) << 1))
+
+
+IDENT = (0, 0, 2)
+
+
+def predicted_running_sum(terms, nthreads, max_segs=256, shift_pred=None):
+    """The table kernel's predicted pass: per-thread FP64 sums give every term a
+    predicted prefix (another summation order), a change of its binade key
+    starts a segment, each segment's run of per-term maps is composed, and the
+    binades are walked in order from s = +0 -- first term by a plain add, the
+    run below the binade's top -- until a check fails; the terms from there
+    on go to the windowed scan.  shift_pred(k, key) may alter a predicted key
+    (to exercise the checks)."""
+    m = len(terms)
+    if m == 0:
+        return []
+    T = -(-m // nthreads)
+    ranges = [(min(m, t * T), min(m, t * T + T)) for t in range(nthreads)]
+    # prediction: exclusive prefix of the thread sums, then running adds
+    sums = []
+    for k0, k1 in ranges:
+        s = 0.0
+        for k in range(k0, k1):
+            s += terms[k]
+        sums.append(s)
+    pins, acc = [], 0.0
+    for s in sums:
+        pins.append(acc)
+        acc += s
+    keys, conflict = [None] * m, False
+    last_keys = []
+    for (k0, k1), pin in zip(ranges, pins):
+        key_in = -1 if k0 == 0 else _key(pin)
+        if k0 < k1 and last_keys and key_in != last_keys[-1]:
+            conflict = True
+        P, before = pin, key_in
+        for k in range(k0, k1):
+            P += terms[k]
+            e = _key(P)
+            if shift_pred is not None:
+                e = shift_pred(k, e)
+            keys[k] = e
+            before = e
+        last_keys.append(before)
+    # segments: starts where the key changes (term 0 always)
+    starts = [k for k in range(m) if k == 0 or keys[k] != keys[k - 1]]
+    seen = set()
+    for k in starts:
+        if keys[k] in seen:
+            conflict = True
+        seen.add(keys[k])
+    out = [None] * m
+    fail = 0 if conflict or len(starts) > max_segs else m
+    S = 0.0
+    if fail == m:
+        for i, b in enumerate(starts):
+            e = keys[b]
+            end_k = starts[i + 1] if i + 1 < len(starts) else m
+            sc = S + terms[b]
+            if _key(sc) != e:
+                fail = b
+                break
+            sb = _bits(sc)
+            es = (sb >> 52) & 0x7FF
+            s0 = (sb & ((1 << 52) - 1)) | ((1 << 52) if es else 0)
+            run, vals = IDENT, []
+            for k in range(b + 1, end_k):
+                run = _then(run, _map(terms[k], e))
+                vals.append(run[1] if s0 & 1 else run[0])
+            if s0 + (vals[-1] if vals else 0) >= TWO53:
+                fail = b
+                break
+            out[b] = sc
+            for j, d in enumerate(vals):
+                out[b + 1 + j] = _dbl(((e - 1) << 52) + s0 + d)
+            S = _dbl(((e - 1) << 52) + s0 + (vals[-1] if vals else 0))
+    if fail < m:  # the windowed scan from the sum before term `fail`
+        rest = chunked_running_sum_from(terms[fail:], 4096, S)
+        out[fail:] = rest
+    return out
+
+
+def chunked_running_sum_from(terms, chunk, s0_value):
+    """chunked_running_sum started from the running sum s0_value."""
+    shifted = chunked_running_sum([s0_value] + list(terms), chunk) if s0_value != 0.0 else \
+        chunked_running_sum(list(terms), chunk)
+    return shifted[1:] if s0_value != 0.0 else shifted
+
+
+@pytest.mark.parametrize("kind", ["halfway", "dyadic", "subnormal", "zeros", "binades", "beta"])
+@pytest.mark.parametrize("nthreads", [1, 5, 64, 1000])
+def test_predicted_pass_equals_sequential(kind, nthreads):
+    terms = _inputs(kind, 3000) if kind != "beta" else \
+        sorted(np.random.default_rng(9).beta(0.5, 2.0, 3000).tolist())
+    assert [_bits(v) for v in predicted_running_sum(terms, nthreads)] == [_bits(v) for v in _sequential(terms)]
+
+
+def test_predicted_pass_checks_catch_wrong_predictions():
+    """Keys shifted one binade early or late at one term are caught (a first
+    term off its binade, a run past its top, a binade entered twice) and the
+    rest of the sum comes from the windowed scan, still bit for bit."""
+    terms = sorted(np.random.default_rng(2).beta(0.5, 2.0, 2000).tolist())
+    ref = [_bits(v) for v in _sequential(terms)]
+    for at in (0, 1, 37, 500, 1999):
+        for delta in (-1, 1):
+            got = predicted_running_sum(terms, 16, shift_pred=lambda k, e: e + delta if k == at else e)
+            assert [_bits(v) for v in got] == ref
+    # more binades than the resolution holds: all from the windowed scan
+    assert [_bits(v) for v in predicted_running_sum(terms, 16, max_segs=2)] == ref
