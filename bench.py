@@ -353,18 +353,29 @@ def extra_uneven(binding, synth, torch, stream, flush, steps: int, seed_base: in
         binding.percis_backward(eng.ctx, gvec, gx, 1)
         return infos
 
-    step(seed_base + 70_000)  # warm-up (records the sampling graphs)
-    ts, pairs = [], 0
-    for k in range(steps):
-        dt, infos = _timed(torch, stream, flush, lambda: step(seed_base + k))
-        ts.append(dt)
-        pairs += sum(f["ell1"] + f["ell"] for f in infos)
+    def run():
+        step(seed_base + 70_000)  # warm-up (records the sampling graphs)
+        ts, pairs = [], 0
+        for k in range(steps):
+            dt, infos = _timed(torch, stream, flush, lambda: step(seed_base + k))
+            ts.append(dt)
+            pairs += sum(f["ell1"] + f["ell"] for f in infos)
+        return pairs / sum(ts), 1000.0 * sum(ts) / len(ts), pairs / steps
+
+    value, ms, pps = run()
+    # the same batch with the options the autotuner picks on probe phases (not timed)
+    t0 = time.time()
+    o = eng.autotune(probe_samples=65536, seed=seed_base + 90_000)
+    tune_s = time.time() - t0
+    tv, tms, _ = run()
     eng.close()
-    return {"workload": "uneven512_ws_ba_grid", "value": pairs / sum(ts), "unit": "pairs/s",
-            "ms_per_step": 1000.0 * sum(ts) / len(ts), "steps": steps, "graphs": 512, "n": n,
+    return {"workload": "uneven512_ws_ba_grid", "value": value, "unit": "pairs/s",
+            "ms_per_step": ms, "steps": steps, "graphs": 512, "n": n,
             "nnz": int(col.shape[0]), "eps": 0.01,
             "form": "bidirectional, sampling launches in CUDA graphs, forward + backward (dPC/dx)",
-            "pairs_per_step": pairs / steps}
+            "pairs_per_step": pps,
+            "tuned": {"value": tv, "ms_per_step": tms, "tuning_s": tune_s,
+                      "options": {k: o[k] for k in ("bi_heavy_edges", "bi_table_log", "bi_blocks_per_sm")}}}
 
 
 def main():

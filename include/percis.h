@@ -114,6 +114,11 @@ typedef struct {
     int32_t bi_scratch_gib;   /* direct store: device memory its blocks may use, GiB (0 = 48);
                                  it holds 56 bytes per vertex and block, so it caps the blocks
                                  (the heavy pass wants one block per SM: 152 x 56 x n bytes) */
+    int32_t bi_blocks_per_sm; /* bidirectional first pass: resident blocks per SM, 0 (default) = as
+                                 many as fit (4); fewer leave more memory bandwidth to each */
+    int32_t tune_form;        /* 1: percis_autotune may also switch between the batched and the
+                                 bidirectional form (results then change with the form: both
+                                 draw a uniform shortest path, by different procedures) */
     int64_t bi_heavy_edges;   /* a sample whose next level would scan more than this many edges
                                  stops untouched and runs again after the first pass, alone in
                                  a block of 1,024 threads in the direct store (the heavy pass);
@@ -303,15 +308,20 @@ int32_t percis_num_graphs(percis_ctx *ctx);  /* 0 for a single-graph context */
 percis_status percis_estimate_graphs(percis_ctx *ctx, double eps, double delta, uint64_t seed, double *pc_out,
                                      int pc_on_device, percis_info *info);
 
-/* Autotuner (the batched form's batch width, frontier direction rule and
- * lane order; not in the paper, whose results these options do not change).
- * Coordinate descent: lane order {0, 1}, then lanes {64, 128, 256, 512},
- * then direction {pull, push, work estimate with push_alpha 0.25, 0.5, 1, 2};
- * each candidate is timed (CUDA events, best of two) on probe phases of
- * probe_samples pairs drawn with `seed` from the loaded graph and states.
- * The winner is stored in the context's options (other fields unchanged) and
- * copied to *chosen when chosen is not NULL.  The probe replaces the last
- * sample, so percis_backward needs a new percis_estimate first.
+/* Autotuner (speed options only; not in the paper, whose results these options
+ * do not change).  Coordinate descent, each candidate timed (CUDA events, best
+ * of two) on probe phases of probe_samples pairs drawn with `seed` from the
+ * loaded graph and states:
+ *  - batched form: lane order {0, 1}, then lanes {64, 128, 256, 512}, then
+ *    direction {pull, push, work estimate with push_alpha 0.25, 0.5, 1, 2};
+ *  - bidirectional form: bi_heavy_edges {2048, 4096, 8192, 16384, 65536,
+ *    never}, then the first pass's store {default, hashed 2^16, hashed 2^18},
+ *    then bi_blocks_per_sm {2, 3, 4}.
+ * With options.tune_form = 1 both forms are tuned and the faster one is kept
+ * (its options as tuned).  The winner is stored in the context's options
+ * (other fields unchanged) and copied to *chosen when chosen is not NULL.  The
+ * probe replaces the last sample, so percis_backward needs a new
+ * percis_estimate first.
  * Errors: STATE before percis_set_states; INVALID for probe_samples < 1 or the
  * plain form; any error of the probe phases (options are then left as they
  * were). */

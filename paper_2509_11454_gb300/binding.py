@@ -42,6 +42,7 @@ class percis_options(ctypes.Structure):
                 ("direction", ctypes.c_int32), ("estimator", ctypes.c_int32), ("push_alpha", ctypes.c_double),
                 ("cuda_graphs", ctypes.c_int32), ("bi_table_log", ctypes.c_int32),
                 ("bi_table_max_log", ctypes.c_int32), ("bi_scratch_gib", ctypes.c_int32),
+                ("bi_blocks_per_sm", ctypes.c_int32), ("tune_form", ctypes.c_int32),
                 ("bi_heavy_edges", ctypes.c_int64), ("reserved", ctypes.c_int64)]
 
 
@@ -335,8 +336,10 @@ class PercIS:
         percis_set_options(self.ctx, self.options)
 
     def autotune(self, probe_samples: int = 8192, seed: int = 0) -> dict:
-        """Pick lane width, lane order and direction rule by timing probe
-        phases; returns the chosen options."""
+        """Pick the speed options of the form (batched: lane width, lane order,
+        direction rule; bidirectional: heavy-level threshold, store, blocks per
+        SM; with tune_form=1 also the form) by timing probe phases; returns the
+        chosen options."""
         o = percis_autotune(self.ctx, probe_samples, seed)
         self.options = o
         return {name: getattr(o, name) for name, _ in o._fields_}

@@ -93,7 +93,7 @@ struct alignas(16) PhaseStats {
 };
 
 __global__ void k_phase_stats(int64_t count, const int32_t *kind, const int32_t *ilen, int64_t n, const double *lam,
-                              const unsigned long long *cnt, const double *acc, double ell, PhaseStats *out) {
+                              const unsigned long long *cnt, const double *acc, PhaseStats *out) {
     long long s1 = 0, s2 = 0, zw = 0, un = 0;
     double pm = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -104,8 +104,12 @@ __global__ void k_phase_stats(int64_t count, const int32_t *kind, const int32_t 
         zw += kind[i] == 1;
         un += kind[i] == 2;
     }
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        pm = fmax(pm, lam[v] * (acc ? acc[v] : (double)cnt[v]) / ell);
+    // the largest lambda_v cnt_v (the division by l is monotone, so it is applied
+    // once to the maximum, on the host); zero counts skip the FP64 product
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const double c = acc ? acc[v] : (double)cnt[v];
+        if (c != 0.0) pm = fmax(pm, __dmul_rn(lam[v], c));
+    }
     for (int off = 16; off > 0; off >>= 1) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, off);
         s2 += __shfl_xor_sync(0xffffffffu, s2, off);
@@ -126,8 +130,10 @@ __global__ void k_phase_stats(int64_t count, const int32_t *kind, const int32_t 
 __global__ void k_finalize(const double *lam, const unsigned long long *cnt, const double *acc, int64_t n, double ell,
                            double *pc) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        pc[v] = lam[v] * (acc ? acc[v] : (double)cnt[v]) / ell;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const double c = acc ? acc[v] : (double)cnt[v];
+        pc[v] = c == 0.0 ? 0.0 : __ddiv_rn(__dmul_rn(lam[v], c), ell);  // (lambda is finite: 0 stays +0)
+    }
 }
 
 __global__ void k_ilen_i64(const int32_t *ilen, int64_t count, long long *out) {
@@ -290,16 +296,25 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
 
 namespace {
 
-percis_status phase_stats(percis_ctx *ctx, int64_t count, double ell, PhaseStats *hs) {
+// Sums over the phase's samples and, when want_pmax, max_v lambda_v cnt_v / l
+// (as pmax_bits: the division applied on the host to the largest product).
+percis_status phase_stats(percis_ctx *ctx, int64_t count, double ell, bool want_pmax, PhaseStats *hs) {
     PERCIS_TRY(ensure(ctx, ctx->red, sizeof(PhaseStats), "stats"));
     PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(PhaseStats), ctx->stream));
-    k_phase_stats<<<grid_for(ctx, std::max(count, ctx->n), 256), 256, 0, ctx->stream>>>(
-        count, ctx->kind.as<int32_t>(), ctx->ilen.as<int32_t>(), ctx->n, ctx->lam.as<double>(),
-        ctx->cnt.as<unsigned long long>(), ctx->opt.estimator == 1 ? ctx->acc_ap.as<double>() : nullptr, ell,
+    const int64_t nv = want_pmax ? ctx->n : 0;
+    k_phase_stats<<<grid_for(ctx, std::max<int64_t>(std::max<int64_t>(count, nv), 1), 256), 256, 0, ctx->stream>>>(
+        count, ctx->kind.as<int32_t>(), ctx->ilen.as<int32_t>(), nv, ctx->lam.as<double>(),
+        ctx->cnt.as<unsigned long long>(), ctx->opt.estimator == 1 ? ctx->acc_ap.as<double>() : nullptr,
         ctx->red.as<PhaseStats>());
     PERCIS_CHECK_LAUNCH(ctx, "phase stats");
     PERCIS_CUDA(ctx, cudaMemcpyAsync(hs, ctx->red.p, sizeof(PhaseStats), cudaMemcpyDeviceToHost, ctx->stream));
     PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (want_pmax) {
+        double pm;
+        memcpy(&pm, &hs->pmax_bits, sizeof(pm));
+        pm = pm / ell;  // IEEE division, as on the device: max_v fl(fl(lambda_v cnt_v) / l)
+        memcpy(&hs->pmax_bits, &pm, sizeof(pm));
+    }
     return PERCIS_OK;
 }
 
@@ -490,7 +505,7 @@ percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_
         PhaseOut po;
         PERCIS_TRY(run_phase(ctx, seed, 0, ell1, &po));
         record(0, po);
-        PERCIS_TRY(phase_stats(ctx, ell1, (double)ell1, &hs));
+        PERCIS_TRY(phase_stats(ctx, ell1, (double)ell1, true, &hs));
         inf.zero_weight[0] = hs.zero_w;
         inf.unreachable[0] = hs.unreach;
         inf.sum_internal[0] = hs.s1;
@@ -523,7 +538,7 @@ percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_
     PERCIS_CHECK_LAUNCH(ctx, "finalize");
     if (info) {
         PhaseStats h2{};
-        PERCIS_TRY(phase_stats(ctx, ell, (double)ell, &h2));
+        PERCIS_TRY(phase_stats(ctx, ell, (double)ell, false, &h2));
         inf.zero_weight[1] = h2.zero_w;
         inf.unreachable[1] = h2.unreach;
         inf.sum_internal[1] = h2.s1;
@@ -691,7 +706,8 @@ percis_status percis_run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_
 percis_status percis_autotune(percis_ctx *ctx, int64_t probe_samples, uint64_t seed, percis_options *chosen) {
     PERCIS_TRY(need_states(ctx));
     if (probe_samples < 1) return set_err(ctx, PERCIS_E_INVALID, "probe_samples >= 1");
-    if (ctx->opt.form == PERCIS_FORM_PLAIN) return set_err(ctx, PERCIS_E_INVALID, "the autotuner tunes the batched form");
+    if (ctx->opt.form == PERCIS_FORM_PLAIN)
+        return set_err(ctx, PERCIS_E_INVALID, "the autotuner tunes the batched and bidirectional forms");
     DeviceGuard g(ctx->device);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PERCIS_CUDA(ctx, cudaEventCreate(&e0));
@@ -718,34 +734,74 @@ percis_status percis_autotune(percis_ctx *ctx, int64_t probe_samples, uint64_t s
         *ms = bestms;
         return PERCIS_OK;
     };
+    // coordinate descent over one form's options, from o0; *o_best / *ms_best the winner
+    auto tune_form = [&](percis_options o0, percis_options *o_best, float *ms_best) -> percis_status {
+        percis_options b = o0;
+        float bms = 0.f;
+        PERCIS_TRY(time_opt(b, &bms));
+        auto try_opt = [&](const percis_options &o) -> percis_status {
+            float ms = 0.f;
+            PERCIS_TRY(time_opt(o, &ms));
+            if (ms < bms) bms = ms, b = o;
+            return PERCIS_OK;
+        };
+        if (o0.form == PERCIS_FORM_BIDIR) {
+            // 1. heavy-level threshold
+            const int64_t heavy[6] = {2048, 4096, 8192, 16384, 65536, -1};
+            for (int k = 0; k < 6; ++k) {
+                percis_options o = b;
+                o.bi_heavy_edges = heavy[k];
+                PERCIS_TRY(try_opt(o));
+            }
+            // 2. the first pass's store: the default, or hashed tables of 2^16 or 2^18
+            const int tl[2] = {16, 18};
+            for (int k = 0; k < 2; ++k) {
+                percis_options o = b;
+                o.bi_table_log = o.bi_table_max_log = tl[k];
+                PERCIS_TRY(try_opt(o));
+            }
+            // 3. resident blocks per SM
+            for (int bp = 2; bp <= 4; ++bp) {
+                percis_options o = b;
+                o.bi_blocks_per_sm = bp;
+                PERCIS_TRY(try_opt(o));
+            }
+        } else {
+            // 1. lane order
+            for (int lo = 0; lo <= 1; ++lo) {
+                percis_options o = b;
+                o.lane_order = lo;
+                PERCIS_TRY(try_opt(o));
+            }
+            // 2. lane width
+            const int widths[4] = {64, 128, 256, 512};
+            for (int k = 0; k < 4; ++k) {
+                percis_options o = b;
+                o.lanes = widths[k];
+                PERCIS_TRY(try_opt(o));
+            }
+            // 3. direction: pull, push, or by work estimate with the push threshold
+            const double alphas[4] = {0.25, 0.5, 1.0, 2.0};
+            for (int k = 0; k < 6; ++k) {
+                percis_options o = b;
+                o.direction = k < 2 ? k : 2;
+                if (k >= 2) o.push_alpha = alphas[k - 2];
+                PERCIS_TRY(try_opt(o));
+            }
+        }
+        *o_best = b;
+        *ms_best = bms;
+        return PERCIS_OK;
+    };
     float best_ms = 0.f;
-    st = time_opt(best, &best_ms);
-    // 1. lane order
-    for (int lo = 0; lo <= 1 && st == PERCIS_OK; ++lo) {
-        percis_options o = best;
-        o.lane_order = lo;
-        float ms = 0.f;
-        st = time_opt(o, &ms);
-        if (st == PERCIS_OK && ms < best_ms) best_ms = ms, best = o;
-    }
-    // 2. lane width
-    const int widths[4] = {64, 128, 256, 512};
-    for (int k = 0; k < 4 && st == PERCIS_OK; ++k) {
-        percis_options o = best;
-        o.lanes = widths[k];
-        float ms = 0.f;
-        st = time_opt(o, &ms);
-        if (st == PERCIS_OK && ms < best_ms) best_ms = ms, best = o;
-    }
-    // 3. direction: pull, push, or by work estimate with the push threshold
-    const double alphas[4] = {0.25, 0.5, 1.0, 2.0};
-    for (int k = 0; k < 6 && st == PERCIS_OK; ++k) {
-        percis_options o = best;
-        o.direction = k < 2 ? k : 2;
-        if (k >= 2) o.push_alpha = alphas[k - 2];
-        float ms = 0.f;
-        st = time_opt(o, &ms);
-        if (st == PERCIS_OK && ms < best_ms) best_ms = ms, best = o;
+    st = tune_form(saved, &best, &best_ms);
+    if (st == PERCIS_OK && saved.tune_form) {
+        percis_options other = saved;
+        other.form = saved.form == PERCIS_FORM_BIDIR ? PERCIS_FORM_BATCHED : PERCIS_FORM_BIDIR;
+        percis_options ob;
+        float oms = 0.f;
+        st = tune_form(other, &ob, &oms);
+        if (st == PERCIS_OK && oms < best_ms) best = ob, best_ms = oms;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -754,12 +810,18 @@ percis_status percis_autotune(percis_ctx *ctx, int64_t probe_samples, uint64_t s
         ctx->opt = saved;
         return st;
     }
-    // only the speed options change; everything else stays as the caller set it
+    // only the speed options (and, when allowed, the form) change; everything else
+    // stays as the caller set it
     ctx->opt = saved;
+    ctx->opt.form = best.form;
     ctx->opt.lane_order = best.lane_order;
     ctx->opt.lanes = best.lanes;
     ctx->opt.direction = best.direction;
     ctx->opt.push_alpha = best.push_alpha;
+    ctx->opt.bi_heavy_edges = best.bi_heavy_edges;
+    ctx->opt.bi_table_log = best.bi_table_log;
+    ctx->opt.bi_table_max_log = best.bi_table_max_log;
+    ctx->opt.bi_blocks_per_sm = best.bi_blocks_per_sm;
     if (chosen) *chosen = ctx->opt;
     return PERCIS_OK;
 }

@@ -105,7 +105,8 @@ struct BiArgs {
     // hashed store
     int32_t h0_log, hmax_log;    // first and largest table: 2^h0_log, 2^hmax_log entries (step x4)
     uint32_t *slot_epoch;        // per slot: last epoch used (20 bits; persists across launches)
-    int32_t *deferred;           // samples handed to the direct store
+    int32_t *deferred;           // samples handed to the heavy pass
+    unsigned long long *defer_cost;  // edges of the level each was handed over at
     unsigned int *n_deferred;
     int32_t sorted;              // every adjacency list strictly increasing (reverse backtrack allowed)
     unsigned long long heavy_edges;  // a level scanning more edges than this hands the sample over (0: never)
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
     __shared__ int64_t s_pre[kFlat + 1];  // prefix sums of the chunk's degrees
     __shared__ unsigned long long s_work[6];
     __shared__ long long s_wsum[nw];    // per-warp degree sums of a chunk
+    __shared__ double s_wcnt[nw];       // per-warp sums of a chunk's path counts
     if (threadIdx.x < 6) s_work[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) s_tlast = -1;
     unsigned long long n_add = 0ull;
@@ -441,14 +443,12 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                 // first (prefetch), for several edges at once, then resolved
                 struct Pre {
                     int32_t v;
-                    uint32_t dg;
                     int64_t p;
                     unsigned long long ow, oc, oy;
                 };
                 auto prefetch = [&](const int32_t v) -> Pre {
                     Pre r;
                     r.v = v;
-                    r.dg = (uint32_t)(px[v + 1] - px[v]);  // < 2^31
                     r.p = HASH ? (int64_t)hash_home(v, lg) : (int64_t)v;
                     ld_pair(&tab[4 * r.p + xs], r.ow, r.oc);
                     r.oy = __ldcg(&tab[4 * r.p + ys]);
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                 // level.  A claim swaps the whole {word, count} pair, so it also sets the
                 // count to the claiming parent's and counts never need clearing: a count
                 // is read only where its word carries the sample's epoch.
-                auto resolve = [&](Pre &r, const C su) {
+                auto resolve = [&](Pre &r, const C su, const bool checked) {
                     if (HASH && s_full) return;  // the sample goes to the direct store
                     const int32_t v = r.v;
                     const unsigned long long want = W::make(v, ep, nl);
@@ -502,11 +502,13 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                     if (won) {
                         // the lanes that claimed together reserve their queue slots and
                         // add their degrees with one shared atomic each (a 64-bit shared
-                        // add would be a contended compare-and-swap loop per lane)
+                        // add would be a contended compare-and-swap loop per lane); the
+                        // degree is loaded by the claim's winner alone
+                        const uint32_t dg = (uint32_t)(px[v + 1] - px[v]);  // < 2^31
                         const unsigned grp = __activemask();
                         const int lead = __ffs(grp) - 1;
-                        const uint32_t dlo = __reduce_add_sync(grp, r.dg & 0xffffu);
-                        const uint32_t dhi = __reduce_add_sync(grp, r.dg >> 16);
+                        const uint32_t dlo = __reduce_add_sync(grp, dg & 0xffffu);
+                        const uint32_t dhi = __reduce_add_sync(grp, dg >> 16);
                         int q0 = 0;
                         if (lane == lead) {
                             q0 = atomicAdd(&s_new[cs], __popc(grp));
@@ -526,10 +528,18 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                     if (a.work && (at || won)) ++n_add;
                     if (at) {
                         C *cp = reinterpret_cast<C *>(&tab[4 * p + xs + 1]);
-                        const C o = atomicAdd(cp, su);
-                        if ((double)(o + su) >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                        if (checked) {  // counts may pass 2^53: find the addition that does
+                            const C o = atomicAdd(cp, su);
+                            if ((double)(o + su) >= kTwo53) atomicOr(a.status, DEV_SIGMA_OVERFLOW);
+                        } else {
+                            atomicAdd(cp, su);  // (no result waited for)
+                        }
                     }
                 };
+                // every count of the new level is at most the sum of the frontier's counts
+                // loaded so far (fcnt, FP64): below 2^52 no count can reach 2^53, so the
+                // count additions need not wait for their results
+                double fcnt = 0.0;
                 // the level's edges spread evenly over the block, kFlat frontier vertices
                 // at a time (a hub's adjacency is not left to one warp): the block loads
                 // the chunk, a few vertices per thread with their loads in flight
@@ -541,6 +551,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                         constexpr int per = kFlat >= BT ? kFlat / BT : 1;
                         int64_t loc[per];
                         int64_t tot = 0;
+                        double csum = 0.0;  // the chunk's path counts
 #pragma unroll
                         for (int r = 0; r < per; ++r) {
                             const int k = (int)threadIdx.x * per + r;
@@ -549,7 +560,9 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                                 const int2 qe = qx[c0 + k];
                                 const int64_t e0 = px[qe.x];
                                 s_fe[k] = e0;
-                                s_fs[k] = count_of<C>(__ldcg(&tab[4ll * qe.y + xs + 1]));
+                                const C fs = count_of<C>(__ldcg(&tab[4ll * qe.y + xs + 1]));
+                                s_fs[k] = fs;
+                                csum += (double)fs;
                                 dg = px[qe.x + 1] - e0;
                             }
                             loc[r] = tot;
@@ -562,9 +575,13 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                             if (lane >= o) incl += t2;
                         }
                         if (lane == 31) s_wsum[warp] = incl;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
+                        if (lane == 0) s_wcnt[warp] = csum;
                         __syncthreads();
                         int64_t first = incl - tot;
                         for (int q = 0; q < warp; ++q) first += s_wsum[q];
+                        for (int q = 0; q < nw; ++q) fcnt += s_wcnt[q];
 #pragma unroll
                         for (int r = 0; r < per; ++r) {
                             const int k = (int)threadIdx.x * per + r;
@@ -599,7 +616,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                             if (vv[b] >= 0) pr[b] = prefetch(vv[b]);
 #pragma unroll
                         for (int b = 0; b < kEdgeBatch; ++b)
-                            if (vv[b] >= 0) resolve(pr[b], s_fs[kk[b]]);
+                            if (vv[b] >= 0) resolve(pr[b], s_fs[kk[b]], fcnt >= 0x1p52);
                     }
                     if (c0 + kFlat < hi) __syncthreads();  // the chunk's shared arrays are reused
                 }
@@ -635,11 +652,14 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
         if (handed) {
             // nothing of the sample was written outside the slot: the heavy pass runs it
             if (threadIdx.x == 0) {
-                a.deferred[atomicAdd(a.n_deferred, 1u)] = (int32_t)i;
+                const unsigned int d = atomicAdd(a.n_deferred, 1u);
+                a.deferred[d] = (int32_t)i;
+                a.defer_cost[d] = x ? cost[1] : cost[0];
                 if (a.work) s_work[4] += 1ull;
             }
             continue;
         }
+
         if (!met) {
             if (threadIdx.x == 0) {
                 a.kind[i] = 2;
@@ -1036,6 +1056,41 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
     if (a.work && threadIdx.x < 6 && s_work[threadIdx.x]) atomicAdd(&a.work[threadIdx.x], s_work[threadIdx.x]);
 }
 
+constexpr int kHeavySort = 4096;  // heavy samples ordered by cost when there are at most this many
+
+// The handed-over samples in decreasing cost, ties by sample number: one block,
+// a bitonic sort of (~cost, sample) keys in shared memory.
+__global__ void __launch_bounds__(1024) k_order_heavy(int32_t *defer, const unsigned long long *cost, int nd) {
+    __shared__ unsigned long long s_k[kHeavySort];
+    int P = 1;
+    while (P < nd) P <<= 1;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+        if (j < nd) {
+            const unsigned long long c = cost[j] < 0xffffffffull ? cost[j] : 0xffffffffull;
+            s_k[j] = ((0xffffffffull - c) << 32) | (uint32_t)defer[j];
+        } else {
+            s_k[j] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const unsigned long long A = s_k[t], B = s_k[u];
+                    if ((A > B) == ((t & k) == 0)) {
+                        s_k[t] = B;
+                        s_k[u] = A;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int j = threadIdx.x; j < nd; j += blockDim.x) defer[j] = (int32_t)(uint32_t)s_k[j];
+}
+
 constexpr int kHeavyBlock = 1024;                        // threads per sample in the heavy pass
 constexpr unsigned long long kDefaultHeavyEdges = 4096;   // a level scanning more edges is heavy
 constexpr int64_t kDefaultScratchGiB = 48;  // direct store: one heavy-pass block per SM up to n = 6M
@@ -1091,13 +1146,15 @@ BiArgs common_args(percis_ctx *ctx, uint64_t seed, uint32_t tag_path) {
 // defer (heavy_edges = 0: none).
 template <int BT>
 percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count, const int32_t *list,
-                          unsigned long long heavy_edges, int32_t *defer, unsigned int *n_def) {
+                          unsigned long long heavy_edges, int32_t *defer, unsigned long long *defer_cost,
+                          unsigned int *n_def) {
     const int32_t *gid = nullptr;
     const int64_t *vbase = nullptr;
     int64_t nslot = ctx->n;
     if (ctx->multi) multi_graph_view(ctx, &gid, &vbase, &nslot);
     const size_t per_slot = (size_t)nslot * (sizeof(unsigned long long) * 4 + sizeof(int2) * 3);
-    const int per_sm = blocks_per_sm<false, BT>(BT == kBiBlock ? &ctx->bi_per_sm : &ctx->bi_heavy_per_sm);
+    int per_sm = blocks_per_sm<false, BT>(BT == kBiBlock ? &ctx->bi_per_sm : &ctx->bi_heavy_per_sm);
+    if (BT == kBiBlock && ctx->opt.bi_blocks_per_sm > 0) per_sm = std::min(per_sm, ctx->opt.bi_blocks_per_sm);
     const int64_t budget = (int64_t)(ctx->opt.bi_scratch_gib > 0 ? ctx->opt.bi_scratch_gib : kDefaultScratchGiB) << 30;
     int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, budget / (int64_t)per_slot));
     slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
@@ -1132,6 +1189,7 @@ percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     a.next = ctx->red.as<unsigned long long>();
     a.heavy_edges = heavy_edges;
     a.deferred = defer;
+    a.defer_cost = defer_cost;
     a.n_deferred = n_def;
     launch<false, BT>(ctx, (int)slots, a);
     PERCIS_CHECK_LAUNCH(ctx, BT == kBiBlock ? "bidirectional sigma-BFS (direct)" : "bidirectional sigma-BFS (heavy)");
@@ -1159,9 +1217,12 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     const unsigned long long heavy =
         ctx->opt.bi_heavy_edges == 0 ? kDefaultHeavyEdges
                                      : (ctx->opt.bi_heavy_edges < 0 ? 0ull : (unsigned long long)ctx->opt.bi_heavy_edges);
-    PERCIS_TRY(ensure(ctx, ctx->bi_defer, sizeof(int32_t) * std::max<int64_t>(count, 1) + 64, "handed-over samples"));
-    int32_t *defer = ctx->bi_defer.as<int32_t>();
-    unsigned int *n_def = reinterpret_cast<unsigned int *>(defer + std::max<int64_t>(count, 1));
+    const int64_t cd = std::max<int64_t>(count, 1);
+    PERCIS_TRY(ensure(ctx, ctx->bi_defer, (sizeof(unsigned long long) + sizeof(int32_t)) * cd + 64,
+                      "handed-over samples"));
+    unsigned long long *defer_cost = ctx->bi_defer.as<unsigned long long>();
+    int32_t *defer = reinterpret_cast<int32_t *>(defer_cost + cd);
+    unsigned int *n_def = reinterpret_cast<unsigned int *>(defer + cd);
     PERCIS_CUDA(ctx, cudaMemsetAsync(n_def, 0, sizeof(unsigned int), ctx->stream));
     int64_t nslot = ctx->n;
     if (ctx->multi) {
@@ -1180,7 +1241,7 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         direct = full * per_slot <= budget;
     }
     if (direct) {
-        PERCIS_TRY(direct_pass<kBiBlock>(ctx, seed, tag_path, count, nullptr, heavy, defer, n_def));
+        PERCIS_TRY(direct_pass<kBiBlock>(ctx, seed, tag_path, count, nullptr, heavy, defer, defer_cost, n_def));
     } else {
         // default: one table per block that holds the (largest) graph's vertices half
         // full, at most 2^18 entries; else 2^h0 growing 4x up to 2^hmax
@@ -1198,7 +1259,8 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         int64_t region = 0;
         for (int l = h0; l <= hmax; l += 2) region += 1ll << l;
         const int64_t qcap = 1ll << hmax;
-        const int per_sm = blocks_per_sm<true, kBiBlock>(&ctx->bi_hash_per_sm);
+        int per_sm = blocks_per_sm<true, kBiBlock>(&ctx->bi_hash_per_sm);
+        if (ctx->opt.bi_blocks_per_sm > 0) per_sm = std::min(per_sm, ctx->opt.bi_blocks_per_sm);
         const int64_t slots = (int64_t)per_sm * ctx->num_sms;
         const size_t ent_bytes = sizeof(unsigned long long) * 4 * (size_t)region * slots;
         const size_t q_bytes = sizeof(int2) * 3 * (size_t)qcap * slots;
@@ -1227,6 +1289,7 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         a.hmax_log = hmax;
         a.slot_epoch = ctx->bi_hep.as<uint32_t>();
         a.deferred = defer;
+        a.defer_cost = defer_cost;
         a.n_deferred = n_def;
         a.heavy_edges = heavy;
         launch<true, kBiBlock>(ctx, (int)std::min<int64_t>(slots, std::max<int64_t>(count, 1)), a);
@@ -1236,7 +1299,14 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     PERCIS_CUDA(ctx, cudaMemcpyAsync(&nd, n_def, sizeof(nd), cudaMemcpyDeviceToHost, ctx->stream));
     PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->bi_handed = nd;
-    if (nd > 0) PERCIS_TRY(direct_pass<kHeavyBlock>(ctx, seed, tag_path, (int64_t)nd, defer, 0ull, nullptr, nullptr));
+    if (nd > 1 && nd <= (unsigned)kHeavySort) {
+        // largest first (by the level each was handed over at), so that the
+        // longest samples do not start last
+        k_order_heavy<<<1, 1024, 0, ctx->stream>>>(defer, defer_cost, (int)nd);
+        PERCIS_CHECK_LAUNCH(ctx, "heavy-pass order");
+    }
+    if (nd > 0)
+        PERCIS_TRY(direct_pass<kHeavyBlock>(ctx, seed, tag_path, (int64_t)nd, defer, 0ull, nullptr, nullptr, nullptr));
     return PERCIS_OK;
 }
 

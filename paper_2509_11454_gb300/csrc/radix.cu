@@ -159,19 +159,20 @@ __global__ void __launch_bounds__(kRadixBlock, 3) k_radix_scatter(const K *kin, 
     }
 }
 
-// src[e] = the row of edge e (one warp per row, so long rows are spread over lanes)
+// src[e] = the row of edge e: a warp takes 32 consecutive rows (their offsets
+// loaded together) and writes them one after the other, all lanes on each row,
+// so long rows are spread over the lanes and short ones cost one step each
 __global__ void k_edge_rows(const int64_t *rp, int64_t n, int32_t *src) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-        const int64_t e1 = rp[u + 1];
-        for (int64_t e = rp[u] + lane; e < e1; e += 32) src[e] = (int32_t)u;
+    for (int64_t u0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; u0 < n; u0 += warps * 32) {
+        const int64_t u = u0 + lane;
+        const int64_t b = u < n ? rp[u] : 0, e = u < n ? rp[u + 1] : 0;
+        for (int r = 0; r < 32; ++r) {
+            const int64_t e0 = __shfl_sync(0xffffffffu, b, r), e1 = __shfl_sync(0xffffffffu, e, r);
+            for (int64_t x = e0 + lane; x < e1; x += 32) src[x] = (int32_t)(u0 + r);
+        }
     }
-}
-
-__global__ void k_copy_u32(const int32_t *in, int64_t n, uint32_t *out) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (uint32_t)in[i];
 }
 
 // irp[v] = first position of target v in the sorted targets (= nnz past the last):
@@ -235,10 +236,12 @@ int radix_grid(percis_ctx *ctx, int64_t ntiles) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, cap));
 }
 
+// keys_in, when given, is the first pass's input instead of keys (which is then
+// only scratch): the pass does not modify its input.
 template <class K>
 percis_status radix_sort_impl(percis_ctx *ctx, K *keys, int32_t *vals, K *tk, int32_t *tv, int64_t n, int lo_bit,
-                              int bits, K **out_keys, int32_t **out_vals) {
-    *out_keys = keys;
+                              int bits, K **out_keys, int32_t **out_vals, const K *keys_in = nullptr) {
+    *out_keys = keys_in ? const_cast<K *>(keys_in) : keys;
     *out_vals = vals;
     if (n <= 1 || bits <= 0) return PERCIS_OK;
     const int64_t ntiles = (n + kRadixTile - 1) / kRadixTile;
@@ -252,10 +255,11 @@ percis_status radix_sort_impl(percis_ctx *ctx, K *keys, int32_t *vals, K *tk, in
     K *ka = keys, *kb = tk;
     int32_t *va = vals, *vb = tv;
     for (int shift = lo_bit; shift < lo_bit + bits; shift += 8) {
-        k_radix_count<K><<<grid, kRadixBlock, 0, ctx->stream>>>(ka, n, shift, ntiles, counts);
+        const K *kin = (shift == lo_bit && keys_in) ? keys_in : ka;
+        k_radix_count<K><<<grid, kRadixBlock, 0, ctx->stream>>>(kin, n, shift, ntiles, counts);
         PERCIS_CHECK_LAUNCH(ctx, "radix count");
         PERCIS_TRY(scan_exclusive_i64(ctx, (const int64_t *)counts, (int64_t *)counts, nc));
-        k_radix_scatter<K><<<grid, kRadixBlock, scatter_smem<K>(), ctx->stream>>>(ka, va, kb, vb, n, shift, ntiles,
+        k_radix_scatter<K><<<grid, kRadixBlock, scatter_smem<K>(), ctx->stream>>>(kin, va, kb, vb, n, shift, ntiles,
                                                                                    counts);
         PERCIS_CHECK_LAUNCH(ctx, "radix scatter");
         std::swap(ka, kb);
@@ -312,16 +316,15 @@ percis_status build_transpose(percis_ctx *ctx) {
     PERCIS_TRY(ensure(ctx, ctx->sort_b, kb, "transpose values"));
     uint32_t *k1 = ctx->sort_a.as<uint32_t>(), *k2 = k1 + nnz;
     int32_t *v1 = ctx->icol.as<int32_t>(), *v2 = ctx->sort_b.as<int32_t>();
-    const int g = grid_for(ctx, nnz, 256);
-    k_copy_u32<<<g, 256, 0, ctx->stream>>>(ctx->col.as<int32_t>(), nnz, k1);
-    PERCIS_CHECK_LAUNCH(ctx, "transpose keys");
-    k_edge_rows<<<grid_for(ctx, n * 32, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, v1);
+    k_edge_rows<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, v1);
     PERCIS_CHECK_LAUNCH(ctx, "edge rows");
     int bits = 1;
     while (bits < 32 && (1ll << bits) < n) ++bits;
     uint32_t *ok;
     int32_t *ov;
-    PERCIS_TRY(radix_sort_impl<unsigned int>(ctx, k1, v1, k2, v2, nnz, 0, bits, &ok, &ov));
+    // the columns (ids >= 0, validated) are the first pass's keys as they are
+    PERCIS_TRY(radix_sort_impl<unsigned int>(ctx, k1, v1, k2, v2, nnz, 0, bits, &ok, &ov,
+                                             reinterpret_cast<const uint32_t *>(ctx->col.as<int32_t>())));
     if (ov != v1)
         PERCIS_CUDA(ctx, cudaMemcpyAsync(v1, ov, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, ctx->stream));
     k_offsets_from_sorted<<<grid_for(ctx, nnz + 1, 256), 256, 0, ctx->stream>>>(ok, nnz, n, ctx->irp.as<int64_t>());

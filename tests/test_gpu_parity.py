@@ -440,6 +440,38 @@ def test_percis_di_matches_oracle(binding):
     eng.close()
 
 
+@pytest.mark.parametrize("name", ["rmat14", "ba20000"])
+def test_autotune_bidir_keeps_results(binding, name):
+    """Tuning the bidirectional form (heavy-level threshold, store, blocks per
+    SM) keeps the estimate bit-identical to the default options' and to the
+    oracle's bidirectional replica; with tune_form the form may change and
+    the estimate is then that form's at the same seed."""
+    g = synth.rmat(14, 16, 0.57, 0.19, 0.19, 5) if name == "rmat14" else synth.barabasi_albert(20000, 3, 5)
+    og = oracle.from_synth(g)
+    x = synth.states_uniform(g.n, 6)
+    ref_eng = _engine(binding, g, x, form="bidir", ell1=1000, ell=4000)
+    ref, _ = ref_eng.estimate(0.05, 0.1, seed=8)
+    eng = _engine(binding, g, x, form="bidir", ell1=1000, ell=4000)
+    o = eng.autotune(probe_samples=2000, seed=1)
+    assert o["form"] == binding.FORM_BIDIR
+    assert o["bi_heavy_edges"] in (0, 2048, 4096, 8192, 16384, 65536, -1)
+    assert o["bi_table_log"] in (0, 16, 18) and o["bi_blocks_per_sm"] in (0, 2, 3, 4)
+    pc, info = eng.estimate(0.05, 0.1, seed=8)
+    assert np.array_equal(_np(pc), _np(ref))
+    prep = oracle.prepare(x)
+    ph = oracle.run_samples(og, prep, 8, 1, 3, 0, 4000, keep_paths=False, bidir=True)
+    assert np.max(np.abs(_np(pc) - prep.lam * ph.cnt / 4000)) <= 1e-12
+    eng.set_options(tune_form=1)
+    o2 = eng.autotune(probe_samples=2000, seed=1)
+    assert o2["form"] in (binding.FORM_BIDIR, binding.FORM_BATCHED)
+    pc2, _ = eng.estimate(0.05, 0.1, seed=8)
+    ph2 = oracle.run_samples(og, prep, 8, 1, 3, 0, 4000, keep_paths=False,
+                             bidir=o2["form"] == binding.FORM_BIDIR)
+    assert np.max(np.abs(_np(pc2) - prep.lam * ph2.cnt / 4000)) <= 1e-12
+    ref_eng.close()
+    eng.close()
+
+
 def test_autotune_keeps_results(binding):
     """The autotuner only picks speed options: the estimate after tuning is
     bit-identical to the default one and to the oracle's."""
