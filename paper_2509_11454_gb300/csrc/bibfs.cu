@@ -63,9 +63,15 @@ constexpr int kFlat = 512;  // frontier vertices per chunk whose edges are sprea
 #define PERCIS_EDGE_BATCH 2
 #endif
 constexpr int kEdgeBatch = PERCIS_EDGE_BATCH;  // edges a thread has in flight (their loads issued together)
+#ifndef PERCIS_HEAVY_EDGE_BATCH
+#define PERCIS_HEAVY_EDGE_BATCH 2
+#endif
+constexpr int kHeavyEdgeBatch = PERCIS_HEAVY_EDGE_BATCH;  // the same in the heavy pass
 #ifndef PERCIS_BI_MINB
 #define PERCIS_BI_MINB 4
 #endif
+constexpr double kMeetOnlyHits = 3.0;  // expected meeting hits above which a level is scanned for them first
+constexpr unsigned long long kLazyDegEdges = 2048;  // levels of this many edges load degrees after
 constexpr uint32_t kHashLevels = 4095;            // levels a hashed word holds (12 bits)
 constexpr uint32_t kHashEpochs = (1u << 20) - 1;  // epochs a hashed word holds (20 bits)
 constexpr int kMaxHLog = 20;                      // largest table: at most 2^20 entries
@@ -216,7 +222,7 @@ __device__ __forceinline__ int64_t hash_find(const unsigned long long *tab, int 
 // C = unsigned long long: exact counts (flagged at 2^53, products checked);
 // C = double: FP64 counts, the rerun of a phase whose counts passed 2^53.
 template <class C, bool HASH, int BT>
-__global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bibfs(BiArgs a) {
+__global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / BT) k_bibfs(BiArgs a) {
     using W = Word<HASH>;
     constexpr bool FP = std::is_floating_point<C>::value;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -336,6 +342,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                                       (unsigned long long)(a.irp[t + 1] - a.irp[t])};
         int x = 0;
         bool met = s != t, handed = false;
+        double meet_hits = kMeetOnlyHits;  // expected hits that try a level for its meeting layer first
         if (met) {
             met = false;
             for (int it = 0;; ++it) {
@@ -419,6 +426,8 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                     }
                 }
                 const int cs = it % 3;
+                // a large level's claims leave the degrees to a pass after it (lazy_deg)
+                const bool lazy_deg = (x ? cost[1] : cost[0]) >= kLazyDegEdges;
                 if (threadIdx.x == 0) {
                     s_new[(it + 1) % 3] = 0;
                     s_newcost[(it + 1) % 3] = 0ull;
@@ -458,7 +467,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                 // level.  A claim swaps the whole {word, count} pair, so it also sets the
                 // count to the claiming parent's and counts never need clearing: a count
                 // is read only where its word carries the sample's epoch.
-                auto resolve = [&](Pre &r, const C su, const bool checked) {
+                auto resolve = [&](Pre &r, const C su, const bool checked, const bool meet_only) {
                     if (HASH && s_full) return;  // the sample goes to the direct store
                     const int32_t v = r.v;
                     const unsigned long long want = W::make(v, ep, nl);
@@ -477,7 +486,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                                     break;
                                 }
                                 again = true;
-                            } else if (!xc && !yc && known + s_new[cs] >= cap_new) {  // would overfill
+                            } else if (!xc && !yc && !meet_only && known + s_new[cs] >= cap_new) {  // would overfill
                                 s_full = 1;
                                 break;
                             }
@@ -487,6 +496,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                                 at = ow == want;
                                 break;
                             }
+                            if (meet_only && !yc) break;  // not in the meeting layer: left to a full pass
                             unsigned long long pw, pc;
                             cas_pair(&tab[4 * p + xs], ow, oc, want, count_bits(su), pw, pc);
                             if (pw == ow && pc == oc) {
@@ -503,8 +513,9 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                         // the lanes that claimed together reserve their queue slots and
                         // add their degrees with one shared atomic each (a 64-bit shared
                         // add would be a contended compare-and-swap loop per lane); the
-                        // degree is loaded by the claim's winner alone
-                        const uint32_t dg = (uint32_t)(px[v + 1] - px[v]);  // < 2^31
+                        // degree is loaded by the claim's winner alone, and in a large
+                        // level not at all (lazy_deg)
+                        const uint32_t dg = lazy_deg ? 0u : (uint32_t)(px[v + 1] - px[v]);  // < 2^31
                         const unsigned grp = __activemask();
                         const int lead = __ffs(grp) - 1;
                         const uint32_t dlo = __reduce_add_sync(grp, dg & 0xffffu);
@@ -536,89 +547,106 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                         }
                     }
                 };
-                // every count of the new level is at most the sum of the frontier's counts
-                // loaded so far (fcnt, FP64): below 2^52 no count can reach 2^53, so the
-                // count additions need not wait for their results
-                double fcnt = 0.0;
-                // the level's edges spread evenly over the block, kFlat frontier vertices
-                // at a time (a hub's adjacency is not left to one warp): the block loads
-                // the chunk, a few vertices per thread with their loads in flight
-                // together, and writes its degree prefix sums to shared memory; each
-                // edge then finds its vertex by bisection
-                for (long long c0 = lo; c0 < hi; c0 += kFlat) {
-                    const int fc = (int)(hi - c0 < kFlat ? hi - c0 : kFlat);
-                    {
-                        constexpr int per = kFlat >= BT ? kFlat / BT : 1;
-                        int64_t loc[per];
-                        int64_t tot = 0;
-                        double csum = 0.0;  // the chunk's path counts
-#pragma unroll
-                        for (int r = 0; r < per; ++r) {
-                            const int k = (int)threadIdx.x * per + r;
-                            int64_t dg = 0;
-                            if (k < fc) {
-                                const int2 qe = qx[c0 + k];
-                                const int64_t e0 = px[qe.x];
-                                s_fe[k] = e0;
-                                const C fs = count_of<C>(__ldcg(&tab[4ll * qe.y + xs + 1]));
-                                s_fs[k] = fs;
-                                csum += (double)fs;
-                                dg = px[qe.x + 1] - e0;
+                constexpr int EB = BT == kBiBlock ? kEdgeBatch : kHeavyEdgeBatch;
+                // A level likely to meet the other side (the edges it scans times the
+                // vertices the other side holds reach kMeetOnlyHits n) is first scanned for
+                // the meeting layer alone: only vertices the other side holds are claimed,
+                // which is all a level that meets needs (nothing reads its other
+                // vertices).  If it holds none the level is scanned again in full.
+                bool meet_only = a.gid == nullptr &&
+                                 (double)(x ? cost[1] : cost[0]) * (double)(x ? qhi[0] : qhi[1]) >=
+                                     meet_hits * (double)a.n;
+                for (;;) {
+                    // every count of the new level is at most the sum of the frontier's
+                    // counts loaded so far (fcnt, FP64): below 2^52 no count can reach 2^53,
+                    // so the count additions need not wait for their results
+                    double fcnt = 0.0;
+                    // the level's edges spread evenly over the block, kFlat frontier vertices
+                    // at a time (a hub's adjacency is not left to one warp): the block loads
+                    // the chunk, a few vertices per thread with their loads in flight
+                    // together, and writes its degree prefix sums to shared memory; each
+                    // edge then finds its vertex by bisection
+                    for (long long c0 = lo; c0 < hi; c0 += kFlat) {
+                        const int fc = (int)(hi - c0 < kFlat ? hi - c0 : kFlat);
+                        {
+                            constexpr int per = kFlat >= BT ? kFlat / BT : 1;
+                            int64_t loc[per];
+                            int64_t tot = 0;
+                            double csum = 0.0;  // the chunk's path counts
+    #pragma unroll
+                            for (int r = 0; r < per; ++r) {
+                                const int k = (int)threadIdx.x * per + r;
+                                int64_t dg = 0;
+                                if (k < fc) {
+                                    const int2 qe = qx[c0 + k];
+                                    const int64_t e0 = px[qe.x];
+                                    s_fe[k] = e0;
+                                    const C fs = count_of<C>(__ldcg(&tab[4ll * qe.y + xs + 1]));
+                                    s_fs[k] = fs;
+                                    csum += (double)fs;
+                                    dg = px[qe.x + 1] - e0;
+                                }
+                                loc[r] = tot;
+                                tot += dg;
                             }
-                            loc[r] = tot;
-                            tot += dg;
+                            int64_t incl = tot;
+    #pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int64_t t2 = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += t2;
+                            }
+                            if (lane == 31) s_wsum[warp] = incl;
+    #pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
+                            if (lane == 0) s_wcnt[warp] = csum;
+                            __syncthreads();
+                            int64_t first = incl - tot;
+                            for (int q = 0; q < warp; ++q) first += s_wsum[q];
+                            for (int q = 0; q < nw; ++q) fcnt += s_wcnt[q];
+    #pragma unroll
+                            for (int r = 0; r < per; ++r) {
+                                const int k = (int)threadIdx.x * per + r;
+                                if (k < fc) s_pre[k] = first + loc[r];
+                            }
+                            if (threadIdx.x == BT - 1) s_pre[fc] = first + tot;  // (vertices past fc add 0)
                         }
-                        int64_t incl = tot;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int64_t t2 = __shfl_up_sync(0xffffffffu, incl, o);
-                            if (lane >= o) incl += t2;
-                        }
-                        if (lane == 31) s_wsum[warp] = incl;
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
-                        if (lane == 0) s_wcnt[warp] = csum;
                         __syncthreads();
-                        int64_t first = incl - tot;
-                        for (int q = 0; q < warp; ++q) first += s_wsum[q];
-                        for (int q = 0; q < nw; ++q) fcnt += s_wcnt[q];
-#pragma unroll
-                        for (int r = 0; r < per; ++r) {
-                            const int k = (int)threadIdx.x * per + r;
-                            if (k < fc) s_pre[k] = first + loc[r];
+                        const int64_t E = s_pre[fc];
+                        if (threadIdx.x == 0) ne += (unsigned long long)E;
+                        auto vertex_of = [&](int64_t j) -> int {  // last k with s_pre[k] <= j
+                            int klo = 0, khi = fc - 1;
+                            while (klo < khi) {
+                                const int mid = (klo + khi + 1) >> 1;
+                                if (s_pre[mid] <= j) klo = mid;
+                                else khi = mid - 1;
+                            }
+                            return klo;
+                        };
+                        for (int64_t j = threadIdx.x; j < E; j += (int64_t)EB * BT) {
+                            Pre pr[EB];
+                            int kk[EB];
+                            int32_t vv[EB];
+    #pragma unroll
+                            for (int b = 0; b < EB; ++b) {
+                                const int64_t jb = j + (int64_t)b * BT;
+                                kk[b] = jb < E ? vertex_of(jb) : 0;
+                                vv[b] = jb < E ? ax[s_fe[kk[b]] + (jb - s_pre[kk[b]])] : -1;
+                            }
+    #pragma unroll
+                            for (int b = 0; b < EB; ++b)
+                                if (vv[b] >= 0) pr[b] = prefetch(vv[b]);
+    #pragma unroll
+                            for (int b = 0; b < EB; ++b)
+                                if (vv[b] >= 0) resolve(pr[b], s_fs[kk[b]], fcnt >= 0x1p52, meet_only);
                         }
-                        if (threadIdx.x == BT - 1) s_pre[fc] = first + tot;  // (vertices past fc add 0)
+                        if (c0 + kFlat < hi) __syncthreads();  // the chunk's shared arrays are reused
                     }
+                    if (!meet_only) break;
                     __syncthreads();
-                    const int64_t E = s_pre[fc];
-                    if (threadIdx.x == 0) ne += (unsigned long long)E;
-                    auto vertex_of = [&](int64_t j) -> int {  // last k with s_pre[k] <= j
-                        int klo = 0, khi = fc - 1;
-                        while (klo < khi) {
-                            const int mid = (klo + khi + 1) >> 1;
-                            if (s_pre[mid] <= j) klo = mid;
-                            else khi = mid - 1;
-                        }
-                        return klo;
-                    };
-                    for (int64_t j = threadIdx.x; j < E; j += (int64_t)kEdgeBatch * BT) {
-                        Pre pr[kEdgeBatch];
-                        int kk[kEdgeBatch];
-                        int32_t vv[kEdgeBatch];
-#pragma unroll
-                        for (int b = 0; b < kEdgeBatch; ++b) {
-                            const int64_t jb = j + (int64_t)b * BT;
-                            kk[b] = jb < E ? vertex_of(jb) : 0;
-                            vv[b] = jb < E ? ax[s_fe[kk[b]] + (jb - s_pre[kk[b]])] : -1;
-                        }
-#pragma unroll
-                        for (int b = 0; b < kEdgeBatch; ++b)
-                            if (vv[b] >= 0) pr[b] = prefetch(vv[b]);
-#pragma unroll
-                        for (int b = 0; b < kEdgeBatch; ++b)
-                            if (vv[b] >= 0) resolve(pr[b], s_fs[kk[b]], fcnt >= 0x1p52);
-                    }
-                    if (c0 + kFlat < hi) __syncthreads();  // the chunk's shared arrays are reused
+                    if (s_meet || (HASH && s_full)) break;  // (the same in every thread after the barrier)
+                    meet_only = false;  // no member: the level in full (nothing was claimed)
+                    meet_hits *= 8.0;   // (targets are not uniform: on grids the balls meet late)
+                    __syncthreads();    // the chunk's shared arrays are reloaded
                 }
                 if (a.work && ne) atomicAdd(&s_work[0], ne);
                 smp_edges += ne;
@@ -629,7 +657,24 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1) k_bib
                     break;
                 }
                 const long long nh = hi + s_new[cs];
-                const unsigned long long nc = s_newcost[cs];
+                unsigned long long nc = s_newcost[cs];
+                if (lazy_deg && !s_meet) {
+                    // the new level's degrees, which the claims of this large level did not
+                    // load: most such levels end the search, and then nothing reads them
+                    long long part = 0;
+                    for (long long q = hi + threadIdx.x; q < nh; q += BT) {
+                        const int32_t v = qx[q].x;
+                        part += px[v + 1] - px[v];
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    if (lane == 0) s_wsum[warp] = part;
+                    __syncthreads();
+                    long long tot = 0;
+                    for (int q = 0; q < nw; ++q) tot += s_wsum[q];
+                    nc = (unsigned long long)tot;
+                    __syncthreads();  // s_wsum is reused by the next level's chunks
+                }
                 if (threadIdx.x == 0 && nl + 1 <= (uint32_t)kLvCap) s_lv[x][nl + 1] = (int32_t)nh;
                 if (x) {
                     qlo[1] = hi;
@@ -1091,8 +1136,12 @@ __global__ void __launch_bounds__(1024) k_order_heavy(int32_t *defer, const unsi
     for (int j = threadIdx.x; j < nd; j += blockDim.x) defer[j] = (int32_t)(uint32_t)s_k[j];
 }
 
-constexpr int kHeavyBlock = 1024;                        // threads per sample in the heavy pass
+#ifndef PERCIS_HEAVY_BLOCK
+#define PERCIS_HEAVY_BLOCK 1024
+#endif
+constexpr int kHeavyBlock = PERCIS_HEAVY_BLOCK;  // threads per sample in the heavy pass
 constexpr unsigned long long kDefaultHeavyEdges = 4096;   // a level scanning more edges is heavy
+constexpr int64_t kHubDegree = 16384;          // graphs with a vertex of this degree get a heavy pass by default
 constexpr int64_t kDefaultScratchGiB = 48;  // direct store: one heavy-pass block per SM up to n = 6M
 
 template <bool HASH, int BT>
@@ -1214,9 +1263,12 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->bi_trace.p, 0, sizeof(unsigned long long) * 8 * count, ctx->stream));
         ctx->bi_trace_n = count;
     }
+    // default: a heavy pass only where hubs can make a single level huge (a vertex of
+    // degree >= kHubDegree); without hubs a handed-over sample runs no faster there
     const unsigned long long heavy =
-        ctx->opt.bi_heavy_edges == 0 ? kDefaultHeavyEdges
-                                     : (ctx->opt.bi_heavy_edges < 0 ? 0ull : (unsigned long long)ctx->opt.bi_heavy_edges);
+        ctx->opt.bi_heavy_edges == 0
+            ? (ctx->max_degree >= kHubDegree ? kDefaultHeavyEdges : 0ull)
+            : (ctx->opt.bi_heavy_edges < 0 ? 0ull : (unsigned long long)ctx->opt.bi_heavy_edges);
     const int64_t cd = std::max<int64_t>(count, 1);
     PERCIS_TRY(ensure(ctx, ctx->bi_defer, (sizeof(unsigned long long) + sizeof(int32_t)) * cd + 64,
                       "handed-over samples"));

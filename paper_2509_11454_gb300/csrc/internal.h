@@ -96,7 +96,8 @@ struct percis_ctx {
                                                        // slot epochs, samples handed to the direct store
     int64_t bi_hregion = 0, bi_hslots = 0;
     int bi_h0 = 0, bi_hash_per_sm = 0, bi_heavy_per_sm = 0;
-    bool groups_ready = false;  // grp_lo / grp_hi hold the current states' tie groups
+    bool groups_ready = false;
+    int64_t max_degree = 0;     // largest out- or in-degree of the loaded graph(s)  // grp_lo / grp_hi hold the current states' tie groups
     int64_t bi_handed = 0;   // samples the last first pass handed to the heavy pass
     int64_t phase_span = 0;  // samples of the running phase (direct-store epochs are indexed by sample)
     percis::DevBuf bi_trace;  // per-sample trace of the last bidirectional phase (instrument = 2)

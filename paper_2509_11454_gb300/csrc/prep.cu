@@ -44,6 +44,17 @@ __global__ void k_check_csr(const int64_t *rp, const int32_t *col, int64_t n, in
     }
 }
 
+// Largest row length of a CSR (out- or in-degree) into *out.
+__global__ void k_max_degree(const int64_t *rp, int64_t n, unsigned long long *out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long m = 0ull;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        m = max(m, (unsigned long long)(rp[v + 1] - rp[v]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 __global__ void k_check_states(const double *x, int64_t n, uint32_t *status) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
@@ -832,6 +843,21 @@ percis_status prep_graph(percis_ctx *ctx) {
     if (ctx->directed) {
         PERCIS_TRY(build_transpose(ctx));
         PERCIS_CUDA(ctx, cudaGetLastError());
+    }
+    // the largest out- and in-degree (the bidirectional form's default heavy-level rule)
+    {
+        unsigned long long *md = desc + 2;
+        PERCIS_CUDA(ctx, cudaMemsetAsync(md, 0, sizeof(unsigned long long), ctx->stream));
+        k_max_degree<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, md);
+        PERCIS_CHECK_LAUNCH(ctx, "max degree");
+        if (ctx->directed) {
+            k_max_degree<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->irp.as<int64_t>(), n, md);
+            PERCIS_CHECK_LAUNCH(ctx, "max in-degree");
+        }
+        unsigned long long hm = 0ull;
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(&hm, md, sizeof(hm), cudaMemcpyDeviceToHost, ctx->stream));
+        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx->max_degree = (int64_t)hm;
     }
     ctx->vorder_ready = false;  // built on first use by the batched form
     if (!ctx->skip_diam) {

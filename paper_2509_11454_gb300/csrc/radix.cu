@@ -5,7 +5,7 @@
 // launches: per-tile digit counts (tiles of 4096 pairs), one exclusive scan of
 // the counts laid out digit-major (so the scan gives every (digit, tile) its
 // first output slot), and a scatter in which every tile ranks its pairs among
-// equal digits in index order (per-warp match groups and counters), regroups
+// equal digits in index order (per-warp ballot groups and counters), regroups
 // them by digit in shared memory and writes each digit's run contiguously.
 // Passes run from the lowest digit up, so the result is ordered by the key's
 // sorted bits and, among equal keys, by input position.
@@ -33,23 +33,35 @@ __device__ __forceinline__ int digit_of(K key, int shift) {
     return (int)((key >> shift) & (K)(kRadixBins - 1));
 }
 
-// counts[d * ntiles + tile] = pairs of the tile whose digit is d
+// counts[d * ntiles + tile] = pairs of the tile whose digit is d.  A block takes
+// kCountGroup consecutive tiles at a time, so each digit's counts of the group
+// are written together (one sector instead of one per tile).
+constexpr int kCountGroup = 4;
+
 template <class K>
 __global__ void __launch_bounds__(kRadixBlock) k_radix_count(const K *keys, int64_t n, int shift, int64_t ntiles,
                                                              long long *counts) {
-    __shared__ int s_hist[kRadixBins];
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        for (int d = threadIdx.x; d < kRadixBins; d += kRadixBlock) s_hist[d] = 0;
+    __shared__ int s_hist[kCountGroup][kRadixBins];
+    const int64_t ngroups = (ntiles + kCountGroup - 1) / kCountGroup;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        for (int j = threadIdx.x; j < kCountGroup * kRadixBins; j += kRadixBlock) (&s_hist[0][0])[j] = 0;
         __syncthreads();
-        const int64_t base = tile * kRadixTile;
-#pragma unroll 4
-        for (int r = 0; r < kRadixRounds; ++r) {
-            const int64_t i = base + (int64_t)r * kRadixBlock + threadIdx.x;
-            if (i < n) atomicAdd(&s_hist[digit_of(keys[i], shift)], 1);
+        const int64_t t0 = grp * kCountGroup;
+        for (int g = 0; g < kCountGroup && t0 + g < ntiles; ++g) {
+            const int64_t base = (t0 + g) * kRadixTile;
+            K kk[kRadixRounds];  // the tile's keys loaded first, all in flight together
+#pragma unroll
+            for (int r = 0; r < kRadixRounds; ++r) {
+                const int64_t i = base + (int64_t)r * kRadixBlock + threadIdx.x;
+                kk[r] = i < n ? keys[i] : K(0);
+            }
+#pragma unroll
+            for (int r = 0; r < kRadixRounds; ++r)
+                if (base + (int64_t)r * kRadixBlock + threadIdx.x < n) atomicAdd(&s_hist[g][digit_of(kk[r], shift)], 1);
         }
         __syncthreads();
         for (int d = threadIdx.x; d < kRadixBins; d += kRadixBlock)
-            counts[(int64_t)d * ntiles + tile] = s_hist[d];
+            for (int g = 0; g < kCountGroup && t0 + g < ntiles; ++g) counts[(int64_t)d * ntiles + t0 + g] = s_hist[g][d];
         __syncthreads();
     }
 }
@@ -100,8 +112,15 @@ __global__ void __launch_bounds__(kRadixBlock, 3) k_radix_scatter(const K *kin, 
 #pragma unroll
         for (int r = 0; r < kRounds; ++r) {
             const bool valid = wbase + r * 32 + lane < n;
-            const int d = valid ? digit_of(key[r], shift) : kRadixBins;  // invalid lanes: a group of their own
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int d = valid ? digit_of(key[r], shift) : 0;
+            // lanes with the same digit (and validity): one ballot per digit bit
+            const unsigned vm = __ballot_sync(0xffffffffu, valid);
+            unsigned peers = valid ? vm : ~vm;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1);
+                peers &= ((d >> b) & 1) ? bb : ~bb;
+            }
             const int lead = __ffs(peers) - 1;
             int run = (valid && lane == lead) ? wc[d] : 0;
             run = __shfl_sync(0xffffffffu, run, lead);
