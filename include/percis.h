@@ -193,7 +193,11 @@ percis_status percis_set_options(percis_ctx *ctx, const percis_options *opt);
  * (Algorithm 1): for undirected graphs one BFS from the largest-degree vertex
  * of every component, D = 2*ecc - 1; for directed graphs D = n - 2.
  * on_device: 1 if row_ptr/col are device pointers.  Errors: INVALID (bad
- * sizes or indices), OOM, CUDA.  Synchronises the stream. */
+ * sizes or indices), OOM, CUDA.  Synchronises the stream once the CSR is
+ * validated.  A directed graph's in-adjacency (the stable transpose) is then
+ * built on a second stream of the context, so that percis_set_states can run
+ * meanwhile; every later call that reads it first makes the context's stream
+ * wait for it (no host synchronisation). */
 percis_status percis_load_csr(percis_ctx *ctx, int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
                               int directed, int on_device);
 

@@ -189,6 +189,7 @@ void clear_status(percis_ctx *ctx) {
 // One sampling phase (pair tag = phase, path tag = 2 + phase) of `count`
 // samples.  Leaves pairs, kinds, |I|, paths and cnt in the context.
 percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count, PhaseOut *po) {
+    PERCIS_TRY(wait_graph(ctx));
     int64_t *sources = &po->sources, *batches = &po->batches;
     int32_t *overflow = &po->overflow;
     const int64_t n = ctx->n;
@@ -376,6 +377,7 @@ void percis_destroy(percis_ctx *ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->aux) cudaStreamSynchronize(ctx->aux);
     DevBuf *bufs[] = {&ctx->rp, &ctx->col, &ctx->irp, &ctx->icol, &ctx->x, &ctx->xs, &ctx->perm, &ctx->w, &ctx->ci,
                       &ctx->r, &ctx->Cv, &ctx->lam, &ctx->grp_lo, &ctx->grp_hi, &ctx->dscal, &ctx->ep, &ctx->lvl,
                       &ctx->sigma1, &ctx->qa, &ctx->qb, &ctx->plain_ctl, &ctx->vis, &ctx->fhist, &ctx->sigmaW,
@@ -388,13 +390,16 @@ void percis_destroy(percis_ctx *ctx) {
                       &ctx->ap_tau, &ctx->ap_stamp, &ctx->ap_list, &ctx->plan_dev, &ctx->bi_info,
                       &ctx->bi_queue, &ctx->radix_counts, &ctx->sort_a, &ctx->sort_b,
                       &ctx->table_ctl, &ctx->bi_hent, &ctx->bi_hq, &ctx->bi_hep, &ctx->bi_defer,
-                      &ctx->bi_trace};
+                      &ctx->bi_trace, &ctx->tr_counts, &ctx->tr_scratch, &ctx->graph_info};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->counters.p) cudaFree(ctx->counters.p);
     if (ctx->levdeg.p) cudaFree(ctx->levdeg.p);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     multi_free(ctx);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->aux_go) cudaEventDestroy(ctx->aux_go);
+    if (ctx->graph_ready) cudaEventDestroy(ctx->graph_ready);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -558,6 +563,7 @@ percis_status percis_exact_small(percis_ctx *ctx, double *pc_out, int pc_on_devi
     if ((double)ctx->n * (double)std::max<int64_t>(ctx->nnz, 1) > 1099511627776.0)
         return set_err(ctx, PERCIS_E_TOO_LARGE, "n * nnz above 2^40");
     DeviceGuard g(ctx->device);
+    PERCIS_TRY(wait_graph(ctx));
     double *dst = pc_out;
     PERCIS_TRY(ensure(ctx, ctx->grad_tmp, sizeof(double) * ctx->n, "exact output"));
     if (!pc_on_device) dst = ctx->grad_tmp.as<double>();
@@ -643,6 +649,7 @@ percis_status percis_bfs(percis_ctx *ctx, int32_t source, int32_t target, int32_
     PERCIS_TRY(need_graph(ctx));
     if (source < 0 || source >= ctx->n || target >= ctx->n) return set_err(ctx, PERCIS_E_INVALID, "bad vertex");
     DeviceGuard g(ctx->device);
+    PERCIS_TRY(wait_graph(ctx));
     clear_status(ctx);
     PERCIS_TRY(plain_bfs(ctx, nullptr, nullptr, 0, source, target < 0 ? -1 : target));
     PERCIS_TRY(plain_dist_sigma(ctx, dist, sigma));
@@ -657,6 +664,7 @@ percis_status percis_msbfs(percis_ctx *ctx, int32_t nsrc, const int32_t *sources
     PERCIS_TRY(need_graph(ctx));
     if (nsrc < 1 || nsrc > 512 || !sources) return set_err(ctx, PERCIS_E_INVALID, "need 1..512 sources");
     DeviceGuard g(ctx->device);
+    PERCIS_TRY(wait_graph(ctx));
     {
         int32_t hsrc[512];
         PERCIS_CUDA(ctx, cudaMemcpyAsync(hsrc, sources, sizeof(int32_t) * nsrc, cudaMemcpyDeviceToHost, ctx->stream));

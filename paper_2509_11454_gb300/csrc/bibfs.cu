@@ -70,6 +70,7 @@ constexpr int kHeavyEdgeBatch = PERCIS_HEAVY_EDGE_BATCH;  // the same in the hea
 #ifndef PERCIS_BI_MINB
 #define PERCIS_BI_MINB 4
 #endif
+constexpr unsigned long long kHubDegree = 16384;  // graphs with a vertex of this degree get a heavy pass by default
 constexpr double kMeetOnlyHits = 3.0;  // expected meeting hits above which a level is scanned for them first
 constexpr unsigned long long kLazyDegEdges = 2048;  // levels of this many edges load degrees after
 constexpr uint32_t kHashLevels = 4095;            // levels a hashed word holds (12 bits)
@@ -116,6 +117,8 @@ struct BiArgs {
     unsigned int *n_deferred;
     int32_t sorted;              // every adjacency list strictly increasing (reverse backtrack allowed)
     unsigned long long heavy_edges;  // a level scanning more edges than this hands the sample over (0: never)
+    const unsigned long long *max_degree;  // largest out- or in-degree of the graph (device word)
+    int32_t heavy_auto;          // heavy_edges applies only where max_degree >= kHubDegree
     unsigned long long *trace;   // optional, per sample: {start ns, end ns, edges scanned,
                                  // levels | store << 32 | slot << 33 | heavy pass << 63, end of the
                                  // levels ns, end of the meeting vertex's choice ns, and where a
@@ -264,6 +267,9 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
     if (threadIdx.x == 0) s_tlast = -1;
     unsigned long long n_add = 0ull;
     uint32_t ep_slot = HASH ? a.slot_epoch[slot] : 0u;
+    // default rule: a heavy pass only where hubs can make a single level huge
+    const unsigned long long heavy_lim =
+        (a.heavy_auto && a.max_degree && __ldg(a.max_degree) < kHubDegree) ? 0ull : a.heavy_edges;
 
     for (;;) {
         __syncthreads();
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
                 x = cost[0] <= cost[1] ? 0 : 1;
                 const long long lo = x ? qlo[1] : qlo[0], hi = x ? qhi[1] : qhi[0];
                 const uint32_t nl = (x ? lev[1] : lev[0]) + 1;
-                if (a.heavy_edges && (x ? cost[1] : cost[0]) > a.heavy_edges) {
+                if (heavy_lim && (x ? cost[1] : cost[0]) > heavy_lim) {
                     handed = true;  // a heavy level: the pass with larger blocks takes the sample
                     break;
                 }
@@ -1141,7 +1147,6 @@ __global__ void __launch_bounds__(1024) k_order_heavy(int32_t *defer, const unsi
 #endif
 constexpr int kHeavyBlock = PERCIS_HEAVY_BLOCK;  // threads per sample in the heavy pass
 constexpr unsigned long long kDefaultHeavyEdges = 4096;   // a level scanning more edges is heavy
-constexpr int64_t kHubDegree = 16384;          // graphs with a vertex of this degree get a heavy pass by default
 constexpr int64_t kDefaultScratchGiB = 48;  // direct store: one heavy-pass block per SM up to n = 6M
 
 template <bool HASH, int BT>
@@ -1187,6 +1192,7 @@ BiArgs common_args(percis_ctx *ctx, uint64_t seed, uint32_t tag_path) {
     a.work = ctx->opt.instrument ? ctx->counters.as<unsigned long long>() : nullptr;
     a.trace = ctx->opt.instrument >= 2 ? ctx->bi_trace.as<unsigned long long>() : nullptr;
     a.sorted = ctx->rows_sorted ? 1 : 0;
+    a.max_degree = ctx->graph_info.as<unsigned long long>();
     return a;
 }
 
@@ -1195,8 +1201,8 @@ BiArgs common_args(percis_ctx *ctx, uint64_t seed, uint32_t tag_path) {
 // defer (heavy_edges = 0: none).
 template <int BT>
 percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count, const int32_t *list,
-                          unsigned long long heavy_edges, int32_t *defer, unsigned long long *defer_cost,
-                          unsigned int *n_def) {
+                          unsigned long long heavy_edges, int32_t heavy_auto, int32_t *defer,
+                          unsigned long long *defer_cost, unsigned int *n_def) {
     const int32_t *gid = nullptr;
     const int64_t *vbase = nullptr;
     int64_t nslot = ctx->n;
@@ -1237,6 +1243,7 @@ percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     a.qcap = nslot;
     a.next = ctx->red.as<unsigned long long>();
     a.heavy_edges = heavy_edges;
+    a.heavy_auto = heavy_auto;
     a.deferred = defer;
     a.defer_cost = defer_cost;
     a.n_deferred = n_def;
@@ -1264,11 +1271,12 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         ctx->bi_trace_n = count;
     }
     // default: a heavy pass only where hubs can make a single level huge (a vertex of
-    // degree >= kHubDegree); without hubs a handed-over sample runs no faster there
+    // degree >= kHubDegree, decided on the device from the graph's largest degree);
+    // without hubs a handed-over sample runs no faster there
     const unsigned long long heavy =
-        ctx->opt.bi_heavy_edges == 0
-            ? (ctx->max_degree >= kHubDegree ? kDefaultHeavyEdges : 0ull)
-            : (ctx->opt.bi_heavy_edges < 0 ? 0ull : (unsigned long long)ctx->opt.bi_heavy_edges);
+        ctx->opt.bi_heavy_edges == 0 ? kDefaultHeavyEdges
+                                     : (ctx->opt.bi_heavy_edges < 0 ? 0ull : (unsigned long long)ctx->opt.bi_heavy_edges);
+    const int32_t heavy_auto = ctx->opt.bi_heavy_edges == 0 ? 1 : 0;
     const int64_t cd = std::max<int64_t>(count, 1);
     PERCIS_TRY(ensure(ctx, ctx->bi_defer, (sizeof(unsigned long long) + sizeof(int32_t)) * cd + 64,
                       "handed-over samples"));
@@ -1293,7 +1301,8 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         direct = full * per_slot <= budget;
     }
     if (direct) {
-        PERCIS_TRY(direct_pass<kBiBlock>(ctx, seed, tag_path, count, nullptr, heavy, defer, defer_cost, n_def));
+        PERCIS_TRY(
+            direct_pass<kBiBlock>(ctx, seed, tag_path, count, nullptr, heavy, heavy_auto, defer, defer_cost, n_def));
     } else {
         // default: one table per block that holds the (largest) graph's vertices half
         // full, at most 2^18 entries; else 2^h0 growing 4x up to 2^hmax
@@ -1344,6 +1353,7 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         a.defer_cost = defer_cost;
         a.n_deferred = n_def;
         a.heavy_edges = heavy;
+        a.heavy_auto = heavy_auto;
         launch<true, kBiBlock>(ctx, (int)std::min<int64_t>(slots, std::max<int64_t>(count, 1)), a);
         PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS (hashed)");
     }
@@ -1358,7 +1368,8 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         PERCIS_CHECK_LAUNCH(ctx, "heavy-pass order");
     }
     if (nd > 0)
-        PERCIS_TRY(direct_pass<kHeavyBlock>(ctx, seed, tag_path, (int64_t)nd, defer, 0ull, nullptr, nullptr, nullptr));
+        PERCIS_TRY(
+            direct_pass<kHeavyBlock>(ctx, seed, tag_path, (int64_t)nd, defer, 0ull, 0, nullptr, nullptr, nullptr));
     return PERCIS_OK;
 }
 

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/percis.h"
@@ -96,8 +97,7 @@ struct percis_ctx {
                                                        // slot epochs, samples handed to the direct store
     int64_t bi_hregion = 0, bi_hslots = 0;
     int bi_h0 = 0, bi_hash_per_sm = 0, bi_heavy_per_sm = 0;
-    bool groups_ready = false;
-    int64_t max_degree = 0;     // largest out- or in-degree of the loaded graph(s)  // grp_lo / grp_hi hold the current states' tie groups
+    bool groups_ready = false;  // grp_lo / grp_hi hold the current states' tie groups
     int64_t bi_handed = 0;   // samples the last first pass handed to the heavy pass
     int64_t phase_span = 0;  // samples of the running phase (direct-store epochs are indexed by sample)
     percis::DevBuf bi_trace;  // per-sample trace of the last bidirectional phase (instrument = 2)
@@ -123,6 +123,14 @@ struct percis_ctx {
     // scratch for reductions/scans
     percis::DevBuf scratch, red, status;
     percis::DevBuf radix_counts, sort_a, sort_b;  // radix sort: per-tile digit counts, transpose scratch
+    // The in-adjacency of a directed graph is built on `aux` while the states are
+    // prepared on the context stream; every use of it first makes the context
+    // stream wait for graph_ready (wait_graph).  tr_counts / tr_scratch are the
+    // transpose's own radix counts and scan partials.
+    cudaStream_t aux = nullptr;
+    cudaEvent_t aux_go = nullptr, graph_ready = nullptr;
+    bool graph_pending = false;
+    percis::DevBuf tr_counts, tr_scratch, graph_info;  // graph_info[0]: largest out- or in-degree (u64)
     percis::DevBuf table_ctl;                      // cooperative table scan: barrier, window state, block runs
     int table_grid = 0;                            // co-resident blocks of the table scan (0 = not yet queried)
     percis::DevBuf pc_tmp, grad_tmp, host_pinned;
@@ -131,6 +139,23 @@ struct percis_ctx {
     percis::MultiGraph *multi = nullptr;
     bool skip_diam = false;  // the union of many graphs takes the per-graph bounds
 };
+
+namespace percis {
+// The launches of a scope go to ctx->aux, with the transpose's own radix counts
+// and scan partials; the context's stream and buffers are restored at exit.
+struct AuxScope {
+    percis_ctx *c;
+    explicit AuxScope(percis_ctx *ctx) : c(ctx) { swap(); }
+    ~AuxScope() { swap(); }
+    AuxScope(const AuxScope &) = delete;
+    AuxScope &operator=(const AuxScope &) = delete;
+    void swap() {
+        std::swap(c->stream, c->aux);
+        std::swap(c->radix_counts, c->tr_counts);
+        std::swap(c->scratch, c->tr_scratch);
+    }
+};
+}  // namespace percis
 
 namespace percis {
 
@@ -178,7 +203,8 @@ percis_status build_transpose(percis_ctx *ctx);
 // prep.cu
 percis_status prep_graph(percis_ctx *ctx);  // transpose (directed), validation, VertexDiamUB
 percis_status prep_states(percis_ctx *ctx);  // sort, tables, C_v, lambda, d^
-percis_status prep_groups(percis_ctx *ctx);  // tie groups of the sorted states (backward, on first use)
+percis_status prep_groups(percis_ctx *ctx);
+percis_status wait_graph(percis_ctx *ctx);  // the context stream waits for the in-adjacency  // tie groups of the sorted states (backward, on first use)
 percis_status prep_vorder(percis_ctx *ctx);  // lane order of the batched form (on first use)
 
 // sampler.cu

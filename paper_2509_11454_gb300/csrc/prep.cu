@@ -840,30 +840,50 @@ percis_status prep_graph(percis_ctx *ctx) {
         return set_err(ctx, PERCIS_E_INVALID, "malformed CSR (row_ptr not monotone or column out of range)");
     ctx->rows_sorted = hst[1] == hst[2];  // (the in-lists of a stable transpose are then sorted too)
 
+    // the largest out- and in-degree (read on the device by the bidirectional form's
+    // default heavy-level rule)
+    PERCIS_TRY(ensure(ctx, ctx->graph_info, 64, "graph info"));
+    unsigned long long *md = ctx->graph_info.as<unsigned long long>();
+    PERCIS_CUDA(ctx, cudaMemsetAsync(md, 0, sizeof(unsigned long long), ctx->stream));
+    k_max_degree<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, md);
+    PERCIS_CHECK_LAUNCH(ctx, "max degree");
     if (ctx->directed) {
-        PERCIS_TRY(build_transpose(ctx));
-        PERCIS_CUDA(ctx, cudaGetLastError());
-    }
-    // the largest out- and in-degree (the bidirectional form's default heavy-level rule)
-    {
-        unsigned long long *md = desc + 2;
-        PERCIS_CUDA(ctx, cudaMemsetAsync(md, 0, sizeof(unsigned long long), ctx->stream));
-        k_max_degree<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, md);
-        PERCIS_CHECK_LAUNCH(ctx, "max degree");
-        if (ctx->directed) {
-            k_max_degree<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->irp.as<int64_t>(), n, md);
-            PERCIS_CHECK_LAUNCH(ctx, "max in-degree");
+        // the in-adjacency on the second stream, after everything issued so far (earlier
+        // work may still read the previous one); the states can be prepared meanwhile
+        if (!ctx->aux) {
+            PERCIS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+            PERCIS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->aux_go, cudaEventDisableTiming));
+            PERCIS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->graph_ready, cudaEventDisableTiming));
         }
-        unsigned long long hm = 0ull;
-        PERCIS_CUDA(ctx, cudaMemcpyAsync(&hm, md, sizeof(hm), cudaMemcpyDeviceToHost, ctx->stream));
-        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        ctx->max_degree = (int64_t)hm;
+        PERCIS_CUDA(ctx, cudaEventRecord(ctx->aux_go, ctx->stream));
+        PERCIS_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, ctx->aux_go, 0));
+        percis_status st;
+        {
+            AuxScope scope(ctx);
+            st = build_transpose(ctx);
+            if (st == PERCIS_OK) {
+                k_max_degree<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->irp.as<int64_t>(), n, md);
+                st = cudaGetLastError() == cudaSuccess ? PERCIS_OK : set_err(ctx, PERCIS_E_CUDA, "max in-degree");
+                ctx->launches++;
+            }
+        }
+        PERCIS_TRY(st);
+        PERCIS_CUDA(ctx, cudaEventRecord(ctx->graph_ready, ctx->aux));
+        ctx->graph_pending = true;
     }
     ctx->vorder_ready = false;  // built on first use by the batched form
     if (!ctx->skip_diam) {
         int64_t D = 0;
         PERCIS_TRY(vertex_diam_ub(ctx, &D));
         ctx->vertex_diam = D;
+    }
+    return PERCIS_OK;
+}
+
+percis_status wait_graph(percis_ctx *ctx) {
+    if (ctx->graph_pending) {
+        PERCIS_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->graph_ready, 0));
+        ctx->graph_pending = false;
     }
     return PERCIS_OK;
 }
