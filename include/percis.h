@@ -122,7 +122,8 @@ typedef struct {
     int64_t bi_heavy_edges;   /* a sample whose next level would scan more than this many edges
                                  stops untouched and runs again after the first pass, alone in
                                  a block of 1,024 threads in the direct store (the heavy pass);
-                                 0 = default (4,096), < 0 = never */
+                                 0 = default: 8,192 on graphs with a vertex of degree >= 16,384
+                                 (hubs make single levels huge), else never; < 0 = never */
     int64_t reserved;         /* must be 0 */
 } percis_options;
 

@@ -240,7 +240,7 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
             if (e0) cudaEventRecord(e0, ctx->stream);
             PERCIS_TRY(bidir_phase(ctx, seed, (uint32_t)(2 + phase), count));
             if (e1) cudaEventRecord(e1, ctx->stream);
-            *batches = ctx->bi_handed > 0 ? 2 : 1;
+            *batches = ctx->bi_launches;
         } else {
             int64_t U = 0, valid = 0;
             PERCIS_TRY(group_by_source(ctx, count, &U, &valid));

@@ -84,6 +84,7 @@ struct BiArgs {
     const int64_t *rp, *irp;
     const int32_t *col, *icol;
     int64_t count;               // samples of the phase, or of the list
+    const unsigned int *count_dev;  // when set: the list's length, read on the device
     const int32_t *list;         // sample indices to run (null: 0 .. count-1)
     const int32_t *pair_s, *pair_t;
     int32_t *kind, *ilen;
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
     if (threadIdx.x == 0) s_tlast = -1;
     unsigned long long n_add = 0ull;
     uint32_t ep_slot = HASH ? a.slot_epoch[slot] : 0u;
+    const long long count = a.count_dev ? (long long)__ldcg(a.count_dev) : a.count;
     // default rule: a heavy pass only where hubs can make a single level huge
     const unsigned long long heavy_lim =
         (a.heavy_auto && a.max_degree && __ldg(a.max_degree) < kHubDegree) ? 0ull : a.heavy_edges;
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
         __syncthreads();
         if (threadIdx.x == 0) {
             const long long k = (long long)atomicAdd(a.next, 1ull);
-            s_i = k < a.count ? (a.list ? (long long)a.list[k] : k) : -1ll;
+            s_i = k < count ? (a.list ? (long long)a.list[k] : k) : -1ll;
         }
         __syncthreads();
         const long long i = s_i;
@@ -1111,8 +1113,11 @@ constexpr int kHeavySort = 4096;  // heavy samples ordered by cost when there ar
 
 // The handed-over samples in decreasing cost, ties by sample number: one block,
 // a bitonic sort of (~cost, sample) keys in shared memory.
-__global__ void __launch_bounds__(1024) k_order_heavy(int32_t *defer, const unsigned long long *cost, int nd) {
+__global__ void __launch_bounds__(1024) k_order_heavy(int32_t *defer, const unsigned long long *cost,
+                                                      const unsigned int *n_def) {
     __shared__ unsigned long long s_k[kHeavySort];
+    const int nd = (int)*n_def;
+    if (nd <= 1 || nd > kHeavySort) return;  // (more: taken in the order they came)
     int P = 1;
     while (P < nd) P <<= 1;
     for (int j = threadIdx.x; j < P; j += blockDim.x) {
@@ -1146,7 +1151,7 @@ __global__ void __launch_bounds__(1024) k_order_heavy(int32_t *defer, const unsi
 #define PERCIS_HEAVY_BLOCK 1024
 #endif
 constexpr int kHeavyBlock = PERCIS_HEAVY_BLOCK;  // threads per sample in the heavy pass
-constexpr unsigned long long kDefaultHeavyEdges = 4096;   // a level scanning more edges is heavy
+constexpr unsigned long long kDefaultHeavyEdges = 8192;   // a level scanning more edges is heavy
 constexpr int64_t kDefaultScratchGiB = 48;  // direct store: one heavy-pass block per SM up to n = 6M
 
 template <bool HASH, int BT>
@@ -1202,7 +1207,7 @@ BiArgs common_args(percis_ctx *ctx, uint64_t seed, uint32_t tag_path) {
 template <int BT>
 percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int64_t count, const int32_t *list,
                           unsigned long long heavy_edges, int32_t heavy_auto, int32_t *defer,
-                          unsigned long long *defer_cost, unsigned int *n_def) {
+                          unsigned long long *defer_cost, unsigned int *n_def, const unsigned int *count_dev = nullptr) {
     const int32_t *gid = nullptr;
     const int64_t *vbase = nullptr;
     int64_t nslot = ctx->n;
@@ -1212,7 +1217,7 @@ percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     if (BT == kBiBlock && ctx->opt.bi_blocks_per_sm > 0) per_sm = std::min(per_sm, ctx->opt.bi_blocks_per_sm);
     const int64_t budget = (int64_t)(ctx->opt.bi_scratch_gib > 0 ? ctx->opt.bi_scratch_gib : kDefaultScratchGiB) << 30;
     int64_t slots = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<int64_t>(1, budget / (int64_t)per_slot));
-    slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));
+    slots = std::min<int64_t>(slots, std::max<int64_t>(count, 1));  // (count: at most that many with count_dev)
     if (ctx->bi_slots < slots || ctx->bi_n != nslot) {
         PERCIS_TRY(ensure(ctx, ctx->bi_info, sizeof(unsigned long long) * 4 * nslot * slots, "bidirectional records"));
         PERCIS_TRY(ensure(ctx, ctx->bi_queue, sizeof(int2) * 3 * nslot * slots, "bidirectional queues"));
@@ -1232,6 +1237,7 @@ percis_status direct_pass(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
     PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(unsigned long long), ctx->stream));
     BiArgs a = common_args(ctx, seed, tag_path);
     a.count = count;
+    a.count_dev = count_dev;
     a.list = list;
     a.gid = gid;
     a.vbase = vbase;
@@ -1277,6 +1283,15 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         ctx->opt.bi_heavy_edges == 0 ? kDefaultHeavyEdges
                                      : (ctx->opt.bi_heavy_edges < 0 ? 0ull : (unsigned long long)ctx->opt.bi_heavy_edges);
     const int32_t heavy_auto = ctx->opt.bi_heavy_edges == 0 ? 1 : 0;
+    if (heavy_auto && ctx->max_degree_host < 0) {
+        // the graph's largest degree, once per graph (the in-degree is computed with
+        // the in-adjacency, which this phase waits for anyway)
+        unsigned long long md = 0ull;
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(&md, ctx->graph_info.p, sizeof(md), cudaMemcpyDeviceToHost, ctx->stream));
+        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx->max_degree_host = (int64_t)md;
+    }
+    const bool heavy_on = heavy != 0ull && (!heavy_auto || ctx->max_degree_host >= (int64_t)kHubDegree);
     const int64_t cd = std::max<int64_t>(count, 1);
     PERCIS_TRY(ensure(ctx, ctx->bi_defer, (sizeof(unsigned long long) + sizeof(int32_t)) * cd + 64,
                       "handed-over samples"));
@@ -1357,19 +1372,30 @@ percis_status bidir_phase(percis_ctx *ctx, uint64_t seed, uint32_t tag_path, int
         launch<true, kBiBlock>(ctx, (int)std::min<int64_t>(slots, std::max<int64_t>(count, 1)), a);
         PERCIS_CHECK_LAUNCH(ctx, "bidirectional sigma-BFS (hashed)");
     }
-    unsigned int nd = 0;
-    PERCIS_CUDA(ctx, cudaMemcpyAsync(&nd, n_def, sizeof(nd), cudaMemcpyDeviceToHost, ctx->stream));
-    PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    ctx->bi_handed = nd;
-    if (nd > 1 && nd <= (unsigned)kHeavySort) {
-        // largest first (by the level each was handed over at), so that the
-        // longest samples do not start last
-        k_order_heavy<<<1, 1024, 0, ctx->stream>>>(defer, defer_cost, (int)nd);
+    // The heavy pass.  Where heavy levels hand samples over, it is launched at once
+    // with one block per SM, its sample count read on the device (no host round
+    // trip; blocks without a sample return).  Otherwise only a hashed first pass
+    // can hand samples over (a full table, a side past 4,095 levels): rare, so the
+    // count is read first and the direct store sized for it.
+    ctx->bi_launches = 1;
+    if (heavy_on) {
+        k_order_heavy<<<1, 1024, 0, ctx->stream>>>(defer, defer_cost, n_def);  // largest first
         PERCIS_CHECK_LAUNCH(ctx, "heavy-pass order");
+        PERCIS_TRY(direct_pass<kHeavyBlock>(ctx, seed, tag_path, count, defer, 0ull, 0, nullptr, nullptr, nullptr,
+                                            n_def));
+        ctx->bi_launches = 2;
+    } else if (!direct) {
+        unsigned int nd = 0;
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(&nd, n_def, sizeof(nd), cudaMemcpyDeviceToHost, ctx->stream));
+        PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (nd > 0) {
+            k_order_heavy<<<1, 1024, 0, ctx->stream>>>(defer, defer_cost, n_def);
+            PERCIS_CHECK_LAUNCH(ctx, "heavy-pass order");
+            PERCIS_TRY(
+                direct_pass<kHeavyBlock>(ctx, seed, tag_path, (int64_t)nd, defer, 0ull, 0, nullptr, nullptr, nullptr));
+            ctx->bi_launches = 2;
+        }
     }
-    if (nd > 0)
-        PERCIS_TRY(
-            direct_pass<kHeavyBlock>(ctx, seed, tag_path, (int64_t)nd, defer, 0ull, 0, nullptr, nullptr, nullptr));
     return PERCIS_OK;
 }
 

@@ -98,7 +98,8 @@ struct percis_ctx {
     int64_t bi_hregion = 0, bi_hslots = 0;
     int bi_h0 = 0, bi_hash_per_sm = 0, bi_heavy_per_sm = 0;
     bool groups_ready = false;  // grp_lo / grp_hi hold the current states' tie groups
-    int64_t bi_handed = 0;   // samples the last first pass handed to the heavy pass
+    int bi_launches = 1;         // launches of the last bidirectional phase (first pass, heavy pass)
+    int64_t max_degree_host = -1;  // largest degree of the loaded graph(s), read on first use (-1: not yet)
     int64_t phase_span = 0;  // samples of the running phase (direct-store epochs are indexed by sample)
     percis::DevBuf bi_trace;  // per-sample trace of the last bidirectional phase (instrument = 2)
     int64_t bi_trace_n = 0;

@@ -843,6 +843,7 @@ percis_status prep_graph(percis_ctx *ctx) {
     // the largest out- and in-degree (read on the device by the bidirectional form's
     // default heavy-level rule)
     PERCIS_TRY(ensure(ctx, ctx->graph_info, 64, "graph info"));
+    ctx->max_degree_host = -1;
     unsigned long long *md = ctx->graph_info.as<unsigned long long>();
     PERCIS_CUDA(ctx, cudaMemsetAsync(md, 0, sizeof(unsigned long long), ctx->stream));
     k_max_degree<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, md);

@@ -333,19 +333,24 @@ percis_status build_transpose(percis_ctx *ctx) {
     const size_t kb = sizeof(uint32_t) * (size_t)nnz;
     PERCIS_TRY(ensure(ctx, ctx->sort_a, 2 * kb, "transpose keys"));
     PERCIS_TRY(ensure(ctx, ctx->sort_b, kb, "transpose values"));
-    uint32_t *k1 = ctx->sort_a.as<uint32_t>(), *k2 = k1 + nnz;
-    int32_t *v1 = ctx->icol.as<int32_t>(), *v2 = ctx->sort_b.as<int32_t>();
-    k_edge_rows<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, v1);
-    PERCIS_CHECK_LAUNCH(ctx, "edge rows");
     int bits = 1;
     while (bits < 32 && (1ll << bits) < n) ++bits;
+    // the values ping-pong between icol and the scratch array once per pass: start
+    // them where an even number of passes leaves them in icol (no final copy)
+    const int passes = (bits + 7) / 8;
+    uint32_t *k1 = ctx->sort_a.as<uint32_t>(), *k2 = k1 + nnz;
+    int32_t *v1 = ctx->icol.as<int32_t>(), *v2 = ctx->sort_b.as<int32_t>();
+    if (passes & 1) std::swap(v1, v2);
+    k_edge_rows<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, v1);
+    PERCIS_CHECK_LAUNCH(ctx, "edge rows");
     uint32_t *ok;
     int32_t *ov;
     // the columns (ids >= 0, validated) are the first pass's keys as they are
     PERCIS_TRY(radix_sort_impl<unsigned int>(ctx, k1, v1, k2, v2, nnz, 0, bits, &ok, &ov,
                                              reinterpret_cast<const uint32_t *>(ctx->col.as<int32_t>())));
-    if (ov != v1)
-        PERCIS_CUDA(ctx, cudaMemcpyAsync(v1, ov, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ov != ctx->icol.as<int32_t>())
+        PERCIS_CUDA(ctx, cudaMemcpyAsync(ctx->icol.as<int32_t>(), ov, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
     k_offsets_from_sorted<<<grid_for(ctx, nnz + 1, 256), 256, 0, ctx->stream>>>(ok, nnz, n, ctx->irp.as<int64_t>());
     PERCIS_CHECK_LAUNCH(ctx, "in-CSR offsets");
     return PERCIS_OK;
