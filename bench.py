@@ -66,9 +66,9 @@ DEFAULT_WORKLOAD = "rmat22_beta"
 # DRAM traffic per launch of the dominant kernel from an ncu capture, valid only
 # for the kernel source it was taken on (sha256 of the .cu file) and the workload.
 NCU_TRAFFIC = {
-    # one phase-2 pass (first pass + heavy pass) of a warm-up estimate: 5.256 GB read + 1.313 GB written
-    ("rmat22_beta", "bibfs.cu"): {"sha256": "4e18a0dedb0c2ed78a41b1d6ac788fb74a4477bd7776a6b91f9fe973e5c7f7cc",
-                                  "bytes_per_unit": 6.569e9},
+    # one phase-2 pass (first pass + heavy pass) of a warm-up estimate: 3.923 GB read + 0.736 GB written
+    ("rmat22_beta", "bibfs.cu"): {"sha256": "415ddd39f2e7dba547ba21a06490cb8226c1c079396cee8f44ca5c53fafa7e13",
+                                  "bytes_per_unit": 4.659e9},
 }
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 L2_FLUSH_BYTES = 256 << 20
