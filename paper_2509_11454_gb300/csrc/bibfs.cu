@@ -71,6 +71,7 @@ constexpr int kHeavyEdgeBatch = PERCIS_HEAVY_EDGE_BATCH;  // the same in the hea
 #define PERCIS_BI_MINB 4
 #endif
 constexpr unsigned long long kHubDegree = 16384;  // graphs with a vertex of this degree get a heavy pass by default
+constexpr int kBloomWords = 1 << 15;  // heavy pass: a 2^20-bit filter of the other side's vertices (128 KB)
 constexpr double kMeetOnlyHits = 3.0;  // expected meeting hits above which a level is scanned for them first
 constexpr unsigned long long kLazyDegEdges = 2048;  // levels of this many edges load degrees after
 constexpr uint32_t kHashLevels = 4095;            // levels a hashed word holds (12 bits)
@@ -228,6 +229,17 @@ __device__ __forceinline__ int64_t hash_find(const unsigned long long *tab, int 
 template <class C, bool HASH, int BT>
 __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / BT) k_bibfs(BiArgs a) {
     using W = Word<HASH>;
+    // The heavy pass scans a meeting level against a Bloom filter of the other
+    // side's vertices in shared memory (two hashes of the vertex id): a vertex
+    // whose bits are not both set is not in the meeting layer, and its entry is
+    // never loaded.  (The first pass has no room for it.)
+    constexpr bool BLOOM = BT != kBiBlock;
+    extern __shared__ uint32_t s_bloom[];  // kBloomWords words when BLOOM
+    auto bloom_bits = [](int32_t v, uint32_t &h1, uint32_t &h2) {
+        const unsigned long long m = (unsigned long long)(uint32_t)v * 0x9E3779B97F4A7C15ull;
+        h1 = (uint32_t)(m >> 44);
+        h2 = (uint32_t)(m >> 24) & 0xFFFFFu;
+    };
     constexpr bool FP = std::is_floating_point<C>::value;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nw = BT / 32;
@@ -351,6 +363,8 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
         int x = 0;
         bool met = s != t, handed = false;
         double meet_hits = kMeetOnlyHits;  // expected hits that try a level for its meeting layer first
+        int bloom_side = -1;                // the filter holds side bloom_side's first bloom_n vertices
+        long long bloom_n = 0;
         if (met) {
             met = false;
             for (int it = 0;; ++it) {
@@ -564,6 +578,29 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
                 bool meet_only = a.gid == nullptr &&
                                  (double)(x ? cost[1] : cost[0]) * (double)(x ? qhi[0] : qhi[1]) >=
                                      meet_hits * (double)a.n;
+                if (BLOOM && meet_only) {
+                    // the other side's vertices into the filter (it only grows: a side's
+                    // queue lists every vertex it reached, in order)
+                    const int y = 1 - x;
+                    const long long ny = y ? qhi[1] : qhi[0];
+                    if (bloom_side != y || bloom_n != ny) {
+                        const long long from = bloom_side == y ? bloom_n : 0;
+                        if (from == 0) {
+                            for (int w = threadIdx.x; w < kBloomWords; w += BT) s_bloom[w] = 0u;
+                            __syncthreads();
+                        }
+                        const int2 *qy = y ? queue1 : queue0;
+                        for (long long q = from + threadIdx.x; q < ny; q += BT) {
+                            uint32_t h1, h2;
+                            bloom_bits(qy[q].x, h1, h2);
+                            atomicOr(&s_bloom[h1 >> 5], 1u << (h1 & 31));
+                            atomicOr(&s_bloom[h2 >> 5], 1u << (h2 & 31));
+                        }
+                        __syncthreads();
+                        bloom_side = y;
+                        bloom_n = ny;
+                    }
+                }
                 for (;;) {
                     // every count of the new level is at most the sum of the frontier's
                     // counts loaded so far (fcnt, FP64): below 2^52 no count can reach 2^53,
@@ -639,6 +676,16 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
                                 const int64_t jb = j + (int64_t)b * BT;
                                 kk[b] = jb < E ? vertex_of(jb) : 0;
                                 vv[b] = jb < E ? ax[s_fe[kk[b]] + (jb - s_pre[kk[b]])] : -1;
+                            }
+                            if (BLOOM && meet_only) {
+    #pragma unroll
+                                for (int b = 0; b < EB; ++b) {
+                                    if (vv[b] < 0) continue;
+                                    uint32_t h1, h2;
+                                    bloom_bits(vv[b], h1, h2);
+                                    if (!((s_bloom[h1 >> 5] >> (h1 & 31)) & (s_bloom[h2 >> 5] >> (h2 & 31)) & 1u))
+                                        vv[b] = -1;  // not a member of the other side
+                                }
                             }
     #pragma unroll
                             for (int b = 0; b < EB; ++b)
@@ -1158,7 +1205,11 @@ template <bool HASH, int BT>
 int blocks_per_sm(int *cache) {
     if (!*cache) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs<unsigned long long, HASH, BT>, BT, 0) !=
+        const int dyn = BT == kBiBlock ? 0 : (int)(sizeof(uint32_t) * kBloomWords);
+        if (dyn)
+            cudaFuncSetAttribute(k_bibfs<unsigned long long, HASH, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dyn);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs<unsigned long long, HASH, BT>, BT, dyn) !=
                 cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
@@ -1171,8 +1222,14 @@ int blocks_per_sm(int *cache) {
 
 template <bool HASH, int BT>
 void launch(percis_ctx *ctx, int grid, const BiArgs &a) {
-    if (ctx->sigma_mode == 2) k_bibfs<double, HASH, BT><<<grid, BT, 0, ctx->stream>>>(a);
-    else k_bibfs<unsigned long long, HASH, BT><<<grid, BT, 0, ctx->stream>>>(a);
+    // the heavy pass's Bloom filter (dynamic shared memory)
+    const int dyn = BT == kBiBlock ? 0 : (int)(sizeof(uint32_t) * kBloomWords);
+    if (dyn) {
+        cudaFuncSetAttribute(k_bibfs<double, HASH, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(k_bibfs<unsigned long long, HASH, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    }
+    if (ctx->sigma_mode == 2) k_bibfs<double, HASH, BT><<<grid, BT, dyn, ctx->stream>>>(a);
+    else k_bibfs<unsigned long long, HASH, BT><<<grid, BT, dyn, ctx->stream>>>(a);
 }
 
 BiArgs common_args(percis_ctx *ctx, uint64_t seed, uint32_t tag_path) {
