@@ -72,7 +72,14 @@ constexpr int kHeavyEdgeBatch = PERCIS_HEAVY_EDGE_BATCH;  // the same in the hea
 #endif
 constexpr unsigned long long kHubDegree = 16384;  // graphs with a vertex of this degree get a heavy pass by default
 constexpr int kBloomWords = 1 << 15;  // heavy pass: a 2^20-bit filter of the other side's vertices (128 KB)
-constexpr double kMeetOnlyHits = 3.0;  // expected meeting hits above which a level is scanned for them first
+// expected meeting hits above which a level is scanned for its meeting layer
+// first: in the first pass, and in the heavy pass (whose filter makes a scan
+// that finds no member cheap)
+constexpr double kMeetOnlyHits = 3.0;
+#ifndef PERCIS_MEET_HITS_BLOOM
+#define PERCIS_MEET_HITS_BLOOM 0.02
+#endif
+constexpr double kMeetOnlyHitsBloom = PERCIS_MEET_HITS_BLOOM;
 constexpr unsigned long long kLazyDegEdges = 2048;  // levels of this many edges load degrees after
 constexpr uint32_t kHashLevels = 4095;            // levels a hashed word holds (12 bits)
 constexpr uint32_t kHashEpochs = (1u << 20) - 1;  // epochs a hashed word holds (20 bits)
@@ -362,7 +369,9 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
                                       (unsigned long long)(a.irp[t + 1] - a.irp[t])};
         int x = 0;
         bool met = s != t, handed = false;
-        double meet_hits = kMeetOnlyHits;  // expected hits that try a level for its meeting layer first
+        // expected hits that try a level for its meeting layer first (lower where the
+        // filter makes a scan that finds no member cheap)
+        double meet_hits = BLOOM ? kMeetOnlyHitsBloom : kMeetOnlyHits;
         int bloom_side = -1;                // the filter holds side bloom_side's first bloom_n vertices
         long long bloom_n = 0;
         if (met) {
