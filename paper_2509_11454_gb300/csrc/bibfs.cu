@@ -72,10 +72,19 @@ constexpr int kHeavyEdgeBatch = PERCIS_HEAVY_EDGE_BATCH;  // the same in the hea
 #endif
 constexpr unsigned long long kHubDegree = 16384;  // graphs with a vertex of this degree get a heavy pass by default
 constexpr int kBloomWords = 1 << 15;  // heavy pass: a 2^20-bit filter of the other side's vertices (128 KB)
+#ifndef PERCIS_FIRST_BLOOM
+#define PERCIS_FIRST_BLOOM 0
+#endif
+#ifndef PERCIS_MEET_HITS_FIRST
+#define PERCIS_MEET_HITS_FIRST 3.0
+#endif
+// first pass: none by default (a 2^17-bit filter, 16 KB beside four blocks per SM,
+// measured neutral on R-MAT 22 and Barabasi-Albert graphs)
+constexpr int kBloomWordsFirst = PERCIS_FIRST_BLOOM ? (1 << 12) : 0;
 // expected meeting hits above which a level is scanned for its meeting layer
 // first: in the first pass, and in the heavy pass (whose filter makes a scan
 // that finds no member cheap)
-constexpr double kMeetOnlyHits = 3.0;
+constexpr double kMeetOnlyHits = PERCIS_MEET_HITS_FIRST;
 #ifndef PERCIS_MEET_HITS_BLOOM
 #define PERCIS_MEET_HITS_BLOOM 0.02
 #endif
@@ -240,12 +249,14 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
     // side's vertices in shared memory (two hashes of the vertex id): a vertex
     // whose bits are not both set is not in the meeting layer, and its entry is
     // never loaded.  (The first pass has no room for it.)
-    constexpr bool BLOOM = BT != kBiBlock;
-    extern __shared__ uint32_t s_bloom[];  // kBloomWords words when BLOOM
+    constexpr bool BLOOM = BT != kBiBlock || kBloomWordsFirst > 0;
+    constexpr int NBW = BT == kBiBlock ? kBloomWordsFirst : kBloomWords;  // filter words
+    constexpr int NBB = BT == kBiBlock ? 17 : 20;                          // filter bits (log2)
+    extern __shared__ uint32_t s_bloom[];  // NBW words
     auto bloom_bits = [](int32_t v, uint32_t &h1, uint32_t &h2) {
         const unsigned long long m = (unsigned long long)(uint32_t)v * 0x9E3779B97F4A7C15ull;
-        h1 = (uint32_t)(m >> 44);
-        h2 = (uint32_t)(m >> 24) & 0xFFFFFu;
+        h1 = (uint32_t)(m >> (64 - NBB));
+        h2 = (uint32_t)(m >> 24) & ((1u << NBB) - 1u);
     };
     constexpr bool FP = std::is_floating_point<C>::value;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -371,7 +382,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
         bool met = s != t, handed = false;
         // expected hits that try a level for its meeting layer first (lower where the
         // filter makes a scan that finds no member cheap)
-        double meet_hits = BLOOM ? kMeetOnlyHitsBloom : kMeetOnlyHits;
+        double meet_hits = BT != kBiBlock ? kMeetOnlyHitsBloom : kMeetOnlyHits;
         int bloom_side = -1;                // the filter holds side bloom_side's first bloom_n vertices
         long long bloom_n = 0;
         if (met) {
@@ -595,7 +606,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
                     if (bloom_side != y || bloom_n != ny) {
                         const long long from = bloom_side == y ? bloom_n : 0;
                         if (from == 0) {
-                            for (int w = threadIdx.x; w < kBloomWords; w += BT) s_bloom[w] = 0u;
+                            for (int w = threadIdx.x; w < NBW; w += BT) s_bloom[w] = 0u;
                             __syncthreads();
                         }
                         const int2 *qy = y ? queue1 : queue0;
@@ -1214,8 +1225,8 @@ template <bool HASH, int BT>
 int blocks_per_sm(int *cache) {
     if (!*cache) {
         int per_sm = 0;
-        const int dyn = BT == kBiBlock ? 0 : (int)(sizeof(uint32_t) * kBloomWords);
-        if (dyn)
+        const int dyn = (int)(sizeof(uint32_t) * (BT == kBiBlock ? kBloomWordsFirst : kBloomWords));
+        if (dyn > 48 * 1024)
             cudaFuncSetAttribute(k_bibfs<unsigned long long, HASH, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  dyn);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bibfs<unsigned long long, HASH, BT>, BT, dyn) !=
@@ -1232,8 +1243,8 @@ int blocks_per_sm(int *cache) {
 template <bool HASH, int BT>
 void launch(percis_ctx *ctx, int grid, const BiArgs &a) {
     // the heavy pass's Bloom filter (dynamic shared memory)
-    const int dyn = BT == kBiBlock ? 0 : (int)(sizeof(uint32_t) * kBloomWords);
-    if (dyn) {
+    const int dyn = (int)(sizeof(uint32_t) * (BT == kBiBlock ? kBloomWordsFirst : kBloomWords));
+    if (dyn > 48 * 1024) {
         cudaFuncSetAttribute(k_bibfs<double, HASH, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         cudaFuncSetAttribute(k_bibfs<unsigned long long, HASH, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     }
