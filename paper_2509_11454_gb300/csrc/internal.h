@@ -132,6 +132,7 @@ struct percis_ctx {
     cudaEvent_t aux_go = nullptr, graph_ready = nullptr;
     bool graph_pending = false;
     percis::DevBuf tr_counts, tr_scratch, graph_info;  // graph_info[0]: largest out- or in-degree (u64)
+    uint32_t *tr_sorted_keys = nullptr;  // the sorted targets between transpose_sort and transpose_finish
     percis::DevBuf table_ctl;                      // cooperative table scan: barrier, window state, block runs
     int table_grid = 0;                            // co-resident blocks of the table scan (0 = not yet queried)
     percis::DevBuf pc_tmp, grad_tmp, host_pinned;
@@ -199,7 +200,8 @@ int grid_for(percis_ctx *ctx, int64_t work, int block);
 // (irp, icol) of the loaded directed CSR, every in-list ordered by source
 percis_status radix_sort_u64(percis_ctx *ctx, uint64_t *keys, int32_t *vals, uint64_t *tk, int32_t *tv, int64_t n,
                              int lo_bit, int bits);
-percis_status build_transpose(percis_ctx *ctx);
+percis_status transpose_sort(percis_ctx *ctx);    // in-adjacency: edges sorted by target (valid row_ptr)
+percis_status transpose_finish(percis_ctx *ctx);  // in-adjacency: offsets (valid columns)
 
 // prep.cu
 percis_status prep_graph(percis_ctx *ctx);  // transpose (directed), validation, VertexDiamUB

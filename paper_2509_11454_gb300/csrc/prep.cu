@@ -12,36 +12,51 @@ namespace {
 
 // ------------------------------------------------------------- validation
 
-// Validation, and whether every row is strictly increasing: desc[0] counts the
-// positions e >= 1 with col[e] <= col[e-1], desc[1] those among them that start
-// a row; the rows are strictly sorted when the counts agree.
-__global__ void k_check_csr(const int64_t *rp, const int32_t *col, int64_t n, int64_t nnz, uint32_t *status,
-                            unsigned long long *desc) {
-    // counts are summed per warp: one atomic per warp and loop instead of per
-    // position (most rows of a sorted CSR start below the previous row's end)
+// Validation, and whether every row is strictly increasing, in two kernels so
+// that the in-adjacency can be built while the columns are checked: the rows
+// (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz; desc[1] counts the rows
+// whose first column is <= the previous row's last; the largest row length into
+// *maxdeg), then the columns (in [0, n); desc[0] counts the positions e >= 1
+// with col[e] <= col[e-1]).  The rows are strictly sorted when the counts agree.
+// Counts are summed per warp: one atomic per warp and loop.
+__global__ void k_check_rows(const int64_t *rp, const int32_t *col, int64_t n, int64_t nnz, uint32_t *status,
+                             unsigned long long *desc, unsigned long long *maxdeg) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    unsigned long long d0 = 0, d1 = 0;
+    unsigned long long d1 = 0, m = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const int64_t r0 = rp[v], r1 = rp[v + 1];
-        if (r0 > r1 || r0 < 0 || r1 > nnz) atomicOr(status, 1u);
-        else if (r0 > 0 && r0 < r1 && col[r0] <= col[r0 - 1]) ++d1;
+        if (r0 > r1 || r0 < 0 || r1 > nnz) {
+            atomicOr(status, 1u);
+        } else {
+            m = max(m, (unsigned long long)(r1 - r0));
+            if (r0 > 0 && r0 < r1 && col[r0] <= col[r0 - 1]) ++d1;
+        }
         if (v == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, 1u);
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        d1 += __shfl_xor_sync(0xffffffffu, d1, off);
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    }
+    if (lane == 0) {
+        if (d1) atomicAdd(&desc[1], d1);
+        if (m) atomicMax(maxdeg, m);
+    }
+}
+
+__global__ void k_check_cols(const int32_t *col, int64_t n, int64_t nnz, uint32_t *status, unsigned long long *desc) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    unsigned long long d0 = 0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
         const int32_t c = col[e];
         if (c < 0 || (int64_t)c >= n) atomicOr(status, 1u);
         if (e > 0 && c <= col[e - 1]) ++d0;
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        d0 += __shfl_xor_sync(0xffffffffu, d0, off);
-        d1 += __shfl_xor_sync(0xffffffffu, d1, off);
-    }
-    if (lane == 0) {
-        if (d0) atomicAdd(&desc[0], d0);
-        if (d1) atomicAdd(&desc[1], d1);
-    }
+    for (int off = 16; off > 0; off >>= 1) d0 += __shfl_xor_sync(0xffffffffu, d0, off);
+    if (lane == 0 && d0) atomicAdd(&desc[0], d0);
 }
 
 // Largest row length of a CSR (out- or in-degree) into *out.
@@ -830,27 +845,25 @@ percis_status prep_graph(percis_ctx *ctx) {
     uint32_t *st = ctx->status.as<uint32_t>();
     PERCIS_CUDA(ctx, cudaMemsetAsync(st, 0, 64, ctx->stream));
     unsigned long long *desc = reinterpret_cast<unsigned long long *>(ctx->status.as<char>() + 8);
-    k_check_csr<<<grid_for(ctx, std::max(n, nnz), 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(),
-                                                                             ctx->col.as<int32_t>(), n, nnz, st, desc);
-    PERCIS_CHECK_LAUNCH(ctx, "check csr");
-    unsigned long long hst[3] = {0ull, 0ull, 0ull};
-    PERCIS_CUDA(ctx, cudaMemcpyAsync(hst, st, sizeof(hst), cudaMemcpyDeviceToHost, ctx->stream));
-    PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if ((uint32_t)hst[0])
-        return set_err(ctx, PERCIS_E_INVALID, "malformed CSR (row_ptr not monotone or column out of range)");
-    ctx->rows_sorted = hst[1] == hst[2];  // (the in-lists of a stable transpose are then sorted too)
-
     // the largest out- and in-degree (read on the device by the bidirectional form's
     // default heavy-level rule)
     PERCIS_TRY(ensure(ctx, ctx->graph_info, 64, "graph info"));
     ctx->max_degree_host = -1;
     unsigned long long *md = ctx->graph_info.as<unsigned long long>();
     PERCIS_CUDA(ctx, cudaMemsetAsync(md, 0, sizeof(unsigned long long), ctx->stream));
-    k_max_degree<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), n, md);
-    PERCIS_CHECK_LAUNCH(ctx, "max degree");
+    k_check_rows<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->rp.as<int64_t>(), ctx->col.as<int32_t>(), n,
+                                                                 nnz, st, desc, md);
+    PERCIS_CHECK_LAUNCH(ctx, "check rows");
+    unsigned long long hst[3] = {0ull, 0ull, 0ull};
+    PERCIS_CUDA(ctx, cudaMemcpyAsync(hst, st, sizeof(hst), cudaMemcpyDeviceToHost, ctx->stream));
+    PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if ((uint32_t)hst[0]) return set_err(ctx, PERCIS_E_INVALID, "malformed CSR (row_ptr not monotone)");
     if (ctx->directed) {
-        // the in-adjacency on the second stream, after everything issued so far (earlier
-        // work may still read the previous one); the states can be prepared meanwhile
+        // the in-adjacency's sort on the second stream, after everything issued so far
+        // (earlier work may still read the previous one), while the columns are checked
+        // here; the sort's digits are masked, so it reads and writes in bounds whatever
+        // the columns hold.  Its last step (the offsets, indexed by column) waits for the
+        // check.  The states can be prepared on this stream meanwhile.
         if (!ctx->aux) {
             PERCIS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
             PERCIS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->aux_go, cudaEventDisableTiming));
@@ -858,17 +871,30 @@ percis_status prep_graph(percis_ctx *ctx) {
         }
         PERCIS_CUDA(ctx, cudaEventRecord(ctx->aux_go, ctx->stream));
         PERCIS_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, ctx->aux_go, 0));
-        percis_status st;
+    }
+    // the column check first, so that it starts before the sort's launches are issued
+    k_check_cols<<<grid_for(ctx, nnz, 256), 256, 0, ctx->stream>>>(ctx->col.as<int32_t>(), n, nnz, st, desc);
+    PERCIS_CHECK_LAUNCH(ctx, "check columns");
+    if (ctx->directed) {
+        AuxScope scope(ctx);
+        PERCIS_TRY(transpose_sort(ctx));
+    }
+    PERCIS_CUDA(ctx, cudaMemcpyAsync(hst, st, sizeof(hst), cudaMemcpyDeviceToHost, ctx->stream));
+    PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if ((uint32_t)hst[0]) return set_err(ctx, PERCIS_E_INVALID, "malformed CSR (column out of range)");
+    ctx->rows_sorted = hst[1] == hst[2];  // (the in-lists of a stable transpose are then sorted too)
+    if (ctx->directed) {
+        percis_status tst;
         {
             AuxScope scope(ctx);
-            st = build_transpose(ctx);
-            if (st == PERCIS_OK) {
+            tst = transpose_finish(ctx);
+            if (tst == PERCIS_OK) {
                 k_max_degree<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(ctx->irp.as<int64_t>(), n, md);
-                st = cudaGetLastError() == cudaSuccess ? PERCIS_OK : set_err(ctx, PERCIS_E_CUDA, "max in-degree");
+                tst = cudaGetLastError() == cudaSuccess ? PERCIS_OK : set_err(ctx, PERCIS_E_CUDA, "max in-degree");
                 ctx->launches++;
             }
         }
-        PERCIS_TRY(st);
+        PERCIS_TRY(tst);
         PERCIS_CUDA(ctx, cudaEventRecord(ctx->graph_ready, ctx->aux));
         ctx->graph_pending = true;
     }

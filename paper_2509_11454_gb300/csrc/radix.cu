@@ -321,7 +321,10 @@ percis_status radix_sort_u64(percis_ctx *ctx, uint64_t *keys, int32_t *vals, uin
 
 // In-adjacency of the loaded directed CSR: irp (int64[n+1]) and icol (int32[nnz],
 // every in-list ordered by source).
-percis_status build_transpose(percis_ctx *ctx) {
+// The in-adjacency in two steps: the sort of the edges by target (valid row
+// offsets needed; any column values are sorted in bounds), then the offsets
+// (valid columns needed).
+percis_status transpose_sort(percis_ctx *ctx) {
     const int64_t n = ctx->n, nnz = ctx->nnz;
     PERCIS_TRY(ensure(ctx, ctx->irp, sizeof(int64_t) * (n + 1), "in-CSR offsets"));
     PERCIS_TRY(ensure(ctx, ctx->icol, sizeof(int32_t) * std::max<int64_t>(nnz, 1), "in-CSR columns"));
@@ -345,13 +348,21 @@ percis_status build_transpose(percis_ctx *ctx) {
     PERCIS_CHECK_LAUNCH(ctx, "edge rows");
     uint32_t *ok;
     int32_t *ov;
-    // the columns (ids >= 0, validated) are the first pass's keys as they are
+    // the columns are the first pass's keys as they are
     PERCIS_TRY(radix_sort_impl<unsigned int>(ctx, k1, v1, k2, v2, nnz, 0, bits, &ok, &ov,
                                              reinterpret_cast<const uint32_t *>(ctx->col.as<int32_t>())));
     if (ov != ctx->icol.as<int32_t>())
         PERCIS_CUDA(ctx, cudaMemcpyAsync(ctx->icol.as<int32_t>(), ov, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice,
                                          ctx->stream));
-    k_offsets_from_sorted<<<grid_for(ctx, nnz + 1, 256), 256, 0, ctx->stream>>>(ok, nnz, n, ctx->irp.as<int64_t>());
+    ctx->tr_sorted_keys = ok;
+    return PERCIS_OK;
+}
+
+percis_status transpose_finish(percis_ctx *ctx) {
+    const int64_t n = ctx->n, nnz = ctx->nnz;
+    if (nnz == 0) return PERCIS_OK;  // (irp zeroed by transpose_sort)
+    k_offsets_from_sorted<<<grid_for(ctx, nnz + 1, 256), 256, 0, ctx->stream>>>(ctx->tr_sorted_keys, nnz, n,
+                                                                               ctx->irp.as<int64_t>());
     PERCIS_CHECK_LAUNCH(ctx, "in-CSR offsets");
     return PERCIS_OK;
 }
