@@ -167,14 +167,59 @@ percis_status need_states(percis_ctx *ctx) {
     return PERCIS_OK;
 }
 
+// Pinned host words (status at 0, phase statistics at 64): asynchronous copies
+// there complete with the stream, so one synchronisation reads them all.
+char *host_mirror(percis_ctx *ctx) {
+    if (!ctx->hmirror && cudaMallocHost(&ctx->hmirror, 256) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->hmirror = nullptr;
+    }
+    return static_cast<char *>(ctx->hmirror);
+}
+
 uint32_t read_status(percis_ctx *ctx) {
+    char *hm = host_mirror(ctx);
     uint32_t st = 0, st2 = 0;
+    uint32_t *d1 = hm ? reinterpret_cast<uint32_t *>(hm) : &st, *d2 = hm ? reinterpret_cast<uint32_t *>(hm) + 1 : &st2;
+    *d1 = 0u;
+    *d2 = 0u;
     if (ctx->ms_ctl.p)
-        cudaMemcpyAsync(&st, &ctx->ms_ctl.as<MsCtl>()->status, 4, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(d1, &ctx->ms_ctl.as<MsCtl>()->status, 4, cudaMemcpyDeviceToHost, ctx->stream);
     if (ctx->plain_ctl.p)
-        cudaMemcpyAsync(&st2, &ctx->plain_ctl.as<PlainCtl>()->status, 4, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(d2, &ctx->plain_ctl.as<PlainCtl>()->status, 4, cudaMemcpyDeviceToHost, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
-    return st | st2;
+    return *d1 | *d2;
+}
+
+// The phase statistics kernel and the copy of its result to the host mirror
+// (offset 64), without synchronising; want_pmax adds the max of lambda cnt over the vertices.
+percis_status issue_phase_stats(percis_ctx *ctx, int64_t count, bool want_pmax) {
+    PERCIS_TRY(ensure(ctx, ctx->red, sizeof(PhaseStats), "stats"));
+    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(PhaseStats), ctx->stream));
+    const int64_t nv = want_pmax ? ctx->n : 0;
+    k_phase_stats<<<grid_for(ctx, std::max<int64_t>(std::max<int64_t>(count, nv), 1), 256), 256, 0, ctx->stream>>>(
+        count, ctx->kind.as<int32_t>(), ctx->ilen.as<int32_t>(), nv, ctx->lam.as<double>(),
+        ctx->cnt.as<unsigned long long>(), ctx->opt.estimator == 1 ? ctx->acc_ap.as<double>() : nullptr,
+        ctx->red.as<PhaseStats>());
+    PERCIS_CHECK_LAUNCH(ctx, "phase stats");
+    char *hm = host_mirror(ctx);
+    if (!hm) return set_err(ctx, PERCIS_E_OOM, "pinned host words");
+    PERCIS_CUDA(ctx, cudaMemcpyAsync(hm + 64, ctx->red.p, sizeof(PhaseStats), cudaMemcpyDeviceToHost, ctx->stream));
+    return PERCIS_OK;
+}
+
+// The statistics copied by issue_phase_stats, once the stream has synchronised;
+// pmax = max lambda cnt / ell (the IEEE division applied once to the largest product).
+void read_phase_stats(percis_ctx *ctx, double ell, PhaseOut *po) {
+    PhaseStats hs;
+    memcpy(&hs, host_mirror(ctx) + 64, sizeof(hs));
+    po->s1 = hs.s1;
+    po->s2 = hs.s2;
+    po->zero_w = hs.zero_w;
+    po->unreach = hs.unreach;
+    double pm;
+    memcpy(&pm, &hs.pmax_bits, sizeof(pm));
+    po->pmax = pm / ell;
 }
 
 // Reset status words and grid-barrier counters (a launch that gave up on a
@@ -247,6 +292,7 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
             *sources = U;
             if (U > 0) PERCIS_TRY(batched_phase(ctx, seed, (uint32_t)(2 + phase), count, U, batches));
         }
+        if (po->want_stats) PERCIS_TRY(issue_phase_stats(ctx, count, po->stats_pmax));
         const uint32_t st = read_status(ctx);
         PERCIS_CUDA(ctx, cudaGetLastError());
         if (st & DEV_TIMEOUT) return set_err(ctx, PERCIS_E_TIMEOUT, "device wait exceeded its budget");
@@ -281,6 +327,7 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
         *overflow = (st & DEV_SIGMA_OVERFLOW) ? 1 : 0;
         po->bfs_ms = events_elapsed_ms(ctx);
         po->bfs_launches = *batches;
+        if (po->want_stats) read_phase_stats(ctx, (double)count, po);
         if (ctx->opt.instrument && ctx->opt.form != PERCIS_FORM_PLAIN) {
             unsigned long long hc[8];
             PERCIS_CUDA(ctx, cudaMemcpy(hc, ctx->counters.p, sizeof(hc), cudaMemcpyDeviceToHost));
@@ -295,31 +342,6 @@ percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count
     return set_err(ctx, PERCIS_E_TOO_LARGE, "phase could not be sized (levels/arena)");
 }
 
-namespace {
-
-// Sums over the phase's samples and, when want_pmax, max_v lambda_v cnt_v / l
-// (as pmax_bits: the division applied on the host to the largest product).
-percis_status phase_stats(percis_ctx *ctx, int64_t count, double ell, bool want_pmax, PhaseStats *hs) {
-    PERCIS_TRY(ensure(ctx, ctx->red, sizeof(PhaseStats), "stats"));
-    PERCIS_CUDA(ctx, cudaMemsetAsync(ctx->red.p, 0, sizeof(PhaseStats), ctx->stream));
-    const int64_t nv = want_pmax ? ctx->n : 0;
-    k_phase_stats<<<grid_for(ctx, std::max<int64_t>(std::max<int64_t>(count, nv), 1), 256), 256, 0, ctx->stream>>>(
-        count, ctx->kind.as<int32_t>(), ctx->ilen.as<int32_t>(), nv, ctx->lam.as<double>(),
-        ctx->cnt.as<unsigned long long>(), ctx->opt.estimator == 1 ? ctx->acc_ap.as<double>() : nullptr,
-        ctx->red.as<PhaseStats>());
-    PERCIS_CHECK_LAUNCH(ctx, "phase stats");
-    PERCIS_CUDA(ctx, cudaMemcpyAsync(hs, ctx->red.p, sizeof(PhaseStats), cudaMemcpyDeviceToHost, ctx->stream));
-    PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (want_pmax) {
-        double pm;
-        memcpy(&pm, &hs->pmax_bits, sizeof(pm));
-        pm = pm / ell;  // IEEE division, as on the device: max_v fl(fl(lambda_v cnt_v) / l)
-        memcpy(&hs->pmax_bits, &pm, sizeof(pm));
-    }
-    return PERCIS_OK;
-}
-
-}  // namespace
 }  // namespace percis
 
 using namespace percis;
@@ -398,6 +420,7 @@ void percis_destroy(percis_ctx *ctx) {
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     multi_free(ctx);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->hmirror) cudaFreeHost(ctx->hmirror);
     if (ctx->aux_go) cudaEventDestroy(ctx->aux_go);
     if (ctx->graph_ready) cudaEventDestroy(ctx->graph_ready);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -497,7 +520,6 @@ percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_
     const bool di = ctx->opt.data_independent != 0;
     const int64_t ell1 = di ? 0 : (ctx->opt.ell1 > 0 ? ctx->opt.ell1 : ell1_default(eps, delta));
     inf.ell1 = ell1;
-    PhaseStats hs{};
     auto record = [&](int ph, const PhaseOut &po) {
         inf.sources[ph] = po.sources;
         inf.batches[ph] = po.batches;
@@ -506,18 +528,21 @@ percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_
         inf.bfs_launches[ph] = po.bfs_launches;
         for (int k = 0; k < 8; ++k) inf.work[ph][k] = po.work[k];
     };
+    int64_t s1 = 0, s2 = 0;
+    double p1_max = 0.0;
     if (!di) {
         PhaseOut po;
+        po.want_stats = po.stats_pmax = true;  // read back with the phase's status
         PERCIS_TRY(run_phase(ctx, seed, 0, ell1, &po));
         record(0, po);
-        PERCIS_TRY(phase_stats(ctx, ell1, (double)ell1, true, &hs));
-        inf.zero_weight[0] = hs.zero_w;
-        inf.unreachable[0] = hs.unreach;
-        inf.sum_internal[0] = hs.s1;
+        inf.zero_weight[0] = po.zero_w;
+        inf.unreachable[0] = po.unreach;
+        inf.sum_internal[0] = po.s1;
+        s1 = po.s1;
+        s2 = po.s2;
+        p1_max = po.pmax;
     }
-    double p1_max = 0.0;
-    memcpy(&p1_max, &hs.pmax_bits, sizeof(double));
-    const Bounds b = compute_bounds(eps, delta, ctx->dhat_host, D, ell1, hs.s1, hs.s2, p1_max, di ? 1 : 0);
+    const Bounds b = compute_bounds(eps, delta, ctx->dhat_host, D, ell1, s1, s2, p1_max, di ? 1 : 0);
     inf.rho_tilde = b.rho_tilde;
     inf.Lambda = b.Lambda;
     inf.rho_hat = b.rho_hat;
@@ -541,16 +566,17 @@ percis_status percis_estimate(percis_ctx *ctx, double eps, double delta, uint64_
         ctx->lam.as<double>(), ctx->cnt.as<unsigned long long>(),
         ctx->opt.estimator == 1 ? ctx->acc_ap.as<double>() : nullptr, ctx->n, (double)ell, dst);
     PERCIS_CHECK_LAUNCH(ctx, "finalize");
-    if (info) {
-        PhaseStats h2{};
-        PERCIS_TRY(phase_stats(ctx, ell, (double)ell, false, &h2));
-        inf.zero_weight[1] = h2.zero_w;
-        inf.unreachable[1] = h2.unreach;
-        inf.sum_internal[1] = h2.s1;
-    }
+    if (info) PERCIS_TRY(issue_phase_stats(ctx, ell, false));  // read after the synchronisation below
     if (!pc_on_device)
         PERCIS_CUDA(ctx, cudaMemcpyAsync(pc_out, dst, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
     PERCIS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (info) {
+        PhaseOut p2;
+        read_phase_stats(ctx, (double)ell, &p2);
+        inf.zero_weight[1] = p2.zero_w;
+        inf.unreachable[1] = p2.unreach;
+        inf.sum_internal[1] = p2.s1;
+    }
     inf.lanes = ctx->opt.form == PERCIS_FORM_PLAIN ? 1 : ctx->lanes_alloc;
     inf.kernel_launches = ctx->launches - launches0;
     if (info) *info = inf;

@@ -133,6 +133,7 @@ struct percis_ctx {
     bool graph_pending = false;
     percis::DevBuf tr_counts, tr_scratch, graph_info;  // graph_info[0]: largest out- or in-degree (u64)
     uint32_t *tr_sorted_keys = nullptr;  // the sorted targets between transpose_sort and transpose_finish
+    void *hmirror = nullptr;  // pinned host words: status and phase statistics read back together
     percis::DevBuf table_ctl;                      // cooperative table scan: barrier, window state, block runs
     int table_grid = 0;                            // co-resident blocks of the table scan (0 = not yet queried)
     percis::DevBuf pc_tmp, grad_tmp, host_pinned;
@@ -246,6 +247,12 @@ struct PhaseOut {
     double bfs_ms = 0.0;
     int64_t bfs_launches = 0;
     int64_t work[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // asked for by setting want_stats (read back with the phase's status):
+    // sum |I|, sum |I|^2, zero-weight and unreachable samples, and with
+    // stats_pmax max_v lambda_v cnt_v / count
+    bool want_stats = false, stats_pmax = false;
+    int64_t s1 = 0, s2 = 0, zero_w = 0, unreach = 0;
+    double pmax = 0.0;
 };
 percis_status run_phase(percis_ctx *ctx, uint64_t seed, int phase, int64_t count, PhaseOut *po);
 
