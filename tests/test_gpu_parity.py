@@ -212,6 +212,27 @@ def test_phase_bitexact(binding, gcase, form, direction):
     eng.close()
 
 
+@pytest.mark.parametrize("scale", [17, 18])
+def test_bidir_directed_large_transpose_bitexact(binding, scale):
+    """Directed graphs of more than 2^16 vertices: the in-adjacency sort takes
+    three digit passes (the last with one or two bits) over a ragged last tile;
+    every in-list must come out in source order, so the bidirectional phase's
+    paths (which scan in-lists in that order) equal the oracle's bit for bit."""
+    g = synth.rmat(scale, 16, 0.57, 0.19, 0.19, 8)
+    og = oracle.from_synth(g)
+    x = synth.states_beta(g.n, 0.5, 2.0, 8)
+    eng = _engine(binding, g, x, form="bidir")
+    prep = oracle.prepare(x)
+    got = eng.run_phase(seed=13, phase=1, count=2000)
+    ph = oracle.run_samples(og, prep, 13, 1, 3, 0, 2000, keep_paths=True, bidir=True)
+    assert np.array_equal(_np(got["kind"]), ph.kind)
+    assert np.array_equal(_np(got["ilen"]), ph.ilen)
+    ptr, nodes = eng.get_paths(2000)
+    assert np.array_equal(_np(ptr), ph.path_ptr)
+    assert np.array_equal(_np(nodes), ph.path_nodes)
+    eng.close()
+
+
 def test_estimate_matches_oracle(binding):
     g, x, eps, delta = synth.workload("er1000")
     og = oracle.from_synth(g)
