@@ -71,7 +71,14 @@ constexpr int kHeavyEdgeBatch = PERCIS_HEAVY_EDGE_BATCH;  // the same in the hea
 #define PERCIS_BI_MINB 4
 #endif
 constexpr unsigned long long kHubDegree = 16384;  // graphs with a vertex of this degree get a heavy pass by default
-constexpr int kBloomWords = 1 << 15;  // heavy pass: a 2^20-bit filter of the other side's vertices (128 KB)
+// Meeting-scan filters and thresholds (build-time tuning constants, like the
+// ones above: a variant build defines them).  Heavy pass: a 2^20-bit filter of
+// the other side's vertices (128 KB; 2^19 measured the same).
+#ifndef PERCIS_HEAVY_BLOOM_LOG
+#define PERCIS_HEAVY_BLOOM_LOG 20
+#endif
+constexpr int kHeavyBloomLog = PERCIS_HEAVY_BLOOM_LOG;
+constexpr int kBloomWords = 1 << (kHeavyBloomLog - 5);
 #ifndef PERCIS_FIRST_BLOOM
 #define PERCIS_FIRST_BLOOM 0
 #endif
@@ -251,7 +258,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
     // never loaded.  (The first pass has no room for it.)
     constexpr bool BLOOM = BT != kBiBlock || kBloomWordsFirst > 0;
     constexpr int NBW = BT == kBiBlock ? kBloomWordsFirst : kBloomWords;  // filter words
-    constexpr int NBB = BT == kBiBlock ? 17 : 20;                          // filter bits (log2)
+    constexpr int NBB = BT == kBiBlock ? 17 : kHeavyBloomLog;              // filter bits (log2)
     extern __shared__ uint32_t s_bloom[];  // NBW words
     auto bloom_bits = [](int32_t v, uint32_t &h1, uint32_t &h2) {
         const unsigned long long m = (unsigned long long)(uint32_t)v * 0x9E3779B97F4A7C15ull;
