@@ -96,6 +96,10 @@ constexpr double kMeetOnlyHits = PERCIS_MEET_HITS_FIRST;
 #define PERCIS_MEET_HITS_BLOOM 0.02
 #endif
 constexpr double kMeetOnlyHitsBloom = PERCIS_MEET_HITS_BLOOM;
+#ifndef PERCIS_MEET_BATCH
+#define PERCIS_MEET_BATCH 8
+#endif
+constexpr int kMeetBatch = PERCIS_MEET_BATCH;  // columns a thread loads together in a filtered meeting scan
 constexpr unsigned long long kLazyDegEdges = 2048;  // levels of this many edges load degrees after
 constexpr uint32_t kHashLevels = 4095;            // levels a hashed word holds (12 bits)
 constexpr uint32_t kHashEpochs = (1u << 20) - 1;  // epochs a hashed word holds (20 bits)
@@ -694,32 +698,61 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
                             }
                             return klo;
                         };
-                        for (int64_t j = threadIdx.x; j < E; j += (int64_t)EB * BT) {
-                            Pre pr[EB];
-                            int kk[EB];
-                            int32_t vv[EB];
+                        if (BLOOM && meet_only) {
+                            // a meeting scan with the filter: each thread takes a contiguous
+                            // range of the chunk's edges (one bisection), loads eight columns
+                            // at a time and tests them; only the members are claimed
+                            const int64_t per_t = (E + BT - 1) / BT;
+                            int64_t jb = (int64_t)threadIdx.x * per_t;
+                            const int64_t je = jb + per_t < E ? jb + per_t : E;
+                            int k = jb < je ? vertex_of(jb) : 0;
+                            for (; jb < je; jb += kMeetBatch) {
+                                int kk[kMeetBatch];
+                                int32_t vv[kMeetBatch];
     #pragma unroll
-                            for (int b = 0; b < EB; ++b) {
-                                const int64_t jb = j + (int64_t)b * BT;
-                                kk[b] = jb < E ? vertex_of(jb) : 0;
-                                vv[b] = jb < E ? ax[s_fe[kk[b]] + (jb - s_pre[kk[b]])] : -1;
-                            }
-                            if (BLOOM && meet_only) {
+                                for (int b = 0; b < kMeetBatch; ++b) {
+                                    const int64_t e = jb + b;
+                                    vv[b] = -1;
+                                    kk[b] = k;
+                                    if (e < je) {
+                                        while (s_pre[k + 1] <= e) ++k;  // (s_pre[fc] = E > e)
+                                        kk[b] = k;
+                                        vv[b] = ax[s_fe[k] + (e - s_pre[k])];
+                                    }
+                                }
     #pragma unroll
-                                for (int b = 0; b < EB; ++b) {
+                                for (int b = 0; b < kMeetBatch; ++b) {
                                     if (vv[b] < 0) continue;
                                     uint32_t h1, h2;
                                     bloom_bits(vv[b], h1, h2);
                                     if (!((s_bloom[h1 >> 5] >> (h1 & 31)) & (s_bloom[h2 >> 5] >> (h2 & 31)) & 1u))
                                         vv[b] = -1;  // not a member of the other side
                                 }
+    #pragma unroll
+                                for (int b = 0; b < kMeetBatch; ++b) {
+                                    if (vv[b] < 0) continue;
+                                    Pre pr = prefetch(vv[b]);
+                                    resolve(pr, s_fs[kk[b]], fcnt >= 0x1p52, true);
+                                }
                             }
+                        } else {
+                            for (int64_t j = threadIdx.x; j < E; j += (int64_t)EB * BT) {
+                                Pre pr[EB];
+                                int kk[EB];
+                                int32_t vv[EB];
     #pragma unroll
-                            for (int b = 0; b < EB; ++b)
-                                if (vv[b] >= 0) pr[b] = prefetch(vv[b]);
+                                for (int b = 0; b < EB; ++b) {
+                                    const int64_t jb = j + (int64_t)b * BT;
+                                    kk[b] = jb < E ? vertex_of(jb) : 0;
+                                    vv[b] = jb < E ? ax[s_fe[kk[b]] + (jb - s_pre[kk[b]])] : -1;
+                                }
     #pragma unroll
-                            for (int b = 0; b < EB; ++b)
-                                if (vv[b] >= 0) resolve(pr[b], s_fs[kk[b]], fcnt >= 0x1p52, meet_only);
+                                for (int b = 0; b < EB; ++b)
+                                    if (vv[b] >= 0) pr[b] = prefetch(vv[b]);
+    #pragma unroll
+                                for (int b = 0; b < EB; ++b)
+                                    if (vv[b] >= 0) resolve(pr[b], s_fs[kk[b]], fcnt >= 0x1p52, meet_only);
+                            }
                         }
                         if (c0 + kFlat < hi) __syncthreads();  // the chunk's shared arrays are reused
                     }

@@ -22,11 +22,23 @@ namespace percis {
 
 namespace {
 
-constexpr int kRadixBlock = 256;
-constexpr int kRadixRounds = 16;
+// tile shape (build-time tuning constants): threads per block, pairs per thread,
+// resident scatter blocks per SM
+#ifndef PERCIS_RADIX_BLOCK
+#define PERCIS_RADIX_BLOCK 256
+#endif
+#ifndef PERCIS_RADIX_ROUNDS
+#define PERCIS_RADIX_ROUNDS 16
+#endif
+#ifndef PERCIS_RADIX_MINB
+#define PERCIS_RADIX_MINB 3
+#endif
+constexpr int kRadixBlock = PERCIS_RADIX_BLOCK;
+constexpr int kRadixRounds = PERCIS_RADIX_ROUNDS;
 constexpr int kRadixTile = kRadixBlock * kRadixRounds;
 constexpr int kRadixBins = 256;
 constexpr int kRadixWarps = kRadixBlock / 32;
+static_assert(kRadixBlock % kRadixBins == 0, "every digit has a thread in the count scan");
 
 template <class K>
 __device__ __forceinline__ int digit_of(K key, int shift) {
@@ -79,7 +91,7 @@ constexpr size_t scatter_smem() {
 }
 
 template <class K>
-__global__ void __launch_bounds__(kRadixBlock, 3) k_radix_scatter(const K *kin, const int32_t *vin, K *kout,
+__global__ void __launch_bounds__(kRadixBlock, PERCIS_RADIX_MINB) k_radix_scatter(const K *kin, const int32_t *vin, K *kout,
                                                                   int32_t *vout, int64_t n, int shift,
                                                                   int64_t ntiles, const long long *offs) {
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -91,7 +103,6 @@ __global__ void __launch_bounds__(kRadixBlock, 3) k_radix_scatter(const K *kin, 
     int *s_wtot = s_lpre + kRadixBins;
     constexpr int kPerWarp = kRadixTile / kRadixWarps;
     constexpr int kRounds = kPerWarp / 32;
-    static_assert(kRadixBins == kRadixBlock, "one digit per thread in the count scan");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     int *wc = s_wc + warp * kRadixBins;
@@ -131,30 +142,36 @@ __global__ void __launch_bounds__(kRadixBlock, 3) k_radix_scatter(const K *kin, 
         }
         __syncthreads();
         {
-            // digit d = this thread: its count in the tile, its first place in the tile
-            // (exclusive scan over the digits), and each warp's first place among it
+            // digit d = this thread (the first kRadixBins threads): its count in the
+            // tile, its first place in the tile (exclusive scan over the digits), and
+            // each warp's first place among it
             const int d = threadIdx.x;
+            const bool dt = d < kRadixBins;  // (whole warps)
             int wpre[kRadixWarps];
-            int c = 0;
+            int c = 0, inc = 0;
+            if (dt) {
 #pragma unroll
-            for (int w = 0; w < kRadixWarps; ++w) {
-                wpre[w] = c;
-                c += s_wc[w * kRadixBins + d];
-            }
-            int inc = c;
+                for (int w = 0; w < kRadixWarps; ++w) {
+                    wpre[w] = c;
+                    c += s_wc[w * kRadixBins + d];
+                }
+                inc = c;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t2 = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += t2;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t2 = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += t2;
+                }
+                if (lane == 31) s_wtot[warp] = inc;
+                s_base[d] = offs[(int64_t)d * ntiles + tile];
             }
-            if (lane == 31) s_wtot[warp] = inc;
-            s_base[d] = offs[(int64_t)d * ntiles + tile];
             __syncthreads();
-            int lp = inc - c;
-            for (int q = 0; q < warp; ++q) lp += s_wtot[q];
-            s_lpre[d] = lp;
+            if (dt) {
+                int lp = inc - c;
+                for (int q = 0; q < warp; ++q) lp += s_wtot[q];
+                s_lpre[d] = lp;
 #pragma unroll
-            for (int w = 0; w < kRadixWarps; ++w) s_wc[w * kRadixBins + d] = lp + wpre[w];
+                for (int w = 0; w < kRadixWarps; ++w) s_wc[w * kRadixBins + d] = lp + wpre[w];
+            }
         }
         __syncthreads();
 #pragma unroll
