@@ -123,7 +123,10 @@ typedef struct {
                                  stops untouched and runs again after the first pass, alone in
                                  a block of 1,024 threads in the direct store (the heavy pass);
                                  0 = default: 8,192 on graphs with a vertex of degree >= 16,384
-                                 (hubs make single levels huge), else never; < 0 = never */
+                                 (hubs make single levels huge), else never; < 0 = never.
+                                 Samples the first pass takes in the last two rounds of its
+                                 queue (a sample per block) hand over above min(this, 2,048),
+                                 so that its blocks end together.  Results do not depend on it. */
     int64_t reserved;         /* must be 0 */
 } percis_options;
 

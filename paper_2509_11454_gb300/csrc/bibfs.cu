@@ -100,6 +100,19 @@ constexpr double kMeetOnlyHitsBloom = PERCIS_MEET_HITS_BLOOM;
 #define PERCIS_MEET_BATCH 8
 #endif
 constexpr int kMeetBatch = PERCIS_MEET_BATCH;  // columns a thread loads together in a filtered meeting scan
+// first pass: samples taken in the queue's last kTailRounds rounds (one round =
+// a sample per block) hand levels above kTailEdges to the heavy pass, so that
+// no block of the pass ends long after the others (0: off; on R-MAT 22, two
+// rounds at 2,048 edges cut the first passes by 0.17 ms a step, one or four
+// rounds and 4,096 edges less)
+#ifndef PERCIS_TAIL_ROUNDS
+#define PERCIS_TAIL_ROUNDS 2
+#endif
+#ifndef PERCIS_TAIL_EDGES
+#define PERCIS_TAIL_EDGES 2048
+#endif
+constexpr int kTailRounds = PERCIS_TAIL_ROUNDS;
+constexpr unsigned long long kTailEdges = PERCIS_TAIL_EDGES;
 constexpr unsigned long long kLazyDegEdges = 2048;  // levels of this many edges load degrees after
 constexpr uint32_t kHashLevels = 4095;            // levels a hashed word holds (12 bits)
 constexpr uint32_t kHashEpochs = (1u << 20) - 1;  // epochs a hashed word holds (20 bits)
@@ -279,6 +292,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
     int2 *const memb = queue1 + a.qcap;
 
     __shared__ long long s_i;
+    __shared__ int s_tail;
     // claims of a level go to counter set it % 3; thread 0 clears set (it + 1) % 3
     // at the start of level it, two barriers after its last readers
     __shared__ int s_new[3], s_meet, s_full;
@@ -319,9 +333,13 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
         if (threadIdx.x == 0) {
             const long long k = (long long)atomicAdd(a.next, 1ull);
             s_i = k < count ? (a.list ? (long long)a.list[k] : k) : -1ll;
+            s_tail = kTailRounds > 0 && k >= count - (long long)kTailRounds * gridDim.x;
         }
         __syncthreads();
         const long long i = s_i;
+        // (block-uniform) the level size above which this sample is handed over
+        const unsigned long long lim =
+            (heavy_lim && s_tail && kTailEdges < heavy_lim) ? kTailEdges : heavy_lim;
         if (i < 0) break;
         const unsigned long long t_start = a.trace && threadIdx.x == 0 ? globaltimer_ns() : 0ull;
         unsigned long long t_levels = 0ull, t_meet = 0ull;
@@ -403,7 +421,7 @@ __global__ void __launch_bounds__(BT, BT == kBiBlock ? PERCIS_BI_MINB : 1024 / B
                 x = cost[0] <= cost[1] ? 0 : 1;
                 const long long lo = x ? qlo[1] : qlo[0], hi = x ? qhi[1] : qhi[0];
                 const uint32_t nl = (x ? lev[1] : lev[0]) + 1;
-                if (heavy_lim && (x ? cost[1] : cost[0]) > heavy_lim) {
+                if (lim && (x ? cost[1] : cost[0]) > lim) {
                     handed = true;  // a heavy level: the pass with larger blocks takes the sample
                     break;
                 }
