@@ -122,7 +122,7 @@ typedef struct {
     int64_t bi_heavy_edges;   /* a sample whose next level would scan more than this many edges
                                  stops untouched and runs again after the first pass, alone in
                                  a block of 1,024 threads in the direct store (the heavy pass);
-                                 0 = default: 8,192 on graphs with a vertex of degree >= 16,384
+                                 0 = default: 16,384 on graphs with a vertex of degree >= 16,384
                                  (hubs make single levels huge), else never; < 0 = never.
                                  Samples the first pass takes in the last two rounds of its
                                  queue (a sample per block) hand over above min(this, 2,048),

@@ -1276,7 +1276,7 @@ __global__ void __launch_bounds__(1024) k_order_heavy(int32_t *defer, const unsi
 #define PERCIS_HEAVY_BLOCK 1024
 #endif
 constexpr int kHeavyBlock = PERCIS_HEAVY_BLOCK;  // threads per sample in the heavy pass
-constexpr unsigned long long kDefaultHeavyEdges = 8192;   // a level scanning more edges is heavy
+constexpr unsigned long long kDefaultHeavyEdges = 16384;  // a level scanning more edges is heavy
 constexpr int64_t kDefaultScratchGiB = 48;  // direct store: one heavy-pass block per SM up to n = 6M
 
 template <bool HASH, int BT>
